@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the block renderer: 1080p frames/s and Mrays/s.
+
+Workload (default "city_lod_1080p"): 8x8 ground blocks of side 2 with three
+LOD levels (256^3 grid + 1024^2 planes at LOD 1, 128^3/512^2 at LOD 2,
+64^3/256^2 at LOD 3), features stored in BF16, one 1920x1080 aerial camera
+that sees every block, LOD chosen by distance thresholds; the same frame is
+also rendered from FP32 storage ("plain FP32") for comparison.  Inputs are
+seeded synthetic stand-ins for the paper's aerial city captures.
+
+A step renders one frame through the C ABI (cow_render).  Timing: CUDA events
+on the launching stream around each step, a 512 MiB write between steps to
+flush L2, barrier + synchronize around the K timed steps, max over ranks.
+With --gpus N > 1 every rank renders its own frame (replicas, weak scaling).
+
+--impl reference runs the FP64 CPU oracle on the host cores on a bounded
+sample of the same frame's pixels.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
+L2_FLUSH_BYTES = 512 << 20
+GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160}  # per occupied sample: 20 texels x 8 ch
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["cow", "reference"], default="cow")
+    ap.add_argument("--workload", choices=["city_lod_1080p", "city_4x4_720p", "single_block_128"],
+                    default="city_lod_1080p")
+    ap.add_argument("--storage", default=None, help="override the storage dtype")
+    ap.add_argument("--ert", type=float, default=1e-5, help="early ray termination threshold")
+    ap.add_argument("--cpu-pixels", type=int, default=0, help="oracle sample size (0 = automatic)")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--res-div", type=int, default=1, help="divide grid / plane resolutions (profiling runs)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "cow" else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, util, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                util.append(float(r[4]))
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 6 + k and r[6 + k].lower().startswith("active"):
+                    reasons.add(n)
+        loaded = [s for s, u in zip(sm, util) if u > 0] or sm
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+
+
+def make_workload(name, device, div=1):
+    from paper_2312_16457_gb300 import synth
+
+    if name == "city_lod_1080p":
+        res = tuple((r // div, p // div) for r, p in ((256, 1024), (128, 512), (64, 256)))
+        sc, cams, mlp = synth.workload_city_lod(res=res, device=device)
+        return sc, cams[0], mlp, "bf16", "8x8 blocks x 3 LOD (%s), 1920x1080 aerial" % ", ".join(
+            f"{r}^3/{p}^2" for r, p in res)
+    if name == "city_4x4_720p":
+        sc, cams, mlp = synth.workload_city_4x4(R=256 // div, P=1024 // div, device=device)
+        return sc, cams[0], mlp, "fp16", f"4x4 blocks, {256 // div}^3 grid + {1024 // div}^2 planes, 1280x720 oblique"
+    sc, cams, mlp = synth.workload_single_block(R=64 // div, P=256 // div, device=device)
+    return sc, cams[0], mlp, "fp32", f"single block {64 // div}^3 + {256 // div}^2, 128x128"
+
+
+def block_ids(ctx, sc, cam):
+    if sc.n_levels > 1:
+        return ctx.select_lod(cam, sc.lod_thresh)
+    return ctx.sort_blocks(cam, list(range(len(sc.blocks))))
+
+
+def sub_scene(sc, ids):
+    """The selected blocks only, re-indexed (what the oracle needs for one view)."""
+    from paper_2312_16457_gb300 import synth
+
+    blocks = []
+    for i in ids:
+        b = sc.blocks[int(i)]
+        blocks.append(synth.Block(b.lo, b.hi, b.R, b.P, 1, -1, b.grid.to("cpu"), [p.to("cpu") for p in b.planes]))
+    return synth.Scene(blocks, sc.box_lo, sc.box_hi, [], sc.occ_cell, sc.occ_thresh)
+
+
+def oracle_sample(sc, cam, ids, mlp, n_pix, seed=0):
+    """Time the oracle (as it stands, all host cores) on n_pix random pixels."""
+    import oracle
+
+    oracle.build()
+    host = sub_scene(sc, ids)
+    osc = oracle.OracleScene(host)
+    rng = np.random.default_rng(seed)
+    pix = np.sort(rng.choice(cam.width * cam.height, size=n_pix, replace=False))
+    t0 = time.perf_counter()
+    rgb, aux, ns = oracle.render_view(osc, cam, list(range(len(ids))), mlp, pixels=pix)
+    dt = time.perf_counter() - t0
+    return pix, rgb, dt
+
+
+def time_steps(fn, K, W, flush, stream):
+    for _ in range(W):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        flush.zero_()
+        evs[k][0].record(stream)
+        fn()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def psnr(a, b):
+    mse = float(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2))
+    return math.inf if mse == 0 else 10 * math.log10(1.0 / mse)
+
+
+# ---------------------------------------------------------------------------
+
+
+def run_cow(args, ws, rank, local):
+    from paper_2312_16457_gb300 import build, cow
+
+    build.build()
+    dev = torch.device("cuda", local)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    sc, cam, mlp, storage, desc = make_workload(args.workload, dev, args.res_div)
+    storage = args.storage or storage
+    ctx = cow.Context(sc, storage)
+    ids = block_ids(ctx, sc, cam)
+    ctx32 = cow.Context(sc, "fp32") if (not args.no_fp32 and storage != "fp32") else None
+    need_master = rank == 0 and ws == 1 and not args.no_cpu
+    if not need_master:  # the contexts hold packed copies; drop the FP32 masters
+        for b in sc.blocks:
+            b.grid, b.planes = None, []
+        torch.cuda.empty_cache()
+    mlp_d = torch.from_numpy(mlp).to(dev)
+    stream = torch.cuda.current_stream()
+    npix = cam.width * cam.height
+    out = (torch.empty((npix, 3), device=dev), None, None)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # occupied samples of this frame (the units the roofline counts)
+    _, aux0, ns0 = ctx.render([cam], [ids], mlp_d, ert_eps=args.ert, nsamp=True)
+    ctx.sync_check()
+    n_samples = int(ns0.to(torch.int64).sum().item())
+    rgb_main = ctx.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False)[0].cpu().numpy()
+
+    def step():
+        ctx.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=out)
+
+    clocks = Clocks(torch.cuda.current_device())
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    times = time_steps(step, args.steps, args.warmup, flush, stream)
+    barrier(ws)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ck = clocks.stop()
+    ctx.sync_check()
+    ms = max_over_ranks(ws, float(np.mean(times)))
+    fps = 1000.0 / ms
+    value = fps * ws
+
+    # end to end through the C ABI: host MLP in, pinned host frame out
+    host_out = (torch.empty((npix, 3)).pin_memory(), None, None)
+    for _ in range(max(2, args.warmup)):
+        ctx.render([cam], [ids], mlp, ert_eps=args.ert, aux=False, out=host_out)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        ctx.render([cam], [ids], mlp, ert_eps=args.ert, aux=False, out=host_out)
+        stream.synchronize()
+        e2e_t.append(time.perf_counter() - a)
+    e2e_ms = max_over_ranks(ws, 1000.0 * float(np.mean(e2e_t)))
+    h2d = 80 + 4 * len(ids) + 4 * 499 + 4 * 2  # camera record, ids, MLP, offsets
+    d2h = npix * 12
+
+    # plain FP32 storage, same frame
+    fp32 = {}
+    if ctx32 is not None:
+        out32 = (torch.empty((npix, 3), device=dev), None, None)
+        t32 = time_steps(lambda: ctx32.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=out32),
+                         max(5, args.steps // 2), 3, flush, stream)
+        ctx32.sync_check()
+        rgb32 = out32[0].cpu().numpy()
+        fp32 = {"plain_fp32_frames_per_s": round(1000.0 / float(np.mean(t32)), 3),
+                "psnr_vs_plain_fp32_db": round(psnr(rgb_main, rgb32), 2)}
+        ctx32.close()
+
+    # oracle on a bounded sample of this frame (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        n_pix = args.cpu_pixels or (4096 if npix > 100000 else npix)
+        pix, rgb_o, dt = oracle_sample(sc, cam, ids, mlp, n_pix)
+        cpu = {"value": round((n_pix / dt) / npix, 6), "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n_pix} random pixels of the frame, FP64 oracle on the FP32 master, {dt:.1f} s",
+               "mrays_per_s": round(n_pix / dt / 1e6, 6),
+               "psnr_vs_oracle_db": round(psnr(rgb_main[pix], rgb_o), 2),
+               "max_abs_drgb_vs_oracle": float(np.abs(rgb_main[pix] - rgb_o).max())}
+
+    gb = GATHER_BYTES[storage] * n_samples / 1e9
+    hbm = peaks.get("hbm_gbs")
+    achieved = gb / (ms / 1000.0)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "scene": desc, "storage": storage, "n_blocks_selected": int(len(ids)),
+                   "width": cam.width, "height": cam.height, "ert_eps": args.ert,
+                   "l2": "512 MiB write between timed steps, outside the per-step events",
+                   "parallelism": f"replicas x{ws}"},
+        "mrays_per_s": round(value * npix / 1e6, 3),
+        "occupied_samples_per_frame": n_samples,
+        "samples_per_ray": round(n_samples / npix, 2),
+        **fp32,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 3) if hbm else None, "traffic": None,
+                     "note": "achieved = gathered bytes (20 texels x 8 ch per occupied sample) / march time; "
+                             "most gathers hit L1/L2, so this exceeds the HBM copy peak"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(1000.0 / e2e_ms * ws, 3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": ck,
+        "wall_s_timed_region": round(wall, 3),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_reference(args, ws, rank, local):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    dev = torch.device("cuda", 0) if torch.cuda.is_available() else torch.device("cpu")
+    from paper_2312_16457_gb300 import build, cow
+
+    sc, cam, mlp, storage, desc = make_workload(args.workload, dev, args.res_div)
+    # LOD selection by the oracle itself (App. D), on host copies of the blocks
+    host_all = type(sc)([b.to("cpu") for b in sc.blocks], sc.box_lo, sc.box_hi, sc.lod_thresh, sc.occ_cell,
+                        sc.occ_thresh)
+    osc_all = oracle.OracleScene(host_all)
+    if sc.n_levels > 1:
+        ids = oracle.select_lod(osc_all, cam, sc.lod_thresh)
+    else:
+        ids = oracle.sort_view(osc_all, list(range(len(sc.blocks))), cam)
+    del osc_all
+    host = sub_scene(host_all, ids)
+    osc = oracle.OracleScene(host)
+    npix = cam.width * cam.height
+    n_pix = args.cpu_pixels or (1024 if npix > 100000 else min(npix, 4096))
+    rng = np.random.default_rng(1)
+    order = list(range(len(ids)))
+
+    def step(k):
+        pix = np.sort(rng.choice(npix, size=n_pix, replace=False))
+        oracle.render_view(osc, cam, order, mlp, pixels=pix)
+
+    for k in range(args.warmup):
+        step(k)
+    times = []
+    for k in range(args.steps):
+        t = time.perf_counter()
+        step(k)
+        times.append(time.perf_counter() - t)
+    dt = float(np.mean(times))
+    fps = (n_pix / dt) / npix
+    line = {"metric": METRIC, "value": round(fps, 6), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1000 * dt, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "scene": desc, "storage": "fp32 master",
+                       "n_blocks_selected": int(len(ids)), "width": cam.width, "height": cam.height},
+            "mrays_per_s": round(n_pix / dt / 1e6, 6),
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": round(fps, 6), "unit": "frames/s",
+                             "sample": f"{n_pix} random pixels of the frame per step"},
+            "e2e": {"value": round(fps, 6), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank, local)
+    else:
+        run_cow(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * cow.h -- C ABI of libcow: block-based volume rendering of baked MERF-style
+ * scene blocks on one NVIDIA GB300 (sm_103a), after City-on-Web
+ * (arXiv 2312.16457).
+ *
+ * The problem the calls solve (Sec. 4.1 rendering stage, Sec. 4.2, App. D):
+ * given a scene partitioned on the ground plane into blocks, each baked at
+ * several levels of detail into a low-resolution 3D feature grid plus three
+ * high-resolution feature planes, and given cameras, render images with
+ * correct occlusion between blocks: per pixel, march the ray through every
+ * selected block (Eq. 1-2 within a block, Eq. 11), composite the blocks in
+ * depth order (Eq. 5 / Eq. 12) and shade the composited diffuse colour and
+ * specular feature with one deferred MLP (Eq. 3).
+ *
+ * Conventions for every call:
+ *  - No C++ exception crosses this boundary.  Every call returns a
+ *    cow_status; on failure cow_last_error() returns a message (thread-local,
+ *    valid until the next call on the same thread).
+ *  - Caller-owned inputs are read-only and may be freed when the call
+ *    returns.  A context owns its packed device copies until cow_free.
+ *  - Outputs are caller-allocated.  Device work is enqueued asynchronously on
+ *    the caller's CUDA stream (`stream` is a cudaStream_t; NULL = legacy
+ *    default stream).  Calls that use one context must be issued on one stream
+ *    or be ordered by the caller, because a context reuses its per-call
+ *    device buffers.
+ *  - Kernels that detect a fault (a sample range beyond the bound, a wait
+ *    that ran out) set an error word instead of trapping; cow_sync_check
+ *    reports it as COW_ERR_DEVICE_ASSERT or COW_ERR_TIMEOUT.
+ *
+ * Notation: block b has the world AABB [lo, hi]; R = grid vertices per axis,
+ * P = plane texels per axis.  Channels: 0 pre-activation log-density
+ * (sigma = exp), 1-3 diffuse colour, 4-7 specular feature (sigmoid).
+ */
+#ifndef COW_H
+#define COW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COW_NCH 8           /* feature channels per grid vertex / plane texel */
+#define COW_MLP_NPARAM 499  /* deferred MLP 10 -> 16 -> 16 -> 3 */
+
+typedef enum cow_status {
+    COW_OK = 0,
+    COW_ERR_INVALID_ARG = 1,   /* a null pointer, size or layout the call rejects */
+    COW_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has the CUDA error) */
+    COW_ERR_OOM = 3,           /* device allocation failed */
+    COW_ERR_UNSUPPORTED = 4,   /* valid request this build does not implement */
+    COW_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    COW_ERR_DEVICE_ASSERT = 6  /* a kernel's own range check fired */
+} cow_status;
+
+/* Storage format of the packed features (Sec. 4.5 bakes 8-bit textures; the
+ * formats here are the GPU equivalents).  FP8 uses per-channel power-of-two
+ * scales: channel c of each tensor is stored as x / 2^e_c with the smallest
+ * e_c such that max|x_c| <= 448 * 2^e_c.  FP32 / FP16 / BF16 use scale 1.
+ * Conversion is round-to-nearest-even (FP8 saturating at +-448). */
+typedef enum cow_dtype { COW_FP32 = 0, COW_FP16 = 1, COW_BF16 = 2, COW_FP8_E4M3 = 3 } cow_dtype;
+
+/* One baked block at one level of detail (Sec. 4.1: f^{k,l}; LOD l merges 2x2
+ * blocks of level l-1, Sec. 4.1 and Sec. 4.4). */
+typedef struct cow_block_desc {
+    float lo[3], hi[3];      /* world AABB; xy footprints of one level tile the ground */
+    int32_t lod;             /* level of detail, 1 = finest */
+    int32_t parent;          /* index (in this array) of the covering block one level up, -1 if none */
+    int32_t grid_res;        /* R >= 2; vertex 0 at lo, vertex R-1 at hi (vertex-aligned) */
+    int32_t plane_res;       /* P >= 2; sample spacing delta = (hi_x - lo_x) / P */
+    const float *grid;       /* FP32 master, R^3 x 8, index ((z*R + y)*R + x)*8 + c; host or device */
+    const float *planes[3];  /* FP32 master, P^2 x 8 each, index (v*P + u)*8 + c; planes xy, xz, yz */
+} cow_block_desc;
+
+/* Pinhole camera: 3x4 row-major camera-to-world matrix with OpenGL axes
+ * (the camera looks along -z, +y up), image size and vertical field of view.
+ * Pixel (x, y) shoots the ray through its centre (x + 1/2, y + 1/2). */
+typedef struct cow_camera {
+    double c2w[12];
+    int32_t width, height;
+    double fov_y_deg;
+} cow_camera;
+
+typedef struct cow_ctx cow_ctx;
+
+/* render flags */
+#define COW_FLAG_MLP_BF16 1u  /* deferred MLP with BF16 operands and FP32 accumulation */
+
+/* Upload and pack a set of blocks (all levels) on the current CUDA device.
+ *   out        : receives the new context (owned by the caller; cow_free).
+ *   blocks, n  : n >= 1 descriptors; arrays may be host or device memory.
+ *   storage    : packed format of the grid and planes.
+ *   occ_thresh : occupancy threshold on density (Sec. 4.5 bakes a binary
+ *                occupancy grid; here a cell is occupied when any grid vertex
+ *                of it has exp(ch0) > occ_thresh, decided on the FP32 master
+ *                as (double)ch0 > log((double)occ_thresh)).
+ *   occ_cell   : voxels per occupancy-cell edge (>= 1); a block has
+ *                ceil((R-1)/occ_cell)^3 cells; cell c spans vertices
+ *                [c*occ_cell, c*occ_cell + occ_cell] along each axis.
+ *   stream     : packing kernels run on it; the call synchronises it before
+ *                returning, so the masters may be freed afterwards.
+ * Errors: INVALID_ARG (null pointer, R or P < 2, lo >= hi, bad dtype),
+ * OOM, CUDA. */
+cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
+                           float occ_thresh, int32_t occ_cell, void *stream);
+
+/* Release a context and all its device memory (NULL is accepted). */
+cow_status cow_free(cow_ctx *ctx);
+
+/* Number of blocks held, and the z of the highest occupied part of block i
+ * (App. D: the top of its highest occupied cell row, lo_z if empty). */
+cow_status cow_num_blocks(const cow_ctx *ctx, int32_t *out_n);
+cow_status cow_block_ztop(const cow_ctx *ctx, int32_t block, double *out_ztop);
+
+/* LOD selection, visibility and depth sort of the real-time viewer (App. D),
+ * on the host in FP64.
+ *   A block is visible unless all 8 corners of [lo_x,hi_x] x [lo_y,hi_y] x
+ *   [lo_z, ztop] lie strictly outside one of the five planes of the view
+ *   pyramid.  Starting from the visible blocks of the coarsest level, a
+ *   block of level l > 1 is selected when every visible child is farther than
+ *   lod_thresh[l-2] from the camera (distance to (centre_x, centre_y, ztop));
+ *   otherwise its visible children are examined.  Level-1 blocks are always
+ *   selected.  The result is sorted near to far by the xy distance of block
+ *   centres to the camera (ties by index).
+ *   lod_thresh : n_lod thresholds; lod_thresh[k] applies to level k+1.
+ *   out_ids    : host array of cap entries; out_n receives the count (if it
+ *                exceeds cap, nothing is written and INVALID_ARG is returned). */
+cow_status cow_select_lod(const cow_ctx *ctx, const cow_camera *cam, const double *lod_thresh, int32_t n_lod,
+                          int32_t *out_ids, int32_t cap, int32_t *out_n);
+
+/* Depth sort only (App. D): ids sorted near to far by the xy distance of
+ * block centres to the camera, ties by index.  Host arrays of n entries. */
+cow_status cow_sort_blocks(const cow_ctx *ctx, const cow_camera *cam, const int32_t *ids, int32_t n, int32_t *out);
+
+/* Render n_views images (Eq. 1-2, 5/12 and 3).
+ *   cams        : host array of n_views cameras.
+ *   ids         : host array, the block ids of view v (near to far, e.g. from
+ *                 cow_select_lod) are ids[ids_offsets[v] .. ids_offsets[v+1]).
+ *   mlp         : 499 FP32 deferred-MLP parameters W1[10][16], b1[16],
+ *                 W2[16][16], b2[16], W3[16][3], b3[3] (input-major); the
+ *                 MLP input is [C_d (3), F (4), d (3)]; C = C_d + sigmoid(...).
+ *                 Host or device.
+ *   ert_eps     : a ray stops once its transmittance falls below ert_eps
+ *                 (0 = never); the colour changes by at most ert_eps per
+ *                 channel of C_d and F.
+ *   flags       : COW_FLAG_MLP_BF16 or 0.
+ *   out_rgb     : float32, (sum of W*H) x 3, views in order, rows top to
+ *                 bottom.  Device memory, or host memory (the call then
+ *                 renders into context buffers and copies; pinned memory is
+ *                 complete when the stream completes, pageable memory when
+ *                 the call returns).
+ *   out_aux     : NULL or float32 (sum W*H) x 8: C_d (3), F (4) and the
+ *                 transmittance left after the last block; same rules.
+ *   out_nsamp   : NULL or int32 (sum W*H): occupied samples marched per pixel.
+ * Errors: INVALID_ARG (bad id, size, pointer), OOM, CUDA. */
+cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                      const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                      float *out_aux, int32_t *out_nsamp, void *stream);
+
+/* Render independent rays (Sec. 4.2 training-stage form: each ray composites
+ * the given blocks in the xy-distance order of its own origin, App. D).
+ *   o, d        : device float32 n_rays x 3 origins and unit directions.
+ *   ids, n_ids  : host array of the blocks to composite (1..64).
+ *   other arguments as cow_render; outputs have n_rays rows. */
+cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                           int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                           float *out_aux, int32_t *out_nsamp, void *stream);
+
+/* Wait for the stream and report a device-side error word set by a kernel of
+ * this context (COW_ERR_DEVICE_ASSERT or COW_ERR_TIMEOUT); clears it. */
+cow_status cow_sync_check(cow_ctx *ctx, void *stream);
+
+/* Copy out a block's occupancy bits (ceil(ncell/32) words, cell index
+ * (cz*Nc + cy)*Nc + cx, bit c&31 of word c>>5) into host memory. */
+cow_status cow_export_occupancy(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words);
+
+/* Copy out a block's packed tensor (0 = grid, 1..3 = planes xy, xz, yz) in its
+ * storage format into host memory, with its 8 per-channel scale exponents. */
+cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, void *out, int64_t nbytes,
+                             int32_t *out_scale_exp);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *cow_last_error(void);
+
+/* ABI version of this library. */
+int32_t cow_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COW_H */

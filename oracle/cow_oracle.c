@@ -199,6 +199,7 @@ int32_t orc_e4m3_scale_exp(float amax) {
  * decoded value times the channel scale (as float; exact for all formats). */
 void orc_quantize(const float *x, int64_t n, int32_t dtype, const int32_t *scale_exp,
                   void *out_bits, float *out_deq) {
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         int c = (int)(i % NCH);
         int se = scale_exp ? scale_exp[c] : 0;
@@ -318,6 +319,7 @@ void orc_occupancy(const float *grid, int32_t R, int32_t C, float thresh, uint32
     const int64_t ncell = (int64_t)Nc * Nc * Nc;
     memset(bits, 0, (size_t)((ncell + 31) / 32) * 4);
     const double lt = log((double)thresh);
+#pragma omp parallel for schedule(dynamic, 1)
     for (int cz = 0; cz < Nc; cz++)
         for (int cy = 0; cy < Nc; cy++)
             for (int cx = 0; cx < Nc; cx++) {
@@ -328,6 +330,7 @@ void orc_occupancy(const float *grid, int32_t R, int32_t C, float thresh, uint32
                             if ((double)grid[(((int64_t)z * R + y) * R + x) * NCH] > lt) on = 1;
                 if (on) {
                     int64_t c = ((int64_t)cz * Nc + cy) * Nc + cx;
+#pragma omp atomic
                     bits[c >> 5] |= 1u << (c & 31);
                 }
             }

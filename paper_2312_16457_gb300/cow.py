@@ -1,0 +1,236 @@
+"""ctypes binding of libcow's C ABI (include/cow.h): argument marshalling only.
+
+Every step of rendering runs in libcow's CUDA kernels; this module converts
+torch tensors / numpy arrays to pointers and back.  There is no CPU fallback:
+if ``libcow.so`` has not been built, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcow.so")
+_lib = None
+
+DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
+ELEM_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp8": 1}
+FLAG_MLP_BF16 = 1
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE_ASSERT"}
+
+# every symbol include/cow.h declares
+EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
+           "cow_render", "cow_render_rays", "cow_sync_check", "cow_export_occupancy", "cow_export_packed",
+           "cow_last_error", "cow_version"]
+
+
+class CowError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"libcow {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class BlockDesc(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("lod", C.c_int32), ("parent", C.c_int32),
+                ("grid_res", C.c_int32), ("plane_res", C.c_int32), ("grid", C.c_void_p),
+                ("planes", C.c_void_p * 3)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("c2w", C.c_double * 12), ("width", C.c_int32), ("height", C.c_int32), ("fov_y_deg", C.c_double)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libcow.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"libcow.so is not built ({_LIB_PATH}); run __graft_entry__.build() first")
+        L = C.CDLL(_LIB_PATH)
+        P, i32, i64, dbl, flt, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float, C.c_uint32
+        sig = {
+            "cow_load_blocks": [P, P, i32, i32, flt, i32, P],
+            "cow_free": [P],
+            "cow_num_blocks": [P, P],
+            "cow_block_ztop": [P, i32, P],
+            "cow_select_lod": [P, P, P, i32, P, i32, P],
+            "cow_sort_blocks": [P, P, P, i32, P],
+            "cow_render": [P, P, i32, P, P, P, flt, u32, P, P, P, P],
+            "cow_render_rays": [P, P, P, i64, P, i32, P, flt, u32, P, P, P, P],
+            "cow_sync_check": [P, P],
+            "cow_export_occupancy": [P, i32, P, i64],
+            "cow_export_packed": [P, i32, i32, P, i64, P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.cow_last_error.restype = C.c_char_p
+        L.cow_last_error.argtypes = []
+        L.cow_version.restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise CowError(rc, lib().cow_last_error().decode(errors="replace"))
+
+
+def _camera(cam) -> Camera:
+    c = Camera()
+    c.c2w[:] = [float(v) for v in np.asarray(cam.c2w, np.float64).reshape(12)]
+    c.width, c.height, c.fov_y_deg = int(cam.width), int(cam.height), float(cam.fov_y_deg)
+    return c
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous()
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _as_f32(t):
+    if isinstance(t, torch.Tensor):
+        return t.detach().to(torch.float32).contiguous()
+    return np.ascontiguousarray(t, np.float32)
+
+
+class Context:
+    """A packed scene on one GPU (wraps cow_ctx)."""
+
+    def __init__(self, scene, storage: str = "fp32", occ_thresh: Optional[float] = None,
+                 occ_cell: Optional[int] = None, stream=None):
+        self.storage = storage
+        self.scene = scene
+        n = len(scene.blocks)
+        descs = (BlockDesc * n)()
+        keep = []
+        for i, b in enumerate(scene.blocks):
+            d = descs[i]
+            d.lo[:] = [float(v) for v in b.lo]
+            d.hi[:] = [float(v) for v in b.hi]
+            d.lod, d.parent, d.grid_res, d.plane_res = int(b.level), int(b.parent), int(b.R), int(b.P)
+            g = _as_f32(b.grid)
+            pls = [_as_f32(p) for p in b.planes]
+            keep += [g, *pls]
+            d.grid = _ptr(g)
+            for k in range(3):
+                d.planes[k] = _ptr(pls[k])
+        self._ctx = C.c_void_p()
+        th = scene.occ_thresh if occ_thresh is None else occ_thresh
+        cc = scene.occ_cell if occ_cell is None else occ_cell
+        _check(lib().cow_load_blocks(C.byref(self._ctx), descs, n, DTYPES[storage], float(th), int(cc),
+                                     _stream_ptr(stream)))
+        self.n_blocks = n
+        del keep
+
+    def close(self):
+        if self._ctx:
+            lib().cow_free(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- App. D ------------------------------------------------------------
+    def select_lod(self, cam, lod_thresh: Sequence[float]) -> np.ndarray:
+        th = np.ascontiguousarray(lod_thresh, np.float64)
+        out = np.zeros(max(self.n_blocks, 1), np.int32)
+        n = C.c_int32()
+        c = _camera(cam)
+        _check(lib().cow_select_lod(self._ctx, C.byref(c), _ptr(th), len(th), _ptr(out), self.n_blocks, C.byref(n)))
+        return out[:n.value].copy()
+
+    def sort_blocks(self, cam, ids: Sequence[int]) -> np.ndarray:
+        a = np.ascontiguousarray(ids, np.int32)
+        out = np.empty_like(a)
+        c = _camera(cam)
+        _check(lib().cow_sort_blocks(self._ctx, C.byref(c), _ptr(a), len(a), _ptr(out)))
+        return out
+
+    def ztop(self, i: int) -> float:
+        v = C.c_double()
+        _check(lib().cow_block_ztop(self._ctx, int(i), C.byref(v)))
+        return v.value
+
+    # --- rendering ---------------------------------------------------------
+    def render(self, cams, ids_per_view, mlp, ert_eps: float = 0.0, mlp_bf16: bool = False, aux: bool = True,
+               nsamp: bool = False, out=None, stream=None, device="cuda"):
+        """Render views; returns (rgb, aux, nsamp) tensors with one row per
+        pixel (views concatenated).  `out` may pass preallocated tensors
+        (device or pinned host)."""
+        cams = list(cams)
+        cc = (Camera * len(cams))(*[_camera(c) for c in cams])
+        offs = np.zeros(len(cams) + 1, np.int32)
+        for v, ids in enumerate(ids_per_view):
+            offs[v + 1] = offs[v] + len(ids)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(i, np.int32) for i in ids_per_view])
+                                    if offs[-1] > 0 else np.zeros(1, np.int32), np.int32)
+        npix = sum(int(c.width) * int(c.height) for c in cams)
+        if out is None:
+            rgb = torch.empty((npix, 3), dtype=torch.float32, device=device)
+            ax = torch.empty((npix, 8), dtype=torch.float32, device=device) if aux else None
+            ns = torch.empty((npix,), dtype=torch.int32, device=device) if nsamp else None
+        else:
+            rgb, ax, ns = out
+        m = mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp)
+        _check(lib().cow_render(self._ctx, cc, len(cams), _ptr(flat), _ptr(offs), _ptr(m), float(ert_eps),
+                                FLAG_MLP_BF16 if mlp_bf16 else 0, _ptr(rgb), _ptr(ax), _ptr(ns),
+                                _stream_ptr(stream)))
+        return rgb, ax, ns
+
+    def render_rays(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], mlp, ert_eps: float = 0.0,
+                    mlp_bf16: bool = False, aux: bool = True, nsamp: bool = False, stream=None):
+        n = o.shape[0]
+        o = o.contiguous()
+        d = d.contiguous()
+        a = np.ascontiguousarray(ids, np.int32)
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
+        ax = torch.empty((n, 8), dtype=torch.float32, device=o.device) if aux else None
+        ns = torch.empty((n,), dtype=torch.int32, device=o.device) if nsamp else None
+        m = mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp)
+        _check(lib().cow_render_rays(self._ctx, _ptr(o), _ptr(d), n, _ptr(a), len(a), _ptr(m), float(ert_eps),
+                                     FLAG_MLP_BF16 if mlp_bf16 else 0, _ptr(rgb), _ptr(ax), _ptr(ns),
+                                     _stream_ptr(stream)))
+        return rgb, ax, ns
+
+    def sync_check(self, stream=None):
+        _check(lib().cow_sync_check(self._ctx, _stream_ptr(stream)))
+
+    # --- inspection --------------------------------------------------------
+    def occupancy(self, i: int) -> np.ndarray:
+        b = self.scene.blocks[i]
+        nc = -(-(b.R - 1) // self.scene.occ_cell)
+        words = (nc ** 3 + 31) // 32
+        out = np.zeros(words, np.uint32)
+        _check(lib().cow_export_occupancy(self._ctx, int(i), _ptr(out), words))
+        return out
+
+    def packed(self, i: int, tensor: int):
+        b = self.scene.blocks[i]
+        n = (b.R ** 3 if tensor == 0 else b.P ** 2) * 8
+        dt = {"fp32": np.float32, "fp16": np.uint16, "bf16": np.uint16, "fp8": np.uint8}[self.storage]
+        out = np.zeros(n, dt)
+        se = np.zeros(8, np.int32)
+        _check(lib().cow_export_packed(self._ctx, int(i), int(tensor), _ptr(out), out.nbytes, _ptr(se)))
+        return out, se

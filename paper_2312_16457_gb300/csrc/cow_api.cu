@@ -1,0 +1,683 @@
+// cow_api.cu -- the C ABI of libcow (declared in include/cow.h).
+//
+// Host side of the renderer: argument checks, the context that owns the
+// packed device scene, LOD selection / visibility / depth sort of App. D in
+// FP64 on the host, and the launches of the marcher.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cow.h"
+#include "cow_common.cuh"
+#include "cow_kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cow_status fail(cow_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define COW_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            return fail(e_ == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA,       \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                    \
+        }                                                                                   \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Restores the caller's current device when it leaves scope.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int elem_bytes(int dtype) { return dtype == COW_FP32 ? 4 : dtype == COW_FP8_E4M3 ? 1 : 2; }
+
+// smallest e with amax <= 448 * 2^e (e = 0 for an all-zero channel)
+int fp8_exponent(float amax) {
+    if (!(amax > 0.0f)) return 0;
+    int e = 0;
+    while ((double)amax > std::ldexp(448.0, e)) e++;
+    while ((double)amax <= std::ldexp(448.0, e - 1) && e > -120) e--;
+    return e;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct BlockHost {
+    float lo[3], hi[3];
+    int32_t lod, parent, R, P;
+    void *grid = nullptr;
+    void *planes[3] = {nullptr, nullptr, nullptr};
+    uint32_t *occ = nullptr;
+    float *scale = nullptr;
+    int32_t scale_exp[4][8];
+    int64_t occ_words = 0;
+    double ztop = 0.0;
+    std::vector<int32_t> children;
+};
+
+}  // namespace
+
+struct cow_ctx {
+    int device = 0;
+    int dtype = 0;
+    int occ_cell = 4;
+    float occ_thresh = 0.01f;
+    std::vector<BlockHost> blocks;
+    cow::BlockRec *d_blocks = nullptr;
+    unsigned *d_err = nullptr;
+    float *d_mlp = nullptr;
+    DevBuf views, ids, out_rgb, out_aux, out_nsamp;
+};
+
+namespace {
+
+void destroy(cow_ctx *c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    for (auto &b : c->blocks) {
+        cudaFree(b.grid);
+        for (auto *p : b.planes) cudaFree(p);
+        cudaFree(b.occ);
+        cudaFree(b.scale);
+    }
+    cudaFree(c->d_blocks);
+    cudaFree(c->d_err);
+    cudaFree(c->d_mlp);
+    c->views.release();
+    c->ids.release();
+    c->out_rgb.release();
+    c->out_aux.release();
+    c->out_nsamp.release();
+    delete c;
+}
+
+double focal_length(int32_t H, double fov_y_deg) { return (0.5 * (double)H) / tan(0.5 * fov_y_deg * M_PI / 180.0); }
+
+// height of the highest occupied part of a block
+double block_ztop(const BlockHost &b, const std::vector<uint32_t> &bits, int C) {
+    const int Nc = (b.R - 1 + C - 1) / C;
+    for (int cz = Nc - 1; cz >= 0; cz--) {
+        for (int64_t k = (int64_t)cz * Nc * Nc; k < (int64_t)(cz + 1) * Nc * Nc; k++) {
+            if ((bits[k >> 5] >> (k & 31)) & 1u) {
+                int top = std::min((cz + 1) * C, b.R - 1);
+                return (double)b.lo[2] + ((double)top * ((double)b.hi[2] - (double)b.lo[2])) / (double)(b.R - 1);
+            }
+        }
+    }
+    return (double)b.lo[2];
+}
+
+cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *staging, unsigned *d_amax,
+                    float *d_inv, double log_thresh, cudaStream_t st) {
+    const int es = elem_bytes(c->dtype);
+    const int64_t nv[4] = {(int64_t)d.grid_res * d.grid_res * d.grid_res, (int64_t)d.plane_res * d.plane_res,
+                           (int64_t)d.plane_res * d.plane_res, (int64_t)d.plane_res * d.plane_res};
+    const float *src[4] = {d.grid, d.planes[0], d.planes[1], d.planes[2]};
+    void **dst[4] = {&b.grid, &b.planes[0], &b.planes[1], &b.planes[2]};
+    const int Nc = (d.grid_res - 1 + c->occ_cell - 1) / c->occ_cell;
+    b.occ_words = ((int64_t)Nc * Nc * Nc + 31) / 32;
+    COW_CUDA(cudaMalloc((void **)&b.occ, (size_t)b.occ_words * 4));
+    COW_CUDA(cudaMalloc((void **)&b.scale, 32 * sizeof(float)));
+    float scale_h[32];
+    for (int t = 0; t < 4; t++) {
+        COW_CUDA(cudaMalloc(dst[t], (size_t)nv[t] * cow::kNch * es));
+        const float *s = src[t];
+        if (!is_device_ptr(s)) {
+            COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
+            s = (const float *)staging;
+        }
+        int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (c->dtype == COW_FP8_E4M3) {
+            COW_CUDA(cow::launch_amax8(s, nv[t], d_amax, st));
+            unsigned amax_bits[8];
+            COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
+            COW_CUDA(cudaStreamSynchronize(st));
+            for (int k = 0; k < 8; k++) {
+                float a;
+                std::memcpy(&a, &amax_bits[k], 4);
+                e[k] = fp8_exponent(a);
+            }
+        }
+        float inv[8];
+        for (int k = 0; k < 8; k++) {
+            b.scale_exp[t][k] = e[k];
+            inv[k] = std::ldexp(1.0f, -e[k]);
+            scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
+        }
+        COW_CUDA(cudaMemcpyAsync(d_inv, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
+        COW_CUDA(cow::launch_pack(s, nv[t], c->dtype, d_inv, *dst[t], st));
+        if (t == 0) COW_CUDA(cow::launch_occupancy(s, d.grid_res, c->occ_cell, log_thresh, b.occ, st));
+        // the staging buffer and d_inv are reused by the next tensor: the
+        // stream orders the next copies after these kernels
+    }
+    COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
+    std::vector<uint32_t> bits((size_t)b.occ_words);
+    COW_CUDA(cudaMemcpyAsync(bits.data(), b.occ, (size_t)b.occ_words * 4, cudaMemcpyDeviceToHost, st));
+    COW_CUDA(cudaStreamSynchronize(st));
+    b.ztop = block_ztop(b, bits, c->occ_cell);
+    return COW_OK;
+}
+
+cow::BlockRec make_rec(const cow_ctx *c, const BlockHost &b) {
+    cow::BlockRec r;
+    std::memset(&r, 0, sizeof(r));
+    for (int a = 0; a < 3; a++) {
+        r.lo[a] = b.lo[a];
+        r.hi[a] = b.hi[a];
+        const double ext = (double)b.hi[a] - (double)b.lo[a];
+        const double m = 1e-3 * std::max(1.0, ext);
+        r.lo_e[a] = (float)((double)b.lo[a] - m);
+        r.hi_e[a] = (float)((double)b.hi[a] + m);
+        r.kg[a] = (float)((double)(b.R - 1) / ext);
+        r.kp[a] = (float)((double)(b.P - 1) / ext);
+    }
+    r.delta = (float)(((double)b.hi[0] - (double)b.lo[0]) / (double)b.P);
+    r.cx = (float)(0.5 * ((double)b.lo[0] + (double)b.hi[0]));
+    r.cy = (float)(0.5 * ((double)b.lo[1] + (double)b.hi[1]));
+    r.R = b.R;
+    r.P = b.P;
+    r.C = c->occ_cell;
+    r.Nc = (b.R - 1 + c->occ_cell - 1) / c->occ_cell;
+    r.dtype = c->dtype;
+    r.grid = b.grid;
+    for (int k = 0; k < 3; k++) r.planes[k] = b.planes[k];
+    r.occ = b.occ;
+    r.scale = b.scale;
+    return r;
+}
+
+// --- App. D on the host, FP64 ---------------------------------------------
+
+struct ViewGeom {
+    double t[3];
+    double m[9];  // rotation, row-major
+    double kx, ky;
+};
+
+ViewGeom view_geom(const cow_camera &cam) {
+    ViewGeom g;
+    for (int r = 0; r < 3; r++) {
+        g.t[r] = cam.c2w[4 * r + 3];
+        for (int k = 0; k < 3; k++) g.m[3 * r + k] = cam.c2w[4 * r + k];
+    }
+    const double f = focal_length(cam.height, cam.fov_y_deg);
+    g.kx = (double)cam.width / (2.0 * f);
+    g.ky = (double)cam.height / (2.0 * f);
+    return g;
+}
+
+// Conservative: culled only when all 8 corners are strictly outside one plane.
+bool box_in_view(const ViewGeom &g, const double lo[3], const double hi[3]) {
+    bool all_out[5] = {true, true, true, true, true};
+    for (int k = 0; k < 8; k++) {
+        const double q0 = ((k & 1) ? hi[0] : lo[0]) - g.t[0];
+        const double q1 = ((k & 2) ? hi[1] : lo[1]) - g.t[1];
+        const double q2 = ((k & 4) ? hi[2] : lo[2]) - g.t[2];
+        // camera-frame coordinates: transpose(rotation) * q
+        const double xc = (g.m[0] * q0 + g.m[3] * q1) + g.m[6] * q2;
+        const double yc = (g.m[1] * q0 + g.m[4] * q1) + g.m[7] * q2;
+        const double zc = (g.m[2] * q0 + g.m[5] * q1) + g.m[8] * q2;
+        const double depth = -zc;
+        const double side[5] = {depth, xc + g.kx * depth, g.kx * depth - xc, yc + g.ky * depth, g.ky * depth - yc};
+        for (int s = 0; s < 5; s++) all_out[s] = all_out[s] && (side[s] < 0.0);
+    }
+    return !(all_out[0] || all_out[1] || all_out[2] || all_out[3] || all_out[4]);
+}
+
+bool block_in_view(const ViewGeom &g, const BlockHost &b) {
+    const double lo[3] = {b.lo[0], b.lo[1], b.lo[2]};
+    const double hi[3] = {b.hi[0], b.hi[1], b.ztop};
+    return box_in_view(g, lo, hi);
+}
+
+double block_range(const ViewGeom &g, const BlockHost &b) {
+    const double dx = 0.5 * ((double)b.lo[0] + (double)b.hi[0]) - g.t[0];
+    const double dy = 0.5 * ((double)b.lo[1] + (double)b.hi[1]) - g.t[1];
+    const double dz = b.ztop - g.t[2];
+    return std::sqrt((dx * dx + dy * dy) + dz * dz);
+}
+
+void depth_sort(const cow_ctx *c, const cow_camera &cam, std::vector<int32_t> &ids) {
+    std::vector<std::pair<double, int32_t>> keyed;
+    keyed.reserve(ids.size());
+    for (int32_t id : ids) {
+        const BlockHost &b = c->blocks[id];
+        const double dx = 0.5 * ((double)b.lo[0] + (double)b.hi[0]) - cam.c2w[3];
+        const double dy = 0.5 * ((double)b.lo[1] + (double)b.hi[1]) - cam.c2w[7];
+        keyed.emplace_back(dx * dx + dy * dy, id);
+    }
+    std::sort(keyed.begin(), keyed.end());  // (key, id): ties by index
+    for (size_t k = 0; k < ids.size(); k++) ids[k] = keyed[k].second;
+}
+
+// Sizes one launch processes; shared by cow_render and its host-output path.
+struct ViewPlan {
+    std::vector<cow::ViewRec> recs;
+    int64_t n_pix = 0;
+    int n_tiles = 0;
+};
+
+cow_status plan_views(const cow_ctx *c, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                      const int32_t *ids_offsets, ViewPlan &plan) {
+    const int tw = cow::march_tile_w(), th = cow::march_tile_h();
+    plan.recs.resize((size_t)n_views);
+    int64_t tiles = 0;
+    const int32_t nb = (int32_t)c->blocks.size();
+    if (ids_offsets[0] != 0) return fail(COW_ERR_INVALID_ARG, "ids_offsets[0] must be 0");
+    for (int32_t v = 0; v < n_views; v++) {
+        const cow_camera &cam = cams[v];
+        if (cam.width < 1 || cam.height < 1 || cam.width > 32768 || cam.height > 32768)
+            return fail(COW_ERR_INVALID_ARG, "view %d: bad image size %dx%d", v, cam.width, cam.height);
+        if (!(cam.fov_y_deg > 0.0 && cam.fov_y_deg < 180.0))
+            return fail(COW_ERR_INVALID_ARG, "view %d: fov_y_deg must be in (0, 180)", v);
+        if (ids_offsets[v + 1] < ids_offsets[v])
+            return fail(COW_ERR_INVALID_ARG, "ids_offsets must be non-decreasing");
+        for (int32_t k = ids_offsets[v]; k < ids_offsets[v + 1]; k++)
+            if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "view %d: block id %d out of range", v, ids[k]);
+        cow::ViewRec &r = plan.recs[(size_t)v];
+        std::memset(&r, 0, sizeof(r));
+        for (int rr = 0; rr < 3; rr++) {
+            for (int k = 0; k < 3; k++) r.Rm[3 * rr + k] = (float)cam.c2w[4 * rr + k];
+            r.o[rr] = (float)cam.c2w[4 * rr + 3];
+        }
+        r.f = (float)focal_length(cam.height, cam.fov_y_deg);
+        r.W = cam.width;
+        r.H = cam.height;
+        r.tiles_x = (cam.width + tw - 1) / tw;
+        const int tiles_y = (cam.height + th - 1) / th;
+        r.tile_begin = (int32_t)tiles;
+        r.ids_begin = ids_offsets[v];
+        r.ids_count = ids_offsets[v + 1] - ids_offsets[v];
+        r.pix_offset = plan.n_pix;
+        tiles += (int64_t)r.tiles_x * tiles_y;
+        plan.n_pix += (int64_t)cam.width * cam.height;
+    }
+    if (tiles > 0x7fffffff) return fail(COW_ERR_INVALID_ARG, "too many tiles in one call");
+    plan.n_tiles = (int)tiles;
+    return COW_OK;
+}
+
+// Resolve an output pointer: device memory is used in place, host memory goes
+// through a context buffer copied back after the kernel.
+template <typename T>
+cow_status resolve_out(T *user, size_t bytes, DevBuf &buf, T **dev, bool *host) {
+    *host = false;
+    *dev = user;
+    if (!user) return COW_OK;
+    if (is_device_ptr(user)) return COW_OK;
+    COW_CUDA(buf.reserve(bytes));
+    *dev = (T *)buf.p;
+    *host = true;
+    return COW_OK;
+}
+
+cow_status resolve_mlp(cow_ctx *c, const float *mlp, cudaStream_t st, const float **dev) {
+    if (is_device_ptr(mlp)) {
+        *dev = mlp;
+        return COW_OK;
+    }
+    COW_CUDA(cudaMemcpyAsync(c->d_mlp, mlp, cow::kMlpParams * sizeof(float), cudaMemcpyHostToDevice, st));
+    *dev = c->d_mlp;
+    return COW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t cow_version(void) { return 1; }
+
+const char *cow_last_error(void) { return g_last_error.c_str(); }
+
+cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
+                           float occ_thresh, int32_t occ_cell, void *stream) {
+    g_last_error.clear();
+    if (!out || !blocks || n < 1) return fail(COW_ERR_INVALID_ARG, "cow_load_blocks: null pointer or n < 1");
+    *out = nullptr;
+    if ((int)storage < 0 || (int)storage > 3) return fail(COW_ERR_INVALID_ARG, "unknown storage dtype %d", (int)storage);
+    if (occ_cell < 1) return fail(COW_ERR_INVALID_ARG, "occ_cell must be >= 1");
+    if (!(occ_thresh > 0.0f)) return fail(COW_ERR_INVALID_ARG, "occ_thresh must be > 0");
+    size_t max_vec = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const cow_block_desc &d = blocks[i];
+        if (!d.grid || !d.planes[0] || !d.planes[1] || !d.planes[2])
+            return fail(COW_ERR_INVALID_ARG, "block %d: null array", i);
+        for (const float *q : {d.grid, d.planes[0], d.planes[1], d.planes[2]})
+            if (((uintptr_t)q & 15u) != 0) return fail(COW_ERR_INVALID_ARG, "block %d: arrays must be 16-byte aligned", i);
+        if (d.grid_res < 2 || d.plane_res < 2 || d.grid_res > 1024 || d.plane_res > 16384)
+            return fail(COW_ERR_INVALID_ARG, "block %d: resolutions must be in [2, 1024] / [2, 16384]", i);
+        for (int a = 0; a < 3; a++)
+            if (!(d.lo[a] < d.hi[a])) return fail(COW_ERR_INVALID_ARG, "block %d: lo must be < hi", i);
+        if (d.lod < 1) return fail(COW_ERR_INVALID_ARG, "block %d: lod must be >= 1", i);
+        if (d.parent < -1 || d.parent >= n || d.parent == i)
+            return fail(COW_ERR_INVALID_ARG, "block %d: bad parent index %d", i, d.parent);
+        if (d.parent >= 0 && blocks[d.parent].lod != d.lod + 1)
+            return fail(COW_ERR_INVALID_ARG, "block %d: parent must be one level coarser", i);
+        max_vec = std::max(max_vec, (size_t)d.grid_res * d.grid_res * d.grid_res);
+        max_vec = std::max(max_vec, (size_t)d.plane_res * d.plane_res);
+    }
+    cow_ctx *c = new cow_ctx();
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        delete c;
+        return fail(COW_ERR_CUDA, "no CUDA device");
+    }
+    c->dtype = (int)storage;
+    c->occ_cell = occ_cell;
+    c->occ_thresh = occ_thresh;
+    c->blocks.resize((size_t)n);
+    void *staging = nullptr;
+    unsigned *d_amax = nullptr;
+    float *d_inv = nullptr;
+    cow_status rc = COW_OK;
+    auto cleanup = [&](cow_status s) {
+        cudaFree(staging);
+        cudaFree(d_amax);
+        cudaFree(d_inv);
+        if (s != COW_OK) destroy(c);
+        return s;
+    };
+    bool any_host = false;
+    for (int32_t i = 0; i < n && !any_host; i++) {
+        const cow_block_desc &d = blocks[i];
+        any_host = !is_device_ptr(d.grid) || !is_device_ptr(d.planes[0]) || !is_device_ptr(d.planes[1]) ||
+                   !is_device_ptr(d.planes[2]);
+    }
+    cudaError_t e = cudaSuccess;
+    if (any_host) e = cudaMalloc(&staging, max_vec * 32);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_amax, 8 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&d_inv, 8 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_mlp, 512 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess)
+        return cleanup(fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "cow_load_blocks: %s",
+                            cudaGetErrorString(e)));
+    const double log_thresh = std::log((double)occ_thresh);
+    for (int32_t i = 0; i < n && rc == COW_OK; i++) {
+        const cow_block_desc &d = blocks[i];
+        BlockHost &b = c->blocks[(size_t)i];
+        for (int a = 0; a < 3; a++) {
+            b.lo[a] = d.lo[a];
+            b.hi[a] = d.hi[a];
+        }
+        b.lod = d.lod;
+        b.parent = d.parent;
+        b.R = d.grid_res;
+        b.P = d.plane_res;
+        rc = load_one(c, d, b, staging, d_amax, d_inv, log_thresh, st);
+    }
+    if (rc != COW_OK) return cleanup(rc);
+    for (int32_t i = 0; i < n; i++)
+        if (blocks[i].parent >= 0) c->blocks[(size_t)blocks[i].parent].children.push_back(i);
+    std::vector<cow::BlockRec> recs((size_t)n);
+    for (int32_t i = 0; i < n; i++) recs[(size_t)i] = make_rec(c, c->blocks[(size_t)i]);
+    e = cudaMalloc((void **)&c->d_blocks, recs.size() * sizeof(cow::BlockRec));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_blocks, recs.data(), recs.size() * sizeof(cow::BlockRec), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+        return cleanup(fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "cow_load_blocks: %s",
+                            cudaGetErrorString(e)));
+    cleanup(COW_OK);
+    *out = c;
+    return COW_OK;
+}
+
+cow_status cow_free(cow_ctx *ctx) {
+    destroy(ctx);
+    return COW_OK;
+}
+
+cow_status cow_num_blocks(const cow_ctx *ctx, int32_t *out_n) {
+    if (!ctx || !out_n) return fail(COW_ERR_INVALID_ARG, "null argument");
+    *out_n = (int32_t)ctx->blocks.size();
+    return COW_OK;
+}
+
+cow_status cow_block_ztop(const cow_ctx *ctx, int32_t block, double *out_ztop) {
+    if (!ctx || !out_ztop) return fail(COW_ERR_INVALID_ARG, "null argument");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
+    *out_ztop = ctx->blocks[(size_t)block].ztop;
+    return COW_OK;
+}
+
+cow_status cow_select_lod(const cow_ctx *ctx, const cow_camera *cam, const double *lod_thresh, int32_t n_lod,
+                          int32_t *out_ids, int32_t cap, int32_t *out_n) {
+    if (!ctx || !cam || !out_n || (n_lod > 0 && !lod_thresh) || (cap > 0 && !out_ids))
+        return fail(COW_ERR_INVALID_ARG, "cow_select_lod: null argument");
+    const ViewGeom g = view_geom(*cam);
+    int32_t top = 1;
+    for (const auto &b : ctx->blocks) top = std::max(top, b.lod);
+    std::vector<int32_t> sel, stack;
+    for (int32_t i = (int32_t)ctx->blocks.size() - 1; i >= 0; i--)
+        if (ctx->blocks[(size_t)i].lod == top && block_in_view(g, ctx->blocks[(size_t)i])) stack.push_back(i);
+    while (!stack.empty()) {
+        const int32_t i = stack.back();
+        stack.pop_back();
+        const BlockHost &b = ctx->blocks[(size_t)i];
+        if (b.lod <= 1) {
+            sel.push_back(i);
+            continue;
+        }
+        std::vector<int32_t> vis;
+        bool keep = true;
+        for (int32_t ch : b.children) {
+            const BlockHost &cb = ctx->blocks[(size_t)ch];
+            if (!block_in_view(g, cb)) continue;
+            vis.push_back(ch);
+            const int k = cb.lod - 1;
+            const double tau = (k >= 0 && k < n_lod) ? lod_thresh[k] : 0.0;
+            if (!(block_range(g, cb) > tau)) keep = false;
+        }
+        if (keep) sel.push_back(i);
+        else
+            for (int32_t ch : vis) stack.push_back(ch);
+    }
+    depth_sort(ctx, *cam, sel);
+    *out_n = (int32_t)sel.size();
+    if ((int32_t)sel.size() > cap) return fail(COW_ERR_INVALID_ARG, "cow_select_lod: %d blocks exceed cap %d", (int)sel.size(), cap);
+    std::copy(sel.begin(), sel.end(), out_ids);
+    return COW_OK;
+}
+
+cow_status cow_sort_blocks(const cow_ctx *ctx, const cow_camera *cam, const int32_t *ids, int32_t n, int32_t *out) {
+    if (!ctx || !cam || (n > 0 && (!ids || !out)) || n < 0) return fail(COW_ERR_INVALID_ARG, "cow_sort_blocks: bad argument");
+    std::vector<int32_t> v(ids, ids + n);
+    for (int32_t id : v)
+        if (id < 0 || id >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", id);
+    depth_sort(ctx, *cam, v);
+    std::copy(v.begin(), v.end(), out);
+    return COW_OK;
+}
+
+cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                      const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                      float *out_aux, int32_t *out_nsamp, void *stream) {
+    g_last_error.clear();
+    if (!ctx || !cams || n_views < 1 || !ids_offsets || !mlp || !out_rgb)
+        return fail(COW_ERR_INVALID_ARG, "cow_render: null argument or n_views < 1");
+    if (ids_offsets[n_views] > 0 && !ids) return fail(COW_ERR_INVALID_ARG, "cow_render: null ids");
+    if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
+    if (flags & ~COW_FLAG_MLP_BF16) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    if (((uintptr_t)out_rgb & 3u) || ((uintptr_t)out_aux & 15u)) return fail(COW_ERR_INVALID_ARG, "misaligned output");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ViewPlan plan;
+    cow_status rc = plan_views(ctx, cams, n_views, ids, ids_offsets, plan);
+    if (rc != COW_OK) return rc;
+    const int32_t n_ids = ids_offsets[n_views];
+    COW_CUDA(ctx->views.reserve(plan.recs.size() * sizeof(cow::ViewRec)));
+    COW_CUDA(ctx->ids.reserve((size_t)std::max(n_ids, 1) * sizeof(int32_t)));
+    COW_CUDA(cudaMemcpyAsync(ctx->views.p, plan.recs.data(), plan.recs.size() * sizeof(cow::ViewRec),
+                             cudaMemcpyHostToDevice, st));
+    if (n_ids > 0)
+        COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const float *d_mlp = nullptr;
+    if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
+    float *rgb, *aux;
+    int32_t *ns;
+    bool h_rgb, h_aux, h_ns;
+    if ((rc = resolve_out(out_rgb, (size_t)plan.n_pix * 12, ctx->out_rgb, &rgb, &h_rgb)) != COW_OK) return rc;
+    if ((rc = resolve_out(out_aux, (size_t)plan.n_pix * 32, ctx->out_aux, &aux, &h_aux)) != COW_OK) return rc;
+    if ((rc = resolve_out(out_nsamp, (size_t)plan.n_pix * 4, ctx->out_nsamp, &ns, &h_ns)) != COW_OK) return rc;
+    cow::MarchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.blocks = ctx->d_blocks;
+    a.views = (const cow::ViewRec *)ctx->views.p;
+    a.n_views = n_views;
+    a.dtype = ctx->dtype;
+    a.ids = (const int32_t *)ctx->ids.p;
+    a.mlp = d_mlp;
+    a.ert_eps = ert_eps;
+    a.flags = flags;
+    a.out_rgb = rgb;
+    a.out_aux = aux;
+    a.out_nsamp = ns;
+    a.err = ctx->d_err;
+    COW_CUDA(cow::launch_march_views(a, plan.n_tiles, st));
+    if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)plan.n_pix * 12, cudaMemcpyDeviceToHost, st));
+    if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)plan.n_pix * 32, cudaMemcpyDeviceToHost, st));
+    if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)plan.n_pix * 4, cudaMemcpyDeviceToHost, st));
+    return COW_OK;
+}
+
+cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                           int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                           float *out_aux, int32_t *out_nsamp, void *stream) {
+    g_last_error.clear();
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !out_rgb)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_rays: null argument");
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
+    if (flags & ~COW_FLAG_MLP_BF16) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    if (!is_device_ptr(o) || !is_device_ptr(d)) return fail(COW_ERR_INVALID_ARG, "ray origins and directions must be device memory");
+    if (((uintptr_t)out_rgb & 3u) || ((uintptr_t)out_aux & 15u)) return fail(COW_ERR_INVALID_ARG, "misaligned output");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
+    COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    cow_status rc;
+    const float *d_mlp = nullptr;
+    if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
+    float *rgb, *aux;
+    int32_t *ns;
+    bool h_rgb, h_aux, h_ns;
+    if ((rc = resolve_out(out_rgb, (size_t)n_rays * 12, ctx->out_rgb, &rgb, &h_rgb)) != COW_OK) return rc;
+    if ((rc = resolve_out(out_aux, (size_t)n_rays * 32, ctx->out_aux, &aux, &h_aux)) != COW_OK) return rc;
+    if ((rc = resolve_out(out_nsamp, (size_t)n_rays * 4, ctx->out_nsamp, &ns, &h_ns)) != COW_OK) return rc;
+    cow::MarchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.blocks = ctx->d_blocks;
+    a.dtype = ctx->dtype;
+    a.ids = (const int32_t *)ctx->ids.p;
+    a.mlp = d_mlp;
+    a.ert_eps = ert_eps;
+    a.flags = flags;
+    a.out_rgb = rgb;
+    a.out_aux = aux;
+    a.out_nsamp = ns;
+    a.err = ctx->d_err;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.n_ray_ids = n_ids;
+    COW_CUDA(cow::launch_march_rays(a, st));
+    if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)n_rays * 12, cudaMemcpyDeviceToHost, st));
+    if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)n_rays * 32, cudaMemcpyDeviceToHost, st));
+    if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)n_rays * 4, cudaMemcpyDeviceToHost, st));
+    return COW_OK;
+}
+
+cow_status cow_sync_check(cow_ctx *ctx, void *stream) {
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    COW_CUDA(cudaStreamSynchronize(st));
+    unsigned err = 0;
+    COW_CUDA(cudaMemcpy(&err, ctx->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err) {
+        COW_CUDA(cudaMemset(ctx->d_err, 0, sizeof(unsigned)));
+        if (err & cow::kErrTimeout) return fail(COW_ERR_TIMEOUT, "a bounded device-side wait ran out (error word 0x%x)", err);
+        return fail(COW_ERR_DEVICE_ASSERT, "a kernel range check fired (error word 0x%x)", err);
+    }
+    return COW_OK;
+}
+
+cow_status cow_export_occupancy(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words) {
+    if (!ctx || !out_bits) return fail(COW_ERR_INVALID_ARG, "null argument");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
+    const BlockHost &b = ctx->blocks[(size_t)block];
+    if (n_words < b.occ_words) return fail(COW_ERR_INVALID_ARG, "need %lld words", (long long)b.occ_words);
+    DeviceGuard dg(ctx->device);
+    COW_CUDA(cudaMemcpy(out_bits, b.occ, (size_t)b.occ_words * 4, cudaMemcpyDeviceToHost));
+    return COW_OK;
+}
+
+cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, void *out, int64_t nbytes,
+                             int32_t *out_scale_exp) {
+    if (!ctx || !out) return fail(COW_ERR_INVALID_ARG, "null argument");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size() || tensor < 0 || tensor > 3)
+        return fail(COW_ERR_INVALID_ARG, "block or tensor out of range");
+    const BlockHost &b = ctx->blocks[(size_t)block];
+    const int64_t nv = tensor == 0 ? (int64_t)b.R * b.R * b.R : (int64_t)b.P * b.P;
+    const int64_t need = nv * cow::kNch * elem_bytes(ctx->dtype);
+    if (nbytes < need) return fail(COW_ERR_INVALID_ARG, "need %lld bytes", (long long)need);
+    DeviceGuard dg(ctx->device);
+    COW_CUDA(cudaMemcpy(out, tensor == 0 ? b.grid : b.planes[tensor - 1], (size_t)need, cudaMemcpyDeviceToHost));
+    if (out_scale_exp)
+        for (int k = 0; k < 8; k++) out_scale_exp[k] = b.scale_exp[tensor][k];
+    return COW_OK;
+}
+
+}  // extern "C"

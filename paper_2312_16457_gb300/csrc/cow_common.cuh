@@ -1,0 +1,197 @@
+// cow_common.cuh -- records and device helpers shared by the libcow kernels.
+//
+// Geometry decisions (which lattice samples exist, which block a sample falls
+// in, which occupancy cell it lies in) are taken on FP32 values produced by a
+// fixed sequence of IEEE round-to-nearest operations.  The __f*_rn intrinsics
+// below keep nvcc from fusing or reordering them, so the decisions are a pure
+// function of the inputs.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cow {
+
+constexpr int kNch = 8;
+constexpr int kMlpParams = 499;
+constexpr int kOffW1 = 0, kOffB1 = 160, kOffW2 = 176, kOffB2 = 432, kOffW3 = 448, kOffB3 = 496;
+constexpr int kMaxRayIds = 64;       // blocks one ray of the ray-batch form composites
+constexpr int kMaxSpan = 1 << 22;    // lattice indices one (ray, block) pair may scan
+
+// error word bits (device-side faults are recorded, never trapped)
+constexpr unsigned kErrRange = 1u;    // a (ray, block) candidate range exceeded kMaxSpan
+constexpr unsigned kErrTimeout = 2u;  // a bounded wait ran out
+constexpr unsigned kErrArg = 4u;      // a kernel met an argument it cannot handle
+
+enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3 };
+
+// One block as the kernels see it (host fills it once at load time).
+struct alignas(16) BlockRec {
+    float lo[3], hi[3];      // world AABB (FP32, exactly the caller's values)
+    float lo_e[3], hi_e[3];  // AABB grown by 1e-3 * max(1, extent): candidate-range box
+    float kg[3];             // (float)((R-1) / (hi-lo)) per axis, computed in double
+    float kp[3];             // (float)((P-1) / (hi-lo)) per axis, computed in double
+    float delta;             // (float)((hi_x - lo_x) / P), computed in double
+    float cx, cy;            // (float)((lo + hi) / 2) in double: ray-batch sort key
+    int32_t R, P, Nc, C;     // resolutions, occupancy cells per axis, voxels per cell
+    int32_t dtype, pad0;
+    const void *grid;        // packed R^3 x 8
+    const void *planes[3];   // packed P^2 x 8 each (xy, xz, yz)
+    const uint32_t *occ;     // occupancy bits
+    const float *scale;      // 32 floats: per-channel scale of grid, xy, xz, yz
+};
+static_assert(sizeof(BlockRec) % 16 == 0, "BlockRec must be a multiple of 16 bytes");
+
+// One camera as the kernels see it.
+struct alignas(16) ViewRec {
+    float Rm[9];         // (float)c2w rotation, row-major
+    float o[3];          // (float)c2w translation
+    float f;             // (float)((H/2) / tan(fov/2)), computed in double
+    int32_t W, H;
+    int32_t tiles_x;     // tiles per image row
+    int32_t tile_begin;  // first global tile index of this view
+    int32_t ids_begin, ids_count;
+    int32_t pad0;
+    int64_t pix_offset;  // first output row of this view
+};
+static_assert(sizeof(ViewRec) % 16 == 0, "ViewRec must be a multiple of 16 bytes");
+
+// ---------------------------------------------------------------------------
+// FP32 decision sequence
+
+// Pinhole ray through the centre of pixel (px, py).
+__device__ __forceinline__ void pixel_ray(const ViewRec &v, int px, int py, float o[3], float d[3]) {
+    const float bx = __fsub_rn(__fadd_rn((float)px, 0.5f), __fmul_rn(0.5f, (float)v.W));
+    const float by = __fsub_rn(__fadd_rn((float)py, 0.5f), __fmul_rn(0.5f, (float)v.H));
+    const float xc = __fdiv_rn(bx, v.f);
+    const float yc = -__fdiv_rn(by, v.f);
+    float dw[3];
+#pragma unroll
+    for (int r = 0; r < 3; r++) {
+        const float s = __fadd_rn(__fmul_rn(v.Rm[3 * r + 0], xc), __fmul_rn(v.Rm[3 * r + 1], yc));
+        dw[r] = __fsub_rn(s, v.Rm[3 * r + 2]);
+        o[r] = v.o[r];
+    }
+    const float n2 =
+        __fadd_rn(__fadd_rn(__fmul_rn(dw[0], dw[0]), __fmul_rn(dw[1], dw[1])), __fmul_rn(dw[2], dw[2]));
+    const float n = __fsqrt_rn(n2);
+#pragma unroll
+    for (int r = 0; r < 3; r++) d[r] = __fdiv_rn(dw[r], n);
+}
+
+// Lattice sample i of a ray: t = (i + 1/2) delta, p = o + t d.
+__device__ __forceinline__ void lattice_point(const float o[3], const float d[3], float delta, int i,
+                                              float p[3]) {
+    const float t = __fmul_rn(__fadd_rn(__int2float_rn(i), 0.5f), delta);
+#pragma unroll
+    for (int a = 0; a < 3; a++) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
+}
+
+// Ground-plane membership: half-open in x and y, closed in z.
+__device__ __forceinline__ bool inside_block(const BlockRec &b, const float p[3]) {
+    return p[0] >= b.lo[0] && p[0] < b.hi[0] && p[1] >= b.lo[1] && p[1] < b.hi[1] && p[2] >= b.lo[2] &&
+           p[2] <= b.hi[2];
+}
+
+// Continuous vertex coordinate along one axis: (p - lo) * k.
+__device__ __forceinline__ float axis_coord(float p, float lo, float k) { return __fmul_rn(__fsub_rn(p, lo), k); }
+
+// Candidate lattice range of a ray in a block: FP32 slab test on the grown
+// box, widened by two indices at each end.  Returns false on a miss.
+__device__ __forceinline__ bool candidate_range(const BlockRec &b, const float o[3], const float d[3], int &i0,
+                                                int &i1) {
+    float tn = 0.f, tf = 3.0e38f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const float lo = b.lo_e[a], hi = b.hi_e[a];
+        if (d[a] == 0.f) {
+            if (o[a] < lo || o[a] > hi) return false;
+        } else {
+            const float inv = 1.0f / d[a];
+            const float t0 = (lo - o[a]) * inv, t1 = (hi - o[a]) * inv;
+            tn = fmaxf(tn, fminf(t0, t1));
+            tf = fminf(tf, fmaxf(t0, t1));
+        }
+    }
+    if (!(tn <= tf)) return false;
+    const float inv_delta = 1.0f / b.delta;
+    const float a0 = floorf(tn * inv_delta - 0.5f) - 2.f;
+    const float a1 = ceilf(tf * inv_delta - 0.5f) + 2.f;
+    i0 = a0 < 0.f ? 0 : a0 > 2.0e9f ? 2000000000 : (int)a0;
+    i1 = a1 > 2.0e9f ? 2000000000 : (int)a1;
+    return i1 >= i0;
+}
+
+// ---------------------------------------------------------------------------
+// storage loads: 8 channels of one vertex / texel as float (unscaled)
+
+template <int DT>
+struct Store;
+
+template <>
+struct Store<kF32> {
+    using T = float;
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+        const float4 *p = reinterpret_cast<const float4 *>(base) + 2 * idx;
+        const float4 a = __ldg(p), b = __ldg(p + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+
+template <>
+struct Store<kF16> {
+    using T = __half;
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&w[k]);
+            float2 f = __half22float2(h);
+            v[2 * k] = f.x;
+            v[2 * k + 1] = f.y;
+        }
+    }
+};
+
+template <>
+struct Store<kBF16> {
+    using T = __nv_bfloat16;
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[2 * k] = __uint_as_float(w[k] << 16);
+            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+        }
+    }
+};
+
+template <>
+struct Store<kFP8> {
+    using T = __nv_fp8_e4m3;
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(base) + idx);
+        const uint32_t w[2] = {q.x, q.y};
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[k] >> (16 * h)) & 0xffffu);
+                const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+                v[4 * k + 2 * h] = f.x;
+                v[4 * k + 2 * h + 1] = f.y;
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+
+}  // namespace cow

@@ -1,0 +1,42 @@
+// cow_kernels.h -- launch interfaces of the libcow kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cow {
+
+struct BlockRec;
+struct ViewRec;
+
+struct MarchArgs {
+    const BlockRec *blocks;
+    const ViewRec *views;
+    int32_t n_views;
+    int32_t dtype;
+    const int32_t *ids;    // view mode: CSR by view; ray mode: the blocks to composite
+    const float *mlp;      // 499 FP32 (device)
+    float ert_eps;
+    uint32_t flags;
+    float *out_rgb;
+    float *out_aux;        // may be null
+    int32_t *out_nsamp;    // may be null
+    unsigned *err;
+    const float *ray_o;    // ray mode
+    const float *ray_d;
+    int64_t n_rays;
+    int32_t n_ray_ids;
+};
+
+cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, cudaStream_t st);
+cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st);
+int march_tile_w();
+int march_tile_h();
+
+// K4 / K5: packing and occupancy (pack.cu)
+cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cudaStream_t st);
+cudaError_t launch_pack(const float *x, int64_t n_vec, int dtype, const float *inv_scale8, void *out,
+                        cudaStream_t st);
+cudaError_t launch_occupancy(const float *grid, int R, int C, double log_thresh, uint32_t *bits, cudaStream_t st);
+
+}  // namespace cow

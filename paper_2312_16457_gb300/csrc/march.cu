@@ -1,0 +1,305 @@
+// march.cu -- K1 ray marcher with in-register block compositor and the fused
+// K3 deferred-MLP epilogue.
+//
+// Per pixel (Sec. 4.2 rendering stage):
+//   for each selected block, near to far (App. D depth sort):
+//     for each lattice sample of the ray inside the block (Eq. 4 membership)
+//       skip it when its occupancy cell is empty (Sec. 4.1, Sec. 4.5)
+//       f = trilinear(grid) + bilinear(xy) + bilinear(xz) + bilinear(yz)
+//       sigma = exp(f0), alpha = 1 - exp(-sigma delta)            (Eq. 1)
+//       C_d += T alpha sigmoid(f1..3), F += T alpha sigmoid(f4..7) (Eq. 2)
+//       T *= 1 - alpha
+//   Carrying T across blocks is Eq. 12 with Eq. 13 (1 - alpha^k equals the
+//   product of the block's (1 - alpha_i)), so no per-block partials exist.
+//   C = C_d + sigmoid(MLP(C_d, F, d))                                (Eq. 3)
+#include "cow_common.cuh"
+#include "cow_kernels.h"
+
+namespace cow {
+
+namespace {
+
+constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+
+struct RayState {
+    float Cd[3], F[4], T;
+    int nsamp;
+    bool done;
+};
+
+template <int DT>
+__device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], float f[8]) {
+    // grid: vertex-aligned trilinear; g is the same FP32 coordinate the cell
+    // decision used
+    float fr[3];
+    int c0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float g = axis_coord(p[a], b.lo[a], b.kg[a]);
+        int v = __float2int_rd(g);
+        v = min(max(v, 0), b.R - 2);
+        g = fminf(fmaxf(g, 0.f), (float)(b.R - 1));
+        c0[a] = v;
+        fr[a] = g - (float)v;
+    }
+    const int R = b.R;
+    const int64_t base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
+    float acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) acc[c] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+        const float w = (dx ? fr[0] : 1.f - fr[0]) * (dy ? fr[1] : 1.f - fr[1]) * (dz ? fr[2] : 1.f - fr[2]);
+        float v[8];
+        Store<DT>::load8(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
+#pragma unroll
+        for (int c = 0; c < 8; c++) acc[c] = fmaf(w, v[c], acc[c]);
+    }
+    if (DT == kFP8) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) f[c] = acc[c] * __ldg(b.scale + c);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 8; c++) f[c] = acc[c];
+    }
+    // planes: vertex-aligned bilinear in (x, y), (x, z), (y, z)
+    float hf[3];
+    int h0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        int u = __float2int_rd(h);
+        u = min(max(u, 0), b.P - 2);
+        h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
+        h0[a] = u;
+        hf[a] = h - (float)u;
+    }
+    const int P = b.P;
+#pragma unroll
+    for (int pl = 0; pl < 3; pl++) {
+        const int ua = pl == 2 ? 1 : 0, va = pl == 0 ? 1 : 2;
+        const int64_t tb = (int64_t)h0[va] * P + h0[ua];
+        float pacc[8];
+#pragma unroll
+        for (int c = 0; c < 8; c++) pacc[c] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int du = q & 1, dv = q >> 1;
+            const float w = (du ? hf[ua] : 1.f - hf[ua]) * (dv ? hf[va] : 1.f - hf[va]);
+            float v[8];
+            Store<DT>::load8(b.planes[pl], tb + (int64_t)dv * P + du, v);
+#pragma unroll
+            for (int c = 0; c < 8; c++) pacc[c] = fmaf(w, v[c], pacc[c]);
+        }
+        if (DT == kFP8) {
+#pragma unroll
+            for (int c = 0; c < 8; c++) f[c] = fmaf(pacc[c], __ldg(b.scale + 8 * (pl + 1) + c), f[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; c++) f[c] += pacc[c];
+        }
+    }
+}
+
+// March one ray through one block, updating its state.
+template <int DT>
+__device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3], float ert_eps,
+                                            RayState &s, unsigned *err) {
+    int i0, i1;
+    if (!candidate_range(b, o, d, i0, i1)) return;
+    if (i1 - i0 > kMaxSpan) {
+        atomicOr(err, kErrRange);
+        i1 = i0 + kMaxSpan;
+    }
+    const float delta = b.delta;
+    const int Nc = b.Nc, C = b.C, R = b.R;
+    for (int i = i0; i <= i1; i++) {
+        float p[3];
+        lattice_point(o, d, delta, i, p);
+        if (!inside_block(b, p)) continue;
+        int cell[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            int v = __float2int_rd(axis_coord(p[a], b.lo[a], b.kg[a]));
+            v = min(max(v, 0), R - 2);
+            cell[a] = v / C;
+        }
+        const int ci = (cell[2] * Nc + cell[1]) * Nc + cell[0];
+        if (!((__ldg(b.occ + (ci >> 5)) >> (ci & 31)) & 1u)) continue;
+        float f[8];
+        accumulate_sample<DT>(b, p, f);
+        const float sigma = __expf(f[0]);
+        const float e = __expf(-sigma * delta);
+        const float w = s.T * (1.f - e);
+#pragma unroll
+        for (int c = 0; c < 3; c++) s.Cd[c] = fmaf(w, sigmoidf_fast(f[1 + c]), s.Cd[c]);
+#pragma unroll
+        for (int c = 0; c < 4; c++) s.F[c] = fmaf(w, sigmoidf_fast(f[4 + c]), s.F[c]);
+        s.T *= e;
+        s.nsamp++;
+        if (s.T < ert_eps) {
+            s.done = true;
+            return;
+        }
+    }
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Deferred MLP (Eq. 3) from weights in shared memory.
+__device__ __forceinline__ void deferred_mlp(const float *w, const float x_in[10], bool bf16, float out[3]) {
+    float x[10];
+#pragma unroll
+    for (int i = 0; i < 10; i++) x[i] = bf16 ? bf16r(x_in[i]) : x_in[i];
+    float h1[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        float a = w[kOffB1 + j];
+#pragma unroll
+        for (int i = 0; i < 10; i++) a = fmaf(x[i], w[kOffW1 + i * 16 + j], a);
+        a = fmaxf(a, 0.f);
+        h1[j] = bf16 ? bf16r(a) : a;
+    }
+    float h2[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        float a = w[kOffB2 + j];
+#pragma unroll
+        for (int i = 0; i < 16; i++) a = fmaf(h1[i], w[kOffW2 + i * 16 + j], a);
+        a = fmaxf(a, 0.f);
+        h2[j] = bf16 ? bf16r(a) : a;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        float a = w[kOffB3 + j];
+#pragma unroll
+        for (int i = 0; i < 16; i++) a = fmaf(h2[i], w[kOffW3 + i * 3 + j], a);
+        out[j] = sigmoidf_fast(a);
+    }
+}
+
+__device__ __forceinline__ void load_mlp(const float *g, float *s, bool bf16) {
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
+        const float v = __ldg(g + i);
+        // biases stay FP32 (they add into the FP32 accumulator)
+        const bool is_bias = (i >= kOffB1 && i < kOffW2) || (i >= kOffB2 && i < kOffW3) || i >= kOffB3;
+        s[i] = (bf16 && !is_bias) ? bf16r(v) : v;
+    }
+}
+
+__device__ __forceinline__ void write_outputs(const MarchArgs &a, int64_t row, const RayState &s, const float d[3],
+                                              const float *w_mlp) {
+    float x[10] = {s.Cd[0], s.Cd[1], s.Cd[2], s.F[0], s.F[1], s.F[2], s.F[3], d[0], d[1], d[2]};
+    float o[3];
+    deferred_mlp(w_mlp, x, (a.flags & 1u) != 0, o);
+    float *rgb = a.out_rgb + 3 * row;
+    rgb[0] = s.Cd[0] + o[0];
+    rgb[1] = s.Cd[1] + o[1];
+    rgb[2] = s.Cd[2] + o[2];
+    if (a.out_aux) {
+        float4 *ap = reinterpret_cast<float4 *>(a.out_aux + 8 * row);
+        ap[0] = make_float4(s.Cd[0], s.Cd[1], s.Cd[2], s.F[0]);
+        ap[1] = make_float4(s.F[1], s.F[2], s.F[3], s.T);
+    }
+    if (a.out_nsamp) a.out_nsamp[row] = s.nsamp;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_march_views(MarchArgs a) {
+    __shared__ float s_mlp[kMlpParams + 1];
+    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+    // view of this tile (views are ordered by tile_begin)
+    const int tile = blockIdx.x;
+    int lo = 0, hi = a.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.views[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    const ViewRec &v = a.views[lo];
+    __syncthreads();
+    const int t = tile - v.tile_begin;
+    const int tx = t % v.tiles_x, ty = t / v.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px = tx * kTileW + (warp & 1) * 8 + (lane & 7);
+    const int py = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    if (px >= v.W || py >= v.H) return;
+    float o[3], d[3];
+    pixel_ray(v, px, py, o, d);
+    RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+    const int32_t *ids = a.ids + v.ids_begin;
+    for (int k = 0; k < v.ids_count && !s.done; k++) {
+        const BlockRec &b = a.blocks[__ldg(ids + k)];
+        march_block<DT>(b, o, d, a.ert_eps, s, a.err);
+    }
+    write_outputs(a, v.pix_offset + (int64_t)py * v.W + px, s, d, s_mlp);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads) k_march_rays(MarchArgs a) {
+    __shared__ float s_mlp[kMlpParams + 1];
+    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= a.n_rays) return;
+    float o[3], d[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o[c] = __ldg(a.ray_o + 3 * r + c);
+        d[c] = __ldg(a.ray_d + 3 * r + c);
+    }
+    // per-ray depth order: xy distance of block centres to this origin (App. D)
+    int order[kMaxRayIds];
+    float key[kMaxRayIds];
+    const int n = a.n_ray_ids;
+    for (int i = 0; i < n; i++) {
+        const int id = __ldg(a.ids + i);
+        const BlockRec &b = a.blocks[id];
+        const float dx = __fsub_rn(b.cx, o[0]), dy = __fsub_rn(b.cy, o[1]);
+        const float kk = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        int j = i - 1;
+        while (j >= 0 && (key[j] > kk || (key[j] == kk && order[j] > id))) {
+            key[j + 1] = key[j];
+            order[j + 1] = order[j];
+            j--;
+        }
+        key[j + 1] = kk;
+        order[j + 1] = id;
+    }
+    RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+    for (int k = 0; k < n && !s.done; k++) march_block<DT>(a.blocks[order[k]], o, d, a.ert_eps, s, a.err);
+    write_outputs(a, r, s, d, s_mlp);
+}
+
+}  // namespace
+
+cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, cudaStream_t st) {
+    if (n_tiles <= 0) return cudaSuccess;
+    switch (a.dtype) {
+    case kF32: k_march_views<kF32><<<n_tiles, kThreads, 0, st>>>(a); break;
+    case kF16: k_march_views<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
+    case kBF16: k_march_views<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
+    case kFP8: k_march_views<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st) {
+    if (a.n_rays <= 0) return cudaSuccess;
+    const int64_t nb = (a.n_rays + kThreads - 1) / kThreads;
+    switch (a.dtype) {
+    case kF32: k_march_rays<kF32><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
+    case kF16: k_march_rays<kF16><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
+    case kBF16: k_march_rays<kBF16><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
+    case kFP8: k_march_rays<kFP8><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int march_tile_w() { return kTileW; }
+int march_tile_h() { return kTileH; }
+
+}  // namespace cow

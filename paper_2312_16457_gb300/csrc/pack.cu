@@ -1,0 +1,138 @@
+// pack.cu -- K4 quantize / pack and K5 occupancy build.
+//
+// K4: FP32 master (8 interleaved channels) -> storage format, after
+// multiplying channel c by an exact power of two (the inverse of its scale).
+// Conversions round to nearest even; FP8 E4M3 saturates at +-448.
+// K5: occupancy bit of a cell = any grid vertex of the cell's closed vertex
+// range has ch0 > ln(threshold), compared in double (Sec. 4.5 bakes a binary
+// occupancy grid used for empty-space skipping).
+#include "cow_common.cuh"
+#include "cow_kernels.h"
+
+namespace cow {
+
+namespace {
+
+__global__ void k_amax8(const float *__restrict__ x, int64_t n_vec, unsigned *amax_bits) {
+    float m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vec; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i);
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i + 1);
+        m[0] = fmaxf(m[0], fabsf(a.x)); m[1] = fmaxf(m[1], fabsf(a.y));
+        m[2] = fmaxf(m[2], fabsf(a.z)); m[3] = fmaxf(m[3], fabsf(a.w));
+        m[4] = fmaxf(m[4], fabsf(b.x)); m[5] = fmaxf(m[5], fabsf(b.y));
+        m[6] = fmaxf(m[6], fabsf(b.z)); m[7] = fmaxf(m[7], fabsf(b.w));
+    }
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        float v = m[c];
+        for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+        // non-negative floats order like their bit patterns
+        if ((threadIdx.x & 31) == 0) atomicMax(amax_bits + c, __float_as_uint(v));
+    }
+}
+
+template <int DT>
+__global__ void k_pack(const float *__restrict__ x, int64_t n_vec, const float *__restrict__ inv_scale, void *out) {
+    float s[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) s[c] = inv_scale[c];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vec; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i);
+        const float4 b = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i + 1);
+        float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int c = 0; c < 8; c++) v[c] = __fmul_rn(v[c], s[c]);  // exact: power-of-two factor
+        if (DT == kF32) {
+            float4 *o = reinterpret_cast<float4 *>(out) + 2 * i;
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else if (DT == kF16) {
+            uint4 q;
+            uint32_t *w = &q.x;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+                w[k] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            reinterpret_cast<uint4 *>(out)[i] = q;
+        } else if (DT == kBF16) {
+            uint4 q;
+            uint32_t *w = &q.x;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                w[k] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            reinterpret_cast<uint4 *>(out)[i] = q;
+        } else {
+            uint2 q;
+            uint32_t *w = &q.x;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const __nv_fp8x2_storage_t lo =
+                    __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k], v[4 * k + 1]), __NV_SATFINITE, __NV_E4M3);
+                const __nv_fp8x2_storage_t hi =
+                    __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k + 2], v[4 * k + 3]), __NV_SATFINITE, __NV_E4M3);
+                w[k] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+            reinterpret_cast<uint2 *>(out)[i] = q;
+        }
+    }
+}
+
+__global__ void k_occupancy(const float *__restrict__ grid, int R, int C, int Nc, double lt, uint32_t *bits) {
+    const int64_t ncell = (int64_t)Nc * Nc * Nc;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * blockDim.x) {
+        const int cx = (int)(c % Nc), cy = (int)((c / Nc) % Nc), cz = (int)(c / ((int64_t)Nc * Nc));
+        bool on = false;
+        const int z1 = min(cz * C + C, R - 1), y1 = min(cy * C + C, R - 1), x1 = min(cx * C + C, R - 1);
+        for (int z = cz * C; z <= z1 && !on; z++)
+            for (int y = cy * C; y <= y1 && !on; y++)
+                for (int x = cx * C; x <= x1; x++)
+                    if ((double)__ldg(grid + ((((int64_t)z * R + y) * R + x) << 3)) > lt) {
+                        on = true;
+                        break;
+                    }
+        if (on) atomicOr(bits + (c >> 5), 1u << (c & 31));
+    }
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b > 152 * 64) b = 152 * 64;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(amax_bits, 0, 8 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    k_amax8<<<grid_for(n_vec, 256), 256, 0, st>>>(x, n_vec, amax_bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float *x, int64_t n_vec, int dtype, const float *inv_scale8, void *out,
+                        cudaStream_t st) {
+    const int g = grid_for(n_vec, 256);
+    switch (dtype) {
+    case kF32: k_pack<kF32><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
+    case kF16: k_pack<kF16><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
+    case kBF16: k_pack<kBF16><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
+    case kFP8: k_pack<kFP8><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_occupancy(const float *grid, int R, int C, double log_thresh, uint32_t *bits, cudaStream_t st) {
+    const int Nc = (R - 1 + C - 1) / C;
+    const int64_t ncell = (int64_t)Nc * Nc * Nc;
+    cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)((ncell + 31) / 32) * 4, st);
+    if (e != cudaSuccess) return e;
+    k_occupancy<<<grid_for(ncell, 128), 128, 0, st>>>(grid, R, C, Nc, log_thresh, bits);
+    return cudaGetLastError();
+}
+
+}  // namespace cow

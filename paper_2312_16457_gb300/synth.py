@@ -331,11 +331,13 @@ def workload_city_4x4(R=256, P=1024, device="cpu", width=1280, height=720):
 
 
 def workload_city_lod(res=((256, 1024), (128, 512), (64, 256)), device="cpu", width=1920, height=1080,
-                      lod_thresh=(9.0, 16.0, 0.0)):
+                      lod_thresh=(12.5, 16.5, 0.0)):
     """8x8 LOD-1 blocks of side 2 with 3 LOD levels (64 + 16 + 4 blocks),
-    one 1920x1080 aerial camera that sees every block; scene seed 3, MLP seed 103."""
+    one 1920x1080 aerial camera (altitude 9, oblique) that sees every block;
+    the thresholds keep the near blocks at level 1 and the far ones coarser.
+    Scene seed 3, MLP seed 103."""
     sc = city_scene(3, 8, 2.0, list(res), lod_thresh=list(lod_thresh), device=device)
-    cam = camera((0.0, -17.0, 12.0), (0.0, -1.5, -1.0), width, height, 60.0)
+    cam = camera((0.0, -13.0, 9.0), (0.0, -0.5, -1.0), width, height, 60.0)
     return sc, [cam], mlp_weights(103)
 
 
