@@ -94,7 +94,7 @@ typedef struct cow_ctx cow_ctx;
  *                occupancy grid; here a cell is occupied when any grid vertex
  *                of it has exp(ch0) > occ_thresh, decided on the FP32 master
  *                as (double)ch0 > log((double)occ_thresh)).
- *   occ_cell   : voxels per occupancy-cell edge (>= 1); a block has
+ *   occ_cell   : voxels per occupancy-cell edge (1..4096); a block has
  *                ceil((R-1)/occ_cell)^3 cells; cell c spans vertices
  *                [c*occ_cell, c*occ_cell + occ_cell] along each axis.
  *   stream     : packing kernels run on it; the call synchronises it before

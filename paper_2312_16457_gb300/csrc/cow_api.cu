@@ -112,6 +112,7 @@ struct cow_ctx {
     float occ_thresh = 0.01f;
     std::vector<BlockHost> blocks;
     cow::BlockRec *d_blocks = nullptr;
+    std::vector<cow::BlockRec> recs;  // host copy of d_blocks
     unsigned *d_err = nullptr;
     float *d_mlp = nullptr;
     DevBuf views, ids, out_rgb, out_aux, out_nsamp;
@@ -220,12 +221,19 @@ cow::BlockRec make_rec(const cow_ctx *c, const BlockHost &b) {
         r.kp[a] = (float)((double)(b.P - 1) / ext);
     }
     r.delta = (float)(((double)b.hi[0] - (double)b.lo[0]) / (double)b.P);
+    double bm = 0.0;
+    for (int a = 0; a < 3; a++) {
+        r.vox[a] = (float)(((double)b.hi[a] - (double)b.lo[a]) / (double)(b.R - 1));
+        bm = std::max(bm, std::max(std::fabs((double)b.lo[a]), std::fabs((double)b.hi[a])));
+    }
+    r.bmax = (float)bm;
     r.cx = (float)(0.5 * ((double)b.lo[0] + (double)b.hi[0]));
     r.cy = (float)(0.5 * ((double)b.lo[1] + (double)b.hi[1]));
     r.R = b.R;
     r.P = b.P;
     r.C = c->occ_cell;
     r.Nc = (b.R - 1 + c->occ_cell - 1) / c->occ_cell;
+    r.cdiv = c->occ_cell > 1 ? (uint32_t)((0x100000000ull + (uint64_t)c->occ_cell - 1) / (uint64_t)c->occ_cell) : 0u;
     r.dtype = c->dtype;
     r.grid = b.grid;
     for (int k = 0; k < 3; k++) r.planes[k] = b.planes[k];
@@ -383,7 +391,7 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
     if (!out || !blocks || n < 1) return fail(COW_ERR_INVALID_ARG, "cow_load_blocks: null pointer or n < 1");
     *out = nullptr;
     if ((int)storage < 0 || (int)storage > 3) return fail(COW_ERR_INVALID_ARG, "unknown storage dtype %d", (int)storage);
-    if (occ_cell < 1) return fail(COW_ERR_INVALID_ARG, "occ_cell must be >= 1");
+    if (occ_cell < 1 || occ_cell > 4096) return fail(COW_ERR_INVALID_ARG, "occ_cell must be in [1, 4096]");
     if (!(occ_thresh > 0.0f)) return fail(COW_ERR_INVALID_ARG, "occ_thresh must be > 0");
     size_t max_vec = 0;
     for (int32_t i = 0; i < n; i++) {
@@ -458,7 +466,8 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
     if (rc != COW_OK) return cleanup(rc);
     for (int32_t i = 0; i < n; i++)
         if (blocks[i].parent >= 0) c->blocks[(size_t)blocks[i].parent].children.push_back(i);
-    std::vector<cow::BlockRec> recs((size_t)n);
+    std::vector<cow::BlockRec> &recs = c->recs;
+    recs.resize((size_t)n);
     for (int32_t i = 0; i < n; i++) recs[(size_t)i] = make_rec(c, c->blocks[(size_t)i]);
     e = cudaMalloc((void **)&c->d_blocks, recs.size() * sizeof(cow::BlockRec));
     if (e == cudaSuccess)
@@ -555,12 +564,17 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     cow_status rc = plan_views(ctx, cams, n_views, ids, ids_offsets, plan);
     if (rc != COW_OK) return rc;
     const int32_t n_ids = ids_offsets[n_views];
-    COW_CUDA(ctx->views.reserve(plan.recs.size() * sizeof(cow::ViewRec)));
-    COW_CUDA(ctx->ids.reserve((size_t)std::max(n_ids, 1) * sizeof(int32_t)));
-    COW_CUDA(cudaMemcpyAsync(ctx->views.p, plan.recs.data(), plan.recs.size() * sizeof(cow::ViewRec),
-                             cudaMemcpyHostToDevice, st));
-    if (n_ids > 0)
-        COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    // the views' block records, near to far, contiguous per view: each CTA
+    // stages its view's records with one bulk copy
+    std::vector<cow::BlockRec> vrecs((size_t)std::max(n_ids, 1));
+    for (int32_t k = 0; k < n_ids; k++) vrecs[(size_t)k] = ctx->recs[(size_t)ids[k]];
+    const size_t vbytes = plan.recs.size() * sizeof(cow::ViewRec);
+    const size_t rbytes = vrecs.size() * sizeof(cow::BlockRec);
+    COW_CUDA(ctx->views.reserve(vbytes + rbytes));
+    std::vector<unsigned char> staging(vbytes + rbytes);
+    std::memcpy(staging.data(), plan.recs.data(), vbytes);
+    std::memcpy(staging.data() + vbytes, vrecs.data(), rbytes);
+    COW_CUDA(cudaMemcpyAsync(ctx->views.p, staging.data(), vbytes + rbytes, cudaMemcpyHostToDevice, st));
     const float *d_mlp = nullptr;
     if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
     float *rgb, *aux;
@@ -571,11 +585,10 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     if ((rc = resolve_out(out_nsamp, (size_t)plan.n_pix * 4, ctx->out_nsamp, &ns, &h_ns)) != COW_OK) return rc;
     cow::MarchArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.blocks = ctx->d_blocks;
+    a.recs = (const cow::BlockRec *)((unsigned char *)ctx->views.p + vbytes);
     a.views = (const cow::ViewRec *)ctx->views.p;
     a.n_views = n_views;
     a.dtype = ctx->dtype;
-    a.ids = (const int32_t *)ctx->ids.p;
     a.mlp = d_mlp;
     a.ert_eps = ert_eps;
     a.flags = flags;
@@ -618,7 +631,7 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     if ((rc = resolve_out(out_nsamp, (size_t)n_rays * 4, ctx->out_nsamp, &ns, &h_ns)) != COW_OK) return rc;
     cow::MarchArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.blocks = ctx->d_blocks;
+    a.recs = ctx->d_blocks;
     a.dtype = ctx->dtype;
     a.ids = (const int32_t *)ctx->ids.p;
     a.mlp = d_mlp;

@@ -36,8 +36,11 @@ struct alignas(16) BlockRec {
     float kp[3];             // (float)((P-1) / (hi-lo)) per axis, computed in double
     float delta;             // (float)((hi_x - lo_x) / P), computed in double
     float cx, cy;            // (float)((lo + hi) / 2) in double: ray-batch sort key
+    float vox[3];            // (float)((hi-lo) / (R-1)): voxel pitch per axis
+    float bmax;              // max |coordinate| of the box (scale of FP32 position error)
     int32_t R, P, Nc, C;     // resolutions, occupancy cells per axis, voxels per cell
-    int32_t dtype, pad0;
+    int32_t dtype;
+    uint32_t cdiv;           // ceil(2^32 / C): v / C == umulhi(v, cdiv) for 0 <= v < 2^16, C >= 2
     const void *grid;        // packed R^3 x 8
     const void *planes[3];   // packed P^2 x 8 each (xy, xz, yz)
     const uint32_t *occ;     // occupancy bits
@@ -53,7 +56,7 @@ struct alignas(16) ViewRec {
     int32_t W, H;
     int32_t tiles_x;     // tiles per image row
     int32_t tile_begin;  // first global tile index of this view
-    int32_t ids_begin, ids_count;
+    int32_t ids_begin, ids_count;  // this view's block records: recs[ids_begin .. + ids_count)
     int32_t pad0;
     int64_t pix_offset;  // first output row of this view
 };
@@ -101,8 +104,8 @@ __device__ __forceinline__ float axis_coord(float p, float lo, float k) { return
 
 // Candidate lattice range of a ray in a block: FP32 slab test on the grown
 // box, widened by two indices at each end.  Returns false on a miss.
-__device__ __forceinline__ bool candidate_range(const BlockRec &b, const float o[3], const float d[3], int &i0,
-                                                int &i1) {
+__device__ __forceinline__ bool candidate_range(const BlockRec &b, const float o[3], const float d[3],
+                                                const float inv_d[3], int &i0, int &i1, float &tfar) {
     float tn = 0.f, tf = 3.0e38f;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -110,7 +113,7 @@ __device__ __forceinline__ bool candidate_range(const BlockRec &b, const float o
         if (d[a] == 0.f) {
             if (o[a] < lo || o[a] > hi) return false;
         } else {
-            const float inv = 1.0f / d[a];
+            const float inv = inv_d[a];
             const float t0 = (lo - o[a]) * inv, t1 = (hi - o[a]) * inv;
             tn = fmaxf(tn, fminf(t0, t1));
             tf = fminf(tf, fmaxf(t0, t1));
@@ -122,7 +125,45 @@ __device__ __forceinline__ bool candidate_range(const BlockRec &b, const float o
     const float a1 = ceilf(tf * inv_delta - 0.5f) + 2.f;
     i0 = a0 < 0.f ? 0 : a0 > 2.0e9f ? 2000000000 : (int)a0;
     i1 = a1 > 2.0e9f ? 2000000000 : (int)a1;
+    tfar = tf;
     return i1 >= i0;
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copy global -> shared with an mbarrier, and a bounded wait
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one elected thread: announce `bytes` and start the copy (16-byte aligned, multiple of 16)
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Wait for phase `parity` of the barrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit) {
+    const uint32_t a = smem_addr(bar);
+    for (unsigned it = 0; it < limit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------------------
@@ -131,51 +172,47 @@ __device__ __forceinline__ bool candidate_range(const BlockRec &b, const float o
 template <int DT>
 struct Store;
 
+// Each loader returns the 8 channels as four float2 pairs (c0 c1 | c2 c3 | ...).
 template <>
 struct Store<kF32> {
     using T = float;
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
         const float4 *p = reinterpret_cast<const float4 *>(base) + 2 * idx;
         const float4 a = __ldg(p), b = __ldg(p + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(b.x, b.y);
+        v[3] = make_float2(b.z, b.w);
     }
 };
 
 template <>
 struct Store<kF16> {
     using T = __half;
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
         const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
         const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            __half2 h = *reinterpret_cast<const __half2 *>(&w[k]);
-            float2 f = __half22float2(h);
-            v[2 * k] = f.x;
-            v[2 * k + 1] = f.y;
-        }
+        for (int k = 0; k < 4; k++) v[k] = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
     }
 };
 
 template <>
 struct Store<kBF16> {
     using T = __nv_bfloat16;
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+    // a bfloat16 is the upper half of the float with the same value
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
         const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
         const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            v[2 * k] = __uint_as_float(w[k] << 16);
-            v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
-        }
+        for (int k = 0; k < 4; k++) v[k] = make_float2(__uint_as_float(w[k] << 16), __uint_as_float(w[k] & 0xffff0000u));
     }
 };
 
 template <>
 struct Store<kFP8> {
     using T = __nv_fp8_e4m3;
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float v[8]) {
+    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
         const uint2 q = __ldg(reinterpret_cast<const uint2 *>(base) + idx);
         const uint32_t w[2] = {q.x, q.y};
 #pragma unroll
@@ -184,9 +221,7 @@ struct Store<kFP8> {
             for (int h = 0; h < 2; h++) {
                 const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[k] >> (16 * h)) & 0xffffu);
                 const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
-                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
-                v[4 * k + 2 * h] = f.x;
-                v[4 * k + 2 * h + 1] = f.y;
+                v[2 * k + h] = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
             }
         }
     }

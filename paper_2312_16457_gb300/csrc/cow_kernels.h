@@ -10,11 +10,12 @@ struct BlockRec;
 struct ViewRec;
 
 struct MarchArgs {
-    const BlockRec *blocks;
+    const BlockRec *recs;  // view mode: the views' block records, near to far, by ViewRec::ids_begin;
+                           // ray mode: every block of the context, indexed by ids
     const ViewRec *views;
     int32_t n_views;
     int32_t dtype;
-    const int32_t *ids;    // view mode: CSR by view; ray mode: the blocks to composite
+    const int32_t *ids;    // ray mode: the blocks to composite
     const float *mlp;      // 499 FP32 (device)
     float ert_eps;
     uint32_t flags;

@@ -15,11 +15,18 @@
 #include "cow_common.cuh"
 #include "cow_kernels.h"
 
+#ifndef COW_MARCH_MIN_BLOCKS
+#define COW_MARCH_MIN_BLOCKS 4
+#endif
+
 namespace cow {
 
 namespace {
 
 constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+constexpr int kMinBlocks = COW_MARCH_MIN_BLOCKS;  // CTAs per SM the register budget is sized for
+constexpr int kMaxSmemRecs = 96;                  // block records a CTA stages in shared memory
+constexpr unsigned kWaitPolls = 1u << 24;         // bound on mbarrier polls
 
 struct RayState {
     float Cd[3], F[4], T;
@@ -27,41 +34,44 @@ struct RayState {
     bool done;
 };
 
+// Feature lookup f^{k,l}(p): trilinear grid + bilinear xy, xz, yz planes.
+// g: the FP32 grid coordinate the cell decision computed.  The 8 channels are
+// accumulated as four float2 pairs with packed FP32 FMA (same rounding per
+// element as scalar FMA).
 template <int DT>
-__device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], float f[8]) {
-    // grid: vertex-aligned trilinear; g is the same FP32 coordinate the cell
-    // decision used
+__device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], const float g[3],
+                                                  float2 f[4]) {
     float fr[3];
     int c0[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        float g = axis_coord(p[a], b.lo[a], b.kg[a]);
-        int v = __float2int_rd(g);
-        v = min(max(v, 0), b.R - 2);
-        g = fminf(fmaxf(g, 0.f), (float)(b.R - 1));
+        const int v = min(max(__float2int_rd(g[a]), 0), b.R - 2);
         c0[a] = v;
-        fr[a] = g - (float)v;
+        fr[a] = fminf(fmaxf(g[a], 0.f), (float)(b.R - 1)) - (float)v;
     }
     const int R = b.R;
     const int64_t base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
-    float acc[8];
+    float2 acc[4];
 #pragma unroll
-    for (int c = 0; c < 8; c++) acc[c] = 0.f;
+    for (int c = 0; c < 4; c++) acc[c] = make_float2(0.f, 0.f);
+    const float wx[2] = {1.f - fr[0], fr[0]}, wy[2] = {1.f - fr[1], fr[1]}, wz[2] = {1.f - fr[2], fr[2]};
 #pragma unroll
     for (int k = 0; k < 8; k++) {
         const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-        const float w = (dx ? fr[0] : 1.f - fr[0]) * (dy ? fr[1] : 1.f - fr[1]) * (dz ? fr[2] : 1.f - fr[2]);
-        float v[8];
+        const float w = wx[dx] * wy[dy] * wz[dz];
+        const float2 w2 = make_float2(w, w);
+        float2 v[4];
         Store<DT>::load8(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
 #pragma unroll
-        for (int c = 0; c < 8; c++) acc[c] = fmaf(w, v[c], acc[c]);
+        for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
     }
     if (DT == kFP8) {
 #pragma unroll
-        for (int c = 0; c < 8; c++) f[c] = acc[c] * __ldg(b.scale + c);
+        for (int c = 0; c < 4; c++)
+            f[c] = make_float2(acc[c].x * b.scale[2 * c], acc[c].y * b.scale[2 * c + 1]);
     } else {
 #pragma unroll
-        for (int c = 0; c < 8; c++) f[c] = acc[c];
+        for (int c = 0; c < 4; c++) f[c] = acc[c];
     }
     // planes: vertex-aligned bilinear in (x, y), (x, z), (y, z)
     float hf[3];
@@ -69,8 +79,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         float h = axis_coord(p[a], b.lo[a], b.kp[a]);
-        int u = __float2int_rd(h);
-        u = min(max(u, 0), b.P - 2);
+        const int u = min(max(__float2int_rd(h), 0), b.P - 2);
         h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
         h0[a] = u;
         hf[a] = h - (float)u;
@@ -80,55 +89,86 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
     for (int pl = 0; pl < 3; pl++) {
         const int ua = pl == 2 ? 1 : 0, va = pl == 0 ? 1 : 2;
         const int64_t tb = (int64_t)h0[va] * P + h0[ua];
-        float pacc[8];
+        float2 pacc[4];
 #pragma unroll
-        for (int c = 0; c < 8; c++) pacc[c] = 0.f;
+        for (int c = 0; c < 4; c++) pacc[c] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const int du = q & 1, dv = q >> 1;
             const float w = (du ? hf[ua] : 1.f - hf[ua]) * (dv ? hf[va] : 1.f - hf[va]);
-            float v[8];
+            const float2 w2 = make_float2(w, w);
+            float2 v[4];
             Store<DT>::load8(b.planes[pl], tb + (int64_t)dv * P + du, v);
 #pragma unroll
-            for (int c = 0; c < 8; c++) pacc[c] = fmaf(w, v[c], pacc[c]);
+            for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
         }
         if (DT == kFP8) {
+            const float *sc = b.scale + 8 * (pl + 1);
 #pragma unroll
-            for (int c = 0; c < 8; c++) f[c] = fmaf(pacc[c], __ldg(b.scale + 8 * (pl + 1) + c), f[c]);
+            for (int c = 0; c < 4; c++)
+                f[c] = __ffma2_rn(pacc[c], make_float2(sc[2 * c], sc[2 * c + 1]), f[c]);
         } else {
 #pragma unroll
-            for (int c = 0; c < 8; c++) f[c] += pacc[c];
+            for (int c = 0; c < 4; c++) f[c] = __fadd2_rn(f[c], pacc[c]);
         }
     }
 }
 
 // March one ray through one block, updating its state.
+//
+// Empty cells are left with an exact jump: along each axis the FP32 cell
+// index of successive lattice points is monotone (every step of the decision
+// sequence is monotone), so every lattice point before the ray's exit from
+// the cell -- the cell shrunk by a margin m far above the FP32 position and
+// coordinate error -- decides the same empty cell and would be skipped
+// anyway.  The jump lands one lattice step short of that exit.
 template <int DT>
-__device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3], float ert_eps,
-                                            RayState &s, unsigned *err) {
+__device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3],
+                                            const float inv_d[3], float omax, float ert_eps, RayState &s,
+                                            unsigned *err) {
     int i0, i1;
-    if (!candidate_range(b, o, d, i0, i1)) return;
+    float tfar;
+    if (!candidate_range(b, o, d, inv_d, i0, i1, tfar)) return;
     if (i1 - i0 > kMaxSpan) {
         atomicOr(err, kErrRange);
         i1 = i0 + kMaxSpan;
     }
-    const float delta = b.delta;
+    const float delta = b.delta, inv_delta = 1.0f / b.delta;
+    const float m = 4e-6f * (omax + tfar + b.bmax);
     const int Nc = b.Nc, C = b.C, R = b.R;
     for (int i = i0; i <= i1; i++) {
         float p[3];
         lattice_point(o, d, delta, i, p);
         if (!inside_block(b, p)) continue;
         int cell[3];
+        float g[3];
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            int v = __float2int_rd(axis_coord(p[a], b.lo[a], b.kg[a]));
-            v = min(max(v, 0), R - 2);
-            cell[a] = v / C;
+            g[a] = axis_coord(p[a], b.lo[a], b.kg[a]);
+            const int v = min(max(__float2int_rd(g[a]), 0), R - 2);
+            cell[a] = C == 1 ? v : (int)__umulhi((unsigned)v, b.cdiv);
         }
         const int ci = (cell[2] * Nc + cell[1]) * Nc + cell[0];
-        if (!((__ldg(b.occ + (ci >> 5)) >> (ci & 31)) & 1u)) continue;
-        float f[8];
-        accumulate_sample<DT>(b, p, f);
+        if (!((__ldg(b.occ + (ci >> 5)) >> (ci & 31)) & 1u)) {
+            float tx = 3.0e38f;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (d[a] > 0.f) {
+                    const float chi =
+                        cell[a] == Nc - 1 ? b.hi[a] : fmaf((float)((cell[a] + 1) * C), b.vox[a], b.lo[a]);
+                    tx = fminf(tx, (chi - m - o[a]) * inv_d[a]);
+                } else if (d[a] < 0.f) {
+                    const float clo = fmaf((float)(cell[a] * C), b.vox[a], b.lo[a]);
+                    tx = fminf(tx, (clo + m - o[a]) * inv_d[a]);
+                }
+            }
+            const int j = __float2int_rd(tx * inv_delta - 0.5f) - 1;
+            if (j > i) i = min(j, i1);
+            continue;
+        }
+        float2 f2[4];
+        accumulate_sample<DT>(b, p, g, f2);
+        const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
         const float sigma = __expf(f[0]);
         const float e = __expf(-sigma * delta);
         const float w = s.T * (1.f - e);
@@ -143,6 +183,12 @@ __device__ __forceinline__ void march_block(const BlockRec &b, const float o[3],
             return;
         }
     }
+}
+
+__device__ __forceinline__ void ray_setup(const float d[3], const float o[3], float inv_d[3], float &omax) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) inv_d[a] = d[a] != 0.f ? 1.0f / d[a] : 0.f;
+    omax = fmaxf(fabsf(o[0]), fmaxf(fabsf(o[1]), fabsf(o[2])));
 }
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -206,9 +252,10 @@ __device__ __forceinline__ void write_outputs(const MarchArgs &a, int64_t row, c
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kThreads) k_march_views(MarchArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs a) {
     __shared__ float s_mlp[kMlpParams + 1];
-    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+    __shared__ alignas(16) BlockRec s_rec[kMaxSmemRecs];
+    __shared__ alignas(8) uint64_t s_bar;
     // view of this tile (views are ordered by tile_begin)
     const int tile = blockIdx.x;
     int lo = 0, hi = a.n_views - 1;
@@ -218,26 +265,37 @@ __global__ void __launch_bounds__(kThreads) k_march_views(MarchArgs a) {
         else hi = mid - 1;
     }
     const ViewRec &v = a.views[lo];
+    const int n_blk = v.ids_count;
+    const bool staged = n_blk > 0 && n_blk <= kMaxSmemRecs;
+    if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
+    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
+    // the view's block records (near to far) go to shared memory by one TMA bulk copy
+    if (staged) {
+        if (threadIdx.x == 0)
+            bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
+        if (!mbar_wait(&s_bar, 0, kWaitPolls)) {
+            atomicOr(a.err, kErrTimeout);
+            if (!mbar_wait(&s_bar, 0, kWaitPolls)) return;  // copy still in flight: leave without touching it
+        }
+    }
+    const BlockRec *recs = staged ? s_rec : a.recs + v.ids_begin;
     const int t = tile - v.tile_begin;
     const int tx = t % v.tiles_x, ty = t / v.tiles_x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = tx * kTileW + (warp & 1) * 8 + (lane & 7);
     const int py = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
     if (px >= v.W || py >= v.H) return;
-    float o[3], d[3];
+    float o[3], d[3], inv_d[3], omax;
     pixel_ray(v, px, py, o, d);
+    ray_setup(d, o, inv_d, omax);
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
-    const int32_t *ids = a.ids + v.ids_begin;
-    for (int k = 0; k < v.ids_count && !s.done; k++) {
-        const BlockRec &b = a.blocks[__ldg(ids + k)];
-        march_block<DT>(b, o, d, a.ert_eps, s, a.err);
-    }
+    for (int k = 0; k < n_blk && !s.done; k++) march_block<DT>(recs[k], o, d, inv_d, omax, a.ert_eps, s, a.err);
     write_outputs(a, v.pix_offset + (int64_t)py * v.W + px, s, d, s_mlp);
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kThreads) k_march_rays(MarchArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a) {
     __shared__ float s_mlp[kMlpParams + 1];
     load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
@@ -255,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) k_march_rays(MarchArgs a) {
     const int n = a.n_ray_ids;
     for (int i = 0; i < n; i++) {
         const int id = __ldg(a.ids + i);
-        const BlockRec &b = a.blocks[id];
+        const BlockRec &b = a.recs[id];
         const float dx = __fsub_rn(b.cx, o[0]), dy = __fsub_rn(b.cy, o[1]);
         const float kk = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
         int j = i - 1;
@@ -267,8 +325,11 @@ __global__ void __launch_bounds__(kThreads) k_march_rays(MarchArgs a) {
         key[j + 1] = kk;
         order[j + 1] = id;
     }
+    float inv_d[3], omax;
+    ray_setup(d, o, inv_d, omax);
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
-    for (int k = 0; k < n && !s.done; k++) march_block<DT>(a.blocks[order[k]], o, d, a.ert_eps, s, a.err);
+    for (int k = 0; k < n && !s.done; k++)
+        march_block<DT>(a.recs[order[k]], o, d, inv_d, omax, a.ert_eps, s, a.err);
     write_outputs(a, r, s, d, s_mlp);
 }
 

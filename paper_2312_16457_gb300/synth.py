@@ -324,9 +324,10 @@ def workload_single_block(R=64, P=256, device="cpu", width=128, height=128):
 def workload_city_4x4(R=256, P=1024, device="cpu", width=1280, height=720):
     """4x4 ground blocks of side 2 (scene 8 x 8 x 2), 256^3 grids + 1024^2
     planes; one oblique camera at altitude 6 (3x the scene height), 45 deg
-    pitch; scene seed 2, MLP seed 102."""
+    pitch, 40 deg vertical field of view framing the scene; scene seed 2,
+    MLP seed 102."""
     sc = city_scene(2, 4, 2.0, [(R, P)], device=device)
-    cam = camera((0.0, -7.0, 6.0), (0.0, 0.0, -1.0), width, height, 60.0)
+    cam = camera((0.0, -6.5, 6.0), (0.0, 0.5, -1.0), width, height, 40.0)
     return sc, [cam], mlp_weights(102)
 
 
