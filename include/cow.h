@@ -166,6 +166,19 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);
 
+/* Marching schedule of cow_render; both give the same image up to FP32
+ * rounding (the oracle parity holds for either).
+ *   COW_SCHED_THREAD (default): one ray per thread, a warp on an 8x4 pixel
+ *     patch, so neighbouring rays share cache lines;
+ *   COW_SCHED_WARP: one ray per warp, the 32 lanes on 32 consecutive lattice
+ *     samples of that ray, the in-block weights of Eq. 1 as a prefix product
+ *     across the lanes (measured slower on aerial views: rays of one tile are
+ *     marched one after another, so their texels are fetched again).
+ * Errors: INVALID_ARG for a null context or an unknown schedule. */
+#define COW_SCHED_WARP 0
+#define COW_SCHED_THREAD 1
+cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule);
+
 /* Wait for the stream and report a device-side error word set by a kernel of
  * this context (COW_ERR_DEVICE_ASSERT or COW_ERR_TIMEOUT); clears it. */
 cow_status cow_sync_check(cow_ctx *ctx, void *stream);
@@ -175,9 +188,25 @@ cow_status cow_sync_check(cow_ctx *ctx, void *stream);
 cow_status cow_export_occupancy(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words);
 
 /* Copy out a block's packed tensor (0 = grid, 1..3 = planes xy, xz, yz) in its
- * storage format into host memory, with its 8 per-channel scale exponents. */
+ * storage format into host memory, with its 8 per-channel scale exponents.
+ * The output is in the natural layout (vertex after vertex, nbytes >=
+ * count x 8 x element size).  On the device FP16 / BF16 / FP8 are held in a
+ * pair layout (each element also carries the next vertex of its row, so one
+ * 32- or 16-byte load returns both corners of an interpolation pair): twice
+ * the memory of the natural layout. */
 cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, void *out, int64_t nbytes,
                              int32_t *out_scale_exp);
+
+/* Measurement aid (no counterpart in the paper): the throughput of random
+ * aligned gathers of bytes_per_load (16 or 32) bytes by every thread of a
+ * full-GPU launch from a device buffer of buffer_bytes (a power of two, 1 KiB
+ * to 64 GiB), in useful GB/s -- the access pattern of the marcher's texel
+ * gathers.  A buffer that fits L1 gives the L1 scattered-gather rate, tens of
+ * MB the L2 rate, GBs the HBM rate: the denominators of the marcher's gather
+ * roofline.  Allocates and frees its buffer; synchronises `stream`.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+cow_status cow_gather_peak(int32_t bytes_per_load, int64_t buffer_bytes, int32_t iters, double *out_gbs,
+                           void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *cow_last_error(void);

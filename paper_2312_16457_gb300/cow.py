@@ -23,8 +23,9 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
-           "cow_render", "cow_render_rays", "cow_sync_check", "cow_export_occupancy", "cow_export_packed",
-           "cow_last_error", "cow_version"]
+           "cow_render", "cow_render_rays", "cow_set_schedule", "cow_sync_check", "cow_export_occupancy",
+           "cow_export_packed", "cow_gather_peak", "cow_last_error", "cow_version"]
+SCHEDULES = {"warp": 0, "thread": 1}
 
 
 class CowError(RuntimeError):
@@ -65,8 +66,10 @@ def lib():
             "cow_render": [P, P, i32, P, P, P, flt, u32, P, P, P, P],
             "cow_render_rays": [P, P, P, i64, P, i32, P, flt, u32, P, P, P, P],
             "cow_sync_check": [P, P],
+            "cow_set_schedule": [P, i32],
             "cow_export_occupancy": [P, i32, P, i64],
             "cow_export_packed": [P, i32, i32, P, i64, P],
+            "cow_gather_peak": [i32, i64, i32, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -214,6 +217,11 @@ class Context:
                                      _stream_ptr(stream)))
         return rgb, ax, ns
 
+    def set_schedule(self, name: str):
+        """"warp" (one ray per warp, default) or "thread" (one ray per thread)."""
+        _check(lib().cow_set_schedule(self._ctx, SCHEDULES[name]))
+        self.schedule = name
+
     def sync_check(self, stream=None):
         _check(lib().cow_sync_check(self._ctx, _stream_ptr(stream)))
 
@@ -234,3 +242,11 @@ class Context:
         se = np.zeros(8, np.int32)
         _check(lib().cow_export_packed(self._ctx, int(i), int(tensor), _ptr(out), out.nbytes, _ptr(se)))
         return out, se
+
+
+def gather_peak(bytes_per_load: int, buffer_bytes: int, iters: int = 256, stream=None) -> float:
+    """Random-gather throughput (useful GB/s) of bytes_per_load-byte loads from
+    a buffer of buffer_bytes (see cow_gather_peak)."""
+    v = C.c_double()
+    _check(lib().cow_gather_peak(int(bytes_per_load), int(buffer_bytes), int(iters), C.byref(v), _stream_ptr(stream)))
+    return v.value

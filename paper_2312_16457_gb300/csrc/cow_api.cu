@@ -62,6 +62,9 @@ struct DeviceGuard {
 
 int elem_bytes(int dtype) { return dtype == COW_FP32 ? 4 : dtype == COW_FP8_E4M3 ? 1 : 2; }
 
+// bytes of one packed element (a vertex, or a vertex pair in the pair layout)
+int64_t packed_elem_bytes(int dtype) { return dtype == COW_FP32 ? 32 : 2 * 8 * elem_bytes(dtype); }
+
 // smallest e with amax <= 448 * 2^e (e = 0 for an all-zero channel)
 int fp8_exponent(float amax) {
     if (!(amax > 0.0f)) return 0;
@@ -110,6 +113,7 @@ struct cow_ctx {
     int dtype = 0;
     int occ_cell = 4;
     float occ_thresh = 0.01f;
+    int schedule = COW_SCHED_THREAD;
     std::vector<BlockHost> blocks;
     cow::BlockRec *d_blocks = nullptr;
     std::vector<cow::BlockRec> recs;  // host copy of d_blocks
@@ -158,7 +162,6 @@ double block_ztop(const BlockHost &b, const std::vector<uint32_t> &bits, int C) 
 
 cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *staging, unsigned *d_amax,
                     float *d_inv, double log_thresh, cudaStream_t st) {
-    const int es = elem_bytes(c->dtype);
     const int64_t nv[4] = {(int64_t)d.grid_res * d.grid_res * d.grid_res, (int64_t)d.plane_res * d.plane_res,
                            (int64_t)d.plane_res * d.plane_res, (int64_t)d.plane_res * d.plane_res};
     const float *src[4] = {d.grid, d.planes[0], d.planes[1], d.planes[2]};
@@ -169,7 +172,7 @@ cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *sta
     COW_CUDA(cudaMalloc((void **)&b.scale, 32 * sizeof(float)));
     float scale_h[32];
     for (int t = 0; t < 4; t++) {
-        COW_CUDA(cudaMalloc(dst[t], (size_t)nv[t] * cow::kNch * es));
+        COW_CUDA(cudaMalloc(dst[t], (size_t)(nv[t] * packed_elem_bytes(c->dtype))));
         const float *s = src[t];
         if (!is_device_ptr(s)) {
             COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
@@ -194,7 +197,7 @@ cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *sta
             scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
         }
         COW_CUDA(cudaMemcpyAsync(d_inv, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
-        COW_CUDA(cow::launch_pack(s, nv[t], c->dtype, d_inv, *dst[t], st));
+        COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? d.grid_res : d.plane_res, c->dtype, d_inv, *dst[t], st));
         if (t == 0) COW_CUDA(cow::launch_occupancy(s, d.grid_res, c->occ_cell, log_thresh, b.occ, st));
         // the staging buffer and d_inv are reused by the next tensor: the
         // stream orders the next copies after these kernels
@@ -596,7 +599,8 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     a.out_aux = aux;
     a.out_nsamp = ns;
     a.err = ctx->d_err;
-    COW_CUDA(cow::launch_march_views(a, plan.n_tiles, st));
+    COW_CUDA(cow::launch_march_views(a, plan.n_tiles, ctx->schedule == COW_SCHED_THREAD ? cow::kSchedThread
+                                                                                         : cow::kSchedWarp, st));
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)plan.n_pix * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)plan.n_pix * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)plan.n_pix * 4, cudaMemcpyDeviceToHost, st));
@@ -652,6 +656,14 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     return COW_OK;
 }
 
+cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule) {
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    if (schedule != COW_SCHED_WARP && schedule != COW_SCHED_THREAD)
+        return fail(COW_ERR_INVALID_ARG, "unknown schedule %d", schedule);
+    ctx->schedule = schedule;
+    return COW_OK;
+}
+
 cow_status cow_sync_check(cow_ctx *ctx, void *stream) {
     if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
     DeviceGuard dg(ctx->device);
@@ -687,7 +699,16 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
     const int64_t need = nv * cow::kNch * elem_bytes(ctx->dtype);
     if (nbytes < need) return fail(COW_ERR_INVALID_ARG, "need %lld bytes", (long long)need);
     DeviceGuard dg(ctx->device);
-    COW_CUDA(cudaMemcpy(out, tensor == 0 ? b.grid : b.planes[tensor - 1], (size_t)need, cudaMemcpyDeviceToHost));
+    const void *src = tensor == 0 ? b.grid : b.planes[tensor - 1];
+    if (ctx->dtype == COW_FP32) {
+        COW_CUDA(cudaMemcpy(out, src, (size_t)need, cudaMemcpyDeviceToHost));
+    } else {
+        // pair layout on the device: keep the first vertex of every pair
+        const int64_t pe = packed_elem_bytes(ctx->dtype), ve = pe / 2;
+        std::vector<unsigned char> raw((size_t)(nv * pe));
+        COW_CUDA(cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nv; i++) std::memcpy((unsigned char *)out + i * ve, raw.data() + i * pe, (size_t)ve);
+    }
     if (out_scale_exp)
         for (int k = 0; k < 8; k++) out_scale_exp[k] = b.scale_exp[tensor][k];
     return COW_OK;

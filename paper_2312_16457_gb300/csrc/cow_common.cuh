@@ -169,61 +169,92 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
 // ---------------------------------------------------------------------------
 // storage loads: 8 channels of one vertex / texel as float (unscaled)
 
+// 256-bit non-coherent global load (sm_100+); p must be 32-byte aligned.
+__device__ __forceinline__ void ld256(const void *p, uint32_t r[8]) {
+    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "l"(p));
+}
+
+__device__ __forceinline__ float2 bf16x2_to_float2(uint32_t w) {
+    // a bfloat16 is the upper half of the float with the same value
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+__device__ __forceinline__ float2 f16x2_to_float2(uint32_t w) {
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+
+__device__ __forceinline__ float2 fp8x2_to_float2(uint32_t w16) {
+    const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w16 & 0xffffu), __NV_E4M3);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&hr));
+}
+
+// Storage loaders.  FP32 keeps the natural layout: one 32-byte vertex per
+// 256-bit load.  The 16- and 8-bit formats use the pair layout: element i
+// holds vertex i and vertex i+1 of the same row (x for the grid, u for the
+// planes; the last element of a row repeats its vertex), so one load returns
+// both corners of an interpolation pair.  Channels come as four float2
+// pairs (c0 c1 | c2 c3 | c4 c5 | c6 c7).
 template <int DT>
 struct Store;
 
-// Each loader returns the 8 channels as four float2 pairs (c0 c1 | c2 c3 | ...).
 template <>
 struct Store<kF32> {
-    using T = float;
+    static constexpr bool kPaired = false;
     __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
-        const float4 *p = reinterpret_cast<const float4 *>(base) + 2 * idx;
-        const float4 a = __ldg(p), b = __ldg(p + 1);
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
-        v[2] = make_float2(b.x, b.y);
-        v[3] = make_float2(b.z, b.w);
+        uint32_t r[8];
+        ld256(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
+#pragma unroll
+        for (int k = 0; k < 4; k++) v[k] = make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
     }
+    __device__ __forceinline__ static void load_pair(const void *, int64_t, float2[4], float2[4]) {}
 };
 
 template <>
 struct Store<kF16> {
-    using T = __half;
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    static constexpr bool kPaired = true;
+    __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    __device__ __forceinline__ static void load_pair(const void *base, int64_t idx, float2 lo[4], float2 hi[4]) {
+        uint32_t r[8];
+        ld256(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
 #pragma unroll
-        for (int k = 0; k < 4; k++) v[k] = __half22float2(*reinterpret_cast<const __half2 *>(&w[k]));
+        for (int k = 0; k < 4; k++) {
+            lo[k] = f16x2_to_float2(r[k]);
+            hi[k] = f16x2_to_float2(r[4 + k]);
+        }
     }
 };
 
 template <>
 struct Store<kBF16> {
-    using T = __nv_bfloat16;
-    // a bfloat16 is the upper half of the float with the same value
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
-        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+    static constexpr bool kPaired = true;
+    __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    __device__ __forceinline__ static void load_pair(const void *base, int64_t idx, float2 lo[4], float2 hi[4]) {
+        uint32_t r[8];
+        ld256(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
 #pragma unroll
-        for (int k = 0; k < 4; k++) v[k] = make_float2(__uint_as_float(w[k] << 16), __uint_as_float(w[k] & 0xffff0000u));
+        for (int k = 0; k < 4; k++) {
+            lo[k] = bf16x2_to_float2(r[k]);
+            hi[k] = bf16x2_to_float2(r[4 + k]);
+        }
     }
 };
 
 template <>
 struct Store<kFP8> {
-    using T = __nv_fp8_e4m3;
-    __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
-        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(base) + idx);
-        const uint32_t w[2] = {q.x, q.y};
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[k] >> (16 * h)) & 0xffffu);
-                const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);
-                v[2 * k + h] = __half22float2(*reinterpret_cast<const __half2 *>(&hr));
-            }
-        }
+    static constexpr bool kPaired = true;
+    __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    __device__ __forceinline__ static void load_pair(const void *base, int64_t idx, float2 lo[4], float2 hi[4]) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
+        lo[0] = fp8x2_to_float2(q.x);
+        lo[1] = fp8x2_to_float2(q.x >> 16);
+        lo[2] = fp8x2_to_float2(q.y);
+        lo[3] = fp8x2_to_float2(q.y >> 16);
+        hi[0] = fp8x2_to_float2(q.z);
+        hi[1] = fp8x2_to_float2(q.z >> 16);
+        hi[2] = fp8x2_to_float2(q.w);
+        hi[3] = fp8x2_to_float2(q.w >> 16);
     }
 };
 

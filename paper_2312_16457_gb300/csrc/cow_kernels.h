@@ -29,14 +29,19 @@ struct MarchArgs {
     int32_t n_ray_ids;
 };
 
-cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, cudaStream_t st);
+// marching schedules of the view kernel
+constexpr int kSchedWarp = 0;    // one ray per warp, lanes on consecutive lattice samples
+constexpr int kSchedThread = 1;  // one ray per thread
+cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st);
 cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st);
 int march_tile_w();
 int march_tile_h();
 
 // K4 / K5: packing and occupancy (pack.cu)
 cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cudaStream_t st);
-cudaError_t launch_pack(const float *x, int64_t n_vec, int dtype, const float *inv_scale8, void *out,
+// FP32 packs in the natural layout; FP16 / BF16 / FP8 in the pair layout
+// (element i = vertex i and vertex i+1 of its row of `row` vertices).
+cudaError_t launch_pack(const float *x, int64_t n_vec, int row, int dtype, const float *inv_scale8, void *out,
                         cudaStream_t st);
 cudaError_t launch_occupancy(const float *grid, int R, int C, double log_thresh, uint32_t *bits, cudaStream_t st);
 

@@ -18,6 +18,9 @@
 #ifndef COW_MARCH_MIN_BLOCKS
 #define COW_MARCH_MIN_BLOCKS 4
 #endif
+#ifndef COW_MARCH_MIN_BLOCKS_W
+#define COW_MARCH_MIN_BLOCKS_W 4
+#endif
 
 namespace cow {
 
@@ -25,6 +28,7 @@ namespace {
 
 constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
 constexpr int kMinBlocks = COW_MARCH_MIN_BLOCKS;  // CTAs per SM the register budget is sized for
+constexpr int kMinBlocksW = COW_MARCH_MIN_BLOCKS_W;
 constexpr int kMaxSmemRecs = 96;                  // block records a CTA stages in shared memory
 constexpr unsigned kWaitPolls = 1u << 24;         // bound on mbarrier polls
 
@@ -55,15 +59,29 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[c] = make_float2(0.f, 0.f);
     const float wx[2] = {1.f - fr[0], fr[0]}, wy[2] = {1.f - fr[1], fr[1]}, wz[2] = {1.f - fr[2], fr[2]};
+    if (Store<DT>::kPaired) {
+        // four loads, each the x-pair of one (y, z) edge of the voxel
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-        const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-        const float w = wx[dx] * wy[dy] * wz[dz];
-        const float2 w2 = make_float2(w, w);
-        float2 v[4];
-        Store<DT>::load8(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
+        for (int k = 0; k < 4; k++) {
+            const int dy = k & 1, dz = k >> 1;
+            const float wyz = wy[dy] * wz[dz];
+            const float2 w0 = make_float2(wyz * wx[0], wyz * wx[0]), w1 = make_float2(wyz * wx[1], wyz * wx[1]);
+            float2 lo[4], hi[4];
+            Store<DT>::load_pair(b.grid, base + ((int64_t)dz * R + dy) * R, lo, hi);
 #pragma unroll
-        for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
+            for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], acc[c]));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+            const float w = (wy[dy] * wz[dz]) * wx[dx];
+            const float2 w2 = make_float2(w, w);
+            float2 v[4];
+            Store<DT>::load8(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
+        }
     }
     if (DT == kFP8) {
 #pragma unroll
@@ -89,18 +107,31 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
     for (int pl = 0; pl < 3; pl++) {
         const int ua = pl == 2 ? 1 : 0, va = pl == 0 ? 1 : 2;
         const int64_t tb = (int64_t)h0[va] * P + h0[ua];
+        const float wu[2] = {1.f - hf[ua], hf[ua]}, wv[2] = {1.f - hf[va], hf[va]};
         float2 pacc[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) pacc[c] = make_float2(0.f, 0.f);
+        if (Store<DT>::kPaired) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int du = q & 1, dv = q >> 1;
-            const float w = (du ? hf[ua] : 1.f - hf[ua]) * (dv ? hf[va] : 1.f - hf[va]);
-            const float2 w2 = make_float2(w, w);
-            float2 v[4];
-            Store<DT>::load8(b.planes[pl], tb + (int64_t)dv * P + du, v);
+            for (int dv = 0; dv < 2; dv++) {
+                const float2 w0 = make_float2(wv[dv] * wu[0], wv[dv] * wu[0]);
+                const float2 w1 = make_float2(wv[dv] * wu[1], wv[dv] * wu[1]);
+                float2 lo[4], hi[4];
+                Store<DT>::load_pair(b.planes[pl], tb + (int64_t)dv * P, lo, hi);
 #pragma unroll
-            for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
+                for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], pacc[c]));
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int du = q & 1, dv = q >> 1;
+                const float w = wv[dv] * wu[du];
+                const float2 w2 = make_float2(w, w);
+                float2 v[4];
+                Store<DT>::load8(b.planes[pl], tb + (int64_t)dv * P + du, v);
+#pragma unroll
+                for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
+            }
         }
         if (DT == kFP8) {
             const float *sc = b.scale + 8 * (pl + 1);
@@ -294,6 +325,184 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs 
     write_outputs(a, v.pix_offset + (int64_t)py * v.W + px, s, d, s_mlp);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-per-ray schedule.  A warp marches one ray at a time; lane l takes the
+// lattice sample base + l, so the 32 gathers of one instruction read
+// neighbouring texels of the same ray instead of 32 rays' far-apart texels.
+// The in-block weights of Eq. 1 become an exclusive prefix product of
+// exp(-sigma delta) across the lanes; the transmittance carried across chunks
+// and blocks is Eq. 12-13.  Each lane finally owns one of the warp's 32 rays
+// for the deferred MLP and the output writes.
+
+__device__ __forceinline__ float warp_exclusive_product(float x, int lane, float &total) {
+    float incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl *= y;
+    }
+    total = __shfl_sync(0xffffffffu, incl, 31);
+    const float ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    return lane == 0 ? 1.0f : ex;
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+    return x;
+}
+
+template <int DT>
+__device__ __forceinline__ void march_block_warp(const BlockRec &b, const float o[3], const float d[3],
+                                                 const float inv_d[3], float omax, float ert_eps, int lane,
+                                                 float &T, float pc[3], float pf[4], int &nsamp, bool &done,
+                                                 unsigned *err) {
+    int i0, i1;
+    float tfar;
+    if (!candidate_range(b, o, d, inv_d, i0, i1, tfar)) return;
+    if (i1 - i0 > kMaxSpan) {
+        if (lane == 0) atomicOr(err, kErrRange);
+        i1 = i0 + kMaxSpan;
+    }
+    const float delta = b.delta, inv_delta = 1.0f / b.delta;
+    const float m = 4e-6f * (omax + tfar + b.bmax);
+    const int Nc = b.Nc, C = b.C, R = b.R;
+    for (int base = i0; base <= i1;) {
+        const int i = base + lane;
+        bool inb = false, occ = false;
+        float p[3], g[3];
+        int cell[3] = {0, 0, 0};
+        if (i <= i1) {
+            lattice_point(o, d, delta, i, p);
+            inb = inside_block(b, p);
+            if (inb) {
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    g[a] = axis_coord(p[a], b.lo[a], b.kg[a]);
+                    const int v = min(max(__float2int_rd(g[a]), 0), R - 2);
+                    cell[a] = C == 1 ? v : (int)__umulhi((unsigned)v, b.cdiv);
+                }
+                const int ci = (cell[2] * Nc + cell[1]) * Nc + cell[0];
+                occ = (__ldg(b.occ + (ci >> 5)) >> (ci & 31)) & 1u;
+            }
+        }
+        float e = 1.f, c[7];
+        if (occ) {
+            float2 f2[4];
+            accumulate_sample<DT>(b, p, g, f2);
+            const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
+            e = __expf(-__expf(f[0]) * delta);
+#pragma unroll
+            for (int k = 0; k < 7; k++) c[k] = sigmoidf_fast(f[1 + k]);
+        }
+        float chunk;
+        const float ex = warp_exclusive_product(e, lane, chunk);
+        if (occ) {
+            const float w = (T * ex) * (1.f - e);
+#pragma unroll
+            for (int k = 0; k < 3; k++) pc[k] = fmaf(w, c[k], pc[k]);
+#pragma unroll
+            for (int k = 0; k < 4; k++) pf[k] = fmaf(w, c[3 + k], pf[k]);
+        }
+        T *= chunk;
+        nsamp += __popc(__ballot_sync(0xffffffffu, occ));
+        // next chunk: past lane 31's empty cell when it sits in one (exact, as in the thread schedule)
+        int j = -1;
+        if (lane == 31 && inb && !occ) {
+            float tx = 3.0e38f;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (d[a] > 0.f) {
+                    const float chi =
+                        cell[a] == Nc - 1 ? b.hi[a] : fmaf((float)((cell[a] + 1) * C), b.vox[a], b.lo[a]);
+                    tx = fminf(tx, (chi - m - o[a]) * inv_d[a]);
+                } else if (d[a] < 0.f) {
+                    const float clo = fmaf((float)(cell[a] * C), b.vox[a], b.lo[a]);
+                    tx = fminf(tx, (clo + m - o[a]) * inv_d[a]);
+                }
+            }
+            j = __float2int_rd(tx * inv_delta - 0.5f) - 1;
+        }
+        j = __shfl_sync(0xffffffffu, j, 31);
+        base = max(base + 32, j + 1);
+        if (T < ert_eps) {
+            done = true;
+            return;
+        }
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchArgs a) {
+    __shared__ float s_mlp[kMlpParams + 1];
+    __shared__ alignas(16) BlockRec s_rec[kMaxSmemRecs];
+    __shared__ alignas(8) uint64_t s_bar;
+    const int tile = blockIdx.x;
+    int lo = 0, hi = a.n_views - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.views[mid].tile_begin <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    const ViewRec &v = a.views[lo];
+    const int n_blk = v.ids_count;
+    const bool staged = n_blk > 0 && n_blk <= kMaxSmemRecs;
+    if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
+    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+    __syncthreads();
+    if (staged) {
+        if (threadIdx.x == 0)
+            bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
+        if (!mbar_wait(&s_bar, 0, kWaitPolls)) {
+            atomicOr(a.err, kErrTimeout);
+            if (!mbar_wait(&s_bar, 0, kWaitPolls)) return;
+        }
+    }
+    const BlockRec *recs = staged ? s_rec : a.recs + v.ids_begin;
+    const int t = tile - v.tile_begin;
+    const int tx = t % v.tiles_x, ty = t / v.tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px0 = tx * kTileW + (warp & 1) * 8, py0 = ty * kTileH + (warp >> 1) * 4;
+    // this lane's own ray (it writes its outputs at the end)
+    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
+    const bool mine_valid = px < v.W && py < v.H;
+    float mo[3], md[3];
+    pixel_ray(v, min(px, v.W - 1), min(py, v.H - 1), mo, md);
+    float my_acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 1.f};
+    int my_n = 0;
+    for (int q = 0; q < 32; q++) {
+        const int qx = px0 + (q & 7), qy = py0 + (q >> 3);
+        if (qx >= v.W || qy >= v.H) continue;  // uniform across the warp
+        float o[3], d[3], inv_d[3], omax;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            o[k] = __shfl_sync(0xffffffffu, mo[k], q);
+            d[k] = __shfl_sync(0xffffffffu, md[k], q);
+        }
+        ray_setup(d, o, inv_d, omax);
+        float T = 1.f, pc[3] = {0.f, 0.f, 0.f}, pf[4] = {0.f, 0.f, 0.f, 0.f};
+        int nsamp = 0;
+        bool done = false;
+        for (int k = 0; k < n_blk && !done; k++)
+            march_block_warp<DT>(recs[k], o, d, inv_d, omax, a.ert_eps, lane, T, pc, pf, nsamp, done, a.err);
+        float tot[7];
+#pragma unroll
+        for (int k = 0; k < 3; k++) tot[k] = warp_sum(pc[k]);
+#pragma unroll
+        for (int k = 0; k < 4; k++) tot[3 + k] = warp_sum(pf[k]);
+        if (lane == q) {
+#pragma unroll
+            for (int k = 0; k < 7; k++) my_acc[k] = tot[k];
+            my_acc[7] = T;
+            my_n = nsamp;
+        }
+    }
+    if (!mine_valid) return;
+    RayState s = {{my_acc[0], my_acc[1], my_acc[2]}, {my_acc[3], my_acc[4], my_acc[5], my_acc[6]}, my_acc[7], my_n,
+                  false};
+    write_outputs(a, v.pix_offset + (int64_t)py * v.W + px, s, md, s_mlp);
+}
+
 template <int DT>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a) {
     __shared__ float s_mlp[kMlpParams + 1];
@@ -335,14 +544,24 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a
 
 }  // namespace
 
-cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, cudaStream_t st) {
+cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    switch (a.dtype) {
-    case kF32: k_march_views<kF32><<<n_tiles, kThreads, 0, st>>>(a); break;
-    case kF16: k_march_views<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
-    case kBF16: k_march_views<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
-    case kFP8: k_march_views<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
-    default: return cudaErrorInvalidValue;
+    if (schedule == kSchedThread) {
+        switch (a.dtype) {
+        case kF32: k_march_views<kF32><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kF16: k_march_views<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kBF16: k_march_views<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kFP8: k_march_views<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (a.dtype) {
+        case kF32: k_march_views_w<kF32><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kF16: k_march_views_w<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kBF16: k_march_views_w<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kFP8: k_march_views_w<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
     }
     return cudaGetLastError();
 }

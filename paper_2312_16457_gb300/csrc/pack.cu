@@ -32,51 +32,71 @@ __global__ void k_amax8(const float *__restrict__ x, int64_t n_vec, unsigned *am
     }
 }
 
+// Encode one 8-channel vector (already scaled) into its storage bytes.
 template <int DT>
-__global__ void k_pack(const float *__restrict__ x, int64_t n_vec, const float *__restrict__ inv_scale, void *out) {
+__device__ __forceinline__ void encode8(const float v[8], uint32_t w[4]) {
+    if (DT == kF16) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
+            w[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+    } else if (DT == kBF16) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+            w[k] = *reinterpret_cast<uint32_t *>(&h);
+        }
+    } else if (DT == kFP8) {
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+            const __nv_fp8x2_storage_t lo =
+                __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k], v[4 * k + 1]), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi =
+                __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k + 2], v[4 * k + 3]), __NV_SATFINITE, __NV_E4M3);
+            w[k] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        w[2] = w[3] = 0u;
+    }
+}
+
+__device__ __forceinline__ void load_scaled(const float *x, int64_t i, const float s[8], float v[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i);
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i + 1);
+    const float r[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int c = 0; c < 8; c++) v[c] = __fmul_rn(r[c], s[c]);  // exact: power-of-two factor
+}
+
+// FP32: natural layout.  FP16 / BF16 / FP8: pair layout, element i = (vertex
+// i, vertex i+1) along rows of `row` vertices (the last of a row repeats).
+template <int DT>
+__global__ void k_pack(const float *__restrict__ x, int64_t n_vec, int row, const float *__restrict__ inv_scale,
+                       void *out) {
     float s[8];
 #pragma unroll
     for (int c = 0; c < 8; c++) s[c] = inv_scale[c];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_vec; i += (int64_t)gridDim.x * blockDim.x) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i);
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(x) + 2 * i + 1);
-        float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int c = 0; c < 8; c++) v[c] = __fmul_rn(v[c], s[c]);  // exact: power-of-two factor
+        float v[8];
+        load_scaled(x, i, s, v);
         if (DT == kF32) {
             float4 *o = reinterpret_cast<float4 *>(out) + 2 * i;
             o[0] = make_float4(v[0], v[1], v[2], v[3]);
             o[1] = make_float4(v[4], v[5], v[6], v[7]);
-        } else if (DT == kF16) {
-            uint4 q;
-            uint32_t *w = &q.x;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                __half2 h = __floats2half2_rn(v[2 * k], v[2 * k + 1]);
-                w[k] = *reinterpret_cast<uint32_t *>(&h);
-            }
-            reinterpret_cast<uint4 *>(out)[i] = q;
-        } else if (DT == kBF16) {
-            uint4 q;
-            uint32_t *w = &q.x;
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-                w[k] = *reinterpret_cast<uint32_t *>(&h);
-            }
-            reinterpret_cast<uint4 *>(out)[i] = q;
+            continue;
+        }
+        const int64_t j = (i % row) == row - 1 ? i : i + 1;
+        float vn[8];
+        load_scaled(x, j, s, vn);
+        uint32_t a[4], b[4];
+        encode8<DT>(v, a);
+        encode8<DT>(vn, b);
+        if (DT == kFP8) {
+            reinterpret_cast<uint4 *>(out)[i] = make_uint4(a[0], a[1], b[0], b[1]);
         } else {
-            uint2 q;
-            uint32_t *w = &q.x;
-#pragma unroll
-            for (int k = 0; k < 2; k++) {
-                const __nv_fp8x2_storage_t lo =
-                    __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k], v[4 * k + 1]), __NV_SATFINITE, __NV_E4M3);
-                const __nv_fp8x2_storage_t hi =
-                    __nv_cvt_float2_to_fp8x2(make_float2(v[4 * k + 2], v[4 * k + 3]), __NV_SATFINITE, __NV_E4M3);
-                w[k] = (uint32_t)lo | ((uint32_t)hi << 16);
-            }
-            reinterpret_cast<uint2 *>(out)[i] = q;
+            uint4 *o = reinterpret_cast<uint4 *>(out) + 2 * i;
+            o[0] = make_uint4(a[0], a[1], a[2], a[3]);
+            o[1] = make_uint4(b[0], b[1], b[2], b[3]);
         }
     }
 }
@@ -113,14 +133,14 @@ cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(const float *x, int64_t n_vec, int dtype, const float *inv_scale8, void *out,
+cudaError_t launch_pack(const float *x, int64_t n_vec, int row, int dtype, const float *inv_scale8, void *out,
                         cudaStream_t st) {
     const int g = grid_for(n_vec, 256);
     switch (dtype) {
-    case kF32: k_pack<kF32><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
-    case kF16: k_pack<kF16><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
-    case kBF16: k_pack<kBF16><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
-    case kFP8: k_pack<kFP8><<<g, 256, 0, st>>>(x, n_vec, inv_scale8, out); break;
+    case kF32: k_pack<kF32><<<g, 256, 0, st>>>(x, n_vec, row, inv_scale8, out); break;
+    case kF16: k_pack<kF16><<<g, 256, 0, st>>>(x, n_vec, row, inv_scale8, out); break;
+    case kBF16: k_pack<kBF16><<<g, 256, 0, st>>>(x, n_vec, row, inv_scale8, out); break;
+    case kFP8: k_pack<kFP8><<<g, 256, 0, st>>>(x, n_vec, row, inv_scale8, out); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

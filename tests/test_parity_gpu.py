@@ -72,10 +72,12 @@ def test_packed_bits_exact(dtype):
             assert np.array_equal(got.view(want.dtype), want), (i, t)
 
 
-def test_single_block_fp32_full_size():
+@pytest.mark.parametrize("schedule", ["warp", "thread"])
+def test_single_block_fp32_full_size(schedule):
     """64^3 grid + 256^2 planes, one 128x128 camera (the paper-scale single block)."""
     sc, cams, mlp = synth.workload_single_block(device="cuda")
     ctx = cow.Context(sc, "fp32")
+    ctx.set_schedule(schedule)
     rgb, aux, ns = _render(ctx, cams, [[0]], mlp)
     osc = oracle.OracleScene(sc)
     r_o, a_o, n_o = _oracle_view(osc, cams[0], [0], mlp)
@@ -89,11 +91,13 @@ def test_single_block_fp32_full_size():
     assert ns_e.sum() < ns.sum()
 
 
-def test_city_fp16_storage():
+@pytest.mark.parametrize("schedule", ["warp", "thread"])
+def test_city_fp16_storage(schedule):
     """4x4 ground blocks with blobs crossing borders, FP16 storage, FP32 math:
     parity against the oracle on the same FP16 values."""
     sc, cams, mlp = synth.workload_city_4x4(R=48, P=160, width=200, height=120)
     ctx = cow.Context(sc, "fp16")
+    ctx.set_schedule(schedule)
     order = ctx.sort_blocks(cams[0], list(range(len(sc.blocks))))
     rgb, aux, ns = _render(ctx, cams, [order], mlp)
     osc = oracle.OracleScene(sc, values="fp16")
@@ -219,9 +223,11 @@ def _c2w_down(x, y, z):
     return c2w
 
 
-def test_edge_cases():
+@pytest.mark.parametrize("schedule", ["warp", "thread"])
+def test_edge_cases(schedule):
     sc, _, mlp = synth.workload_city_4x4(R=16, P=32)
     ctx = cow.Context(sc, "fp32")
+    ctx.set_schedule(schedule)
     osc = oracle.OracleScene(sc)
     cams = [synth.Camera(_c2w_down(0.0, 0.0, 5.0), 9, 7, 40.0),     # axis-aligned centre ray, block corner
             synth.Camera(_c2w_down(-1.0, 1.0, 0.2), 1, 1, 30.0),    # 1x1 image, camera inside a block
@@ -260,3 +266,14 @@ def test_full_size_city_sampled():
     assert np.abs(rgb[pix] - r_o).max() <= TOL
     assert np.abs(aux[pix, :7] - a_o[:, :7]).max() <= TOL
     assert (n_o > 0).mean() > 0.5
+
+
+def test_gather_peak_probe():
+    """The roofline denominator: random-gather rates order as L1 > L2 > HBM."""
+    l1 = cow.gather_peak(32, 64 << 10)
+    l2 = cow.gather_peak(32, 32 << 20)
+    hb = cow.gather_peak(32, 4 << 30, iters=32)
+    assert l1 > l2 > hb > 100.0
+    assert cow.gather_peak(16, 64 << 10) > 100.0
+    with pytest.raises(cow.CowError):
+        cow.gather_peak(24, 64 << 10)
