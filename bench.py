@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["cow", "reference"], default="cow")
-    ap.add_argument("--workload", choices=["city_lod_1080p", "city_4x4_720p", "single_block_128"],
+    ap.add_argument("--workload", choices=["city_lod_1080p", "city_4x4_720p", "single_block_128", "fit_2x2"],
                     default="city_lod_1080p")
     ap.add_argument("--storage", default=None, help="override the storage dtype")
     ap.add_argument("--ert", type=float, default=1e-5, help="early ray termination threshold")
@@ -344,6 +344,54 @@ def run_cow(args, ws, rank, local):
     ctx.close()
 
 
+def run_fit(args, ws, rank, local):
+    """Differentiation form: 2x2 blocks of FP32 parameters (128^3 grid + 512^2
+    planes), 2^20 random rays, MSE against the render of a second seed's
+    scene; one step = forward + MSE gradient + backward + Adam + re-pack."""
+    from paper_2312_16457_gb300 import build, cow, synth, train
+
+    build.build()
+    dev = torch.device("cuda", local)
+    R, P = 128 // args.res_div, 512 // args.res_div
+    sc, tgt, o, d, mlp, mlp_t = synth.workload_grad(R=R, P=P, device=dev)
+    tctx = cow.Context(tgt, "fp32")
+    target = tctx.render_rays(o, d, [0, 1, 2, 3], mlp_t, aux=False)[0]
+    tctx.close()
+    fit = train.Fitter(sc, mlp)
+    stream = torch.cuda.current_stream()
+
+    def psnr_now():
+        rgb = fit.render(o, d)
+        mse = float(((rgb - target) ** 2).mean().item())
+        return 10 * math.log10(1.0 / mse)
+
+    p0 = psnr_now()
+    for _ in range(args.warmup):
+        fit.step(o, d, target)
+    clocks = Clocks(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        fit.step(o, d, target)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    fit.ctx.sync_check()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    p1 = psnr_now()
+    n = o.shape[0]
+    line = {"metric": "differentiation form: training rays/s (forward + backward + Adam)", "value": round(n / ms / 1e3, 3),
+            "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "fit_2x2", "scene": f"2x2 blocks, {R}^3 grid + {P}^2 planes, FP32 parameters",
+                       "rays": n, "adam_steps": args.warmup + args.steps, "lr_features": fit.lr_feat,
+                       "lr_mlp": fit.lr_mlp},
+            "fit_psnr_db": {"before": round(p0, 2), "after": round(p1, 2)}, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, ws, rank, local):
     if rank != 0:
         return
@@ -398,7 +446,9 @@ def run_reference(args, ws, rank, local):
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.workload == "fit_2x2":
+        run_fit(args, ws, rank, local)
+    elif args.impl == "reference":
         run_reference(args, ws, rank, local)
     else:
         run_cow(args, ws, rank, local)

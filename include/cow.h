@@ -166,6 +166,46 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);
 
+/* Gradients of the ray-batch render (differentiation form): the analytic
+ * adjoint of cow_render_rays with respect to every grid and plane feature and
+ * every deferred-MLP parameter, given dL/dC per ray.  Each ray is marched
+ * again over exactly the forward's samples (occupancy held fixed); the
+ * contribution of the samples behind a sample is the forward's saved total
+ * (out_aux) minus the running prefix, so nothing per sample is stored.
+ *   o, d, ids, n_ids, mlp, ert_eps : as the forward call (device o, d, mlp);
+ *   aux       : the forward's out_aux (device, n_rays x 8, 16-byte aligned);
+ *   dL_drgb   : device float32 n_rays x 3;
+ *   grad_grid : host array of n_blocks device pointers, R^3 x 8 FP32 each in
+ *               the natural layout (NULL entries: no gradient for that block);
+ *   grad_planes : host array of 3 x n_blocks device pointers, P^2 x 8 FP32;
+ *   grad_mlp  : device float32 499.
+ * All gradients are ACCUMULATED (+=); the caller zeroes them.  Gradients are
+ * with respect to the feature values the lookup reads (the dequantised
+ * values for FP16 / BF16 / FP8 storage).  Feature gradients use float
+ * atomics (summation order varies between runs); the MLP gradient is summed
+ * in a fixed order through per-CTA rows the context allocates.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                               int32_t n_ids, const float *mlp, float ert_eps, const float *aux, const float *dL_drgb,
+                               float *const *grad_grid, float *const *grad_planes, float *grad_mlp, void *stream);
+
+/* Re-pack block `block`'s features from new FP32 masters (same layouts as
+ * cow_block_desc; host or device, 16-byte aligned) into the context's
+ * storage format; occupancy and z_top stay as loaded (the differentiation
+ * form holds them fixed while the features are optimised). */
+cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, const float *plane_xy,
+                               const float *plane_xz, const float *plane_yz, void *stream);
+
+/* One Adam step on n FP32 parameters (device arrays param, grad, m, v):
+ *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
+ *   param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+cow_status cow_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
+                         float beta2, float eps, int32_t step, void *stream);
+
+/* Mean squared error of n values (device): dL_drgb = 2 (rgb - target) / n and,
+ * when loss is not NULL, *loss (device float) = mean (rgb - target)^2. */
+cow_status cow_mse_grad(const float *rgb, const float *target, int64_t n, float *dL_drgb, float *loss, void *stream);
+
 /* Marching schedule of cow_render; both give the same image up to FP32
  * rounding (the oracle parity holds for either).
  *   COW_SCHED_THREAD (default): one ray per thread, a warp on an 8x4 pixel

@@ -24,7 +24,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_set_schedule", "cow_sync_check", "cow_export_occupancy",
-           "cow_export_packed", "cow_gather_peak", "cow_last_error", "cow_version"]
+           "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_update_features", "cow_adam_step",
+           "cow_mse_grad", "cow_last_error", "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1}
 
 
@@ -70,6 +71,10 @@ def lib():
             "cow_export_occupancy": [P, i32, P, i64],
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
+            "cow_render_backward": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
+            "cow_update_features": [P, i32, P, P, P, P, P],
+            "cow_adam_step": [P, P, P, P, i64, flt, flt, flt, flt, i32, P],
+            "cow_mse_grad": [P, P, i64, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -217,6 +222,30 @@ class Context:
                                      _stream_ptr(stream)))
         return rgb, ax, ns
 
+    def render_backward(self, o, d, ids, mlp, aux, dL_drgb, grad_grids, grad_planes, grad_mlp,
+                        ert_eps: float = 0.0, stream=None):
+        """Accumulate dL/d(features, MLP) of a ray batch into the given FP32
+        device tensors (grad_grids[i]: R^3 x 8, grad_planes[i][k]: P^2 x 8,
+        grad_mlp: 499; None skips a block)."""
+        a = np.ascontiguousarray(ids, np.int32)
+        nb = self.n_blocks
+        gg = (C.c_void_p * nb)(*[_ptr(g) if g is not None else None for g in grad_grids])
+        flat = []
+        for i in range(nb):
+            pl = grad_planes[i] if grad_planes[i] is not None else [None, None, None]
+            flat += [_ptr(t) if t is not None else None for t in pl]
+        gp = (C.c_void_p * (3 * nb))(*flat)
+        _check(lib().cow_render_backward(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a),
+                                         len(a), _ptr(mlp), float(ert_eps), _ptr(aux), _ptr(dL_drgb.contiguous()),
+                                         gg, gp, _ptr(grad_mlp), _stream_ptr(stream)))
+
+    def update_features(self, i: int, grid, planes, stream=None):
+        """Re-pack block i's features from new FP32 arrays (occupancy kept)."""
+        g = _as_f32(grid)
+        pls = [_as_f32(p) for p in planes]
+        _check(lib().cow_update_features(self._ctx, int(i), _ptr(g), _ptr(pls[0]), _ptr(pls[1]), _ptr(pls[2]),
+                                         _stream_ptr(stream)))
+
     def set_schedule(self, name: str):
         """"warp" (one ray per warp, default) or "thread" (one ray per thread)."""
         _check(lib().cow_set_schedule(self._ctx, SCHEDULES[name]))
@@ -250,3 +279,20 @@ def gather_peak(bytes_per_load: int, buffer_bytes: int, iters: int = 256, stream
     v = C.c_double()
     _check(lib().cow_gather_peak(int(bytes_per_load), int(buffer_bytes), int(iters), C.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+    """In-place Adam update of an FP32 device tensor (cow_adam_step)."""
+    _check(lib().cow_adam_step(_ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(), float(lr), float(beta1),
+                               float(beta2), float(eps), int(step), _stream_ptr(stream)))
+
+
+def mse_grad(rgb: torch.Tensor, target: torch.Tensor, stream=None):
+    """(dL/drgb, loss) of the mean squared error (cow_mse_grad); loss is a
+    1-element device tensor."""
+    g = torch.empty_like(rgb)
+    loss = torch.empty(1, dtype=torch.float32, device=rgb.device)
+    _check(lib().cow_mse_grad(_ptr(rgb.contiguous()), _ptr(target.contiguous()), rgb.numel(), _ptr(g), _ptr(loss),
+                              _stream_ptr(stream)))
+    return g, loss

@@ -1,0 +1,326 @@
+// bwd.cu -- K6 / K7: gradients of the rendered colour with respect to every
+// grid, plane and deferred-MLP parameter, for the ray-batch form.
+//
+// Per ray (one thread), given g = dL/dC:
+//   K7  recompute the deferred MLP (Eq. 3) from the forward's saved C_d, F and
+//       back-propagate it: dL/dC_d = g + dPhi/dC_d^T g, dL/dF, and the ray's
+//       contribution to dL/dW (outer products kept in shared memory).
+//   K6  re-march the ray over exactly the forward's samples (same sequence
+//       code) with the transmittance T and the running prefix sums P_C, P_F;
+//       the contribution of the samples after i is the saved total minus the
+//       prefix, so no sample is stored.  With e = 1 - alpha = exp(-sigma delta)
+//       and the weights of Eq. 1 (w_i = T_i alpha_i):
+//         dL/dc_i  = w_i gC,   dL/ds_i = w_i gF
+//         dL/dalpha_i = T_i (gC.c_i + gF.s_i) - (gC.S_C + gF.S_F) / e_i
+//         dL/df0  = dL/dalpha_i * sigma delta e_i
+//                 = sigma delta (T_i e_i (gC.c_i + gF.s_i) - (gC.S_C + gF.S_F))
+//       (no division), then dL/df = dL/df0, c(1-c) dL/dc, s(1-s) dL/ds is
+//       scattered with the interpolation weights to the 8 grid vertices and
+//       12 plane texels (float4 atomics into FP32 gradient arrays in the
+//       natural layout).
+// The CTA's MLP weight gradient (499 sums over its 128 rays) goes to a
+// per-CTA scratch row; a second kernel adds the rows in a fixed order, so the
+// MLP gradient does not depend on scheduling.
+#include "cow_common.cuh"
+#include "cow_kernels.h"
+#include "march_core.cuh"
+
+namespace cow {
+
+namespace {
+
+constexpr int kBwdThreads = 128;
+constexpr int kVec = 77;  // x (10), dz1 (16), h1 (16), dz2 (16), h2 (16), dz3 (3)
+
+__device__ __forceinline__ void red_add8(float *dst, float s, const float gf[8]) {
+    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(s * gf[0], s * gf[1], s * gf[2], s * gf[3]));
+    atomicAdd(reinterpret_cast<float4 *>(dst) + 1, make_float4(s * gf[4], s * gf[5], s * gf[6], s * gf[7]));
+}
+
+// Scatter an 8-channel feature gradient to the taps of the lookup at (p, g).
+__device__ __forceinline__ void scatter_taps(const BlockRec &b, float *gg, float *const gp[3], const float p[3],
+                                             const float g[3], const float gf[8]) {
+    float fr[3];
+    int c0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int v = min(max(__float2int_rd(g[a]), 0), b.R - 2);
+        c0[a] = v;
+        fr[a] = fminf(fmaxf(g[a], 0.f), (float)(b.R - 1)) - (float)v;
+    }
+    const int64_t R = b.R;
+    const int64_t base = (c0[2] * R + c0[1]) * R + c0[0];
+    const float wx[2] = {1.f - fr[0], fr[0]}, wy[2] = {1.f - fr[1], fr[1]}, wz[2] = {1.f - fr[2], fr[2]};
+    if (gg) {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+            red_add8(gg + 8 * (base + (dz * R + dy) * R + dx), (wy[dy] * wz[dz]) * wx[dx], gf);
+        }
+    }
+    float hf[3];
+    int h0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        const int u = min(max(__float2int_rd(h), 0), b.P - 2);
+        h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
+        h0[a] = u;
+        hf[a] = h - (float)u;
+    }
+    const int64_t P = b.P;
+#pragma unroll
+    for (int pl = 0; pl < 3; pl++) {
+        if (!gp[pl]) continue;
+        const int ua = pl == 2 ? 1 : 0, va = pl == 0 ? 1 : 2;
+        const int64_t tb = (int64_t)h0[va] * P + h0[ua];
+        const float wu[2] = {1.f - hf[ua], hf[ua]}, wv[2] = {1.f - hf[va], hf[va]};
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int du = q & 1, dv = q >> 1;
+            red_add8(gp[pl] + 8 * (tb + dv * P + du), wv[dv] * wu[du], gf);
+        }
+    }
+}
+
+// K7: deferred-MLP backward per ray; writes (dL/dC_d, dL/dF) of the ray to
+// a.gcf (8 floats per ray) and the CTA's 499 weight-gradient sums to its row.
+__global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(BwdArgs a) {
+    __shared__ float s_w[kMlpParams + 1];
+    __shared__ float s_vec[kBwdThreads][kVec];
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) s_w[i] = __ldg(a.mlp + i);
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    float *vec = s_vec[threadIdx.x];
+    if (r >= a.n_rays) {
+        for (int k = 0; k < kVec; k++) vec[k] = 0.f;
+    } else {
+        const float *w = s_w;
+        float x[10], gC[3], gF[4];
+#pragma unroll
+        for (int c = 0; c < 7; c++) x[c] = __ldg(a.aux + 8 * r + c);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            x[7 + c] = __ldg(a.ray_d + 3 * r + c);
+            gC[c] = __ldg(a.dL_drgb + 3 * r + c);
+        }
+        float dz3[3];
+#pragma unroll 1
+        for (int j = 0; j < 16; j++) {
+            float s = w[kOffB1 + j];
+#pragma unroll
+            for (int i = 0; i < 10; i++) s = fmaf(x[i], w[kOffW1 + i * 16 + j], s);
+            vec[26 + j] = fmaxf(s, 0.f);  // h1
+        }
+#pragma unroll 1
+        for (int j = 0; j < 16; j++) {
+            float s = w[kOffB2 + j];
+#pragma unroll
+            for (int i = 0; i < 16; i++) s = fmaf(vec[26 + i], w[kOffW2 + i * 16 + j], s);
+            vec[58 + j] = fmaxf(s, 0.f);  // h2
+        }
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            float s = w[kOffB3 + j];
+#pragma unroll
+            for (int i = 0; i < 16; i++) s = fmaf(vec[58 + i], w[kOffW3 + i * 3 + j], s);
+            const float sg = 1.f / (1.f + expf(-s));
+            dz3[j] = gC[j] * sg * (1.f - sg);
+            vec[74 + j] = dz3[j];
+        }
+#pragma unroll 1
+        for (int i = 0; i < 16; i++) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 3; j++) s = fmaf(w[kOffW3 + i * 3 + j], dz3[j], s);
+            vec[42 + i] = vec[58 + i] > 0.f ? s : 0.f;  // dz2 (h2 > 0 iff z2 > 0)
+        }
+#pragma unroll 1
+        for (int i = 0; i < 16; i++) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; j++) s = fmaf(w[kOffW2 + i * 16 + j], vec[42 + j], s);
+            vec[10 + i] = vec[26 + i] > 0.f ? s : 0.f;  // dz1 (h1 > 0 iff z1 > 0)
+        }
+#pragma unroll 1
+        for (int i = 0; i < 7; i++) {
+            float s = 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; j++) s = fmaf(w[kOffW1 + i * 16 + j], vec[10 + j], s);
+            if (i < 3) gC[i] += s;
+            else gF[i - 3] = s;
+        }
+#pragma unroll
+        for (int k = 0; k < 10; k++) vec[k] = x[k];
+        float4 *out = reinterpret_cast<float4 *>(a.gcf + 8 * r);
+        out[0] = make_float4(gC[0], gC[1], gC[2], gF[0]);
+        out[1] = make_float4(gF[1], gF[2], gF[3], 0.f);
+    }
+    __syncthreads();
+    // MLP weight gradient of this CTA's rays -> its scratch row
+    float *row = a.partials + (int64_t)blockIdx.x * kMlpParams;
+    for (int t = threadIdx.x; t < kMlpParams; t += blockDim.x) {
+        int ia, ib;  // vec offsets of the two factors; ia < 0: bias (single factor)
+        if (t < kOffB1) { ia = t / 16; ib = 10 + t % 16; }
+        else if (t < kOffW2) { ia = -1; ib = 10 + (t - kOffB1); }
+        else if (t < kOffB2) { ia = 26 + (t - kOffW2) / 16; ib = 42 + (t - kOffW2) % 16; }
+        else if (t < kOffW3) { ia = -1; ib = 42 + (t - kOffB2); }
+        else if (t < kOffB3) { ia = 58 + (t - kOffW3) / 3; ib = 74 + (t - kOffW3) % 3; }
+        else { ia = -1; ib = 74 + (t - kOffB3); }
+        float s = 0.f;
+        for (int q = 0; q < kBwdThreads; q++) s = fmaf(ia >= 0 ? s_vec[q][ia] : 1.f, s_vec[q][ib], s);
+        row[t] = s;
+    }
+}
+
+// K6: re-march and scatter the feature gradients.
+template <int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a) {
+    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (r >= a.n_rays) return;
+    float o[3], d[3], Cf[3], Ff[4], gC[3], gF[4];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o[c] = __ldg(a.ray_o + 3 * r + c);
+        d[c] = __ldg(a.ray_d + 3 * r + c);
+        Cf[c] = __ldg(a.aux + 8 * r + c);
+        gC[c] = __ldg(a.gcf + 8 * r + c);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        Ff[c] = __ldg(a.aux + 8 * r + 3 + c);
+        gF[c] = __ldg(a.gcf + 8 * r + 3 + c);
+    }
+    int order[kMaxRayIds];
+    const int n = sort_blocks_for_ray(a.recs, a.ids, a.n_ray_ids, o, order);
+    float inv_d[3], omax;
+    ray_setup(d, o, inv_d, omax);
+    float T = 1.f, PC[3] = {0.f, 0.f, 0.f}, PF[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < n; k++) {
+        const int id = order[k];
+        const BlockRec &b = a.recs[id];
+        float *gg = a.grad_grid[id];
+        float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
+        const float delta = b.delta;
+        const bool more = for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3]) {
+            float2 f2[4];
+            accumulate_sample<DT>(b, p, g, f2);
+            const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
+            const float sigma = __expf(f[0]);
+            const float e = __expf(-sigma * delta);
+            const float wt = T * (1.f - e);
+            float c[7];
+#pragma unroll
+            for (int q = 0; q < 7; q++) c[q] = sigmoidf_fast(f[1 + q]);
+            float gdot = 0.f, sdot = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                PC[q] = fmaf(wt, c[q], PC[q]);
+                gdot = fmaf(gC[q], c[q], gdot);
+                sdot = fmaf(gC[q], Cf[q] - PC[q], sdot);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                PF[q] = fmaf(wt, c[3 + q], PF[q]);
+                gdot = fmaf(gF[q], c[3 + q], gdot);
+                sdot = fmaf(gF[q], Ff[q] - PF[q], sdot);
+            }
+            float gf[8];
+            gf[0] = sigma * delta * (T * e * gdot - sdot);
+#pragma unroll
+            for (int q = 0; q < 3; q++) gf[1 + q] = wt * gC[q] * c[q] * (1.f - c[q]);
+#pragma unroll
+            for (int q = 0; q < 4; q++) gf[4 + q] = wt * gF[q] * c[3 + q] * (1.f - c[3 + q]);
+            scatter_taps(b, gg, gp, p, g, gf);
+            T *= e;
+            return !(T < a.ert_eps);
+        });
+        if (!more) break;
+    }
+}
+
+// grad_mlp[t] += sum over CTA rows, in row order
+__global__ void k_reduce_rows(const float *__restrict__ partials, int n_rows, float *grad_mlp) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kMlpParams) return;
+    float s = 0.f;
+    for (int k = 0; k < n_rows; k++) s += partials[(int64_t)k * kMlpParams + t];
+    grad_mlp[t] += s;
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int64_t n, float lr, float b1, float b2, float eps, float bc1,
+                       float bc2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    }
+}
+
+__global__ void k_mse_grad(const float *__restrict__ rgb, const float *__restrict__ tgt, int64_t n, float scale,
+                           float *__restrict__ grad, float *loss) {
+    __shared__ float s_part[32];
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = rgb[i] - tgt[i];
+        grad[i] = 2.f * scale * e;
+        acc = fmaf(e, e, acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < (blockDim.x >> 5) ? s_part[threadIdx.x] : 0.f;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (threadIdx.x == 0 && loss) atomicAdd(loss, v * scale);
+    }
+}
+
+}  // namespace
+
+int backward_rows(int64_t n_rays) { return (int)((n_rays + kBwdThreads - 1) / kBwdThreads); }
+
+cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st) {
+    if (a.n_rays <= 0) return cudaSuccess;
+    const int nb = backward_rows(a.n_rays);
+    k_mlp_backward<<<nb, kBwdThreads, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_rows<<<(kMlpParams + 127) / 128, 128, 0, st>>>(a.partials, nb, a.grad_mlp);
+    switch (a.dtype) {
+    case kF32: k_remarch_backward<kF32><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kF16: k_remarch_backward<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    k_adam<<<(int)blocks, 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mse_grad(const float *rgb, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (loss) {
+        cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+        if (e != cudaSuccess) return e;
+    }
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_mse_grad<<<(int)blocks, 256, 0, st>>>(rgb, tgt, n, 1.0f / (float)n, grad, loss);
+    return cudaGetLastError();
+}
+
+}  // namespace cow

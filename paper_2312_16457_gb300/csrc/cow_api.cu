@@ -120,6 +120,8 @@ struct cow_ctx {
     unsigned *d_err = nullptr;
     float *d_mlp = nullptr;
     DevBuf views, ids, out_rgb, out_aux, out_nsamp;
+    DevBuf gptrs, partials;  // backward: per-block gradient pointers, per-CTA MLP-gradient rows
+    DevBuf staging;          // host masters of cow_update_features
 };
 
 namespace {
@@ -141,6 +143,9 @@ void destroy(cow_ctx *c) {
     c->out_rgb.release();
     c->out_aux.release();
     c->out_nsamp.release();
+    c->gptrs.release();
+    c->partials.release();
+    c->staging.release();
     delete c;
 }
 
@@ -158,6 +163,44 @@ double block_ztop(const BlockHost &b, const std::vector<uint32_t> &bits, int C) 
         }
     }
     return (double)b.lo[2];
+}
+
+// Re-pack the features of an existing block from new FP32 masters (occupancy
+// and z_top unchanged); FP8 scales are recomputed.
+cow_status repack_block(cow_ctx *c, BlockHost &b, const float *const src_in[4], void *staging, unsigned *d_amax,
+                        float *d_inv, cudaStream_t st) {
+    const int64_t nv[4] = {(int64_t)b.R * b.R * b.R, (int64_t)b.P * b.P, (int64_t)b.P * b.P, (int64_t)b.P * b.P};
+    void *dst[4] = {b.grid, b.planes[0], b.planes[1], b.planes[2]};
+    float scale_h[32];
+    for (int t = 0; t < 4; t++) {
+        const float *s = src_in[t];
+        if (!is_device_ptr(s)) {
+            COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
+            s = (const float *)staging;
+        }
+        int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (c->dtype == COW_FP8_E4M3) {
+            COW_CUDA(cow::launch_amax8(s, nv[t], d_amax, st));
+            unsigned amax_bits[8];
+            COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
+            COW_CUDA(cudaStreamSynchronize(st));
+            for (int k = 0; k < 8; k++) {
+                float a;
+                std::memcpy(&a, &amax_bits[k], 4);
+                e[k] = fp8_exponent(a);
+            }
+        }
+        float inv[8];
+        for (int k = 0; k < 8; k++) {
+            b.scale_exp[t][k] = e[k];
+            inv[k] = std::ldexp(1.0f, -e[k]);
+            scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
+        }
+        COW_CUDA(cudaMemcpyAsync(d_inv + 8 * t, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
+        COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? b.R : b.P, c->dtype, d_inv + 8 * t, dst[t], st));
+    }
+    COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
+    return COW_OK;
 }
 
 cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *staging, unsigned *d_amax,
@@ -653,6 +696,96 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)n_rays * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)n_rays * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)n_rays * 4, cudaMemcpyDeviceToHost, st));
+    return COW_OK;
+}
+
+cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                               int32_t n_ids, const float *mlp, float ert_eps, const float *aux, const float *dL_drgb,
+                               float *const *grad_grid, float *const *grad_planes, float *grad_mlp, void *stream) {
+    g_last_error.clear();
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !aux || !dL_drgb || !grad_grid || !grad_planes || !grad_mlp)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_backward: null argument");
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
+    const int32_t nb = (int32_t)ctx->blocks.size();
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    for (const void *q : {(const void *)o, (const void *)d, (const void *)aux, (const void *)dL_drgb, (const void *)grad_mlp, (const void *)mlp})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "backward arrays and the MLP must be device memory");
+    if (((uintptr_t)aux & 15u)) return fail(COW_ERR_INVALID_ARG, "aux must be 16-byte aligned");
+    std::vector<float *> ptrs((size_t)nb * 4);
+    for (int32_t i = 0; i < nb; i++) {
+        ptrs[(size_t)i] = grad_grid[i];
+        for (int k = 0; k < 3; k++) ptrs[(size_t)nb + 3 * (size_t)i + k] = grad_planes[3 * i + k];
+        for (int k = 0; k < 4; k++) {
+            const float *q = k == 0 ? grad_grid[i] : grad_planes[3 * i + k - 1];
+            if (q && (((uintptr_t)q & 15u) || !is_device_ptr(q)))
+                return fail(COW_ERR_INVALID_ARG, "block %d: gradient arrays must be 16-byte aligned device memory", i);
+        }
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    COW_CUDA(ctx->gptrs.reserve(ptrs.size() * sizeof(float *)));
+    COW_CUDA(cudaMemcpyAsync(ctx->gptrs.p, ptrs.data(), ptrs.size() * sizeof(float *), cudaMemcpyHostToDevice, st));
+    COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
+    COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int rows = cow::backward_rows(n_rays);
+    const size_t part_bytes = ((size_t)std::max(rows, 1) * cow::kMlpParams * sizeof(float) + 255) & ~(size_t)255;
+    COW_CUDA(ctx->partials.reserve(part_bytes + (size_t)std::max<int64_t>(n_rays, 1) * 8 * sizeof(float)));
+    cow::BwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.recs = ctx->d_blocks;
+    a.dtype = ctx->dtype;
+    a.n_ray_ids = n_ids;
+    a.ids = (const int32_t *)ctx->ids.p;
+    a.mlp = mlp;
+    a.ert_eps = ert_eps;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.aux = aux;
+    a.dL_drgb = dL_drgb;
+    a.grad_grid = (float *const *)ctx->gptrs.p;
+    a.grad_planes = (float *const *)ctx->gptrs.p + nb;
+    a.grad_mlp = grad_mlp;
+    a.partials = (float *)ctx->partials.p;
+    a.gcf = (float *)((unsigned char *)ctx->partials.p + part_bytes);
+    a.err = ctx->d_err;
+    COW_CUDA(cow::launch_backward_rays(a, st));
+    return COW_OK;
+}
+
+cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, const float *plane_xy,
+                               const float *plane_xz, const float *plane_yz, void *stream) {
+    g_last_error.clear();
+    if (!ctx || !grid || !plane_xy || !plane_xz || !plane_yz) return fail(COW_ERR_INVALID_ARG, "null argument");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
+    for (const float *q : {grid, plane_xy, plane_xz, plane_yz})
+        if (((uintptr_t)q & 15u) != 0) return fail(COW_ERR_INVALID_ARG, "arrays must be 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    BlockHost &b = ctx->blocks[(size_t)block];
+    const size_t need = (size_t)std::max((int64_t)b.R * b.R * b.R, (int64_t)b.P * b.P) * 32;
+    // staging (host masters) and small scratch for the FP8 scale search
+    COW_CUDA(ctx->staging.reserve(need + 256));
+    unsigned *d_amax = (unsigned *)((unsigned char *)ctx->staging.p + need);
+    float *d_inv = (float *)((unsigned char *)ctx->staging.p + need + 64);
+    const float *src[4] = {grid, plane_xy, plane_xz, plane_yz};
+    return repack_block(ctx, b, src, ctx->staging.p, d_amax, d_inv, st);
+}
+
+cow_status cow_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
+                         float beta2, float eps, int32_t step, void *stream) {
+    if (!param || !grad || !m || !v || n < 0 || step < 1 || !(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) ||
+        !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return fail(COW_ERR_INVALID_ARG, "cow_adam_step: bad argument");
+    COW_CUDA(cow::launch_adam(param, grad, m, v, n, lr, beta1, beta2, eps, step, (cudaStream_t)stream));
+    return COW_OK;
+}
+
+cow_status cow_mse_grad(const float *rgb, const float *target, int64_t n, float *dL_drgb, float *loss, void *stream) {
+    if (!rgb || !target || !dL_drgb || n < 0) return fail(COW_ERR_INVALID_ARG, "cow_mse_grad: bad argument");
+    COW_CUDA(cow::launch_mse_grad(rgb, target, n, dL_drgb, loss, (cudaStream_t)stream));
     return COW_OK;
 }
 

@@ -37,6 +37,31 @@ cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st);
 int march_tile_w();
 int march_tile_h();
 
+// K6 / K7: gradients of the ray-batch form (bwd.cu)
+struct BwdArgs {
+    const BlockRec *recs;         // every block of the context
+    int32_t dtype;
+    int32_t n_ray_ids;
+    const int32_t *ids;           // the blocks to composite
+    const float *mlp;             // 499 FP32 (device)
+    float ert_eps;
+    const float *ray_o, *ray_d;   // n_rays x 3
+    int64_t n_rays;
+    const float *aux;             // forward aux, n_rays x 8
+    const float *dL_drgb;         // n_rays x 3
+    float *const *grad_grid;      // device array of per-block pointers (entries may be null)
+    float *const *grad_planes;    // device array of 3 per-block pointers
+    float *grad_mlp;              // 499, accumulated
+    float *partials;              // scratch: backward_rows(n_rays) x 499
+    float *gcf;                   // scratch: n_rays x 8 (dL/dC_d, dL/dF per ray)
+    unsigned *err;
+};
+int backward_rows(int64_t n_rays);
+cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t st);
+cudaError_t launch_mse_grad(const float *rgb, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);
+
 // K4 / K5: packing and occupancy (pack.cu)
 cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cudaStream_t st);
 // FP32 packs in the natural layout; FP16 / BF16 / FP8 in the pair layout

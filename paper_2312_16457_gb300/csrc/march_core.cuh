@@ -1,0 +1,203 @@
+// march_core.cuh -- the sample sequence of a ray and the feature lookup, shared
+// by the forward marcher and the backward pass so that both visit exactly the
+// same samples.
+#pragma once
+
+#include "cow_common.cuh"
+
+namespace cow {
+
+// Feature lookup f^{k,l}(p): trilinear grid + bilinear xy, xz, yz planes.
+// g: the FP32 grid coordinate the cell decision computed.  The 8 channels are
+// accumulated as four float2 pairs with packed FP32 FMA (same rounding per
+// element as scalar FMA).
+template <int DT>
+__device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], const float g[3],
+                                                  float2 f[4]) {
+    float fr[3];
+    int c0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const int v = min(max(__float2int_rd(g[a]), 0), b.R - 2);
+        c0[a] = v;
+        fr[a] = fminf(fmaxf(g[a], 0.f), (float)(b.R - 1)) - (float)v;
+    }
+    const int R = b.R;
+    const int64_t base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
+    float2 acc[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) acc[c] = make_float2(0.f, 0.f);
+    const float wx[2] = {1.f - fr[0], fr[0]}, wy[2] = {1.f - fr[1], fr[1]}, wz[2] = {1.f - fr[2], fr[2]};
+    if (Store<DT>::kPaired) {
+        // four loads, each the x-pair of one (y, z) edge of the voxel
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int dy = k & 1, dz = k >> 1;
+            const float wyz = wy[dy] * wz[dz];
+            const float2 w0 = make_float2(wyz * wx[0], wyz * wx[0]), w1 = make_float2(wyz * wx[1], wyz * wx[1]);
+            float2 lo[4], hi[4];
+            Store<DT>::load_pair(b.grid, base + ((int64_t)dz * R + dy) * R, lo, hi);
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], acc[c]));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+            const float w = (wy[dy] * wz[dz]) * wx[dx];
+            const float2 w2 = make_float2(w, w);
+            float2 v[4];
+            Store<DT>::load8(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
+#pragma unroll
+            for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
+        }
+    }
+    if (DT == kFP8) {
+#pragma unroll
+        for (int c = 0; c < 4; c++)
+            f[c] = make_float2(acc[c].x * b.scale[2 * c], acc[c].y * b.scale[2 * c + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; c++) f[c] = acc[c];
+    }
+    // planes: vertex-aligned bilinear in (x, y), (x, z), (y, z)
+    float hf[3];
+    int h0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        const int u = min(max(__float2int_rd(h), 0), b.P - 2);
+        h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
+        h0[a] = u;
+        hf[a] = h - (float)u;
+    }
+    const int P = b.P;
+#pragma unroll
+    for (int pl = 0; pl < 3; pl++) {
+        const int ua = pl == 2 ? 1 : 0, va = pl == 0 ? 1 : 2;
+        const int64_t tb = (int64_t)h0[va] * P + h0[ua];
+        const float wu[2] = {1.f - hf[ua], hf[ua]}, wv[2] = {1.f - hf[va], hf[va]};
+        float2 pacc[4];
+#pragma unroll
+        for (int c = 0; c < 4; c++) pacc[c] = make_float2(0.f, 0.f);
+        if (Store<DT>::kPaired) {
+#pragma unroll
+            for (int dv = 0; dv < 2; dv++) {
+                const float2 w0 = make_float2(wv[dv] * wu[0], wv[dv] * wu[0]);
+                const float2 w1 = make_float2(wv[dv] * wu[1], wv[dv] * wu[1]);
+                float2 lo[4], hi[4];
+                Store<DT>::load_pair(b.planes[pl], tb + (int64_t)dv * P, lo, hi);
+#pragma unroll
+                for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], pacc[c]));
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int du = q & 1, dv = q >> 1;
+                const float w = wv[dv] * wu[du];
+                const float2 w2 = make_float2(w, w);
+                float2 v[4];
+                Store<DT>::load8(b.planes[pl], tb + (int64_t)dv * P + du, v);
+#pragma unroll
+                for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
+            }
+        }
+        if (DT == kFP8) {
+            const float *sc = b.scale + 8 * (pl + 1);
+#pragma unroll
+            for (int c = 0; c < 4; c++)
+                f[c] = __ffma2_rn(pacc[c], make_float2(sc[2 * c], sc[2 * c + 1]), f[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; c++) f[c] = __fadd2_rn(f[c], pacc[c]);
+        }
+    }
+}
+
+// Visit the occupied lattice samples of one ray inside one block, in order
+// (Eq. 4 membership, occupancy skip); fn(p, g) is called for each and
+// returns false to stop the ray.  Returns false when fn stopped it.
+//
+// Empty cells are left with an exact jump: along each axis the FP32 cell
+// index of successive lattice points is monotone (every step of the decision
+// sequence is monotone), so every lattice point before the ray's exit from
+// the cell -- the cell shrunk by a margin m far above the FP32 position and
+// coordinate error -- decides the same empty cell and would be skipped
+// anyway.  The jump lands one lattice step short of that exit.
+template <typename Fn>
+__device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o[3], const float d[3],
+                                                const float inv_d[3], float omax, unsigned *err, Fn &&fn) {
+    int i0, i1;
+    float tfar;
+    if (!candidate_range(b, o, d, inv_d, i0, i1, tfar)) return true;
+    if (i1 - i0 > kMaxSpan) {
+        atomicOr(err, kErrRange);
+        i1 = i0 + kMaxSpan;
+    }
+    const float delta = b.delta, inv_delta = 1.0f / b.delta;
+    const float m = 4e-6f * (omax + tfar + b.bmax);
+    const int Nc = b.Nc, C = b.C, R = b.R;
+    for (int i = i0; i <= i1; i++) {
+        float p[3];
+        lattice_point(o, d, delta, i, p);
+        if (!inside_block(b, p)) continue;
+        int cell[3];
+        float g[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            g[a] = axis_coord(p[a], b.lo[a], b.kg[a]);
+            const int v = min(max(__float2int_rd(g[a]), 0), R - 2);
+            cell[a] = C == 1 ? v : (int)__umulhi((unsigned)v, b.cdiv);
+        }
+        const int ci = (cell[2] * Nc + cell[1]) * Nc + cell[0];
+        if (!((__ldg(b.occ + (ci >> 5)) >> (ci & 31)) & 1u)) {
+            float tx = 3.0e38f;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                if (d[a] > 0.f) {
+                    const float chi =
+                        cell[a] == Nc - 1 ? b.hi[a] : fmaf((float)((cell[a] + 1) * C), b.vox[a], b.lo[a]);
+                    tx = fminf(tx, (chi - m - o[a]) * inv_d[a]);
+                } else if (d[a] < 0.f) {
+                    const float clo = fmaf((float)(cell[a] * C), b.vox[a], b.lo[a]);
+                    tx = fminf(tx, (clo + m - o[a]) * inv_d[a]);
+                }
+            }
+            const int j = __float2int_rd(tx * inv_delta - 0.5f) - 1;
+            if (j > i) i = min(j, i1);
+            continue;
+        }
+        if (!fn(p, g)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void ray_setup(const float d[3], const float o[3], float inv_d[3], float &omax) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) inv_d[a] = d[a] != 0.f ? 1.0f / d[a] : 0.f;
+    omax = fmaxf(fabsf(o[0]), fmaxf(fabsf(o[1]), fabsf(o[2])));
+}
+
+// Per-ray depth order of the ray-batch form: xy distance of block centres to
+// this ray's origin (App. D) as the FP32 key dx*dx + dy*dy, ties by id.
+__device__ __forceinline__ int sort_blocks_for_ray(const BlockRec *recs, const int32_t *ids, int n, const float o[3],
+                                                   int order[kMaxRayIds]) {
+    float key[kMaxRayIds];
+    for (int i = 0; i < n; i++) {
+        const int id = __ldg(ids + i);
+        const BlockRec &b = recs[id];
+        const float dx = __fsub_rn(b.cx, o[0]), dy = __fsub_rn(b.cy, o[1]);
+        const float kk = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
+        int j = i - 1;
+        while (j >= 0 && (key[j] > kk || (key[j] == kk && order[j] > id))) {
+            key[j + 1] = key[j];
+            order[j + 1] = order[j];
+            j--;
+        }
+        key[j + 1] = kk;
+        order[j + 1] = id;
+    }
+    return n;
+}
+
+}  // namespace cow

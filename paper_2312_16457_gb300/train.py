@@ -1,0 +1,86 @@
+"""Differentiation form: a torch.autograd.Function over libcow's ray-batch
+render and its backward kernels, and a fitter that optimises block features
+and the deferred MLP with libcow's Adam kernel.
+
+Gradients come from cow_render_backward (re-marching each ray from its saved
+totals); the optimiser step, the loss gradient and the re-packing of the
+updated features run in libcow kernels as well.  Occupancy stays as loaded.
+"""
+from __future__ import annotations
+
+from typing import List, Sequence
+
+import torch
+
+from . import cow
+
+
+class RenderRays(torch.autograd.Function):
+    """rgb = render(o, d; features, mlp).  Inputs: the context, block ids, the
+    MLP (499) and the flat feature parameters [grid_0, xy_0, xz_0, yz_0, grid_1,
+    ...] of every block of the context (FP32 device tensors)."""
+
+    @staticmethod
+    def forward(fctx, cctx: cow.Context, ids: Sequence[int], o, d, ert_eps: float, mlp, *params):
+        nb = cctx.n_blocks
+        assert len(params) == 4 * nb
+        for i in range(nb):
+            cctx.update_features(i, params[4 * i], params[4 * i + 1:4 * i + 4])
+        rgb, aux, _ = cctx.render_rays(o, d, ids, mlp.detach(), ert_eps=ert_eps)
+        fctx.save_for_backward(o, d, mlp, aux)
+        fctx.cctx, fctx.ids, fctx.ert = cctx, list(ids), ert_eps
+        fctx.shapes = [p.shape for p in params]
+        return rgb
+
+    @staticmethod
+    def backward(fctx, grad_rgb):
+        o, d, mlp, aux = fctx.saved_tensors
+        cctx = fctx.cctx
+        nb = cctx.n_blocks
+        grads = [torch.zeros(s, dtype=torch.float32, device=o.device) for s in fctx.shapes]
+        gm = torch.zeros(499, dtype=torch.float32, device=o.device)
+        cctx.render_backward(o, d, fctx.ids, mlp.detach().contiguous(), aux, grad_rgb.contiguous().float(),
+                             [grads[4 * i] for i in range(nb)], [grads[4 * i + 1:4 * i + 4] for i in range(nb)], gm,
+                             ert_eps=fctx.ert)
+        return (None, None, None, None, None, gm, *grads)
+
+
+def render_rays(cctx: cow.Context, ids, o, d, mlp, params: List[torch.Tensor], ert_eps: float = 0.0):
+    return RenderRays.apply(cctx, ids, o, d, ert_eps, mlp, *params)
+
+
+class Fitter:
+    """Fit block features and the deferred MLP to target colours of a ray
+    batch: forward, MSE gradient, backward, Adam, re-pack -- all in libcow."""
+
+    def __init__(self, scene, mlp, lr_feat=1e-2, lr_mlp=1e-3, device="cuda"):
+        self.ctx = cow.Context(scene, "fp32")
+        self.ids = list(range(len(scene.blocks)))
+        self.params = []
+        for b in scene.blocks:
+            self.params += [b.grid.to(device).float().contiguous()] + [p.to(device).float().contiguous() for p in b.planes]
+        self.mlp = torch.as_tensor(mlp, dtype=torch.float32, device=device).contiguous()
+        self.m = [torch.zeros_like(p) for p in self.params] + [torch.zeros_like(self.mlp)]
+        self.v = [torch.zeros_like(p) for p in self.params] + [torch.zeros_like(self.mlp)]
+        self.lr_feat, self.lr_mlp = lr_feat, lr_mlp
+        self.t = 0
+
+    def step(self, o, d, target, ert_eps: float = 0.0):
+        """One optimisation step; returns the loss (device tensor) before it."""
+        nb = len(self.ids)
+        rgb, aux, _ = self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps)
+        g, loss = cow.mse_grad(rgb, target)
+        grads = [torch.zeros_like(p) for p in self.params]
+        gm = torch.zeros_like(self.mlp)
+        self.ctx.render_backward(o, d, self.ids, self.mlp, aux, g, [grads[4 * i] for i in range(nb)],
+                                 [grads[4 * i + 1:4 * i + 4] for i in range(nb)], gm, ert_eps=ert_eps)
+        self.t += 1
+        for k, p in enumerate(self.params):
+            cow.adam_step(p, grads[k], self.m[k], self.v[k], self.lr_feat, self.t)
+        cow.adam_step(self.mlp, gm, self.m[-1], self.v[-1], self.lr_mlp, self.t)
+        for i in range(nb):
+            self.ctx.update_features(i, self.params[4 * i], self.params[4 * i + 1:4 * i + 4])
+        return loss
+
+    def render(self, o, d, ert_eps: float = 0.0):
+        return self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps, aux=False)[0]

@@ -1,0 +1,100 @@
+"""GPU parity of the differentiation form: cow_render_backward against the
+oracle's FP64 analytic gradient (which tests/test_oracle_formats_lod_grad.py
+pins to central finite differences), the autograd.Function path, and a short
+Adam fit.  Tolerance: relative error <= 1e-3 in the L2 norm of each tensor."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_16457_gb300 import cow, synth, train
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2312_16457_gb300 import build
+
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _gpu_grads(ctx, sc, o, d, ids, mlp, g):
+    dev = "cuda"
+    rgb, aux, ns = ctx.render_rays(o, d, ids, mlp, nsamp=True)
+    gg = [torch.zeros(b.grid.shape, device=dev) for b in sc.blocks]
+    gp = [[torch.zeros(p.shape, device=dev) for p in b.planes] for b in sc.blocks]
+    gm = torch.zeros(499, device=dev)
+    ctx.render_backward(o, d, ids, mlp, aux, g, gg, gp, gm)
+    ctx.sync_check()
+    return rgb, ns, gg, gp, gm
+
+
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_backward_matches_oracle_gradient(storage):
+    sc = synth.city_scene(17, 2, 2.0, [(16, 40)])
+    o, d = synth.random_rays(4096, 7, sc.box_lo, sc.box_hi)
+    mlp = synth.mlp_weights(8)
+    g = np.random.default_rng(4).normal(size=(4096, 3)).astype(np.float32)
+    ids = list(range(4))
+    ctx = cow.Context(sc, storage)
+    mlp_d = torch.from_numpy(mlp).cuda()
+    rgb, ns, gg, gp, gm = _gpu_grads(ctx, sc, o.cuda(), d.cuda(), ids, mlp_d, torch.from_numpy(g).cuda())
+    osc = oracle.OracleScene(sc, values="master" if storage == "fp32" else storage)
+    og, op, om = oracle.render_rays_grad(osc, ids, o, d, mlp, g)
+    _, _, n_o = oracle.render_rays(osc, ids, o, d, mlp)
+    assert np.array_equal(ns.cpu().numpy(), n_o)
+    assert (n_o > 0).mean() > 0.5
+    for b in range(4):
+        assert _rel(gg[b].cpu().numpy(), og[b]) <= 1e-3, ("grid", b)
+        for k in range(3):
+            assert _rel(gp[b][k].cpu().numpy(), op[b][k]) <= 1e-3, ("plane", b, k)
+    assert _rel(gm.cpu().numpy(), om) <= 1e-3
+    assert np.abs(om).max() > 1e-3 and max(np.abs(x).max() for x in og) > 1e-4
+
+
+def test_autograd_function_matches_direct_call():
+    sc = synth.city_scene(18, 2, 2.0, [(12, 24)])
+    o, d = synth.random_rays(2048, 9, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    ctx = cow.Context(sc, "fp32")
+    ids = list(range(4))
+    mlp = torch.from_numpy(synth.mlp_weights(3)).cuda().requires_grad_(True)
+    params = []
+    for b in sc.blocks:
+        params += [b.grid.cuda().clone().requires_grad_(True)] + [p.cuda().clone().requires_grad_(True) for p in b.planes]
+    wts = torch.randn(2048, 3, device="cuda")
+    rgb = train.render_rays(ctx, ids, o, d, mlp, params)
+    (rgb * wts).sum().backward()
+    rgb2, ns, gg, gp, gm = _gpu_grads(ctx, sc, o, d, ids, mlp.detach(), wts)
+    assert torch.equal(rgb, rgb2)
+    assert _rel(mlp.grad.cpu().numpy(), gm.cpu().numpy()) <= 1e-6
+    for b in range(4):
+        assert _rel(params[4 * b].grad.cpu().numpy(), gg[b].cpu().numpy()) <= 1e-6
+        for k in range(3):
+            assert _rel(params[4 * b + 1 + k].grad.cpu().numpy(), gp[b][k].cpu().numpy()) <= 1e-6
+
+
+def test_fit_reduces_loss():
+    """A short fit of one scene's features and MLP to another seed's render."""
+    sc = synth.city_scene(4, 2, 2.0, [(24, 64)])
+    tgt_scene = synth.city_scene(40, 2, 2.0, [(24, 64)])
+    o, d = synth.random_rays(1 << 16, 4, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    tctx = cow.Context(tgt_scene, "fp32")
+    target = tctx.render_rays(o, d, [0, 1, 2, 3], synth.mlp_weights(140), aux=False)[0]
+    fit = train.Fitter(sc, synth.mlp_weights(104))
+    losses = [float(fit.step(o, d, target).item()) for _ in range(40)]
+    fit.ctx.sync_check()
+    assert losses[-1] < 0.6 * losses[0], losses[::8]
+    assert all(np.isfinite(losses))
