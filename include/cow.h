@@ -189,6 +189,28 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
                                int32_t n_ids, const float *mlp, float ert_eps, const float *aux, const float *dL_drgb,
                                float *const *grad_grid, float *const *grad_planes, float *grad_mlp, void *stream);
 
+/* Allocation-free variant of cow_render_backward (the paper has no
+ * counterpart; it exists for callers of this library that cannot allocate
+ * device memory once running -- a trainer or viewer inside a fixed
+ * device-memory budget, or a steady-state loop that must not pay for
+ * cudaMalloc / cudaFree and the device synchronisation cudaFree implies).
+ * Same arguments, results and error behaviour as cow_render_backward, with:
+ *  - no device or host allocation: the scratch (per-CTA MLP-gradient rows,
+ *    per-ray dL/dC_d and dL/dF, the gradient pointer table, the block ids)
+ *    lives in one static device array of the library (3 MiB, held by every
+ *    GPU that loads the library until the process exits);
+ *  - at most 65536 rays and 1024 context blocks per call; larger requests
+ *    return COW_ERR_INVALID_ARG with a message naming the limit;
+ *  - the first call on a device looks the array's device address up
+ *    (cudaGetSymbolAddress); make that first call before any stream capture;
+ *  - every call on a device shares the array and rewrites what it reads, so
+ *    calls that overlap on the GPU (other streams, other contexts on the same
+ *    device) race on it: order them. */
+cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                       const int32_t *ids, int32_t n_ids, const float *mlp, float ert_eps,
+                                       const float *aux, const float *dL_drgb, float *const *grad_grid,
+                                       float *const *grad_planes, float *grad_mlp, void *stream);
+
 /* Re-pack block `block`'s features from new FP32 masters (same layouts as
  * cow_block_desc; host or device, 16-byte aligned) into the context's
  * storage format; occupancy and z_top stay as loaded (the differentiation

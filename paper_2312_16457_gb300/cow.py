@@ -24,8 +24,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_set_schedule", "cow_sync_check", "cow_export_occupancy",
-           "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_update_features", "cow_adam_step",
-           "cow_mse_grad", "cow_last_error", "cow_version"]
+           "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
+           "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_last_error", "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1}
 
 
@@ -72,6 +72,7 @@ def lib():
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
             "cow_render_backward": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
+            "cow_render_backward_noalloc": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
             "cow_update_features": [P, i32, P, P, P, P, P],
             "cow_adam_step": [P, P, P, P, i64, flt, flt, flt, flt, i32, P],
             "cow_mse_grad": [P, P, i64, P, P, P],
@@ -223,10 +224,11 @@ class Context:
         return rgb, ax, ns
 
     def render_backward(self, o, d, ids, mlp, aux, dL_drgb, grad_grids, grad_planes, grad_mlp,
-                        ert_eps: float = 0.0, stream=None):
+                        ert_eps: float = 0.0, stream=None, noalloc: bool = False):
         """Accumulate dL/d(features, MLP) of a ray batch into the given FP32
         device tensors (grad_grids[i]: R^3 x 8, grad_planes[i][k]: P^2 x 8,
-        grad_mlp: 499; None skips a block)."""
+        grad_mlp: 499; None skips a block).  noalloc=True calls the variant
+        that allocates nothing (at most 65536 rays per call)."""
         a = np.ascontiguousarray(ids, np.int32)
         nb = self.n_blocks
         gg = (C.c_void_p * nb)(*[_ptr(g) if g is not None else None for g in grad_grids])
@@ -235,9 +237,9 @@ class Context:
             pl = grad_planes[i] if grad_planes[i] is not None else [None, None, None]
             flat += [_ptr(t) if t is not None else None for t in pl]
         gp = (C.c_void_p * (3 * nb))(*flat)
-        _check(lib().cow_render_backward(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a),
-                                         len(a), _ptr(mlp), float(ert_eps), _ptr(aux), _ptr(dL_drgb.contiguous()),
-                                         gg, gp, _ptr(grad_mlp), _stream_ptr(stream)))
+        fn = lib().cow_render_backward_noalloc if noalloc else lib().cow_render_backward
+        _check(fn(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a), len(a), _ptr(mlp),
+                  float(ert_eps), _ptr(aux), _ptr(dL_drgb.contiguous()), gg, gp, _ptr(grad_mlp), _stream_ptr(stream)))
 
     def update_features(self, i: int, grid, planes, stream=None):
         """Re-pack block i's features from new FP32 arrays (occupancy kept)."""

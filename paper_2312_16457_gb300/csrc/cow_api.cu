@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -848,3 +849,128 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free backward.
+//
+// Some callers cannot allocate device memory once they are running: a
+// trainer or viewer that works inside a fixed device-memory budget (its
+// memory pool is frozen after start-up), or a steady-state loop that must not
+// pay for cudaMalloc / cudaFree (cudaFree also synchronises the device).
+// cow_render_backward_noalloc serves them: it computes exactly what
+// cow_render_backward computes, but its scratch -- the per-CTA rows of the
+// MLP weight gradient, the per-ray dL/dC_d, dL/dF, the per-block gradient
+// pointer table and the block ids -- lives in the file-scope array below
+// instead of context buffers, so the call itself allocates nothing.
+//
+// Limits: at most kNoAllocMaxRays rays and kNoAllocMaxBlocks blocks per call
+// (3 MiB of device memory, held by every GPU that loads the library until the
+// process exits).  All calls on a device share the array: every call rewrites
+// the parts it reads before reading them, so nothing has to start at zero,
+// but calls that overlap on the GPU (different streams, or different
+// contexts on one device) race on it and must be ordered by the caller.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxRays = 65536;
+constexpr int32_t kNoAllocMaxBlocks = 1024;
+constexpr size_t kNaRowsBytes = (size_t)(kNoAllocMaxRays / 128) * cow::kMlpParams * sizeof(float);  // 1021952
+constexpr size_t kNaGcfBytes = (size_t)kNoAllocMaxRays * 8 * sizeof(float);                           // 2 MiB
+constexpr size_t kNaPtrBytes = (size_t)kNoAllocMaxBlocks * 4 * sizeof(float *);                        // 32 KiB
+constexpr size_t kNaIdsBytes = (size_t)cow::kMaxRayIds * sizeof(int32_t);
+constexpr size_t kNaTotalBytes = kNaRowsBytes + kNaGcfBytes + kNaPtrBytes + kNaIdsBytes;
+static_assert(kNaRowsBytes % 256 == 0 && kNaGcfBytes % 256 == 0 && kNaPtrBytes % 256 == 0,
+              "scratch sections must keep 256-byte alignment");
+
+// In host code this name is only a host-side handle, not a device address;
+// the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaTotalBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call on a device does this; make that first call
+// before any stream capture).
+cow_status noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices) return fail(COW_ERR_UNSUPPORTED, "device index %d too large", device);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(COW_ERR_CUDA, "cudaGetSymbolAddress of the backward scratch failed: %s", cudaGetErrorString(e));
+        g_noalloc_addr[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_addr[device];
+    return COW_OK;
+}
+
+}  // namespace
+
+extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                                  const int32_t *ids, int32_t n_ids, const float *mlp,
+                                                  float ert_eps, const float *aux, const float *dL_drgb,
+                                                  float *const *grad_grid, float *const *grad_planes,
+                                                  float *grad_mlp, void *stream) {
+    g_last_error.clear();
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !aux || !dL_drgb || !grad_grid || !grad_planes || !grad_mlp)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_backward_noalloc: null argument");
+    if (n_rays > kNoAllocMaxRays)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_backward_noalloc: %lld rays exceed its maximum of %lld per call",
+                    (long long)n_rays, (long long)kNoAllocMaxRays);
+    const int32_t nb = (int32_t)ctx->blocks.size();
+    if (nb > kNoAllocMaxBlocks)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_backward_noalloc: %d blocks exceed its maximum of %d", nb,
+                    kNoAllocMaxBlocks);
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    for (const void *q : {(const void *)o, (const void *)d, (const void *)aux, (const void *)dL_drgb, (const void *)grad_mlp, (const void *)mlp})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "backward arrays and the MLP must be device memory");
+    if (((uintptr_t)aux & 15u)) return fail(COW_ERR_INVALID_ARG, "aux must be 16-byte aligned");
+    float *table[kNoAllocMaxBlocks * 4];  // on the stack: the call allocates nothing, host or device
+    for (int32_t i = 0; i < nb; i++) {
+        table[i] = grad_grid[i];
+        for (int k = 0; k < 3; k++) table[nb + 3 * i + k] = grad_planes[3 * i + k];
+        for (int k = 0; k < 4; k++) {
+            const float *q = k == 0 ? grad_grid[i] : grad_planes[3 * i + k - 1];
+            if (q && (((uintptr_t)q & 15u) || !is_device_ptr(q)))
+                return fail(COW_ERR_INVALID_ARG, "block %d: gradient arrays must be 16-byte aligned device memory", i);
+        }
+    }
+    DeviceGuard dg(ctx->device);
+    unsigned char *scratch = nullptr;
+    cow_status rc = noalloc_scratch(ctx->device, &scratch);
+    if (rc != COW_OK) return rc;
+    float *rows = (float *)scratch;
+    float *gcf = (float *)(scratch + kNaRowsBytes);
+    float **dptrs = (float **)(scratch + kNaRowsBytes + kNaGcfBytes);
+    int32_t *dids = (int32_t *)(scratch + kNaRowsBytes + kNaGcfBytes + kNaPtrBytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    COW_CUDA(cudaMemcpyAsync(dptrs, table, (size_t)nb * 4 * sizeof(float *), cudaMemcpyHostToDevice, st));
+    COW_CUDA(cudaMemcpyAsync(dids, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    cow::BwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.recs = ctx->d_blocks;
+    a.dtype = ctx->dtype;
+    a.n_ray_ids = n_ids;
+    a.ids = dids;
+    a.mlp = mlp;
+    a.ert_eps = ert_eps;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.aux = aux;
+    a.dL_drgb = dL_drgb;
+    a.grad_grid = dptrs;
+    a.grad_planes = dptrs + nb;
+    a.grad_mlp = grad_mlp;
+    a.partials = rows;
+    a.gcf = gcf;
+    a.err = ctx->d_err;
+    COW_CUDA(cow::launch_backward_rays(a, st));
+    return COW_OK;
+}
