@@ -157,6 +157,42 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
                       const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                       float *out_aux, int32_t *out_nsamp, void *stream);
 
+/* Batched form: many cameras of uneven size and LOD set served by one
+ * persistent launch over a (view, tile, block) work queue.  Every CTA takes
+ * the next (view, tile) item from a device counter, culls the view's block
+ * list against the tile's pyramid (blocks that no ray of the tile can sample)
+ * and marches the tile's rays; each pixel equals cow_render's bit for bit.
+ * The launch can be replayed from a CUDA graph, and its tile shape and
+ * resident CTAs per SM can be picked by cow_batch_tune, which times the
+ * candidates on the batch that is set.
+ *
+ * cow_batch_create : pinned + device staging for up to max_views cameras and
+ *                    max_ids block ids (sum over views); owned by the caller
+ *                    (cow_batch_free before the context).
+ * cow_batch_set_views : the cameras and their near-to-far block ids (CSR, as
+ *                    cow_render); out_pixels (may be NULL) receives the total
+ *                    pixel count, the rows of the outputs.  Waits for the
+ *                    previous batch's staging copy before rewriting it.
+ * cow_batch_render : outputs as cow_render but device memory only; use_graph
+ *                    != 0 replays a CUDA graph captured on the first call (and
+ *                    again whenever the arguments or the configuration change).
+ * cow_batch_set_config : tile_cfg 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8
+ *                    pixels per CTA; ctas_per_sm resident CTAs per SM (1..32).
+ * cow_batch_tune   : times every (tile_cfg, ctas_per_sm in {2,3,4,6,8}) on the
+ *                    set views (reps renders each, into out_rgb) and keeps the
+ *                    fastest; reports it and its time per batch in ms.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+typedef struct cow_batch cow_batch;
+cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, cow_batch **out);
+cow_status cow_batch_free(cow_batch *b);
+cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                               const int32_t *ids_offsets, int64_t *out_pixels);
+cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                            float *out_aux, int32_t *out_nsamp, int32_t use_graph, void *stream);
+cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm);
+cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb, int32_t reps,
+                          void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms);
+
 /* Render independent rays (Sec. 4.2 training-stage form: each ray composites
  * the given blocks in the xy-distance order of its own origin, App. D).
  *   o, d        : device float32 n_rays x 3 origins and unit directions.

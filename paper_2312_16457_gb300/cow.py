@@ -25,7 +25,9 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_set_schedule", "cow_sync_check", "cow_export_occupancy",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
-           "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_last_error", "cow_version"]
+           "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
+           "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune", "cow_last_error",
+           "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1}
 
 
@@ -76,6 +78,12 @@ def lib():
             "cow_update_features": [P, i32, P, P, P, P, P],
             "cow_adam_step": [P, P, P, P, i64, flt, flt, flt, flt, i32, P],
             "cow_mse_grad": [P, P, i64, P, P, P],
+            "cow_batch_create": [P, i32, i32, P],
+            "cow_batch_free": [P],
+            "cow_batch_set_views": [P, P, i32, P, P, P],
+            "cow_batch_render": [P, P, flt, u32, P, P, P, i32, P],
+            "cow_batch_set_config": [P, i32, i32],
+            "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -298,3 +306,54 @@ def mse_grad(rgb: torch.Tensor, target: torch.Tensor, stream=None):
     _check(lib().cow_mse_grad(_ptr(rgb.contiguous()), _ptr(target.contiguous()), rgb.numel(), _ptr(g), _ptr(loss),
                               _stream_ptr(stream)))
     return g, loss
+
+
+class Batch:
+    """Many cameras rendered by one persistent launch (cow_batch_*)."""
+
+    TILE_SHAPES = {0: (16, 8), 1: (8, 8), 2: (16, 16), 3: (32, 8)}
+
+    def __init__(self, ctx: Context, max_views: int, max_ids: int):
+        self.ctx = ctx
+        self._b = C.c_void_p()
+        _check(lib().cow_batch_create(ctx._ctx, int(max_views), int(max_ids), C.byref(self._b)))
+        self.n_pixels = 0
+
+    def close(self):
+        if self._b:
+            lib().cow_batch_free(self._b)
+            self._b = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_views(self, cams, ids_per_view) -> int:
+        cams = list(cams)
+        cc = (Camera * len(cams))(*[_camera(c) for c in cams])
+        offs = np.zeros(len(cams) + 1, np.int32)
+        for v, ids in enumerate(ids_per_view):
+            offs[v + 1] = offs[v] + len(ids)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(i, np.int32) for i in ids_per_view])
+                                    if offs[-1] > 0 else np.zeros(1, np.int32), np.int32)
+        n = C.c_int64()
+        _check(lib().cow_batch_set_views(self._b, cc, len(cams), _ptr(flat), _ptr(offs), C.byref(n)))
+        self.n_pixels = n.value
+        return n.value
+
+    def render(self, mlp, out_rgb, out_aux=None, out_nsamp=None, ert_eps: float = 0.0, mlp_bf16: bool = False,
+               graph: bool = False, stream=None):
+        _check(lib().cow_batch_render(self._b, _ptr(mlp), float(ert_eps), FLAG_MLP_BF16 if mlp_bf16 else 0,
+                                      _ptr(out_rgb), _ptr(out_aux), _ptr(out_nsamp), 1 if graph else 0,
+                                      _stream_ptr(stream)))
+
+    def set_config(self, tile_cfg: int, ctas_per_sm: int):
+        _check(lib().cow_batch_set_config(self._b, int(tile_cfg), int(ctas_per_sm)))
+
+    def tune(self, mlp, out_rgb, ert_eps: float = 0.0, mlp_bf16: bool = False, reps: int = 2, stream=None):
+        t, c, ms = C.c_int32(), C.c_int32(), C.c_float()
+        _check(lib().cow_batch_tune(self._b, _ptr(mlp), float(ert_eps), FLAG_MLP_BF16 if mlp_bf16 else 0,
+                                    _ptr(out_rgb), int(reps), _stream_ptr(stream), C.byref(t), C.byref(c), C.byref(ms)))
+        return t.value, c.value, ms.value

@@ -1,0 +1,296 @@
+// batch_api.cu -- C ABI of the batched form: many cameras of uneven size and
+// LOD set served by one persistent launch (K8), optionally replayed from a
+// CUDA graph, with the tile shape and the number of resident CTAs picked by
+// an autotuner that times the candidates on the batch itself.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "cow_internal.h"
+
+using namespace cowi;
+
+struct cow_batch {
+    cow_ctx *ctx = nullptr;
+    int32_t max_views = 0, max_ids = 0;
+    // staging: [hdr 256 B | views max_views x ViewRec | recs max_ids x BlockRec]
+    size_t stage_bytes = 0, views_off = 256, recs_off = 0;
+    unsigned char *h_stage = nullptr;  // pinned
+    unsigned char *d_stage = nullptr;
+    unsigned *d_counter = nullptr;
+    cudaEvent_t copied = nullptr;      // the last H2D copy of h_stage has run
+    cudaStream_t cap_stream = nullptr; // stream for graph capture
+    // views of the current batch
+    std::vector<cow_camera> cams;
+    std::vector<int32_t> ids, offs;
+    int64_t n_pixels = 0;
+    int32_t n_items = 0;
+    bool dirty = true;                 // staging must be rebuilt
+    int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
+    int sms = 0;
+    // captured graph and the arguments it was captured with
+    cudaGraphExec_t exec = nullptr;
+    cow::BatchArgs gargs;
+    int g_tile = -1, g_grid = -1;
+};
+
+namespace {
+
+void batch_destroy(cow_batch *b) {
+    if (!b) return;
+    DeviceGuard dg(b->ctx ? b->ctx->device : 0);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->copied) cudaEventDestroy(b->copied);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFreeHost(b->h_stage);
+    cudaFree(b->d_stage);
+    cudaFree(b->d_counter);
+    delete b;
+}
+
+// Build the pinned staging (header, view records, block records) for the
+// current cameras and tile shape.
+cow_status build_stage(cow_batch *b) {
+    cudaError_t e = cudaEventSynchronize(b->copied);  // the previous copy has read h_stage
+    if (e != cudaSuccess) return fail(COW_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+    int tw, th;
+    cow::batch_tile_shape(b->tile_cfg, &tw, &th);
+    const int32_t nv = (int32_t)b->cams.size();
+    cow::ViewRec *vr = (cow::ViewRec *)(b->h_stage + b->views_off);
+    cow::BlockRec *br = (cow::BlockRec *)(b->h_stage + b->recs_off);
+    int64_t tiles = 0, pix = 0;
+    for (int32_t v = 0; v < nv; v++) {
+        const cow_camera &cam = b->cams[(size_t)v];
+        cow::ViewRec &r = vr[v];
+        std::memset(&r, 0, sizeof(r));
+        for (int rr = 0; rr < 3; rr++) {
+            for (int k = 0; k < 3; k++) r.Rm[3 * rr + k] = (float)cam.c2w[4 * rr + k];
+            r.o[rr] = (float)cam.c2w[4 * rr + 3];
+        }
+        r.f = (float)focal_length(cam.height, cam.fov_y_deg);
+        r.W = cam.width;
+        r.H = cam.height;
+        r.tiles_x = (cam.width + tw - 1) / tw;
+        r.tile_begin = (int32_t)tiles;
+        r.ids_begin = b->offs[(size_t)v];
+        r.ids_count = b->offs[(size_t)v + 1] - b->offs[(size_t)v];
+        r.pix_offset = pix;
+        tiles += (int64_t)r.tiles_x * ((cam.height + th - 1) / th);
+        pix += (int64_t)cam.width * cam.height;
+    }
+    if (tiles > 0x7fffffff) return fail(COW_ERR_INVALID_ARG, "too many tiles in one batch");
+    for (size_t k = 0; k < b->ids.size(); k++) br[k] = b->ctx->recs[(size_t)b->ids[k]];
+    int32_t *hdr = (int32_t *)b->h_stage;
+    hdr[0] = nv;
+    hdr[1] = (int32_t)tiles;
+    b->n_items = (int32_t)tiles;
+    b->n_pixels = pix;
+    b->dirty = false;
+    return COW_OK;
+}
+
+cow::BatchArgs make_args(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *rgb, float *aux,
+                         int32_t *ns) {
+    cow::BatchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.hdr = (const int32_t *)b->d_stage;
+    a.views = (const cow::ViewRec *)(b->d_stage + b->views_off);
+    a.recs = (const cow::BlockRec *)(b->d_stage + b->recs_off);
+    a.mlp = mlp;
+    a.ert_eps = ert_eps;
+    a.flags = flags;
+    a.dtype = b->ctx->dtype;
+    a.out_rgb = rgb;
+    a.out_aux = aux;
+    a.out_nsamp = ns;
+    a.err = b->ctx->d_err;
+    a.counter = b->d_counter;
+    return a;
+}
+
+// The batch on one stream: staging copy, queue reset, persistent launch.
+// `mark` records b->copied after the copy (not inside a graph capture: a
+// captured event cannot be waited on from outside; graph launches record it
+// after the whole graph instead).
+cudaError_t enqueue(cow_batch *b, const cow::BatchArgs &a, int tile_cfg, int grid, cudaStream_t st, bool mark) {
+    cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage, b->stage_bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && mark) e = cudaEventRecord(b->copied, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = cow::launch_march_batch(a, tile_cfg, grid, st);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, cow_batch **out) {
+    g_last_error.clear();
+    if (!ctx || !out || max_views < 1 || max_ids < 0 || max_views > (1 << 16) || max_ids > (1 << 22))
+        return fail(COW_ERR_INVALID_ARG, "cow_batch_create: bad argument");
+    *out = nullptr;
+    DeviceGuard dg(ctx->device);
+    cow_batch *b = new cow_batch();
+    b->ctx = ctx;
+    b->max_views = max_views;
+    b->max_ids = max_ids;
+    b->recs_off = (b->views_off + (size_t)max_views * sizeof(cow::ViewRec) + 255) & ~(size_t)255;
+    b->stage_bytes = b->recs_off + (size_t)std::max(max_ids, 1) * sizeof(cow::BlockRec);
+    cudaError_t e = cudaHostAlloc((void **)&b->h_stage, b->stage_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_stage, b->stage_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_counter, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) {
+        batch_destroy(b);
+        return fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "cow_batch_create: %s",
+                    cudaGetErrorString(e));
+    }
+    std::memset(b->h_stage, 0, b->stage_bytes);
+    *out = b;
+    return COW_OK;
+}
+
+cow_status cow_batch_free(cow_batch *b) {
+    batch_destroy(b);
+    return COW_OK;
+}
+
+cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                               const int32_t *ids_offsets, int64_t *out_pixels) {
+    g_last_error.clear();
+    if (!b || !cams || n_views < 1 || !ids_offsets) return fail(COW_ERR_INVALID_ARG, "cow_batch_set_views: null argument");
+    if (n_views > b->max_views) return fail(COW_ERR_INVALID_ARG, "%d views exceed the batch's %d", n_views, b->max_views);
+    const int32_t n_ids = ids_offsets[n_views];
+    if (ids_offsets[0] != 0 || n_ids < 0 || n_ids > b->max_ids)
+        return fail(COW_ERR_INVALID_ARG, "ids_offsets must start at 0 and end at most at %d", b->max_ids);
+    if (n_ids > 0 && !ids) return fail(COW_ERR_INVALID_ARG, "null ids");
+    const int32_t nb = (int32_t)b->ctx->blocks.size();
+    for (int32_t v = 0; v < n_views; v++) {
+        const cow_camera &c = cams[v];
+        if (c.width < 1 || c.height < 1 || c.width > 32768 || c.height > 32768 || !(c.fov_y_deg > 0.0 && c.fov_y_deg < 180.0))
+            return fail(COW_ERR_INVALID_ARG, "view %d: bad camera", v);
+        if (ids_offsets[v + 1] < ids_offsets[v]) return fail(COW_ERR_INVALID_ARG, "ids_offsets must be non-decreasing");
+    }
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    DeviceGuard dg(b->ctx->device);
+    b->cams.assign(cams, cams + n_views);
+    b->ids.assign(ids, ids + n_ids);
+    b->offs.assign(ids_offsets, ids_offsets + n_views + 1);
+    cow_status rc = build_stage(b);
+    if (rc != COW_OK) return rc;
+    if (out_pixels) *out_pixels = b->n_pixels;
+    return COW_OK;
+}
+
+cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                            float *out_aux, int32_t *out_nsamp, int32_t use_graph, void *stream) {
+    g_last_error.clear();
+    if (!b || !mlp || !out_rgb) return fail(COW_ERR_INVALID_ARG, "cow_batch_render: null argument");
+    if (b->cams.empty()) return fail(COW_ERR_INVALID_ARG, "cow_batch_render: no views set");
+    if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
+    if (flags & ~COW_FLAG_MLP_BF16) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    for (const void *q : {(const void *)mlp, (const void *)out_rgb})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "the MLP and the outputs must be device memory");
+    if ((out_aux && (!is_device_ptr(out_aux) || ((uintptr_t)out_aux & 15u))) || (out_nsamp && !is_device_ptr(out_nsamp)))
+        return fail(COW_ERR_INVALID_ARG, "aux / nsamp must be device memory (aux 16-byte aligned)");
+    DeviceGuard dg(b->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->dirty) {
+        cow_status rc = build_stage(b);
+        if (rc != COW_OK) return rc;
+    }
+    const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp);
+    const int grid = std::max(1, b->sms * b->ctas_per_sm);
+    if (!use_graph) {
+        COW_CUDA(enqueue(b, a, b->tile_cfg, grid, st, true));
+        return COW_OK;
+    }
+    const bool same = b->exec && b->g_tile == b->tile_cfg && b->g_grid == grid &&
+                      std::memcmp(&b->gargs, &a, sizeof(a)) == 0;
+    if (!same) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        // capture on the batch's own stream: the caller's may be the legacy stream
+        COW_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = enqueue(b, a, b->tile_cfg, grid, b->cap_stream, false);
+        cudaGraph_t graph = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (ce != cudaSuccess || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return fail(COW_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+        }
+        cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return fail(COW_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+        b->gargs = a;
+        b->g_tile = b->tile_cfg;
+        b->g_grid = grid;
+    }
+    COW_CUDA(cudaGraphLaunch(b->exec, st));
+    COW_CUDA(cudaEventRecord(b->copied, st));
+    return COW_OK;
+}
+
+cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm) {
+    if (!b || tile_cfg < 0 || tile_cfg > 3 || ctas_per_sm < 1 || ctas_per_sm > 32)
+        return fail(COW_ERR_INVALID_ARG, "cow_batch_set_config: bad argument");
+    if (tile_cfg != b->tile_cfg) b->dirty = true;
+    b->tile_cfg = tile_cfg;
+    b->ctas_per_sm = ctas_per_sm;
+    return COW_OK;
+}
+
+cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb, int32_t reps,
+                          void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms) {
+    g_last_error.clear();
+    if (!b || !mlp || !out_rgb || reps < 1) return fail(COW_ERR_INVALID_ARG, "cow_batch_tune: bad argument");
+    if (b->cams.empty()) return fail(COW_ERR_INVALID_ARG, "cow_batch_tune: no views set");
+    DeviceGuard dg(b->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    COW_CUDA(cudaEventCreate(&e0));
+    COW_CUDA(cudaEventCreate(&e1));
+    static const int kCtas[] = {2, 3, 4, 6, 8};
+    float best = 3.0e38f;
+    int best_t = b->tile_cfg, best_c = b->ctas_per_sm;
+    cow_status rc = COW_OK;
+    for (int t = 0; t < 4 && rc == COW_OK; t++) {
+        for (int c : kCtas) {
+            rc = cow_batch_set_config(b, t, c);
+            if (rc != COW_OK) break;
+            rc = cow_batch_render(b, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, 0, stream);  // warm-up
+            if (rc != COW_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && rc == COW_OK; r++)
+                rc = cow_batch_render(b, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, 0, stream);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(COW_ERR_CUDA, "cow_batch_tune: synchronisation failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < best) {
+                best = ms;
+                best_t = t;
+                best_c = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != COW_OK) return rc;
+    cow_batch_set_config(b, best_t, best_c);
+    if (out_tile_cfg) *out_tile_cfg = best_t;
+    if (out_ctas_per_sm) *out_ctas_per_sm = best_c;
+    if (out_ms) *out_ms = best;
+    return COW_OK;
+}
+
+}  // extern "C"

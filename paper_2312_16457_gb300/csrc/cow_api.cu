@@ -12,11 +12,9 @@
 #include <string>
 #include <vector>
 
-#include "cow.h"
-#include "cow_common.cuh"
-#include "cow_kernels.h"
+#include "cow_internal.h"
 
-namespace {
+namespace cowi {
 
 thread_local std::string g_last_error;
 
@@ -30,15 +28,6 @@ cow_status fail(cow_status st, const char *fmt, ...) {
     return st;
 }
 
-#define COW_CUDA(call)                                                                      \
-    do {                                                                                    \
-        cudaError_t e_ = (call);                                                            \
-        if (e_ != cudaSuccess) {                                                            \
-            return fail(e_ == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA,       \
-                        "%s failed: %s", #call, cudaGetErrorString(e_));                    \
-        }                                                                                   \
-    } while (0)
-
 bool is_device_ptr(const void *p) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -48,18 +37,11 @@ bool is_device_ptr(const void *p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-// Restores the caller's current device when it leaves scope.
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+}  // namespace cowi
+
+using namespace cowi;
+
+namespace {
 
 int elem_bytes(int dtype) { return dtype == COW_FP32 ? 4 : dtype == COW_FP8_E4M3 ? 1 : 2; }
 
@@ -75,55 +57,7 @@ int fp8_exponent(float amax) {
     return e;
 }
 
-struct DevBuf {
-    void *p = nullptr;
-    size_t cap = 0;
-    cudaError_t reserve(size_t bytes) {
-        if (bytes <= cap) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        cudaError_t e = cudaMalloc(&p, bytes);
-        if (e == cudaSuccess) cap = bytes;
-        return e;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-};
-
-struct BlockHost {
-    float lo[3], hi[3];
-    int32_t lod, parent, R, P;
-    void *grid = nullptr;
-    void *planes[3] = {nullptr, nullptr, nullptr};
-    uint32_t *occ = nullptr;
-    float *scale = nullptr;
-    int32_t scale_exp[4][8];
-    int64_t occ_words = 0;
-    double ztop = 0.0;
-    std::vector<int32_t> children;
-};
-
 }  // namespace
-
-struct cow_ctx {
-    int device = 0;
-    int dtype = 0;
-    int occ_cell = 4;
-    float occ_thresh = 0.01f;
-    int schedule = COW_SCHED_THREAD;
-    std::vector<BlockHost> blocks;
-    cow::BlockRec *d_blocks = nullptr;
-    std::vector<cow::BlockRec> recs;  // host copy of d_blocks
-    unsigned *d_err = nullptr;
-    float *d_mlp = nullptr;
-    DevBuf views, ids, out_rgb, out_aux, out_nsamp;
-    DevBuf gptrs, partials;  // backward: per-block gradient pointers, per-CTA MLP-gradient rows
-    DevBuf staging;          // host masters of cow_update_features
-};
 
 namespace {
 
@@ -150,7 +84,6 @@ void destroy(cow_ctx *c) {
     delete c;
 }
 
-double focal_length(int32_t H, double fov_y_deg) { return (0.5 * (double)H) / tan(0.5 * fov_y_deg * M_PI / 180.0); }
 
 // height of the highest occupied part of a block
 double block_ztop(const BlockHost &b, const std::vector<uint32_t> &bits, int C) {

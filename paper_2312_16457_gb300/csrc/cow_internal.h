@@ -1,0 +1,98 @@
+// cow_internal.h -- host-side context and helpers shared by the libcow
+// translation units (not part of the C ABI).
+#pragma once
+
+#include <cmath>
+#include <cstdarg>
+#include <string>
+#include <vector>
+
+#include "cow.h"
+#include "cow_common.cuh"
+#include "cow_kernels.h"
+
+namespace cowi {
+
+extern thread_local std::string g_last_error;
+
+// Record a message for cow_last_error and return `st`.
+cow_status fail(cow_status st, const char *fmt, ...);
+
+bool is_device_ptr(const void *p);
+
+#define COW_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            return cowi::fail(e_ == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, \
+                              "%s failed: %s", #call, cudaGetErrorString(e_));              \
+        }                                                                                   \
+    } while (0)
+
+// Restores the caller's current device when it leaves scope.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// A device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    cudaError_t reserve(size_t bytes) {
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct BlockHost {
+    float lo[3], hi[3];
+    int32_t lod, parent, R, P;
+    void *grid = nullptr;
+    void *planes[3] = {nullptr, nullptr, nullptr};
+    uint32_t *occ = nullptr;
+    float *scale = nullptr;
+    int32_t scale_exp[4][8];
+    int64_t occ_words = 0;
+    double ztop = 0.0;
+    std::vector<int32_t> children;
+};
+
+inline double focal_length(int32_t H, double fov_y_deg) {
+    return (0.5 * (double)H) / tan(0.5 * fov_y_deg * M_PI / 180.0);
+}
+
+}  // namespace cowi
+
+struct cow_ctx {
+    int device = 0;
+    int dtype = 0;
+    int occ_cell = 4;
+    float occ_thresh = 0.01f;
+    int schedule = COW_SCHED_THREAD;
+    std::vector<cowi::BlockHost> blocks;
+    cow::BlockRec *d_blocks = nullptr;
+    std::vector<cow::BlockRec> recs;  // host copy of d_blocks
+    unsigned *d_err = nullptr;
+    float *d_mlp = nullptr;
+    cowi::DevBuf views, ids, out_rgb, out_aux, out_nsamp;
+    cowi::DevBuf gptrs, partials;  // backward: per-block gradient pointers, per-CTA MLP-gradient rows
+    cowi::DevBuf staging;          // host masters of cow_update_features
+};

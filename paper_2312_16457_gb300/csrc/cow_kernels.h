@@ -62,6 +62,26 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n,
                         float eps, int step, cudaStream_t st);
 cudaError_t launch_mse_grad(const float *rgb, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);
 
+// K8: persistent batched renderer (batch.cu)
+struct BatchArgs {
+    const int32_t *hdr;      // device: n_views, n_items (tiles of all views)
+    const ViewRec *views;    // tile_begin ascending
+    const BlockRec *recs;    // the views' block records, near to far, by ViewRec::ids_begin
+    const float *mlp;        // 499 FP32 (device)
+    float ert_eps;
+    uint32_t flags;
+    int32_t dtype;
+    int32_t pad0;
+    float *out_rgb;
+    float *out_aux;          // may be null
+    int32_t *out_nsamp;      // may be null
+    unsigned *err;
+    unsigned *counter;       // work-queue head, zero at launch
+};
+// tile_cfg: 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8 pixels per CTA
+void batch_tile_shape(int tile_cfg, int *tw, int *th);
+cudaError_t launch_march_batch(const BatchArgs &a, int tile_cfg, int grid, cudaStream_t st);
+
 // K4 / K5: packing and occupancy (pack.cu)
 cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cudaStream_t st);
 // FP32 packs in the natural layout; FP16 / BF16 / FP8 in the pair layout

@@ -33,78 +33,7 @@ constexpr int kMinBlocksW = COW_MARCH_MIN_BLOCKS_W;
 constexpr int kMaxSmemRecs = 96;                  // block records a CTA stages in shared memory
 constexpr unsigned kWaitPolls = 1u << 24;         // bound on mbarrier polls
 
-struct RayState {
-    float Cd[3], F[4], T;
-    int nsamp;
-    bool done;
-};
 
-// March one ray through one block, updating its state (Eq. 1-2).
-template <int DT>
-__device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3],
-                                            const float inv_d[3], float omax, float ert_eps, RayState &s,
-                                            unsigned *err) {
-    const float delta = b.delta;
-    const bool more = for_each_sample(b, o, d, inv_d, omax, err, [&](const float p[3], const float g[3]) {
-        float2 f2[4];
-        accumulate_sample<DT>(b, p, g, f2);
-        const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
-        const float sigma = __expf(f[0]);
-        const float e = __expf(-sigma * delta);
-        const float w = s.T * (1.f - e);
-#pragma unroll
-        for (int c = 0; c < 3; c++) s.Cd[c] = fmaf(w, sigmoidf_fast(f[1 + c]), s.Cd[c]);
-#pragma unroll
-        for (int c = 0; c < 4; c++) s.F[c] = fmaf(w, sigmoidf_fast(f[4 + c]), s.F[c]);
-        s.T *= e;
-        s.nsamp++;
-        return !(s.T < ert_eps);
-    });
-    if (!more) s.done = true;
-}
-
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// Deferred MLP (Eq. 3) from weights in shared memory.
-__device__ __forceinline__ void deferred_mlp(const float *w, const float x_in[10], bool bf16, float out[3]) {
-    float x[10];
-#pragma unroll
-    for (int i = 0; i < 10; i++) x[i] = bf16 ? bf16r(x_in[i]) : x_in[i];
-    float h1[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) {
-        float a = w[kOffB1 + j];
-#pragma unroll
-        for (int i = 0; i < 10; i++) a = fmaf(x[i], w[kOffW1 + i * 16 + j], a);
-        a = fmaxf(a, 0.f);
-        h1[j] = bf16 ? bf16r(a) : a;
-    }
-    float h2[16];
-#pragma unroll
-    for (int j = 0; j < 16; j++) {
-        float a = w[kOffB2 + j];
-#pragma unroll
-        for (int i = 0; i < 16; i++) a = fmaf(h1[i], w[kOffW2 + i * 16 + j], a);
-        a = fmaxf(a, 0.f);
-        h2[j] = bf16 ? bf16r(a) : a;
-    }
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-        float a = w[kOffB3 + j];
-#pragma unroll
-        for (int i = 0; i < 16; i++) a = fmaf(h2[i], w[kOffW3 + i * 3 + j], a);
-        out[j] = sigmoidf_fast(a);
-    }
-}
-
-__device__ __forceinline__ void load_mlp(const float *g, float *s, bool bf16) {
-    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
-        const float v = __ldg(g + i);
-        // biases stay FP32 (they add into the FP32 accumulator)
-        const bool is_bias = (i >= kOffB1 && i < kOffW2) || (i >= kOffB2 && i < kOffW3) || i >= kOffB3;
-        s[i] = (bf16 && !is_bias) ? bf16r(v) : v;
-    }
-}
 
 __device__ __forceinline__ void write_outputs(const MarchArgs &a, int64_t row, const RayState &s, const float d[3],
                                               const float *w_mlp) {

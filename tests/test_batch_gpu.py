@@ -1,0 +1,93 @@
+"""Batched form (one persistent launch over a (view, tile, block) queue):
+every pixel has the per-view kernel's occupied samples (bit for bit) and its
+colour up to FP32 rounding (the two kernels inline the same code but the
+compiler may fuse multiply-adds differently), for every tile shape, with and
+without CUDA-graph replay and after autotuning; one view is also checked
+against the FP64 oracle directly."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2312_16457_gb300 import cow, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2312_16457_gb300 import build
+
+    build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def _scene():
+    sc = synth.city_scene(31, 8, 2.0, [(16, 40), (12, 24), (8, 16)], lod_thresh=[5.0, 10.0, 0.0])
+    cams = synth.random_aerial_cameras(9, 12, 8.0, (3.0, 14.0), [(96, 54), (64, 64), (40, 23), (131, 77)])
+    cams.append(synth.camera((0.0, -9.0, 6.0), (0.0, 0.0, -1.0), 57, 33, 60.0))
+    return sc, cams, synth.mlp_weights(7)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp32"])
+def test_batch_equals_per_view(storage):
+    sc, cams, mlp = _scene()
+    ctx = cow.Context(sc, storage)
+    ids = [ctx.select_lod(c, sc.lod_thresh) for c in cams]
+    mlp_d = torch.from_numpy(mlp).cuda()
+    ref = ctx.render(cams, ids, mlp_d, nsamp=True)  # no early termination: sample sets must match exactly
+    ref_ert = ctx.render(cams, ids, mlp_d, ert_eps=1e-5, aux=False)[0]
+    ctx.sync_check()
+    b = cow.Batch(ctx, 16, 4096)
+    n = b.set_views(cams, ids)
+    assert n == sum(c.width * c.height for c in cams)
+    for cfg in range(4):
+        for graph in (False, True):
+            b.set_config(cfg, 3)
+            out = (torch.full((n, 3), -1.0, device="cuda"), torch.zeros((n, 8), device="cuda"),
+                   torch.zeros(n, dtype=torch.int32, device="cuda"))
+            for _ in range(2):
+                b.render(mlp_d, *out, graph=graph)
+            ctx.sync_check()
+            assert torch.equal(out[2], ref[2]), (cfg, graph)
+            for k in range(2):
+                diff = float((out[k] - ref[k]).abs().max())
+                assert diff <= 2e-6, (cfg, graph, k, diff)
+    t, c, ms = b.tune(mlp_d, torch.empty((n, 3), device="cuda"), ert_eps=1e-5)
+    assert t in range(4) and c in (2, 3, 4, 6, 8) and ms > 0
+    out = torch.empty((n, 3), device="cuda")
+    b.render(mlp_d, out, ert_eps=1e-5, graph=True)
+    ctx.sync_check()
+    assert float((out - ref_ert).abs().max()) <= 1e-4  # early termination changes each channel by <= eps
+    b.close()
+
+
+def test_batch_view_against_oracle():
+    sc, cams, mlp = _scene()
+    ctx = cow.Context(sc, "fp32")
+    cam = cams[-1]
+    ids = ctx.select_lod(cam, sc.lod_thresh)
+    b = cow.Batch(ctx, 1, 256)
+    n = b.set_views([cam], [ids])
+    out = (torch.empty((n, 3), device="cuda"), None, torch.empty(n, dtype=torch.int32, device="cuda"))
+    b.render(torch.from_numpy(mlp).cuda(), out[0], None, out[2])
+    ctx.sync_check()
+    osc = oracle.OracleScene(sc)
+    r_o, _, n_o = oracle.render_view(osc, cam, ids, mlp)
+    assert np.array_equal(out[2].cpu().numpy(), n_o)
+    assert np.abs(out[0].cpu().numpy() - r_o).max() <= 1e-4
+
+
+def test_batch_rejects_bad_arguments():
+    sc, cams, mlp = _scene()
+    ctx = cow.Context(sc, "fp32")
+    b = cow.Batch(ctx, 2, 8)
+    with pytest.raises(cow.CowError):
+        b.set_views(cams[:3], [[0]] * 3)  # more views than the batch holds
+    with pytest.raises(cow.CowError):
+        b.set_views(cams[:1], [list(range(9))])  # more ids than the batch holds
+    with pytest.raises(cow.CowError):
+        b.set_config(7, 2)
