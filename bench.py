@@ -34,6 +34,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
+# DRAM bytes (read + write) of one k_march_views launch from an ncu capture of
+# the default workload (profiles/march_views_city_lod_1080p_traffic.md); valid
+# for the marcher revision named here and null for any other configuration.
+MARCH_REVISION = "v4-thread-pair256"
+MEASURED_TRAFFIC = {("city_lod_1080p", "bf16", "thread", 1): 49749571328 + 27278080}
 L2_FLUSH_BYTES = 512 << 20
 GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160}  # per occupied sample: 20 texels x 8 ch
 
@@ -324,7 +329,9 @@ def run_cow(args, ws, rank, local):
         **fp32,
         "roofline": {"bound": "gather", "kernel": "k_march_views", "achieved": round(achieved, 1),
                      "peak": round(peak_l1, 1), "unit": "GB/s", "frac": round(achieved / peak_l1, 3),
-                     "traffic": None,
+                     "traffic": MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div)),
+                     "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, marcher "
+                                       f"{MARCH_REVISION}",
                      "peak_source": f"measured live: random {width}-byte gathers from a 64 KiB (L1-resident) "
                                     "buffer, cow_gather_peak",
                      "levels_gbs": {"l1_gather": round(peak_l1, 1), "l2_gather": round(peak_l2, 1),
