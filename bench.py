@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--res-div", type=int, default=1, help="divide grid / plane resolutions (profiling runs)")
     ap.add_argument("--schedule", choices=["warp", "thread"], default="thread", help="marching schedule")
+    ap.add_argument("--strip", type=int, default=0, help="tile order: 0 raster, k strips of k tile columns")
     return ap.parse_args()
 
 
@@ -225,6 +226,7 @@ def run_cow(args, ws, rank, local):
     storage = args.storage or storage
     ctx = cow.Context(sc, storage)
     ctx.set_schedule(args.schedule)
+    ctx.set_tile_order(args.strip)
     ids = block_ids(ctx, sc, cam)
     ctx32 = cow.Context(sc, "fp32") if (not args.no_fp32 and storage != "fp32") else None
     if ctx32 is not None:
@@ -280,6 +282,16 @@ def run_cow(args, ws, rank, local):
     h2d = 80 + 4 * len(ids) + 4 * 499 + 4 * 2  # camera record, ids, MLP, offsets
     d2h = npix * 12
 
+    # the same frame through the persistent batched path (one view, autotuned)
+    batch = cow.Batch(ctx, 1, len(ids))
+    batch.set_views([cam], [ids])
+    tile, ctas, _ = batch.tune(mlp_d, out[0], ert_eps=args.ert)
+    tb = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), max(5, args.steps // 2), 3,
+                    flush, stream)
+    batch_path = {"frames_per_s": round(1000.0 / float(np.mean(tb)), 3), "tile": cow.Batch.TILE_SHAPES[tile],
+                  "ctas_per_sm": ctas}
+    batch.close()
+
     # plain FP32 storage, same frame
     fp32 = {}
     if ctx32 is not None:
@@ -319,12 +331,13 @@ def run_cow(args, ws, rank, local):
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "scene": desc, "storage": storage, "n_blocks_selected": int(len(ids)),
-                   "schedule": args.schedule,
+                   "schedule": args.schedule, "tile_strip": args.strip,
                    "width": cam.width, "height": cam.height, "ert_eps": args.ert,
                    "l2": "512 MiB write between timed steps, outside the per-step events",
                    "parallelism": f"replicas x{ws}"},
         "mrays_per_s": round(value * npix / 1e6, 3),
         "occupied_samples_per_frame": n_samples,
+        "batched_path_same_frame": batch_path,
         "samples_per_ray": round(n_samples / npix, 2),
         **fp32,
         "roofline": {"bound": "gather", "kernel": "k_march_views", "achieved": round(achieved, 1),

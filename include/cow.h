@@ -277,6 +277,12 @@ cow_status cow_mse_grad(const float *rgb, const float *target, int64_t n, float 
 #define COW_SCHED_THREAD 1
 cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule);
 
+/* Order in which cow_render launches the screen tiles of a view (the image is
+ * the same): 0 = raster order; k > 0 = vertical strips of k tile columns,
+ * each walked row by row, so the tiles in flight cover a compact screen
+ * region (their rays share more texels in L2).  Errors: INVALID_ARG. */
+cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles);
+
 /* Wait for the stream and report a device-side error word set by a kernel of
  * this context (COW_ERR_DEVICE_ASSERT or COW_ERR_TIMEOUT); clears it. */
 cow_status cow_sync_check(cow_ctx *ctx, void *stream);

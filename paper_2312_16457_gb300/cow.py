@@ -23,7 +23,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
-           "cow_render", "cow_render_rays", "cow_set_schedule", "cow_sync_check", "cow_export_occupancy",
+           "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_sync_check", "cow_export_occupancy",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune", "cow_last_error",
@@ -70,6 +70,7 @@ def lib():
             "cow_render_rays": [P, P, P, i64, P, i32, P, flt, u32, P, P, P, P],
             "cow_sync_check": [P, P],
             "cow_set_schedule": [P, i32],
+            "cow_set_tile_order": [P, i32],
             "cow_export_occupancy": [P, i32, P, i64],
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
@@ -260,6 +261,10 @@ class Context:
         """"warp" (one ray per warp, default) or "thread" (one ray per thread)."""
         _check(lib().cow_set_schedule(self._ctx, SCHEDULES[name]))
         self.schedule = name
+
+    def set_tile_order(self, strip_tiles: int):
+        """0: raster tile order; k > 0: vertical strips of k tile columns."""
+        _check(lib().cow_set_tile_order(self._ctx, int(strip_tiles)))
 
     def sync_check(self, stream=None):
         _check(lib().cow_sync_check(self._ctx, _stream_ptr(stream)))

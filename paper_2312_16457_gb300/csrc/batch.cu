@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(TW * TH) k_march_batch(BatchArgs a) {
     constexpr int kNT = TW * TH;
     constexpr int kWarpsX = TW / 8;
     __shared__ float s_mlp[kMlpParams + 1];
-    __shared__ alignas(16) BlockRec s_rec[kMaxBatchRecs];
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // a.smem_recs block records
+    BlockRec *s_rec = reinterpret_cast<BlockRec *>(s_dyn);
     __shared__ alignas(8) uint64_t s_bar;
     __shared__ int s_item, s_n;
     __shared__ unsigned char s_keep[kMaxBatchRecs];
@@ -96,7 +97,7 @@ __global__ void __launch_bounds__(TW * TH) k_march_batch(BatchArgs a) {
         const int n_blk = v.ids_count;
         if (lo != cur_view) {
             cur_view = lo;
-            staged = n_blk > 0 && n_blk <= kMaxBatchRecs;
+            staged = n_blk > 0 && n_blk <= a.smem_recs;
             if (staged) {
                 // thread 0 copies and waits (bounded); the CTA then proceeds or
                 // leaves as one, so no thread is left at a later barrier
@@ -190,11 +191,12 @@ __global__ void __launch_bounds__(TW * TH) k_march_batch(BatchArgs a) {
 
 template <int DT>
 cudaError_t launch_dt(const BatchArgs &a, int tile_cfg, int grid, cudaStream_t st) {
+    const size_t smem = (size_t)a.smem_recs * sizeof(BlockRec);
     switch (tile_cfg) {
-    case 0: k_march_batch<DT, 16, 8><<<grid, 128, 0, st>>>(a); break;
-    case 1: k_march_batch<DT, 8, 8><<<grid, 64, 0, st>>>(a); break;
-    case 2: k_march_batch<DT, 16, 16><<<grid, 256, 0, st>>>(a); break;
-    case 3: k_march_batch<DT, 32, 8><<<grid, 256, 0, st>>>(a); break;
+    case 0: k_march_batch<DT, 16, 8><<<grid, 128, smem, st>>>(a); break;
+    case 1: k_march_batch<DT, 8, 8><<<grid, 64, smem, st>>>(a); break;
+    case 2: k_march_batch<DT, 16, 16><<<grid, 256, smem, st>>>(a); break;
+    case 3: k_march_batch<DT, 32, 8><<<grid, 256, smem, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -25,6 +25,7 @@ struct cow_batch {
     std::vector<int32_t> ids, offs;
     int64_t n_pixels = 0;
     int32_t n_items = 0;
+    int32_t max_blk = 0;               // longest block list of a view
     bool dirty = true;                 // staging must be rebuilt
     int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
     int sms = 0;
@@ -59,7 +60,9 @@ cow_status build_stage(cow_batch *b) {
     cow::ViewRec *vr = (cow::ViewRec *)(b->h_stage + b->views_off);
     cow::BlockRec *br = (cow::BlockRec *)(b->h_stage + b->recs_off);
     int64_t tiles = 0, pix = 0;
+    b->max_blk = 0;
     for (int32_t v = 0; v < nv; v++) {
+        b->max_blk = std::max(b->max_blk, b->offs[(size_t)v + 1] - b->offs[(size_t)v]);
         const cow_camera &cam = b->cams[(size_t)v];
         cow::ViewRec &r = vr[v];
         std::memset(&r, 0, sizeof(r));
@@ -100,6 +103,7 @@ cow::BatchArgs make_args(cow_batch *b, const float *mlp, float ert_eps, uint32_t
     a.ert_eps = ert_eps;
     a.flags = flags;
     a.dtype = b->ctx->dtype;
+    a.smem_recs = b->max_blk <= 96 ? b->max_blk : 0;  // longer lists are read from global memory
     a.out_rgb = rgb;
     a.out_aux = aux;
     a.out_nsamp = ns;

@@ -324,6 +324,7 @@ cow_status plan_views(const cow_ctx *c, const cow_camera *cams, int32_t n_views,
         r.tile_begin = (int32_t)tiles;
         r.ids_begin = ids_offsets[v];
         r.ids_count = ids_offsets[v + 1] - ids_offsets[v];
+        r.strip = c->tile_strip;
         r.pix_offset = plan.n_pix;
         tiles += (int64_t)r.tiles_x * tiles_y;
         plan.n_pix += (int64_t)cam.width * cam.height;
@@ -576,6 +577,9 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     a.out_aux = aux;
     a.out_nsamp = ns;
     a.err = ctx->d_err;
+    int32_t max_blk = 0;
+    for (const auto &r : plan.recs) max_blk = std::max(max_blk, r.ids_count);
+    a.smem_recs = max_blk <= 96 ? max_blk : 0;  // views with more records read them from global memory
     COW_CUDA(cow::launch_march_views(a, plan.n_tiles, ctx->schedule == COW_SCHED_THREAD ? cow::kSchedThread
                                                                                          : cow::kSchedWarp, st));
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)plan.n_pix * 12, cudaMemcpyDeviceToHost, st));
@@ -720,6 +724,13 @@ cow_status cow_adam_step(float *param, const float *grad, float *m, float *v, in
 cow_status cow_mse_grad(const float *rgb, const float *target, int64_t n, float *dL_drgb, float *loss, void *stream) {
     if (!rgb || !target || !dL_drgb || n < 0) return fail(COW_ERR_INVALID_ARG, "cow_mse_grad: bad argument");
     COW_CUDA(cow::launch_mse_grad(rgb, target, n, dL_drgb, loss, (cudaStream_t)stream));
+    return COW_OK;
+}
+
+cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles) {
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    if (strip_tiles < 0 || strip_tiles > 4096) return fail(COW_ERR_INVALID_ARG, "strip_tiles must be in [0, 4096]");
+    ctx->tile_strip = strip_tiles;
     return COW_OK;
 }
 

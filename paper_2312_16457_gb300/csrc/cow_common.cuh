@@ -57,10 +57,27 @@ struct alignas(16) ViewRec {
     int32_t tiles_x;     // tiles per image row
     int32_t tile_begin;  // first global tile index of this view
     int32_t ids_begin, ids_count;  // this view's block records: recs[ids_begin .. + ids_count)
-    int32_t pad0;
+    int32_t strip;                 // tile order: 0 raster, else vertical strips of `strip` tile columns
     int64_t pix_offset;  // first output row of this view
 };
 static_assert(sizeof(ViewRec) % 16 == 0, "ViewRec must be a multiple of 16 bytes");
+
+// Tile t of a view -> tile coordinates.  Raster order, or vertical strips of
+// v.strip tile columns walked row by row (the tiles in flight then cover a
+// compact screen region instead of a full-width band of rows).
+__device__ __forceinline__ void tile_xy(const ViewRec &v, int t, int tile_h, int &tx, int &ty) {
+    if (v.strip <= 0 || v.strip >= v.tiles_x) {
+        tx = t % v.tiles_x;
+        ty = t / v.tiles_x;
+        return;
+    }
+    const int tiles_y = (v.H + tile_h - 1) / tile_h;
+    const int per_strip = v.strip * tiles_y;
+    const int k = t / per_strip, r = t - k * per_strip;
+    const int w = min(v.strip, v.tiles_x - k * v.strip);
+    ty = r / w;
+    tx = k * v.strip + (r - ty * w);
+}
 
 // ---------------------------------------------------------------------------
 // FP32 decision sequence

@@ -87,6 +87,7 @@ struct cow_ctx {
     int occ_cell = 4;
     float occ_thresh = 0.01f;
     int schedule = COW_SCHED_THREAD;
+    int tile_strip = 0;  // cow_set_tile_order
     std::vector<cowi::BlockHost> blocks;
     cow::BlockRec *d_blocks = nullptr;
     std::vector<cow::BlockRec> recs;  // host copy of d_blocks

@@ -27,6 +27,7 @@ struct MarchArgs {
     const float *ray_d;
     int64_t n_rays;
     int32_t n_ray_ids;
+    int32_t smem_recs;     // view mode, thread schedule: block records the launch's shared memory holds
 };
 
 // marching schedules of the view kernel
@@ -71,7 +72,7 @@ struct BatchArgs {
     float ert_eps;
     uint32_t flags;
     int32_t dtype;
-    int32_t pad0;
+    int32_t smem_recs;       // block records the launch's dynamic shared memory holds (0: read from global)
     float *out_rgb;
     float *out_aux;          // may be null
     int32_t *out_nsamp;      // may be null

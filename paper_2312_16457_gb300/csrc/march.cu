@@ -55,7 +55,8 @@ __device__ __forceinline__ void write_outputs(const MarchArgs &a, int64_t row, c
 template <int DT>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs a) {
     __shared__ float s_mlp[kMlpParams + 1];
-    __shared__ alignas(16) BlockRec s_rec[kMaxSmemRecs];
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // a.smem_recs block records
+    BlockRec *s_rec = reinterpret_cast<BlockRec *>(s_dyn);
     __shared__ alignas(8) uint64_t s_bar;
     // view of this tile (views are ordered by tile_begin)
     const int tile = blockIdx.x;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs 
     }
     const ViewRec &v = a.views[lo];
     const int n_blk = v.ids_count;
-    const bool staged = n_blk > 0 && n_blk <= kMaxSmemRecs;
+    const bool staged = n_blk > 0 && n_blk <= a.smem_recs;
     if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
     load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
@@ -82,7 +83,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs 
     }
     const BlockRec *recs = staged ? s_rec : a.recs + v.ids_begin;
     const int t = tile - v.tile_begin;
-    const int tx = t % v.tiles_x, ty = t / v.tiles_x;
+    int tx, ty;
+    tile_xy(v, t, kTileH, tx, ty);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px = tx * kTileW + (warp & 1) * 8 + (lane & 7);
     const int py = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
@@ -230,7 +232,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchAr
     }
     const BlockRec *recs = staged ? s_rec : a.recs + v.ids_begin;
     const int t = tile - v.tile_begin;
-    const int tx = t % v.tiles_x, ty = t / v.tiles_x;
+    int tx, ty;
+    tile_xy(v, t, kTileH, tx, ty);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px0 = tx * kTileW + (warp & 1) * 8, py0 = ty * kTileH + (warp >> 1) * 4;
     // this lane's own ray (it writes its outputs at the end)
@@ -302,11 +305,15 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a
 cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
     if (schedule == kSchedThread) {
+        // records staged in dynamic shared memory sized to the largest view's
+        // list (the driver then sizes the shared-memory carveout for full
+        // occupancy and leaves the rest of the SM's 256 KB to L1)
+        const size_t smem = (size_t)a.smem_recs * sizeof(BlockRec);
         switch (a.dtype) {
-        case kF32: k_march_views<kF32><<<n_tiles, kThreads, 0, st>>>(a); break;
-        case kF16: k_march_views<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
-        case kBF16: k_march_views<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
-        case kFP8: k_march_views<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kF32: k_march_views<kF32><<<n_tiles, kThreads, smem, st>>>(a); break;
+        case kF16: k_march_views<kF16><<<n_tiles, kThreads, smem, st>>>(a); break;
+        case kBF16: k_march_views<kBF16><<<n_tiles, kThreads, smem, st>>>(a); break;
+        case kFP8: k_march_views<kFP8><<<n_tiles, kThreads, smem, st>>>(a); break;
         default: return cudaErrorInvalidValue;
         }
     } else {

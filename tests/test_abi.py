@@ -71,5 +71,6 @@ def test_calls_reject_null_context(L):
     assert L.cow_render_rays(None, None, None, 0, None, 1, None, 0.0, 0, None, None, None, None) == 1
     assert L.cow_sync_check(None, None) == 1
     assert L.cow_set_schedule(None, 0) == 1
+    assert L.cow_set_tile_order(None, 0) == 1
     assert b"null context" in L.cow_last_error()
     assert L.cow_free(None) == 0

@@ -129,6 +129,18 @@ def test_multiview_uneven_equals_single_views():
         off += n
 
 
+def test_tile_order_keeps_the_image():
+    sc, cams, mlp = synth.workload_city_4x4(R=24, P=48, width=203, height=117)
+    ctx = cow.Context(sc, "bf16")
+    order = ctx.sort_blocks(cams[0], list(range(16)))
+    ref = _render(ctx, cams, [order], mlp)
+    for strip in (1, 3, 5, 12, 13, 100):
+        ctx.set_tile_order(strip)
+        got = _render(ctx, cams, [order], mlp)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), strip
+
+
 def test_host_outputs_match_device():
     sc, cams, mlp = synth.workload_single_block(R=32, P=64, width=40, height=24)
     ctx = cow.Context(sc, "fp32")
