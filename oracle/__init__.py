@@ -75,6 +75,10 @@ def lib():
             "orc_block_ztop": (dbl, [P]),
             "orc_select_lod": (i32, [P, i32, P, P, i32, P, i32]),
             "orc_sort_view": (None, [P, P, i32, P, P]),
+            "orc_pe_dim": (i32, [i32]),
+            "orc_block_mlp_nparam": (i32, [i32]),
+            "orc_pe": (None, [P, i32, P]),
+            "orc_render_view_block_mlp": (None, [P, i32, P, i32, P, P, i32, P, i64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -278,6 +282,41 @@ def render_view(osc: OracleScene, cam, order: Sequence[int], mlp=None, mode: int
     w = _mlp64(mlp)
     lib().orc_render_view(osc.ptr(), len(osc), _ptr(ordr), len(ordr), C.byref(oc), _ptr(w), mode,
                           _ptr(pix), 0 if pix is None else len(pix), _ptr(rgb), _ptr(aux), _ptr(ns))
+    return rgb, aux, ns
+
+
+def pe_dim(n_freq: int) -> int:
+    return int(lib().orc_pe_dim(n_freq))
+
+
+def block_mlp_nparam(n_freq: int) -> int:
+    """Parameters of one per-block deferred MLP with n_freq PE frequencies."""
+    return int(lib().orc_block_mlp_nparam(n_freq))
+
+
+def pe(d, n_freq: int) -> np.ndarray:
+    """PE(d) of one direction: d, then sin(2^l d), cos(2^l d) for l < n_freq."""
+    dd = np.ascontiguousarray(d, np.float64).reshape(3)
+    out = np.zeros(pe_dim(n_freq))
+    lib().orc_pe(_ptr(dd), n_freq, _ptr(out))
+    return out
+
+
+def render_view_block_mlp(osc: OracleScene, cam, order: Sequence[int], mlps, n_freq: int,
+                          pixels: Optional[Sequence[int]] = None):
+    """Per-block deferred MLPs blended by Eq. 5.  mlps: [n_blocks, nparam]
+    (row i = block i of the scene).  Returns (rgb, aux, nsamp) like render_view."""
+    oc = make_camera(cam)
+    ordr = np.ascontiguousarray(order, np.int32)
+    pix = None if pixels is None else np.ascontiguousarray(pixels, np.int64)
+    n = cam.width * cam.height if pix is None else len(pix)
+    w = np.ascontiguousarray(_np(mlps, np.float64))
+    assert w.shape == (len(osc), block_mlp_nparam(n_freq)), w.shape
+    rgb = np.zeros((n, 3))
+    aux = np.zeros((n, 8))
+    ns = np.zeros(n, np.int32)
+    lib().orc_render_view_block_mlp(osc.ptr(), len(osc), _ptr(ordr), len(ordr), C.byref(oc), _ptr(w), n_freq,
+                                    _ptr(pix), 0 if pix is None else len(pix), _ptr(rgb), _ptr(aux), _ptr(ns))
     return rgb, aux, ns
 
 

@@ -21,7 +21,8 @@
  *   - cross-block composite in block order (Eq. 5 / Eq. 12), with the
  *     single-pass form (Eq. 14) and the alpha/sum(alpha) blending of the
  *     ablation (Table 4, "no alpha blending") as comparison modes;
- *   - one deferred MLP on the composited features (Eq. 3);
+ *   - one deferred MLP on the composited features (Eq. 3), or per-block
+ *     deferred MLPs with a multi-frequency PE(d) blended by Eq. 5;
  *   - LOD selection, visibility and depth sorting of the real-time viewer
  *     (Appendix D);
  *   - the analytic gradient of the rendered colour with respect to grid,
@@ -696,6 +697,126 @@ void orc_render_view(const orc_block *blocks, int32_t nb, const int32_t *order, 
         }
         free(sv.v);
         free(seg);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Per-block deferred MLPs (Sec. 4.1 rendering stage: every block k of LOD l
+ * carries its own tiny MLP Phi^{k,l}; Sec. 4.2: each block's colour C^k is
+ * Eq. 3 applied to that block's own C_d^k and F^k, and the block colours are
+ * blended near to far by Eq. 5).  The MLP input is [C_d^k, F^k, PE(d)].
+ *
+ * PE(d) with L frequencies: d itself, then for l = 0 .. L-1 the three values
+ * sin(2^l d) followed by the three values cos(2^l d) (component order x, y,
+ * z); L = 0 gives the plain direction of the global form.  Weights of a
+ * block MLP are input-major like the global one: W1[n_in][16], b1[16],
+ * W2[16][16], b2[16], W3[16][3], b3[3], n_in = 7 + 3 + 6 L.
+ *
+ * A block takes part in Eq. 5 when the ray has at least one occupied sample
+ * in it; a block the ray crosses only through empty cells adds nothing (its
+ * C_d^k, F^k and alpha^k are zero, and Phi^k of empty features is not a
+ * colour of that block). */
+
+int32_t orc_pe_dim(int32_t L) { return 3 + 6 * L; }
+
+int32_t orc_block_mlp_nparam(int32_t L) {
+    const int32_t n_in = 7 + orc_pe_dim(L);
+    return n_in * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT;
+}
+
+void orc_pe(const double d[3], int32_t L, double *out) {
+    for (int a = 0; a < 3; a++) out[a] = d[a];
+    double f = 1.0; /* 2^l */
+    for (int32_t l = 0; l < L; l++) {
+        for (int a = 0; a < 3; a++) out[3 + 6 * l + a] = sin(f * d[a]);
+        for (int a = 0; a < 3; a++) out[3 + 6 * l + 3 + a] = cos(f * d[a]);
+        f *= 2.0;
+    }
+}
+
+/* Phi of Eq. 3 for an n_in-input MLP: ReLU, ReLU, sigmoid. */
+static void mlp_n(const double *w, int32_t n_in, const double *x, double out[MLP_OUT]) {
+    const double *W1 = w, *b1 = W1 + n_in * MLP_HID, *W2 = b1 + MLP_HID, *b2 = W2 + MLP_HID * MLP_HID;
+    const double *W3 = b2 + MLP_HID, *b3 = W3 + MLP_HID * MLP_OUT;
+    double h1[MLP_HID], h2[MLP_HID];
+    for (int j = 0; j < MLP_HID; j++) {
+        double a = b1[j];
+        for (int i = 0; i < n_in; i++) a += x[i] * W1[i * MLP_HID + j];
+        h1[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int j = 0; j < MLP_HID; j++) {
+        double a = b2[j];
+        for (int i = 0; i < MLP_HID; i++) a += h1[i] * W2[i * MLP_HID + j];
+        h2[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int j = 0; j < MLP_OUT; j++) {
+        double a = b3[j];
+        for (int i = 0; i < MLP_HID; i++) a += h2[i] * W3[i * MLP_OUT + j];
+        out[j] = sigmoid(a);
+    }
+}
+
+/* Render pixels of one view with per-block MLPs.  mlps: nb blocks' weights,
+ * block i's at mlps + i * orc_block_mlp_nparam(L).  Outputs: rgb = Eq. 5;
+ * aux = the blended C_d, F (Eq. 12) and the transmittance after the last
+ * block; nsamp = occupied samples. */
+void orc_render_view_block_mlp(const orc_block *blocks, int32_t nb, const int32_t *order, int32_t n_order,
+                               const orc_camera *cam, const double *mlps, int32_t L, const int64_t *pix,
+                               int64_t n_pix, double *out_rgb, double *out_aux, int32_t *out_nsamp) {
+    (void)nb;
+    const int64_t W = cam->width;
+    const int64_t npx = pix ? n_pix : W * (int64_t)cam->height;
+    const int32_t n_in = 7 + orc_pe_dim(L), np = orc_block_mlp_nparam(L);
+#pragma omp parallel
+    {
+        sample_vec sv = {0, 0, 0};
+        double *x = (double *)malloc((size_t)n_in * sizeof(double));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < npx; r++) {
+            const int64_t lin = pix ? pix[r] : r;
+            float of[3], df[3];
+            orc_pixel_ray(cam, (int32_t)(lin % W), (int32_t)(lin / W), of, df);
+            const double d[3] = {df[0], df[1], df[2]};
+            double C[3] = {0, 0, 0}, Cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0};
+            double Tb = 1.0; /* prod_{j<k} (1 - alpha^j) */
+            int32_t ns = 0;
+            for (int k = 0; k < n_order; k++) {
+                sv.n = 0;
+                const int64_t nk = block_samples(blocks, order[k], of, df, &sv);
+                if (nk == 0) continue;
+                /* Eq. 11: C_d^k, F^k, alpha^k with in-block weights */
+                double ck[3] = {0, 0, 0}, fk[4] = {0, 0, 0, 0}, ak = 0.0, T = 1.0;
+                for (int64_t i = 0; i < nk; i++) {
+                    const double w = T * sv.v[i].alpha;
+                    for (int c = 0; c < 3; c++) ck[c] += w * sv.v[i].c[c];
+                    for (int c = 0; c < 4; c++) fk[c] += w * sv.v[i].s[c];
+                    ak += w;
+                    T *= 1.0 - sv.v[i].alpha;
+                }
+                /* Eq. 3 with block k's MLP */
+                for (int c = 0; c < 3; c++) x[c] = ck[c];
+                for (int c = 0; c < 4; c++) x[3 + c] = fk[c];
+                orc_pe(d, L, x + 7);
+                double phi[MLP_OUT];
+                mlp_n(mlps + (int64_t)order[k] * np, n_in, x, phi);
+                /* Eq. 5 */
+                for (int c = 0; c < 3; c++) C[c] += Tb * (ck[c] + phi[c]);
+                for (int c = 0; c < 3; c++) Cd[c] += Tb * ck[c];
+                for (int c = 0; c < 4; c++) F[c] += Tb * fk[c];
+                Tb *= 1.0 - ak;
+                ns += (int32_t)nk;
+            }
+            if (out_rgb)
+                for (int c = 0; c < 3; c++) out_rgb[r * 3 + c] = C[c];
+            if (out_aux) {
+                for (int c = 0; c < 3; c++) out_aux[r * 8 + c] = Cd[c];
+                for (int c = 0; c < 4; c++) out_aux[r * 8 + 3 + c] = F[c];
+                out_aux[r * 8 + 7] = Tb;
+            }
+            if (out_nsamp) out_nsamp[r] = ns;
+        }
+        free(sv.v);
+        free(x);
     }
 }
 

@@ -13,7 +13,7 @@ always read identical inputs:
 * ground-plane block partitions with 2x2-merged coarser LOD levels, every
   level sampling the same world field at its own vertices;
 * pinhole cameras (aerial, oblique) and random ray batches;
-* deferred-MLP weights drawn from N(0, 0.3^2).
+* deferred-MLP weights drawn from N(0, 0.3^2), globally or per block.
 
 Scalar parameters come from numpy's PCG64 generator; per-element noise comes
 from a counter-based integer hash evaluated with int64 tensor arithmetic that
@@ -307,6 +307,23 @@ def mlp_weights(seed: int, std=0.3) -> np.ndarray:
     """499 deferred-MLP parameters ~ N(0, std^2): W1[10][16], b1[16], W2[16][16],
     b2[16], W3[16][3], b3[3], weights stored input-major."""
     return np.random.default_rng(seed).normal(0.0, std, size=MLP_NPARAM).astype(np.float32)
+
+
+def block_mlp_nparam(n_freq: int) -> int:
+    """Parameters of one per-block deferred MLP whose input is [C_d (3), F (4),
+    d (3), sin / cos of d at n_freq octaves (6 n_freq)]: 16 n_in + 339."""
+    return 16 * (10 + 6 * n_freq) + 16 + 256 + 16 + 48 + 3
+
+
+def block_mlp_weights(seed: int, n_blocks: int, n_freq: int, std=0.3, spread=0.1) -> np.ndarray:
+    """Per-block deferred-MLP parameters, [n_blocks, block_mlp_nparam(n_freq)]
+    float32: one shared draw ~ N(0, std^2) plus an independent N(0, spread^2)
+    perturbation per block, so neighbouring blocks' MLPs differ a little (the
+    per-block models of the paper are trained separately on the same scene)."""
+    rng = np.random.default_rng(seed)
+    n = block_mlp_nparam(n_freq)
+    base = rng.normal(0.0, std, size=n)
+    return (base[None, :] + rng.normal(0.0, spread, size=(n_blocks, n))).astype(np.float32)
 
 
 # --------------------------------------------------------------------------

@@ -1,0 +1,158 @@
+"""Pins of the oracle's per-block deferred-MLP form (Sec. 4.1 rendering
+stage: one MLP Phi^{k,l} per block; Sec. 4.2, Eq. 5 with Eq. 3 per block)
+and of its multi-frequency PE(d).
+
+Each test fails for a plausible mistake: PE special values catch a wrong
+order of sin / cos or octave; the single-block case pins the per-block MLP
+to the global form's MLP (a wrong layout of the n_in-input weights); the
+Lambertian case is the paper's Appendix A equivalence (a wrong blend weight
+or transmittance); the hand-wired MLP checks which input a PE term reaches;
+the brute force composes single-block renders by Eq. 5 (a wrong block's MLP
+or a transmittance not carried); the empty block pins the reading that a
+block without occupied samples takes no part."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2312_16457_gb300 import synth
+
+
+def _sig(x):
+    return 1.0 / (1.0 + np.exp(-x))
+
+
+def test_param_count_matches_generator(orc):
+    for L in (0, 1, 4):
+        assert orc.block_mlp_nparam(L) == synth.block_mlp_nparam(L)
+        assert orc.pe_dim(L) == 3 + 6 * L
+    assert orc.block_mlp_nparam(0) == synth.MLP_NPARAM
+
+
+def test_pe_special_values(orc):
+    """d = (0, pi/2, pi): sin / cos at octaves 1 and 2 take textbook values."""
+    d = np.array([0.0, math.pi / 2, math.pi])
+    e = orc.pe(d, 2)
+    assert e.shape == (15,)
+    np.testing.assert_allclose(e[0:3], d, atol=0)
+    np.testing.assert_allclose(e[3:6], [0.0, 1.0, 0.0], atol=1e-15)     # sin(d)
+    np.testing.assert_allclose(e[6:9], [1.0, 0.0, -1.0], atol=1e-15)    # cos(d)
+    np.testing.assert_allclose(e[9:12], [0.0, 0.0, 0.0], atol=1e-15)    # sin(2d)
+    np.testing.assert_allclose(e[12:15], [1.0, -1.0, 1.0], atol=1e-15)  # cos(2d)
+    assert orc.pe(d, 0).tolist() == d.tolist()
+
+
+def test_single_block_reduces_to_global_form(orc):
+    """One block, L = 0, its MLP equal to the global one: every pixel with an
+    occupied sample gets the global form's colour; the others get 0."""
+    sc = synth.single_block_scene(1, 24, 64)
+    cam = synth.camera((0.0, -2.5, 0.8), (0.0, 0.0, 0.0), 40, 32, 60.0)
+    osc = orc.OracleScene(sc)
+    mlp = synth.mlp_weights(101)
+    r_g, a_g, n_g = orc.render_view(osc, cam, [0], mlp)
+    r_b, a_b, n_b = orc.render_view_block_mlp(osc, cam, [0], mlp[None, :], 0)
+    assert np.array_equal(n_g, n_b)
+    hit = n_g > 0
+    assert 0.2 < hit.mean() < 1.0
+    np.testing.assert_allclose(r_b[hit], r_g[hit], rtol=0, atol=1e-13)
+    assert np.all(r_b[~hit] == 0.0)
+    np.testing.assert_allclose(a_b, a_g, rtol=0, atol=1e-13)
+
+
+def test_lambertian_equals_single_pass(orc):
+    """Appendix A: with every block's Phi = 0 (final bias -1e4 makes the
+    sigmoid exactly 0) the Eq. 5 blend of per-block colours equals volume
+    rendering over all samples of the scene in one pass."""
+    sc = synth.city_scene(5, 2, 2.0, [(12, 32)])
+    n = len(sc.blocks)
+    L = 3
+    w = synth.block_mlp_weights(7, n, L).astype(np.float64)
+    w[:, -3:] = -1e4
+    osc = orc.OracleScene(sc)
+    cam = synth.camera((0.4, -4.5, 3.5), (0.0, 0.0, -0.5), 48, 36, 60.0)
+    order = orc.sort_view(osc, list(range(n)), cam)
+    r_b, a_b, n_b = orc.render_view_block_mlp(osc, cam, order, w, L)
+    r_s, a_s, n_s = orc.render_view(osc, cam, order, None, orc.MODE_SINGLE_PASS)
+    assert np.array_equal(n_b, n_s)
+    assert (n_b > 0).mean() > 0.25
+    np.testing.assert_allclose(r_b, r_s, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(a_b, a_s, rtol=0, atol=1e-12)
+
+
+def test_pe_term_reaches_its_input(orc):
+    """A hand-wired MLP passes one input through: W1[i][0] = W2[0][0] =
+    W3[0][0] = 1, all else 0.  Then Phi_0 = sigmoid(max(x_i, 0)) and
+    Phi_1 = Phi_2 = 1/2, with x = [C_d, F, d, sin d, cos d, sin 2d, cos 2d]."""
+    sc = synth.single_block_scene(1, 24, 64)
+    cam = synth.camera((0.3, -2.5, 0.8), (0.0, 0.0, 0.0), 24, 20, 60.0)
+    osc = orc.OracleScene(sc)
+    L = 2
+    n_in = 10 + 6 * L
+    o, d = orc.pixel_rays(cam)
+    d = d.astype(np.float64)
+    cases = {7: d[:, 0], 8: d[:, 1], 10 + 1: np.sin(d[:, 1]), 10 + 3 + 2: np.cos(d[:, 2]),
+             10 + 6 + 0: np.sin(2 * d[:, 0]), 10 + 9 + 1: np.cos(2 * d[:, 1]), 3: None}
+    for i, want in cases.items():
+        w = np.zeros(synth.block_mlp_nparam(L))
+        w[i * 16 + 0] = 1.0                          # W1[i][0]
+        w[n_in * 16 + 16 + 0] = 1.0                  # W2[0][0]
+        w[n_in * 16 + 16 + 256 + 16 + 0] = 1.0       # W3[0][0]
+        rgb, aux, ns = orc.render_view_block_mlp(osc, cam, [0], w[None, :], L)
+        hit = ns > 0
+        assert hit.mean() > 0.3
+        phi = rgb[hit] - aux[hit, :3]
+        x = aux[hit, 3] if want is None else want[hit]  # input 3 is F_0
+        np.testing.assert_allclose(phi[:, 0], _sig(np.maximum(x, 0.0)), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(phi[:, 1:], 0.5, rtol=0, atol=1e-15)
+
+
+def test_blend_of_single_block_renders(orc):
+    """Eq. 5 by brute force: render each block alone (its C^k, 1 - alpha^k)
+    and blend near to far in numpy; equals the multi-block render."""
+    sc = synth.city_scene(6, 2, 2.0, [(12, 32)])
+    n = len(sc.blocks)
+    L = 4
+    w = synth.block_mlp_weights(8, n, L, spread=0.5)
+    osc = orc.OracleScene(sc)
+    cam = synth.camera((-0.6, -4.0, 3.0), (0.2, 0.3, -0.5), 40, 30, 70.0)
+    order = orc.sort_view(osc, list(range(n)), cam)
+    rgb, aux, ns = orc.render_view_block_mlp(osc, cam, order, w, L)
+    C = np.zeros_like(rgb)
+    T = np.ones(rgb.shape[0])
+    nsum = np.zeros_like(ns)
+    multi = np.zeros_like(ns)
+    for k in order:
+        r_k, a_k, n_k = orc.render_view_block_mlp(osc, cam, [k], w, L)
+        C += T[:, None] * r_k
+        T *= a_k[:, 7]
+        nsum += n_k
+        multi += n_k > 0
+    assert (multi >= 2).mean() > 0.05  # rays that cross a block border with samples on both sides
+    assert np.array_equal(ns, nsum)
+    np.testing.assert_allclose(rgb, C, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(aux[:, 7], T, rtol=0, atol=1e-15)
+    # the blocks' MLPs differ: a global MLP on the blended features gives another image
+    r_g, _, _ = orc.render_view(osc, cam, order, w[0])
+    assert np.abs(r_g - rgb).max() > 1e-2
+
+
+def test_block_without_samples_takes_no_part(orc):
+    """A block the rays cross only through empty cells adds nothing, although
+    its MLP on empty features is not zero."""
+    sc = synth.city_scene(9, 2, 2.0, [(12, 32)])
+    sc.blocks[1].grid[..., 0] = -12.0  # sigma = 6e-6 < the 0.01 occupancy threshold everywhere
+    n = len(sc.blocks)
+    L = 1
+    w = synth.block_mlp_weights(3, n, L)
+    osc = orc.OracleScene(sc)
+    cam = synth.camera((0.0, -4.0, 3.0), (0.0, 0.0, -0.5), 32, 24, 70.0)
+    order = orc.sort_view(osc, list(range(n)), cam)
+    assert 1 in list(order)
+    rgb, aux, ns = orc.render_view_block_mlp(osc, cam, order, w, L)
+    keep = [k for k in order if k != 1]
+    rgb2, aux2, ns2 = orc.render_view_block_mlp(osc, cam, keep, w, L)
+    assert np.array_equal(ns, ns2)
+    assert np.array_equal(rgb, rgb2) and np.array_equal(aux, aux2)
+    r1, _, n1 = orc.render_view_block_mlp(osc, cam, [1], w, L)
+    assert np.all(n1 == 0) and np.all(r1 == 0.0)
