@@ -37,9 +37,10 @@ METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
 # DRAM bytes (read + write) of one k_march_views launch from an ncu capture of
 # the default workload (profiles/march_views_city_lod_1080p_traffic.md); valid
 # for the marcher revision named here and null for any other configuration.
-MARCH_REVISION = "v4-thread-pair256"
-MEASURED_TRAFFIC = {("city_lod_1080p", "bf16", "thread", 1): 49749571328 + 27278080}
+MARCH_REVISION = "v6-cachehints"
+MEASURED_TRAFFIC = {}
 L2_FLUSH_BYTES = 512 << 20
+KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}
 GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160}  # per occupied sample: 20 texels x 8 ch
 
 
@@ -57,7 +58,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--res-div", type=int, default=1, help="divide grid / plane resolutions (profiling runs)")
-    ap.add_argument("--schedule", choices=["warp", "thread"], default="thread", help="marching schedule")
+    ap.add_argument("--schedule", choices=["warp", "thread", "thread_const"], default="thread_const", help="marching schedule")
     ap.add_argument("--strip", type=int, default=0, help="tile order: 0 raster, k strips of k tile columns")
     return ap.parse_args()
 
@@ -292,6 +293,16 @@ def run_cow(args, ws, rank, local):
                   "ctas_per_sm": ctas}
     batch.close()
 
+    # the same frame with per-block deferred MLPs blended by Eq. 5 (PE(d) at 4 octaves)
+    from paper_2312_16457_gb300 import synth
+
+    ctx.set_block_mlps(synth.block_mlp_weights(104, len(sc.blocks), 4), 4)
+    tbm = time_steps(lambda: ctx.render([cam], [ids], None, ert_eps=args.ert, aux=False, out=out, block_mlps=True),
+                     max(5, args.steps // 2), 3, flush, stream)
+    ctx.sync_check()
+    block_mlp_form = {"frames_per_s": round(1000.0 / float(np.mean(tbm)), 3), "n_freq": 4,
+                      "mlp_params_per_block": synth.block_mlp_nparam(4)}
+
     # plain FP32 storage, same frame
     fp32 = {}
     if ctx32 is not None:
@@ -338,9 +349,10 @@ def run_cow(args, ws, rank, local):
         "mrays_per_s": round(value * npix / 1e6, 3),
         "occupied_samples_per_frame": n_samples,
         "batched_path_same_frame": batch_path,
+        "block_mlp_form_same_frame": block_mlp_form,
         "samples_per_ray": round(n_samples / npix, 2),
         **fp32,
-        "roofline": {"bound": "gather", "kernel": "k_march_views", "achieved": round(achieved, 1),
+        "roofline": {"bound": "gather", "kernel": KERNEL_OF_SCHEDULE[args.schedule], "achieved": round(achieved, 1),
                      "peak": round(peak_l1, 1), "unit": "GB/s", "frac": round(achieved / peak_l1, 3),
                      "traffic": MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div)),
                      "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, marcher "

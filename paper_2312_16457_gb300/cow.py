@@ -19,16 +19,18 @@ _lib = None
 DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
 ELEM_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp8": 1}
 FLAG_MLP_BF16 = 1
+FLAG_BLOCK_MLPS = 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE_ASSERT"}
 
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
-           "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_sync_check", "cow_export_occupancy",
+           "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
+           "cow_sync_check", "cow_export_occupancy",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune", "cow_last_error",
            "cow_version"]
-SCHEDULES = {"warp": 0, "thread": 1}
+SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
 
 class CowError(RuntimeError):
@@ -71,6 +73,7 @@ def lib():
             "cow_sync_check": [P, P],
             "cow_set_schedule": [P, i32],
             "cow_set_tile_order": [P, i32],
+            "cow_set_block_mlps": [P, P, i32, i32, P],
             "cow_export_occupancy": [P, i32, P, i64],
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
@@ -157,6 +160,7 @@ class Context:
         _check(lib().cow_load_blocks(C.byref(self._ctx), descs, n, DTYPES[storage], float(th), int(cc),
                                      _stream_ptr(stream)))
         self.n_blocks = n
+        self.schedule = "thread_const"  # the library default
         del keep
 
     def close(self):
@@ -193,10 +197,11 @@ class Context:
 
     # --- rendering ---------------------------------------------------------
     def render(self, cams, ids_per_view, mlp, ert_eps: float = 0.0, mlp_bf16: bool = False, aux: bool = True,
-               nsamp: bool = False, out=None, stream=None, device="cuda"):
+               nsamp: bool = False, out=None, stream=None, device="cuda", block_mlps: bool = False):
         """Render views; returns (rgb, aux, nsamp) tensors with one row per
         pixel (views concatenated).  `out` may pass preallocated tensors
-        (device or pinned host)."""
+        (device or pinned host).  block_mlps=True renders with the per-block
+        MLPs of set_block_mlps blended by Eq. 5 (`mlp` is then unused)."""
         cams = list(cams)
         cc = (Camera * len(cams))(*[_camera(c) for c in cams])
         offs = np.zeros(len(cams) + 1, np.int32)
@@ -211,11 +216,21 @@ class Context:
             ns = torch.empty((npix,), dtype=torch.int32, device=device) if nsamp else None
         else:
             rgb, ax, ns = out
-        m = mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp)
+        m = None if mlp is None else (mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp))
+        flags = (FLAG_MLP_BF16 if mlp_bf16 else 0) | (FLAG_BLOCK_MLPS if block_mlps else 0)
         _check(lib().cow_render(self._ctx, cc, len(cams), _ptr(flat), _ptr(offs), _ptr(m), float(ert_eps),
-                                FLAG_MLP_BF16 if mlp_bf16 else 0, _ptr(rgb), _ptr(ax), _ptr(ns),
-                                _stream_ptr(stream)))
+                                flags, _ptr(rgb), _ptr(ax), _ptr(ns), _stream_ptr(stream)))
         return rgb, ax, ns
+
+    def set_block_mlps(self, mlps, n_freq: int, stream=None):
+        """Per-block deferred MLPs: [n_blocks, 16 (10 + 6 n_freq) + 339] FP32
+        (row i for block i), host or device; None removes them."""
+        if mlps is None:
+            _check(lib().cow_set_block_mlps(self._ctx, None, 0, 0, _stream_ptr(stream)))
+            return
+        m = _as_f32(mlps)
+        _check(lib().cow_set_block_mlps(self._ctx, _ptr(m), int(m.shape[0]), int(n_freq), _stream_ptr(stream)))
+        self._block_mlp_src = m  # a device source stays alive until the stream has copied it
 
     def render_rays(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], mlp, ert_eps: float = 0.0,
                     mlp_bf16: bool = False, aux: bool = True, nsamp: bool = False, stream=None):

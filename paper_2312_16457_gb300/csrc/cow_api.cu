@@ -81,6 +81,7 @@ void destroy(cow_ctx *c) {
     c->gptrs.release();
     c->partials.release();
     c->staging.release();
+    c->block_mlps.release();
     delete c;
 }
 
@@ -533,11 +534,15 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
                       const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                       float *out_aux, int32_t *out_nsamp, void *stream) {
     g_last_error.clear();
-    if (!ctx || !cams || n_views < 1 || !ids_offsets || !mlp || !out_rgb)
+    const bool block_mlp = (flags & COW_FLAG_BLOCK_MLPS) != 0;
+    if (!ctx || !cams || n_views < 1 || !ids_offsets || (!mlp && !block_mlp) || !out_rgb)
         return fail(COW_ERR_INVALID_ARG, "cow_render: null argument or n_views < 1");
     if (ids_offsets[n_views] > 0 && !ids) return fail(COW_ERR_INVALID_ARG, "cow_render: null ids");
     if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
-    if (flags & ~COW_FLAG_MLP_BF16) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    if (flags & ~(COW_FLAG_MLP_BF16 | COW_FLAG_BLOCK_MLPS)) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    if (block_mlp && (flags & COW_FLAG_MLP_BF16))
+        return fail(COW_ERR_INVALID_ARG, "COW_FLAG_BLOCK_MLPS runs the MLPs in FP32: drop COW_FLAG_MLP_BF16");
+    if (block_mlp && ctx->n_freq < 0) return fail(COW_ERR_INVALID_ARG, "COW_FLAG_BLOCK_MLPS: no block MLPs set");
     if (((uintptr_t)out_rgb & 3u) || ((uintptr_t)out_aux & 15u)) return fail(COW_ERR_INVALID_ARG, "misaligned output");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -551,13 +556,19 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     for (int32_t k = 0; k < n_ids; k++) vrecs[(size_t)k] = ctx->recs[(size_t)ids[k]];
     const size_t vbytes = plan.recs.size() * sizeof(cow::ViewRec);
     const size_t rbytes = vrecs.size() * sizeof(cow::BlockRec);
-    COW_CUDA(ctx->views.reserve(vbytes + rbytes));
-    std::vector<unsigned char> staging(vbytes + rbytes);
+    // per-block MLP form: the weights of each view record, parallel to the records
+    std::vector<const float *> vmlps(block_mlp ? vrecs.size() : 0);
+    for (int32_t k = 0; k < n_ids && block_mlp; k++)
+        vmlps[(size_t)k] = (const float *)ctx->block_mlps.p + (int64_t)ids[k] * ctx->block_mlp_nparam;
+    const size_t mbytes = vmlps.size() * sizeof(const float *);
+    COW_CUDA(ctx->views.reserve(vbytes + rbytes + mbytes));
+    std::vector<unsigned char> staging(vbytes + rbytes + mbytes);
     std::memcpy(staging.data(), plan.recs.data(), vbytes);
     std::memcpy(staging.data() + vbytes, vrecs.data(), rbytes);
-    COW_CUDA(cudaMemcpyAsync(ctx->views.p, staging.data(), vbytes + rbytes, cudaMemcpyHostToDevice, st));
+    if (mbytes) std::memcpy(staging.data() + vbytes + rbytes, vmlps.data(), mbytes);
+    COW_CUDA(cudaMemcpyAsync(ctx->views.p, staging.data(), vbytes + rbytes + mbytes, cudaMemcpyHostToDevice, st));
     const float *d_mlp = nullptr;
-    if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
+    if (!block_mlp && (rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
     float *rgb, *aux;
     int32_t *ns;
     bool h_rgb, h_aux, h_ns;
@@ -577,11 +588,23 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     a.out_aux = aux;
     a.out_nsamp = ns;
     a.err = ctx->d_err;
+    if (block_mlp) {
+        a.block_mlps = (const float *const *)((unsigned char *)ctx->views.p + vbytes + rbytes);
+        a.n_freq = ctx->n_freq;
+    }
     int32_t max_blk = 0;
     for (const auto &r : plan.recs) max_blk = std::max(max_blk, r.ids_count);
     a.smem_recs = max_blk <= 96 ? max_blk : 0;  // views with more records read them from global memory
-    COW_CUDA(cow::launch_march_views(a, plan.n_tiles, ctx->schedule == COW_SCHED_THREAD ? cow::kSchedThread
-                                                                                         : cow::kSchedWarp, st));
+    if (ctx->schedule == COW_SCHED_THREAD_CONST && n_ids <= cow::kParamRecs) {
+        // the records travel in the launch's parameter buffer
+        cow::ParamRecs pr;
+        std::memset(&pr, 0, sizeof(pr));
+        std::copy(vrecs.begin(), vrecs.begin() + n_ids, pr.r);
+        COW_CUDA(cow::launch_march_views(a, plan.n_tiles, cow::kSchedThreadConst, st, &pr));
+    } else {
+        COW_CUDA(cow::launch_march_views(a, plan.n_tiles, ctx->schedule == COW_SCHED_WARP ? cow::kSchedWarp
+                                                                                          : cow::kSchedThread, st));
+    }
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)plan.n_pix * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)plan.n_pix * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)plan.n_pix * 4, cudaMemcpyDeviceToHost, st));
@@ -727,6 +750,34 @@ cow_status cow_mse_grad(const float *rgb, const float *target, int64_t n, float 
     return COW_OK;
 }
 
+cow_status cow_set_block_mlps(cow_ctx *ctx, const float *mlps, int32_t n_mlps, int32_t n_freq, void *stream) {
+    g_last_error.clear();
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    if (!mlps && n_mlps == 0) {
+        ctx->n_freq = -1;
+        ctx->block_mlp_nparam = 0;
+        return COW_OK;
+    }
+    if (!mlps) return fail(COW_ERR_INVALID_ARG, "cow_set_block_mlps: null mlps");
+    if (n_mlps != (int32_t)ctx->blocks.size())
+        return fail(COW_ERR_INVALID_ARG, "cow_set_block_mlps: %d MLPs for %d blocks", n_mlps, (int)ctx->blocks.size());
+    if (n_freq < 0 || n_freq > 8) return fail(COW_ERR_INVALID_ARG, "n_freq must be in [0, 8]");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t n_in = 10 + 6 * n_freq;
+    const int32_t np = 16 * n_in + 16 + 16 * 16 + 16 + 16 * 3 + 3;
+    // the kernel reads W1 / W2 rows as float4: each block's copy starts on a
+    // 16-byte boundary (stride rounded up to 4 floats)
+    const int32_t stride = (np + 3) & ~3;
+    COW_CUDA(ctx->block_mlps.reserve((size_t)n_mlps * (size_t)stride * sizeof(float)));
+    COW_CUDA(cudaMemcpy2DAsync(ctx->block_mlps.p, (size_t)stride * sizeof(float), mlps, (size_t)np * sizeof(float),
+                               (size_t)np * sizeof(float), (size_t)n_mlps,
+                               is_device_ptr(mlps) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    ctx->n_freq = n_freq;
+    ctx->block_mlp_nparam = stride;
+    return COW_OK;
+}
+
 cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles) {
     if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
     if (strip_tiles < 0 || strip_tiles > 4096) return fail(COW_ERR_INVALID_ARG, "strip_tiles must be in [0, 4096]");
@@ -736,7 +787,7 @@ cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles) {
 
 cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule) {
     if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
-    if (schedule != COW_SCHED_WARP && schedule != COW_SCHED_THREAD)
+    if (schedule != COW_SCHED_WARP && schedule != COW_SCHED_THREAD && schedule != COW_SCHED_THREAD_CONST)
         return fail(COW_ERR_INVALID_ARG, "unknown schedule %d", schedule);
     ctx->schedule = schedule;
     return COW_OK;

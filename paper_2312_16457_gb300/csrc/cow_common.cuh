@@ -48,6 +48,13 @@ struct alignas(16) BlockRec {
 };
 static_assert(sizeof(BlockRec) % 16 == 0, "BlockRec must be a multiple of 16 bytes");
 
+// Block records passed by value in a launch's parameter buffer (a kernel's
+// parameters may take up to 32764 bytes).
+constexpr int kParamRecs = 96;
+struct ParamRecs {
+    BlockRec r[kParamRecs];
+};
+
 // One camera as the kernels see it.
 struct alignas(16) ViewRec {
     float Rm[9];         // (float)c2w rotation, row-major
@@ -186,12 +193,43 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
 // ---------------------------------------------------------------------------
 // storage loads: 8 channels of one vertex / texel as float (unscaled)
 
-// 256-bit non-coherent global load (sm_100+); p must be 32-byte aligned.
+// L1 (and L2) cache policy of a read-only feature gather.
+enum LdPolicy {
+    kLdNormal = 0,
+    kLdEvictFirst = 1,           // L1::evict_first
+    kLdEvictLast = 2,            // L1::evict_last
+    kLdNoAllocate = 3,           // L1::no_allocate
+    kLdNoAllocateL2First = 4,    // L1::no_allocate, L2 evict_first
+    kLdL2Last = 5,               // L2 evict_last
+    kLdNoAllocateL2Last = 6,     // L1::no_allocate, L2 evict_last
+};
+
+#define COW_LD256(QUAL)                                                                                          \
+    asm("ld.global.nc" QUAL ".v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                                           \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])         \
+        : "l"(p))
+
+// 256-bit non-coherent global load (sm_100+); p must be 32-byte aligned.  The
+// data is read-only for the kernel's lifetime, so the asm has no side effects
+// and the compiler may schedule it freely.
+#define COW_LD256_L2(QUAL, FRAC)                                                                                 \
+    asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional." FRAC ".b64 pol, 1.0;\n\t"                              \
+        "ld.global.nc" QUAL ".L2::cache_hint.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8], pol;\n\t}"                      \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])         \
+        : "l"(p))
+
+template <int POL = kLdNormal>
 __device__ __forceinline__ void ld256(const void *p, uint32_t r[8]) {
-    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "l"(p));
+    if constexpr (POL == kLdEvictFirst) COW_LD256(".L1::evict_first");
+    else if constexpr (POL == kLdEvictLast) COW_LD256(".L1::evict_last");
+    else if constexpr (POL == kLdNoAllocate) COW_LD256(".L1::no_allocate");
+    else if constexpr (POL == kLdNoAllocateL2First) COW_LD256_L2(".L1::no_allocate", "L2::evict_first");
+    else if constexpr (POL == kLdL2Last) COW_LD256_L2("", "L2::evict_last");
+    else if constexpr (POL == kLdNoAllocateL2Last) COW_LD256_L2(".L1::no_allocate", "L2::evict_last");
+    else COW_LD256("");
 }
+#undef COW_LD256
+#undef COW_LD256_L2
 
 __device__ __forceinline__ float2 bf16x2_to_float2(uint32_t w) {
     // a bfloat16 is the upper half of the float with the same value
@@ -219,22 +257,26 @@ struct Store;
 template <>
 struct Store<kF32> {
     static constexpr bool kPaired = false;
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load8(const void *base, int64_t idx, float2 v[4]) {
         uint32_t r[8];
-        ld256(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
+        ld256<POL>(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
 #pragma unroll
         for (int k = 0; k < 4; k++) v[k] = make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
     }
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load_pair(const void *, int64_t, float2[4], float2[4]) {}
 };
 
 template <>
 struct Store<kF16> {
     static constexpr bool kPaired = true;
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load_pair(const void *base, int64_t idx, float2 lo[4], float2 hi[4]) {
         uint32_t r[8];
-        ld256(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
+        ld256<POL>(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             lo[k] = f16x2_to_float2(r[k]);
@@ -246,10 +288,12 @@ struct Store<kF16> {
 template <>
 struct Store<kBF16> {
     static constexpr bool kPaired = true;
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load_pair(const void *base, int64_t idx, float2 lo[4], float2 hi[4]) {
         uint32_t r[8];
-        ld256(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
+        ld256<POL>(reinterpret_cast<const uint4 *>(base) + 2 * idx, r);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             lo[k] = bf16x2_to_float2(r[k]);
@@ -261,7 +305,9 @@ struct Store<kBF16> {
 template <>
 struct Store<kFP8> {
     static constexpr bool kPaired = true;
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    template <int POL = kLdNormal>
     __device__ __forceinline__ static void load_pair(const void *base, int64_t idx, float2 lo[4], float2 hi[4]) {
         const uint4 q = __ldg(reinterpret_cast<const uint4 *>(base) + idx);
         lo[0] = fp8x2_to_float2(q.x);

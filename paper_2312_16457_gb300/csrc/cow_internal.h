@@ -86,7 +86,7 @@ struct cow_ctx {
     int dtype = 0;
     int occ_cell = 4;
     float occ_thresh = 0.01f;
-    int schedule = COW_SCHED_THREAD;
+    int schedule = COW_SCHED_THREAD_CONST;
     int tile_strip = 0;  // cow_set_tile_order
     std::vector<cowi::BlockHost> blocks;
     cow::BlockRec *d_blocks = nullptr;
@@ -96,4 +96,7 @@ struct cow_ctx {
     cowi::DevBuf views, ids, out_rgb, out_aux, out_nsamp;
     cowi::DevBuf gptrs, partials;  // backward: per-block gradient pointers, per-CTA MLP-gradient rows
     cowi::DevBuf staging;          // host masters of cow_update_features
+    cowi::DevBuf block_mlps;       // cow_set_block_mlps: n_blocks x block_mlp_nparam FP32
+    int32_t n_freq = -1;           // PE frequencies of block_mlps; -1 = none set
+    int32_t block_mlp_nparam = 0;
 };

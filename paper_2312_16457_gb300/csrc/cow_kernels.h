@@ -28,12 +28,17 @@ struct MarchArgs {
     int64_t n_rays;
     int32_t n_ray_ids;
     int32_t smem_recs;     // view mode, thread schedule: block records the launch's shared memory holds
+    const float *const *block_mlps;  // view mode, per-block MLPs: weights of record k, parallel to recs
+    int32_t n_freq;                  // PE frequencies of the per-block MLPs
 };
 
 // marching schedules of the view kernel
-constexpr int kSchedWarp = 0;    // one ray per warp, lanes on consecutive lattice samples
-constexpr int kSchedThread = 1;  // one ray per thread
-cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st);
+constexpr int kSchedWarp = 0;         // one ray per warp, lanes on consecutive lattice samples
+constexpr int kSchedThread = 1;       // one ray per thread, records in shared memory
+constexpr int kSchedThreadConst = 2;  // one ray per thread, records in the parameter buffer
+struct ParamRecs;
+cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st,
+                               const ParamRecs *pr = nullptr);
 cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st);
 int march_tile_w();
 int march_tile_h();

@@ -52,36 +52,64 @@ __device__ __forceinline__ void write_outputs(const MarchArgs &a, int64_t row, c
     if (a.out_nsamp) a.out_nsamp[row] = s.nsamp;
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs a) {
-    __shared__ float s_mlp[kMlpParams + 1];
-    extern __shared__ __align__(16) unsigned char s_dyn[];  // a.smem_recs block records
-    BlockRec *s_rec = reinterpret_cast<BlockRec *>(s_dyn);
-    __shared__ alignas(8) uint64_t s_bar;
-    // view of this tile (views are ordered by tile_begin)
-    const int tile = blockIdx.x;
+// View of a tile: views are ordered by tile_begin.
+__device__ __forceinline__ int view_of_tile(const MarchArgs &a, int tile) {
     int lo = 0, hi = a.n_views - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (a.views[mid].tile_begin <= tile) lo = mid;
         else hi = mid - 1;
     }
-    const ViewRec &v = a.views[lo];
+    return lo;
+}
+
+// Per-block MLP form (Eq. 5 with Eq. 3 per block): every block is marched
+// from an in-block transmittance of 1 (its C_d^k, F^k and 1 - alpha^k, Eq. 1-2
+// / Eq. 11), a block with occupied samples adds T C^k with its own MLP, and
+// T carries the product of the blocks' 1 - alpha^k.  Early termination uses
+// the ray's total transmittance: inside block k it stops once
+// T_k < ert_eps / T.
+template <int DT>
+__device__ __forceinline__ void march_blocks_blend(const MarchArgs &a, const ViewRec &v, const BlockRec *recs,
+                                                   const float o[3], const float d[3], const float inv_d[3],
+                                                   float omax, int64_t row) {
+    float C[3] = {0.f, 0.f, 0.f}, Cd[3] = {0.f, 0.f, 0.f}, F[4] = {0.f, 0.f, 0.f, 0.f}, T = 1.f;
+    int nsamp = 0;
     const int n_blk = v.ids_count;
-    const bool staged = n_blk > 0 && n_blk <= a.smem_recs;
-    if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
-    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
-    __syncthreads();
-    // the view's block records (near to far) go to shared memory by one TMA bulk copy
-    if (staged) {
-        if (threadIdx.x == 0)
-            bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
-        if (!mbar_wait(&s_bar, 0, kWaitPolls)) {
-            atomicOr(a.err, kErrTimeout);
-            if (!mbar_wait(&s_bar, 0, kWaitPolls)) return;  // copy still in flight: leave without touching it
+    for (int k = 0; k < n_blk; k++) {
+        RayState sb = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+        march_block<DT>(recs[k], o, d, inv_d, omax, a.ert_eps > 0.f ? a.ert_eps / T : 0.f, sb, a.err);
+        if (sb.nsamp == 0) continue;
+        float phi[3];
+        block_mlp(a.block_mlps[v.ids_begin + k], a.n_freq, sb.Cd, sb.F, d, phi);
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            C[c] = fmaf(T, sb.Cd[c] + phi[c], C[c]);
+            Cd[c] = fmaf(T, sb.Cd[c], Cd[c]);
         }
+#pragma unroll
+        for (int c = 0; c < 4; c++) F[c] = fmaf(T, sb.F[c], F[c]);
+        T *= sb.T;
+        nsamp += sb.nsamp;
+        if (sb.done) break;
     }
-    const BlockRec *recs = staged ? s_rec : a.recs + v.ids_begin;
+    float *rgb = a.out_rgb + 3 * row;
+    rgb[0] = C[0];
+    rgb[1] = C[1];
+    rgb[2] = C[2];
+    if (a.out_aux) {
+        float4 *ap = reinterpret_cast<float4 *>(a.out_aux + 8 * row);
+        ap[0] = make_float4(Cd[0], Cd[1], Cd[2], F[0]);
+        ap[1] = make_float4(F[1], F[2], F[3], T);
+    }
+    if (a.out_nsamp) a.out_nsamp[row] = nsamp;
+}
+
+// One ray per thread of the tile: march the view's near-to-far block list
+// recs[0 .. ids_count) and write the pixel.
+template <int DT, bool kBlockMlp>
+__device__ __forceinline__ void march_tile_rays(const MarchArgs &a, const ViewRec &v, const BlockRec *recs, int tile,
+                                                const float *s_mlp) {
     const int t = tile - v.tile_begin;
     int tx, ty;
     tile_xy(v, t, kTileH, tx, ty);
@@ -92,9 +120,58 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs 
     float o[3], d[3], inv_d[3], omax;
     pixel_ray(v, px, py, o, d);
     ray_setup(d, o, inv_d, omax);
+    const int64_t row = v.pix_offset + (int64_t)py * v.W + px;
+    if (kBlockMlp) {
+        march_blocks_blend<DT>(a, v, recs, o, d, inv_d, omax, row);
+        return;
+    }
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+    const int n_blk = v.ids_count;
     for (int k = 0; k < n_blk && !s.done; k++) march_block<DT>(recs[k], o, d, inv_d, omax, a.ert_eps, s, a.err);
-    write_outputs(a, v.pix_offset + (int64_t)py * v.W + px, s, d, s_mlp);
+    write_outputs(a, row, s, d, s_mlp);
+}
+
+// Thread schedule, block records in shared memory.
+template <int DT, bool kBlockMlp>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs a) {
+    __shared__ float s_mlp[kMlpParams + 1];
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // a.smem_recs block records
+    BlockRec *s_rec = reinterpret_cast<BlockRec *>(s_dyn);
+    __shared__ alignas(8) uint64_t s_bar;
+    const int tile = blockIdx.x;
+    const ViewRec &v = a.views[view_of_tile(a, tile)];
+    const int n_blk = v.ids_count;
+    const bool staged = n_blk > 0 && n_blk <= a.smem_recs;
+    if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
+    if (!kBlockMlp) load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+    __syncthreads();
+    // the view's block records (near to far) go to shared memory by one TMA bulk copy
+    if (staged) {
+        if (threadIdx.x == 0)
+            bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
+        if (!mbar_wait(&s_bar, 0, kWaitPolls)) {
+            atomicOr(a.err, kErrTimeout);
+            if (!mbar_wait(&s_bar, 0, kWaitPolls)) return;  // copy still in flight: leave without touching it
+        }
+    }
+    march_tile_rays<DT, kBlockMlp>(a, v, staged ? s_rec : a.recs + v.ids_begin, tile, s_mlp);
+}
+
+// Thread schedule, block records in the launch's parameter buffer: the
+// record fields the sample loop re-reads then come through the constant
+// cache instead of taking shared-memory wavefronts from the L1 data pipe
+// that the feature gathers are bound by.
+template <int DT, bool kBlockMlp>
+__global__ void __launch_bounds__(kThreads, kMinBlocks)
+    k_march_views_c(const __grid_constant__ MarchArgs a, const __grid_constant__ ParamRecs pr) {
+    __shared__ float s_mlp[kMlpParams + 1];
+    const int tile = blockIdx.x;
+    const ViewRec &v = a.views[view_of_tile(a, tile)];
+    if (!kBlockMlp) {
+        load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+        __syncthreads();
+    }
+    march_tile_rays<DT, kBlockMlp>(a, v, pr.r + v.ids_begin, tile, s_mlp);
 }
 
 // ---------------------------------------------------------------------------
@@ -210,13 +287,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchAr
     __shared__ alignas(16) BlockRec s_rec[kMaxSmemRecs];
     __shared__ alignas(8) uint64_t s_bar;
     const int tile = blockIdx.x;
-    int lo = 0, hi = a.n_views - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (a.views[mid].tile_begin <= tile) lo = mid;
-        else hi = mid - 1;
-    }
-    const ViewRec &v = a.views[lo];
+    const ViewRec &v = a.views[view_of_tile(a, tile)];
     const int n_blk = v.ids_count;
     const bool staged = n_blk > 0 && n_blk <= kMaxSmemRecs;
     if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
@@ -300,23 +371,38 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a
     write_outputs(a, r, s, d, s_mlp);
 }
 
-}  // namespace
-
-cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st) {
-    if (n_tiles <= 0) return cudaSuccess;
-    if (schedule == kSchedThread) {
+template <int DT, bool kBlockMlp>
+cudaError_t launch_thread(const MarchArgs &a, int n_tiles, bool in_params, cudaStream_t st, const ParamRecs *pr) {
+    if (in_params) {
+        k_march_views_c<DT, kBlockMlp><<<n_tiles, kThreads, 0, st>>>(a, *pr);
+    } else {
         // records staged in dynamic shared memory sized to the largest view's
         // list (the driver then sizes the shared-memory carveout for full
         // occupancy and leaves the rest of the SM's 256 KB to L1)
         const size_t smem = (size_t)a.smem_recs * sizeof(BlockRec);
-        switch (a.dtype) {
-        case kF32: k_march_views<kF32><<<n_tiles, kThreads, smem, st>>>(a); break;
-        case kF16: k_march_views<kF16><<<n_tiles, kThreads, smem, st>>>(a); break;
-        case kBF16: k_march_views<kBF16><<<n_tiles, kThreads, smem, st>>>(a); break;
-        case kFP8: k_march_views<kFP8><<<n_tiles, kThreads, smem, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-        }
-    } else {
+        k_march_views<DT, kBlockMlp><<<n_tiles, kThreads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <bool kBlockMlp>
+cudaError_t launch_thread_dt(const MarchArgs &a, int n_tiles, bool in_params, cudaStream_t st, const ParamRecs *pr) {
+    switch (a.dtype) {
+    case kF32: return launch_thread<kF32, kBlockMlp>(a, n_tiles, in_params, st, pr);
+    case kF16: return launch_thread<kF16, kBlockMlp>(a, n_tiles, in_params, st, pr);
+    case kBF16: return launch_thread<kBF16, kBlockMlp>(a, n_tiles, in_params, st, pr);
+    case kFP8: return launch_thread<kFP8, kBlockMlp>(a, n_tiles, in_params, st, pr);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st,
+                               const ParamRecs *pr) {
+    if (n_tiles <= 0) return cudaSuccess;
+    const bool block_mlp = a.block_mlps != nullptr;
+    if (schedule == kSchedWarp && !block_mlp) {
         switch (a.dtype) {
         case kF32: k_march_views_w<kF32><<<n_tiles, kThreads, 0, st>>>(a); break;
         case kF16: k_march_views_w<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
@@ -324,8 +410,12 @@ cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cu
         case kFP8: k_march_views_w<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
         }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
+    const bool in_params = schedule == kSchedThreadConst;
+    if (in_params && !pr) return cudaErrorInvalidValue;
+    return block_mlp ? launch_thread_dt<true>(a, n_tiles, in_params, st, pr)
+                     : launch_thread_dt<false>(a, n_tiles, in_params, st, pr);
 }
 
 cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st) {

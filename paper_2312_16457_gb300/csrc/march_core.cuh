@@ -5,7 +5,23 @@
 
 #include "cow_common.cuh"
 
+// Cache policies of the feature gathers, chosen by measurement on the 1080p
+// LOD city: plane texels are rarely re-read from L1 by neighbouring rays
+// (the planes are 4x finer than the grid), so they bypass L1 and leave it to
+// the grid; grid lines are kept in L2 ahead of plane lines, while the planes
+// still depend on L2 (an L2 evict-first hint on them halves the frame rate).
+#ifndef COW_GRID_LD_POLICY
+#define COW_GRID_LD_POLICY 5
+#endif
+#ifndef COW_PLANE_LD_POLICY
+#define COW_PLANE_LD_POLICY 6
+#endif
+
 namespace cow {
+
+// L1 policies of the grid and plane gathers (LdPolicy)
+constexpr int kGridLd = COW_GRID_LD_POLICY;
+constexpr int kPlaneLd = COW_PLANE_LD_POLICY;
 
 // Feature lookup f^{k,l}(p): trilinear grid + bilinear xy, xz, yz planes.
 // g: the FP32 grid coordinate the cell decision computed.  The 8 channels are
@@ -36,7 +52,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
             const float wyz = wy[dy] * wz[dz];
             const float2 w0 = make_float2(wyz * wx[0], wyz * wx[0]), w1 = make_float2(wyz * wx[1], wyz * wx[1]);
             float2 lo[4], hi[4];
-            Store<DT>::load_pair(b.grid, base + ((int64_t)dz * R + dy) * R, lo, hi);
+            Store<DT>::template load_pair<kGridLd>(b.grid, base + ((int64_t)dz * R + dy) * R, lo, hi);
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], acc[c]));
         }
@@ -47,7 +63,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
             const float w = (wy[dy] * wz[dz]) * wx[dx];
             const float2 w2 = make_float2(w, w);
             float2 v[4];
-            Store<DT>::load8(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
+            Store<DT>::template load8<kGridLd>(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
 #pragma unroll
             for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
         }
@@ -86,7 +102,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 const float2 w0 = make_float2(wv[dv] * wu[0], wv[dv] * wu[0]);
                 const float2 w1 = make_float2(wv[dv] * wu[1], wv[dv] * wu[1]);
                 float2 lo[4], hi[4];
-                Store<DT>::load_pair(b.planes[pl], tb + (int64_t)dv * P, lo, hi);
+                Store<DT>::template load_pair<kPlaneLd>(b.planes[pl], tb + (int64_t)dv * P, lo, hi);
 #pragma unroll
                 for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], pacc[c]));
             }
@@ -97,7 +113,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 const float w = wv[dv] * wu[du];
                 const float2 w2 = make_float2(w, w);
                 float2 v[4];
-                Store<DT>::load8(b.planes[pl], tb + (int64_t)dv * P + du, v);
+                Store<DT>::template load8<kPlaneLd>(b.planes[pl], tb + (int64_t)dv * P + du, v);
 #pragma unroll
                 for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
             }
@@ -137,6 +153,10 @@ __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o
     const float delta = b.delta, inv_delta = 1.0f / b.delta;
     const float m = 4e-6f * (omax + tfar + b.bmax);
     const int Nc = b.Nc, C = b.C, R = b.R;
+    // the occupancy word of the last lookup: a ray stays in one cell for
+    // many lattice steps, so most lookups reuse it instead of a gather
+    int occ_w = -1;
+    uint32_t occ_bits = 0u;
     for (int i = i0; i <= i1; i++) {
         float p[3];
         lattice_point(o, d, delta, i, p);
@@ -150,7 +170,11 @@ __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o
             cell[a] = C == 1 ? v : (int)__umulhi((unsigned)v, b.cdiv);
         }
         const int ci = (cell[2] * Nc + cell[1]) * Nc + cell[0];
-        if (!((__ldg(b.occ + (ci >> 5)) >> (ci & 31)) & 1u)) {
+        if ((ci >> 5) != occ_w) {
+            occ_w = ci >> 5;
+            occ_bits = __ldg(b.occ + occ_w);
+        }
+        if (!((occ_bits >> (ci & 31)) & 1u)) {
             float tx = 3.0e38f;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
@@ -261,6 +285,65 @@ __device__ __forceinline__ void deferred_mlp(const float *w, const float x_in[10
         float a = w[kOffB3 + j];
 #pragma unroll
         for (int i = 0; i < 16; i++) a = fmaf(h2[i], w[kOffW3 + i * 3 + j], a);
+        out[j] = sigmoidf_fast(a);
+    }
+}
+
+// Per-block deferred MLP Phi^k (Eq. 3 with block k's weights, read from
+// global memory: the weight addresses are the same for every lane of a warp,
+// so each load is one broadcast).  Input [C_d^k, F^k, PE(d)], PE(d) = d, then
+// sin(2^l d) and cos(2^l d) for l < n_freq; weights input-major with
+// n_in = 10 + 6 n_freq rows in W1.
+__device__ __forceinline__ void mlp_row16(const float *__restrict__ row, float x, float h[16]) {
+    const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float4 r = __ldg(r4 + q);
+        h[4 * q + 0] = fmaf(x, r.x, h[4 * q + 0]);
+        h[4 * q + 1] = fmaf(x, r.y, h[4 * q + 1]);
+        h[4 * q + 2] = fmaf(x, r.z, h[4 * q + 2]);
+        h[4 * q + 3] = fmaf(x, r.w, h[4 * q + 3]);
+    }
+}
+
+__device__ __forceinline__ void block_mlp(const float *__restrict__ w, int n_freq, const float cd[3], const float f[4],
+                                          const float d[3], float out[3]) {
+    const int n_in = 10 + 6 * n_freq;
+    const float *b1 = w + n_in * 16, *W2 = b1 + 16, *b2 = W2 + 256, *W3 = b2 + 16, *b3 = W3 + 48;
+    float h[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) h[j] = __ldg(b1 + j);
+#pragma unroll
+    for (int i = 0; i < 3; i++) mlp_row16(w + i * 16, cd[i], h);
+#pragma unroll
+    for (int i = 0; i < 4; i++) mlp_row16(w + (3 + i) * 16, f[i], h);
+#pragma unroll
+    for (int i = 0; i < 3; i++) mlp_row16(w + (7 + i) * 16, d[i], h);
+    float sc = 1.0f;  // 2^l
+#pragma unroll 1
+    for (int l = 0; l < n_freq; l++) {
+        const float *rows = w + (10 + 6 * l) * 16;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            float sn, cs;
+            sincosf(sc * d[a], &sn, &cs);
+            mlp_row16(rows + a * 16, sn, h);
+            mlp_row16(rows + (3 + a) * 16, cs, h);
+        }
+        sc *= 2.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) h[j] = fmaxf(h[j], 0.f);
+    float h2[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) h2[j] = __ldg(b2 + j);
+#pragma unroll
+    for (int i = 0; i < 16; i++) mlp_row16(W2 + i * 16, h[i], h2);
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        float a = __ldg(b3 + j);
+#pragma unroll
+        for (int i = 0; i < 16; i++) a = fmaf(fmaxf(h2[i], 0.f), __ldg(W3 + i * 3 + j), a);
         out[j] = sigmoidf_fast(a);
     }
 }

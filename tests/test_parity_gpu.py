@@ -72,7 +72,7 @@ def test_packed_bits_exact(dtype):
             assert np.array_equal(got.view(want.dtype), want), (i, t)
 
 
-@pytest.mark.parametrize("schedule", ["warp", "thread"])
+@pytest.mark.parametrize("schedule", ["warp", "thread", "thread_const"])
 def test_single_block_fp32_full_size(schedule):
     """64^3 grid + 256^2 planes, one 128x128 camera (the paper-scale single block)."""
     sc, cams, mlp = synth.workload_single_block(device="cuda")
@@ -91,7 +91,7 @@ def test_single_block_fp32_full_size(schedule):
     assert ns_e.sum() < ns.sum()
 
 
-@pytest.mark.parametrize("schedule", ["warp", "thread"])
+@pytest.mark.parametrize("schedule", ["warp", "thread", "thread_const"])
 def test_city_fp16_storage(schedule):
     """4x4 ground blocks with blobs crossing borders, FP16 storage, FP32 math:
     parity against the oracle on the same FP16 values."""
@@ -127,6 +127,27 @@ def test_multiview_uneven_equals_single_views():
         assert np.array_equal(aux[off:off + n], a1)
         assert np.array_equal(ns[off:off + n], n1)
         off += n
+
+
+def test_const_records_equal_shared_records():
+    """Block records in the parameter buffer give the image of the shared-memory
+    staging (the same marcher on the same values); a call whose views select
+    more records than the parameter buffer holds runs staged."""
+    sc, _, mlp = synth.workload_city_4x4(R=24, P=48)
+    ctx = cow.Context(sc, "bf16")
+    cams = [synth.camera((0.3 * k, -7.0, 6.0), (0.0, 0.0, -1.0), 40 + k, 24, 60.0) for k in range(7)]
+    ids = [ctx.sort_blocks(c, list(range(16))) for c in cams]
+    assert sum(len(i) for i in ids) > 96
+    for views in (cams[:1], cams[:3], cams):
+        vid = ids[:len(views)]
+        ctx.set_schedule("thread")
+        want = _render(ctx, views, vid, mlp, ert_eps=1e-5)
+        ctx.set_schedule("thread_const")
+        got = _render(ctx, views, vid, mlp, ert_eps=1e-5)
+        assert np.array_equal(got[2], want[2])
+        assert np.abs(got[0] - want[0]).max() <= 1e-6
+        assert np.abs(got[1] - want[1]).max() <= 1e-6
+    ctx.sync_check()
 
 
 def test_tile_order_keeps_the_image():
@@ -235,7 +256,7 @@ def _c2w_down(x, y, z):
     return c2w
 
 
-@pytest.mark.parametrize("schedule", ["warp", "thread"])
+@pytest.mark.parametrize("schedule", ["warp", "thread", "thread_const"])
 def test_edge_cases(schedule):
     sc, _, mlp = synth.workload_city_4x4(R=16, P=32)
     ctx = cow.Context(sc, "fp32")
