@@ -38,7 +38,7 @@ METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
 # the default workload (profiles/march_views_city_lod_1080p_traffic.md); valid
 # for the marcher revision named here and null for any other configuration.
 MARCH_REVISION = "v6-cachehints"
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("city_lod_1080p", "bf16", "thread_const", 1): 48948587392}
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}
 GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160}  # per occupied sample: 20 texels x 8 ch
@@ -465,6 +465,16 @@ def run_batch(args, ws, rank, local):
     t32 = time_steps(per_view, max(3, args.steps // 4), 2, flush, stream)
     ctx32.sync_check()
     ms32 = float(np.mean(t32))
+    # the same storage, one launch per view (what the persistent batch replaces)
+    outs16 = [torch.empty((c.width * c.height, 3), device=dev) for c in cams]
+
+    def per_view_same():
+        for c, i, o16 in zip(cams, ids, outs16):
+            ctx.render([c], [i], mlp_d, ert_eps=args.ert, aux=False, out=(o16, None, None))
+
+    t16 = time_steps(per_view_same, max(3, args.steps // 4), 2, flush, stream)
+    ctx.sync_check()
+    ms16 = float(np.mean(t16))
     rgb32 = torch.cat(outs32).cpu().numpy()
     p = psnr(out.cpu().numpy(), rgb32)
     px1080 = 1920 * 1080
@@ -482,6 +492,8 @@ def run_batch(args, ws, rank, local):
             "mrays_per_s": round(npix / ms / 1e3 * ws, 3),
             "plain_fp32_per_view": {"ms_per_batch": round(ms32, 3),
                                     "frames_per_s": round(npix / (ms32 / 1000.0) / px1080, 3)},
+            "same_storage_per_view": {"ms_per_batch": round(ms16, 3),
+                                      "frames_per_s": round(npix / (ms16 / 1000.0) / px1080, 3)},
             "psnr_vs_plain_fp32_db": round(p, 2), "clocks": ck}
     if rank == 0:
         print(json.dumps(line), flush=True)
