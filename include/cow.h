@@ -186,6 +186,54 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
  * a render still running on another stream must be finished first. */
 cow_status cow_set_block_mlps(cow_ctx *ctx, const float *mlps, int32_t n_mlps, int32_t n_freq, void *stream);
 
+/* Dynamic loading and unloading under a device-memory budget (App. D's
+ * dynamic loading strategy; Sec. 1 lists it with LOD as the way resources are
+ * managed).  A block's loadable resources are its packed grid and planes
+ * (cow_block_bytes); occupancy, scales and records stay resident.
+ *   cow_set_residency : budget_bytes > 0 keeps a pinned host copy of every
+ *       block's packed features and unloads every block from the device;
+ *       from then on each cow_render / cow_render_rays / cow_render_backward
+ *       / cow_update_features call loads the blocks it uses, after unloading
+ *       the least recently used blocks it does not use (ties: lowest index)
+ *       until they fit.  A call whose blocks alone exceed the budget fails
+ *       with COW_ERR_OOM and changes nothing.  Setting a smaller budget
+ *       unloads least recently used blocks; 0 loads every block back and
+ *       frees the host copies.  Features changed by cow_update_features are
+ *       copied back to the host copy before their block is unloaded.
+ *       Loads are ordered on the calling stream; the host waits for them
+ *       before the call returns (a context serves one stream at a time in
+ *       this mode).  The batched form and this mode exclude each other
+ *       (COW_ERR_UNSUPPORTED); cow_render_backward_noalloc loads nothing and
+ *       rejects unloaded blocks (INVALID_ARG).
+ *   cow_get_residency : the budget, the bytes and blocks now on the device
+ *       and the load / unload counters since the context was created.
+ *   cow_block_bytes   : bytes of block's packed grid and planes on the device. */
+typedef struct {
+    int64_t budget_bytes;
+    int64_t resident_bytes;
+    int32_t resident_blocks;
+    int64_t uploads;       /* blocks loaded */
+    int64_t upload_bytes;  /* bytes copied host -> device by loads */
+    int64_t evictions;     /* blocks unloaded */
+} cow_residency;
+cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream);
+cow_status cow_get_residency(const cow_ctx *ctx, cow_residency *out);
+cow_status cow_block_bytes(const cow_ctx *ctx, int32_t block, int64_t *out_bytes);
+
+/* Residency-aware order of views (host only, needs no context or GPU): given
+ * each block's bytes and every view's block ids (CSR, as cow_render), pick an
+ * order that loads few bytes under budget_bytes, greedily taking next the
+ * view that loads the fewest bytes given what the previous views left
+ * resident.  It simulates exactly the loading rule of cow_set_residency
+ * (from its cold start, one view per call), so rendering the views one per
+ * cow_render call in out_order loads *out_upload_bytes bytes;
+ * *out_upload_bytes_given (may be NULL) is the same for the given order.
+ *   out_order : n_views view indices.
+ * Errors: INVALID_ARG (bad sizes or ids, a view needing more than the budget). */
+cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids,
+                               const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *out_order,
+                               int64_t *out_upload_bytes, int64_t *out_upload_bytes_given);
+
 /* Batched form: many cameras of uneven size and LOD set served by one
  * persistent launch over a (view, tile, block) work queue.  Every CTA takes
  * the next (view, tile) item from a device counter, culls the view's block
@@ -327,6 +375,15 @@ cow_status cow_sync_check(cow_ctx *ctx, void *stream);
 /* Copy out a block's occupancy bits (ceil(ncell/32) words, cell index
  * (cz*Nc + cy)*Nc + cx, bit c&31 of word c>>5) into host memory. */
 cow_status cow_export_occupancy(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words);
+
+/* Copy out the coarse level of a block's two-level occupancy grid (Sec. 4.1,
+ * the multi-level occupancy grid psi^{k,l}): coarse cell (gx, gy, gz) covers
+ * occupancy cells [4g, 4g + 3] per axis (clipped at Nc) and its bit is the OR
+ * of theirs.  Nc2 = ceil(Nc / 4) per axis, index (gz*Nc2 + gy)*Nc2 + gx, bit
+ * g&31 of word g>>5; ceil(Nc2^3 / 32) words into host memory.  The marcher
+ * tests this bit first and leaves an empty coarse cell in one exact jump.
+ * Errors: INVALID_ARG (bad block, n_words too small), CUDA. */
+cow_status cow_export_occupancy_coarse(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words);
 
 /* Copy out a block's packed tensor (0 = grid, 1..3 = planes xy, xz, yz) in its
  * storage format into host memory, with its 8 per-channel scale exponents.

@@ -25,12 +25,18 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
-           "cow_sync_check", "cow_export_occupancy",
+           "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
+           "cow_get_residency", "cow_block_bytes", "cow_plan_view_order",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
+
+
+class Residency(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("resident_bytes", C.c_int64), ("resident_blocks", C.c_int32),
+                ("uploads", C.c_int64), ("upload_bytes", C.c_int64), ("evictions", C.c_int64)]
 
 
 class CowError(RuntimeError):
@@ -75,6 +81,11 @@ def lib():
             "cow_set_tile_order": [P, i32],
             "cow_set_block_mlps": [P, P, i32, i32, P],
             "cow_export_occupancy": [P, i32, P, i64],
+            "cow_export_occupancy_coarse": [P, i32, P, i64],
+            "cow_set_residency": [P, i64, P],
+            "cow_get_residency": [P, P],
+            "cow_block_bytes": [P, i32, P],
+            "cow_plan_view_order": [P, i32, P, P, i32, i64, P, P, P],
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
             "cow_render_backward": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
@@ -273,7 +284,9 @@ class Context:
                                          _stream_ptr(stream)))
 
     def set_schedule(self, name: str):
-        """"warp" (one ray per warp, default) or "thread" (one ray per thread)."""
+        """"thread_const" (default: one ray per thread, block records in the
+        kernel parameter buffer), "thread" (records in shared memory) or
+        "warp" (one ray per warp)."""
         _check(lib().cow_set_schedule(self._ctx, SCHEDULES[name]))
         self.schedule = name
 
@@ -293,6 +306,31 @@ class Context:
         _check(lib().cow_export_occupancy(self._ctx, int(i), _ptr(out), words))
         return out
 
+    # --- dynamic loading ---------------------------------------------------
+    def set_residency(self, budget_bytes: int, stream=None):
+        """Keep at most budget_bytes of packed features on the device (0 = all)."""
+        _check(lib().cow_set_residency(self._ctx, int(budget_bytes), _stream_ptr(stream)))
+
+    def residency(self) -> dict:
+        r = Residency()
+        _check(lib().cow_get_residency(self._ctx, C.byref(r)))
+        return {k: getattr(r, k) for k, _ in Residency._fields_}
+
+    def block_bytes(self, i: int) -> int:
+        out = C.c_int64()
+        _check(lib().cow_block_bytes(self._ctx, int(i), C.byref(out)))
+        return out.value
+
+    def occupancy_coarse(self, i: int) -> np.ndarray:
+        """Coarse level of block i's occupancy grid: one bit per 4^3 cells."""
+        b = self.scene.blocks[i]
+        nc = -(-(b.R - 1) // self.scene.occ_cell)
+        nc2 = -(-nc // 4)
+        words = (nc2 ** 3 + 31) // 32
+        out = np.zeros(words, np.uint32)
+        _check(lib().cow_export_occupancy_coarse(self._ctx, int(i), _ptr(out), words))
+        return out
+
     def packed(self, i: int, tensor: int):
         b = self.scene.blocks[i]
         n = (b.R ** 3 if tensor == 0 else b.P ** 2) * 8
@@ -301,6 +339,23 @@ class Context:
         se = np.zeros(8, np.int32)
         _check(lib().cow_export_packed(self._ctx, int(i), int(tensor), _ptr(out), out.nbytes, _ptr(se)))
         return out, se
+
+
+def plan_view_order(block_bytes: Sequence[int], ids_per_view, budget_bytes: int):
+    """Residency-aware view order (host only): returns (order, bytes loaded in
+    that order, bytes loaded in the given order) under the LRU rule of
+    Context.set_residency, from a cold start, one view per render call."""
+    bb = np.ascontiguousarray(block_bytes, np.int64)
+    offs = np.zeros(len(ids_per_view) + 1, np.int32)
+    for v, ids in enumerate(ids_per_view):
+        offs[v + 1] = offs[v] + len(ids)
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(i, np.int32) for i in ids_per_view])
+                                if offs[-1] > 0 else np.zeros(1, np.int32), np.int32)
+    order = np.zeros(len(ids_per_view), np.int32)
+    planned, given = C.c_int64(), C.c_int64()
+    _check(lib().cow_plan_view_order(_ptr(bb), len(bb), _ptr(flat), _ptr(offs), len(ids_per_view), int(budget_bytes),
+                                     _ptr(order), C.byref(planned), C.byref(given)))
+    return order, planned.value, given.value
 
 
 def gather_peak(bytes_per_load: int, buffer_bytes: int, iters: int = 256, stream=None) -> float:

@@ -18,7 +18,14 @@ namespace cow {
 
 namespace {
 
+#ifndef COW_BATCH_THREADS_PER_SM
+#define COW_BATCH_THREADS_PER_SM 512
+#endif
+
 constexpr int kMaxBatchRecs = 96;             // block records a CTA stages
+// resident threads per SM the register budget is sized for (128 registers a
+// thread; measured faster than the compiler's own ~96-register choice)
+constexpr int kBatchThreadsPerSm = COW_BATCH_THREADS_PER_SM;
 constexpr unsigned kBatchWaitPolls = 1u << 24;  // bound on mbarrier polls
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -64,7 +71,7 @@ __device__ __forceinline__ bool culled(const BlockRec &b, const float o[3], cons
 }
 
 template <int DT, int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) k_march_batch(BatchArgs a) {
+__global__ void __launch_bounds__(TW * TH, kBatchThreadsPerSm / (TW * TH)) k_march_batch(BatchArgs a) {
     constexpr int kNT = TW * TH;
     constexpr int kWarpsX = TW / 8;
     __shared__ float s_mlp[kMlpParams + 1];

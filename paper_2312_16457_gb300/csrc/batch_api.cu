@@ -133,6 +133,8 @@ cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, co
     if (!ctx || !out || max_views < 1 || max_ids < 0 || max_views > (1 << 16) || max_ids > (1 << 22))
         return fail(COW_ERR_INVALID_ARG, "cow_batch_create: bad argument");
     *out = nullptr;
+    if (ctx->budget > 0)
+        return fail(COW_ERR_UNSUPPORTED, "the batched form needs every block resident (residency budget is set)");
     DeviceGuard dg(ctx->device);
     cow_batch *b = new cow_batch();
     b->ctx = ctx;
@@ -152,11 +154,13 @@ cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, co
                     cudaGetErrorString(e));
     }
     std::memset(b->h_stage, 0, b->stage_bytes);
+    ctx->n_batches++;
     *out = b;
     return COW_OK;
 }
 
 cow_status cow_batch_free(cow_batch *b) {
+    if (b && b->ctx) b->ctx->n_batches--;
     batch_destroy(b);
     return COW_OK;
 }

@@ -68,7 +68,10 @@ void destroy(cow_ctx *c) {
         cudaFree(b.grid);
         for (auto *p : b.planes) cudaFree(p);
         cudaFree(b.occ);
+        cudaFree(b.occ2);
         cudaFree(b.scale);
+        for (auto *h : b.host_feat)
+            if (h) cudaFreeHost(h);
     }
     cudaFree(c->d_blocks);
     cudaFree(c->d_err);
@@ -185,6 +188,22 @@ cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *sta
     COW_CUDA(cudaMemcpyAsync(bits.data(), b.occ, (size_t)b.occ_words * 4, cudaMemcpyDeviceToHost, st));
     COW_CUDA(cudaStreamSynchronize(st));
     b.ztop = block_ztop(b, bits, c->occ_cell);
+    // coarse level of the occupancy grid: the OR over each group of
+    // kOccGroup^3 cells (clipped at the far faces)
+    const int Nc2 = (Nc + cow::kOccGroup - 1) / cow::kOccGroup;
+    std::vector<uint32_t> coarse(((size_t)Nc2 * Nc2 * Nc2 + 31) / 32, 0u);
+    for (int z = 0; z < Nc; z++)
+        for (int y = 0; y < Nc; y++)
+            for (int x = 0; x < Nc; x++) {
+                const int64_t ci = ((int64_t)z * Nc + y) * Nc + x;
+                if (!((bits[(size_t)(ci >> 5)] >> (ci & 31)) & 1u)) continue;
+                const int64_t c2 = ((int64_t)(z >> cow::kOccGroupLog2) * Nc2 + (y >> cow::kOccGroupLog2)) * Nc2 +
+                                   (x >> cow::kOccGroupLog2);
+                coarse[(size_t)(c2 >> 5)] |= 1u << (c2 & 31);
+            }
+    b.occ2_words = (int64_t)coarse.size();
+    COW_CUDA(cudaMalloc((void **)&b.occ2, coarse.size() * 4));
+    COW_CUDA(cudaMemcpy(b.occ2, coarse.data(), coarse.size() * 4, cudaMemcpyHostToDevice));
     return COW_OK;
 }
 
@@ -220,6 +239,8 @@ cow::BlockRec make_rec(const cow_ctx *c, const BlockHost &b) {
     for (int k = 0; k < 3; k++) r.planes[k] = b.planes[k];
     r.occ = b.occ;
     r.scale = b.scale;
+    r.occ2 = b.occ2;
+    r.Nc2 = (r.Nc + cow::kOccGroup - 1) / cow::kOccGroup;
     return r;
 }
 
@@ -356,6 +377,120 @@ cow_status resolve_mlp(cow_ctx *c, const float *mlp, cudaStream_t st, const floa
     }
     COW_CUDA(cudaMemcpyAsync(c->d_mlp, mlp, cow::kMlpParams * sizeof(float), cudaMemcpyHostToDevice, st));
     *dev = c->d_mlp;
+    return COW_OK;
+}
+
+// --- dynamic loading / unloading under a device-memory budget (App. D) -----
+// The packed grid and planes of a block are its loadable resources; the
+// occupancy levels, scales and records stay resident (a few KB per block).
+
+int64_t tensor_bytes(const cow_ctx *c, const BlockHost &b, int t) {
+    const int64_t nv = t == 0 ? (int64_t)b.R * b.R * b.R : (int64_t)b.P * b.P;
+    return nv * packed_elem_bytes(c->dtype);
+}
+
+int64_t feature_bytes(const cow_ctx *c, const BlockHost &b) {
+    int64_t s = 0;
+    for (int t = 0; t < 4; t++) s += tensor_bytes(c, b, t);
+    return s;
+}
+
+void **tensor_slot(BlockHost &b, int t) { return t == 0 ? &b.grid : &b.planes[t - 1]; }
+
+// Write the host record of block i and its entry of the device record table.
+cow_status refresh_rec(cow_ctx *c, int32_t i, cudaStream_t st) {
+    c->recs[(size_t)i] = make_rec(c, c->blocks[(size_t)i]);
+    COW_CUDA(cudaMemcpyAsync(c->d_blocks + i, &c->recs[(size_t)i], sizeof(cow::BlockRec), cudaMemcpyHostToDevice, st));
+    COW_CUDA(cudaStreamSynchronize(st));  // the host record is the copy's source
+    return COW_OK;
+}
+
+cow_status evict_block(cow_ctx *c, int32_t i, cudaStream_t st) {
+    BlockHost &b = c->blocks[(size_t)i];
+    if (!b.resident) return COW_OK;
+    if (b.dirty) {  // features changed on the device since the host copy was taken
+        for (int t = 0; t < 4; t++)
+            COW_CUDA(cudaMemcpyAsync(b.host_feat[t], *tensor_slot(b, t), (size_t)tensor_bytes(c, b, t),
+                                     cudaMemcpyDeviceToHost, st));
+        COW_CUDA(cudaStreamSynchronize(st));
+        b.dirty = false;
+    }
+    for (int t = 0; t < 4; t++) {
+        void **slot = tensor_slot(b, t);
+        if (b.async_alloc) COW_CUDA(cudaFreeAsync(*slot, st));
+        else COW_CUDA(cudaFree(*slot));
+        *slot = nullptr;
+    }
+    b.resident = false;
+    c->resident_bytes -= feature_bytes(c, b);
+    c->n_evictions++;
+    return refresh_rec(c, i, st);
+}
+
+cow_status upload_block(cow_ctx *c, int32_t i, cudaStream_t st) {
+    BlockHost &b = c->blocks[(size_t)i];
+    if (b.resident) return COW_OK;
+    for (int t = 0; t < 4; t++) {
+        void **slot = tensor_slot(b, t);
+        const cudaError_t e = cudaMallocAsync(slot, (size_t)tensor_bytes(c, b, t), st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (int u = 0; u < t; u++) {
+                cudaFreeAsync(*tensor_slot(b, u), st);
+                *tensor_slot(b, u) = nullptr;
+            }
+            *slot = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "loading block %d: %s", i,
+                        cudaGetErrorString(e));
+        }
+        COW_CUDA(cudaMemcpyAsync(*slot, b.host_feat[t], (size_t)tensor_bytes(c, b, t), cudaMemcpyHostToDevice, st));
+    }
+    b.async_alloc = true;
+    b.resident = true;
+    const int64_t bytes = feature_bytes(c, b);
+    c->resident_bytes += bytes;
+    c->n_uploads++;
+    c->upload_bytes += bytes;
+    return refresh_rec(c, i, st);
+}
+
+// Make the blocks of one call resident: unload the least recently used
+// blocks the call does not need until the missing ones fit the budget, then
+// load those (in id order).
+cow_status ensure_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) {
+    if (c->budget <= 0) return COW_OK;
+    const int32_t nb = (int32_t)c->blocks.size();
+    std::vector<char> need((size_t)nb, 0);
+    for (int64_t k = 0; k < n; k++) need[(size_t)ids[k]] = 1;
+    int64_t need_bytes = 0, missing = 0;
+    for (int32_t i = 0; i < nb; i++)
+        if (need[(size_t)i]) {
+            const int64_t by = feature_bytes(c, c->blocks[(size_t)i]);
+            need_bytes += by;
+            if (!c->blocks[(size_t)i].resident) missing += by;
+        }
+    if (need_bytes > c->budget)
+        return fail(COW_ERR_OOM, "the call's blocks need %lld bytes, over the residency budget of %lld",
+                    (long long)need_bytes, (long long)c->budget);
+    const uint64_t now = ++c->use_clock;
+    for (int32_t i = 0; i < nb; i++)
+        if (need[(size_t)i]) c->blocks[(size_t)i].last_use = now;
+    while (c->resident_bytes + missing > c->budget) {
+        int32_t victim = -1;
+        for (int32_t i = 0; i < nb; i++) {
+            const BlockHost &b = c->blocks[(size_t)i];
+            if (!b.resident || need[(size_t)i]) continue;
+            if (victim < 0 || b.last_use < c->blocks[(size_t)victim].last_use) victim = i;
+        }
+        if (victim < 0) break;  // cannot happen: the needed blocks alone fit
+        cow_status rc = evict_block(c, victim, st);
+        if (rc != COW_OK) return rc;
+    }
+    for (int32_t i = 0; i < nb; i++)
+        if (need[(size_t)i] && !c->blocks[(size_t)i].resident) {
+            cow_status rc = upload_block(c, i, st);
+            if (rc != COW_OK) return rc;
+        }
     return COW_OK;
 }
 
@@ -550,6 +685,7 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     cow_status rc = plan_views(ctx, cams, n_views, ids, ids_offsets, plan);
     if (rc != COW_OK) return rc;
     const int32_t n_ids = ids_offsets[n_views];
+    if ((rc = ensure_resident(ctx, ids, n_ids, st)) != COW_OK) return rc;
     // the views' block records, near to far, contiguous per view: each CTA
     // stages its view's records with one bulk copy
     std::vector<cow::BlockRec> vrecs((size_t)std::max(n_ids, 1));
@@ -626,9 +762,10 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     if (((uintptr_t)out_rgb & 3u) || ((uintptr_t)out_aux & 15u)) return fail(COW_ERR_INVALID_ARG, "misaligned output");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    cow_status rc;
+    if ((rc = ensure_resident(ctx, ids, n_ids, st)) != COW_OK) return rc;
     COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
     COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    cow_status rc;
     const float *d_mlp = nullptr;
     if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
     float *rgb, *aux;
@@ -686,6 +823,8 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     }
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
+    cow_status rc = ensure_resident(ctx, ids, n_ids, st);
+    if (rc != COW_OK) return rc;
     COW_CUDA(ctx->gptrs.reserve(ptrs.size() * sizeof(float *)));
     COW_CUDA(cudaMemcpyAsync(ctx->gptrs.p, ptrs.data(), ptrs.size() * sizeof(float *), cudaMemcpyHostToDevice, st));
     COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
@@ -732,7 +871,11 @@ cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, c
     unsigned *d_amax = (unsigned *)((unsigned char *)ctx->staging.p + need);
     float *d_inv = (float *)((unsigned char *)ctx->staging.p + need + 64);
     const float *src[4] = {grid, plane_xy, plane_xz, plane_yz};
-    return repack_block(ctx, b, src, ctx->staging.p, d_amax, d_inv, st);
+    cow_status rc = ensure_resident(ctx, &block, 1, st);
+    if (rc != COW_OK) return rc;
+    rc = repack_block(ctx, b, src, ctx->staging.p, d_amax, d_inv, st);
+    if (rc == COW_OK && ctx->budget > 0) b.dirty = true;
+    return rc;
 }
 
 cow_status cow_adam_step(float *param, const float *grad, float *m, float *v, int64_t n, float lr, float beta1,
@@ -778,6 +921,192 @@ cow_status cow_set_block_mlps(cow_ctx *ctx, const float *mlps, int32_t n_mlps, i
     return COW_OK;
 }
 
+cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
+    g_last_error.clear();
+    if (!ctx || budget_bytes < 0) return fail(COW_ERR_INVALID_ARG, "cow_set_residency: null context or budget < 0");
+    if (budget_bytes > 0 && ctx->n_batches > 0)
+        return fail(COW_ERR_UNSUPPORTED, "the batched form needs every block resident: free its batches first");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    COW_CUDA(cudaStreamSynchronize(st));
+    const int32_t nb = (int32_t)ctx->blocks.size();
+    cow_status rc;
+    if (budget_bytes > 0) {
+        // pinned host copies of every block's packed features, taken once
+        for (int32_t i = 0; i < nb; i++) {
+            BlockHost &b = ctx->blocks[(size_t)i];
+            if (b.host_feat[0]) continue;
+            for (int t = 0; t < 4; t++) {
+                const cudaError_t e = cudaMallocHost(&b.host_feat[t], (size_t)tensor_bytes(ctx, b, t));
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    for (int u = 0; u < t; u++) {
+                        cudaFreeHost(b.host_feat[u]);
+                        b.host_feat[u] = nullptr;
+                    }
+                    b.host_feat[t] = nullptr;
+                    return fail(COW_ERR_OOM, "pinned host copy of block %d: %s", i, cudaGetErrorString(e));
+                }
+                COW_CUDA(cudaMemcpy(b.host_feat[t], *tensor_slot(b, t), (size_t)tensor_bytes(ctx, b, t),
+                                    cudaMemcpyDeviceToHost));
+            }
+            b.dirty = false;
+        }
+        if (ctx->budget == 0) {
+            // entering: every block is unloaded; each call loads what it needs
+            ctx->resident_bytes = 0;
+            for (const auto &b : ctx->blocks)
+                if (b.resident) ctx->resident_bytes += feature_bytes(ctx, b);
+            for (int32_t i = 0; i < nb; i++)
+                if ((rc = evict_block(ctx, i, st)) != COW_OK) return rc;
+        }
+        ctx->budget = budget_bytes;
+        while (ctx->resident_bytes > ctx->budget) {  // a smaller budget: unload least recently used first
+            int32_t victim = -1;
+            for (int32_t i = 0; i < nb; i++) {
+                const BlockHost &b = ctx->blocks[(size_t)i];
+                if (b.resident && (victim < 0 || b.last_use < ctx->blocks[(size_t)victim].last_use)) victim = i;
+            }
+            if ((rc = evict_block(ctx, victim, st)) != COW_OK) return rc;
+        }
+        COW_CUDA(cudaStreamSynchronize(st));
+        return COW_OK;
+    }
+    // leaving: load every block back, drop the host copies
+    ctx->budget = 0;
+    for (int32_t i = 0; i < nb; i++)
+        if ((rc = upload_block(ctx, i, st)) != COW_OK) return rc;
+    COW_CUDA(cudaStreamSynchronize(st));
+    for (auto &b : ctx->blocks) {
+        for (int t = 0; t < 4; t++) {
+            if (b.host_feat[t]) cudaFreeHost(b.host_feat[t]);
+            b.host_feat[t] = nullptr;
+        }
+        b.dirty = false;
+    }
+    return COW_OK;
+}
+
+cow_status cow_get_residency(const cow_ctx *ctx, cow_residency *out) {
+    if (!ctx || !out) return fail(COW_ERR_INVALID_ARG, "null argument");
+    out->budget_bytes = ctx->budget;
+    out->resident_bytes = ctx->resident_bytes;
+    int32_t n = 0;
+    for (const auto &b : ctx->blocks) n += b.resident ? 1 : 0;
+    out->resident_blocks = n;
+    out->uploads = ctx->n_uploads;
+    out->upload_bytes = ctx->upload_bytes;
+    out->evictions = ctx->n_evictions;
+    return COW_OK;
+}
+
+cow_status cow_block_bytes(const cow_ctx *ctx, int32_t block, int64_t *out_bytes) {
+    if (!ctx || !out_bytes) return fail(COW_ERR_INVALID_ARG, "null argument");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
+    *out_bytes = feature_bytes(ctx, ctx->blocks[(size_t)block]);
+    return COW_OK;
+}
+
+cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids,
+                               const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *out_order,
+                               int64_t *out_upload_bytes, int64_t *out_upload_bytes_given) {
+    g_last_error.clear();
+    if (!block_bytes || n_blocks < 1 || !ids_offsets || n_views < 1 || budget_bytes < 1 || !out_order)
+        return fail(COW_ERR_INVALID_ARG, "cow_plan_view_order: bad argument");
+    if (ids_offsets[0] != 0) return fail(COW_ERR_INVALID_ARG, "ids_offsets[0] must be 0");
+    for (int32_t i = 0; i < n_blocks; i++)
+        if (block_bytes[i] < 0) return fail(COW_ERR_INVALID_ARG, "block %d: negative size", i);
+    for (int32_t v = 0; v < n_views; v++) {
+        if (ids_offsets[v + 1] < ids_offsets[v]) return fail(COW_ERR_INVALID_ARG, "ids_offsets must be non-decreasing");
+        std::vector<char> seen((size_t)n_blocks, 0);
+        int64_t need = 0;
+        for (int32_t k = ids_offsets[v]; k < ids_offsets[v + 1]; k++) {
+            if (!ids || ids[k] < 0 || ids[k] >= n_blocks)
+                return fail(COW_ERR_INVALID_ARG, "view %d: block id out of range", v);
+            if (!seen[(size_t)ids[k]]) need += block_bytes[ids[k]];
+            seen[(size_t)ids[k]] = 1;
+        }
+        if (need > budget_bytes)
+            return fail(COW_ERR_INVALID_ARG, "view %d needs %lld bytes, over the budget", v, (long long)need);
+    }
+    // the runtime's LRU, from a cold start (cow_set_residency unloads every block)
+    struct Cache {
+        std::vector<char> res;
+        std::vector<uint64_t> last;
+        uint64_t clock = 0;
+        int64_t bytes = 0;
+    };
+    auto cost = [&](const Cache &c, int32_t v) {
+        std::vector<char> seen((size_t)n_blocks, 0);
+        int64_t m = 0;
+        for (int32_t k = ids_offsets[v]; k < ids_offsets[v + 1]; k++)
+            if (!seen[(size_t)ids[k]]) {
+                seen[(size_t)ids[k]] = 1;
+                if (!c.res[(size_t)ids[k]]) m += block_bytes[ids[k]];
+            }
+        return m;
+    };
+    auto apply = [&](Cache &c, int32_t v) {
+        std::vector<char> need((size_t)n_blocks, 0);
+        for (int32_t k = ids_offsets[v]; k < ids_offsets[v + 1]; k++) need[(size_t)ids[k]] = 1;
+        int64_t missing = 0;
+        for (int32_t i = 0; i < n_blocks; i++)
+            if (need[(size_t)i] && !c.res[(size_t)i]) missing += block_bytes[i];
+        const uint64_t now = ++c.clock;
+        for (int32_t i = 0; i < n_blocks; i++)
+            if (need[(size_t)i]) c.last[(size_t)i] = now;
+        while (c.bytes + missing > budget_bytes) {
+            int32_t victim = -1;
+            for (int32_t i = 0; i < n_blocks; i++) {
+                if (!c.res[(size_t)i] || need[(size_t)i]) continue;
+                if (victim < 0 || c.last[(size_t)i] < c.last[(size_t)victim]) victim = i;
+            }
+            if (victim < 0) break;
+            c.res[(size_t)victim] = 0;
+            c.bytes -= block_bytes[victim];
+        }
+        for (int32_t i = 0; i < n_blocks; i++)
+            if (need[(size_t)i] && !c.res[(size_t)i]) {
+                c.res[(size_t)i] = 1;
+                c.bytes += block_bytes[i];
+            }
+        return missing;
+    };
+    auto fresh = [&]() {
+        Cache c;
+        c.res.assign((size_t)n_blocks, 0);
+        c.last.assign((size_t)n_blocks, 0);
+        return c;
+    };
+    // greedy: next the view that loads the fewest bytes now (ties: lowest index)
+    Cache c = fresh();
+    std::vector<char> done((size_t)n_views, 0);
+    int64_t planned = 0;
+    for (int32_t s = 0; s < n_views; s++) {
+        int32_t best = -1;
+        int64_t best_cost = 0;
+        for (int32_t v = 0; v < n_views; v++) {
+            if (done[(size_t)v]) continue;
+            const int64_t m = cost(c, v);
+            if (best < 0 || m < best_cost) {
+                best = v;
+                best_cost = m;
+            }
+        }
+        done[(size_t)best] = 1;
+        out_order[s] = best;
+        planned += apply(c, best);
+    }
+    if (out_upload_bytes) *out_upload_bytes = planned;
+    if (out_upload_bytes_given) {
+        Cache g = fresh();
+        int64_t given = 0;
+        for (int32_t v = 0; v < n_views; v++) given += apply(g, v);
+        *out_upload_bytes_given = given;
+    }
+    return COW_OK;
+}
+
 cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles) {
     if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
     if (strip_tiles < 0 || strip_tiles > 4096) return fail(COW_ERR_INVALID_ARG, "strip_tiles must be in [0, 4096]");
@@ -818,6 +1147,16 @@ cow_status cow_export_occupancy(const cow_ctx *ctx, int32_t block, uint32_t *out
     return COW_OK;
 }
 
+cow_status cow_export_occupancy_coarse(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words) {
+    if (!ctx || !out_bits) return fail(COW_ERR_INVALID_ARG, "null argument");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
+    const BlockHost &b = ctx->blocks[(size_t)block];
+    if (n_words < b.occ2_words) return fail(COW_ERR_INVALID_ARG, "need %lld words", (long long)b.occ2_words);
+    DeviceGuard dg(ctx->device);
+    COW_CUDA(cudaMemcpy(out_bits, b.occ2, (size_t)b.occ2_words * 4, cudaMemcpyDeviceToHost));
+    return COW_OK;
+}
+
 cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, void *out, int64_t nbytes,
                              int32_t *out_scale_exp) {
     if (!ctx || !out) return fail(COW_ERR_INVALID_ARG, "null argument");
@@ -828,14 +1167,15 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
     const int64_t need = nv * cow::kNch * elem_bytes(ctx->dtype);
     if (nbytes < need) return fail(COW_ERR_INVALID_ARG, "need %lld bytes", (long long)need);
     DeviceGuard dg(ctx->device);
-    const void *src = tensor == 0 ? b.grid : b.planes[tensor - 1];
+    // an unloaded block is read from its pinned host copy
+    const void *src = !b.resident ? b.host_feat[tensor] : tensor == 0 ? b.grid : b.planes[tensor - 1];
     if (ctx->dtype == COW_FP32) {
-        COW_CUDA(cudaMemcpy(out, src, (size_t)need, cudaMemcpyDeviceToHost));
+        COW_CUDA(cudaMemcpy(out, src, (size_t)need, cudaMemcpyDefault));
     } else {
         // pair layout on the device: keep the first vertex of every pair
         const int64_t pe = packed_elem_bytes(ctx->dtype), ve = pe / 2;
         std::vector<unsigned char> raw((size_t)(nv * pe));
-        COW_CUDA(cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDeviceToHost));
+        COW_CUDA(cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDefault));
         for (int64_t i = 0; i < nv; i++) std::memcpy((unsigned char *)out + i * ve, raw.data() + i * pe, (size_t)ve);
     }
     if (out_scale_exp)
@@ -923,6 +1263,10 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
     for (int32_t k = 0; k < n_ids; k++)
         if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    for (int32_t k = 0; k < n_ids; k++)
+        if (!ctx->blocks[(size_t)ids[k]].resident)
+            return fail(COW_ERR_INVALID_ARG, "block %d is unloaded: the no-allocation entry point loads no blocks (render "
+                        "the rays with cow_render_rays first)", ids[k]);
     for (const void *q : {(const void *)o, (const void *)d, (const void *)aux, (const void *)dL_drgb, (const void *)grad_mlp, (const void *)mlp})
         if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "backward arrays and the MLP must be device memory");
     if (((uintptr_t)aux & 15u)) return fail(COW_ERR_INVALID_ARG, "aux must be 16-byte aligned");

@@ -28,6 +28,11 @@ constexpr unsigned kErrArg = 4u;      // a kernel met an argument it cannot hand
 
 enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3 };
 
+// Occupancy cells per coarse cell along each axis (the second level of the
+// multi-level occupancy grid).
+constexpr int kOccGroupLog2 = 2;
+constexpr int kOccGroup = 1 << kOccGroupLog2;
+
 // One block as the kernels see it (host fills it once at load time).
 struct alignas(16) BlockRec {
     float lo[3], hi[3];      // world AABB (FP32, exactly the caller's values)
@@ -45,6 +50,9 @@ struct alignas(16) BlockRec {
     const void *planes[3];   // packed P^2 x 8 each (xy, xz, yz)
     const uint32_t *occ;     // occupancy bits
     const float *scale;      // 32 floats: per-channel scale of grid, xy, xz, yz
+    const uint32_t *occ2;    // coarse occupancy: one bit per kOccGroup^3 cells (OR of their bits)
+    int32_t Nc2;             // coarse cells per axis, ceil(Nc / kOccGroup)
+    int32_t pad_;
 };
 static_assert(sizeof(BlockRec) % 16 == 0, "BlockRec must be a multiple of 16 bytes");
 

@@ -68,6 +68,15 @@ struct BlockHost {
     void *grid = nullptr;
     void *planes[3] = {nullptr, nullptr, nullptr};
     uint32_t *occ = nullptr;
+    uint32_t *occ2 = nullptr;  // coarse occupancy level (OR over kOccGroup^3 cells)
+    int64_t occ2_words = 0;
+    // dynamic loading (cow_set_residency): the packed grid and planes may live
+    // only in pinned host memory while the block is unloaded
+    void *host_feat[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool resident = true;
+    bool dirty = false;        // device copy newer than host_feat (cow_update_features)
+    bool async_alloc = false;  // device tensors from cudaMallocAsync
+    uint64_t last_use = 0;
     float *scale = nullptr;
     int32_t scale_exp[4][8];
     int64_t occ_words = 0;
@@ -99,4 +108,11 @@ struct cow_ctx {
     cowi::DevBuf block_mlps;       // cow_set_block_mlps: n_blocks x block_mlp_nparam FP32
     int32_t n_freq = -1;           // PE frequencies of block_mlps; -1 = none set
     int32_t block_mlp_nparam = 0;
+    // dynamic loading: budget for the packed features on the device (0 = all
+    // resident), LRU clock and counters
+    int64_t budget = 0;
+    uint64_t use_clock = 0;
+    int64_t resident_bytes = 0;
+    int64_t n_uploads = 0, upload_bytes = 0, n_evictions = 0;
+    int32_t n_batches = 0;  // live cow_batch objects on this context
 };

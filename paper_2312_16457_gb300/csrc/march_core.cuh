@@ -134,12 +134,16 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
 // (Eq. 4 membership, occupancy skip); fn(p, g) is called for each and
 // returns false to stop the ray.  Returns false when fn stopped it.
 //
-// Empty cells are left with an exact jump: along each axis the FP32 cell
-// index of successive lattice points is monotone (every step of the decision
-// sequence is monotone), so every lattice point before the ray's exit from
-// the cell -- the cell shrunk by a margin m far above the FP32 position and
-// coordinate error -- decides the same empty cell and would be skipped
-// anyway.  The jump lands one lattice step short of that exit.
+// Two-level occupancy (Sec. 4.1's multi-level occupancy grid): a sample
+// tests its own cell; when that is empty it tests the coarse cell around it
+// (kOccGroup^3 cells, the OR of their bits) and leaves the larger of the two
+// empty cells.  Empty cells are left with an exact jump: along each
+// axis the FP32 cell index of successive lattice points is monotone (every
+// step of the decision sequence is monotone, and so is the coarse index
+// cell >> kOccGroupLog2), so every lattice point before the ray's exit from
+// the empty cell -- shrunk by a margin m far above the FP32 position and
+// coordinate error -- decides an empty cell and would be skipped anyway.
+// The jump lands one lattice step short of that exit.
 template <typename Fn>
 __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o[3], const float d[3],
                                                 const float inv_d[3], float omax, unsigned *err, Fn &&fn) {
@@ -152,11 +156,11 @@ __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o
     }
     const float delta = b.delta, inv_delta = 1.0f / b.delta;
     const float m = 4e-6f * (omax + tfar + b.bmax);
-    const int Nc = b.Nc, C = b.C, R = b.R;
-    // the occupancy word of the last lookup: a ray stays in one cell for
-    // many lattice steps, so most lookups reuse it instead of a gather
-    int occ_w = -1;
-    uint32_t occ_bits = 0u;
+    const int Nc = b.Nc, C = b.C, R = b.R, Nc2 = b.Nc2;
+    // the occupancy words of the last lookups: a ray stays in one cell for
+    // many lattice steps, so most lookups reuse them instead of a gather
+    int occ_w = -1, occ2_w = -1;
+    uint32_t occ_bits = 0u, occ2_bits = 0u;
     for (int i = i0; i <= i1; i++) {
         float p[3];
         lattice_point(o, d, delta, i, p);
@@ -175,15 +179,26 @@ __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o
             occ_bits = __ldg(b.occ + occ_w);
         }
         if (!((occ_bits >> (ci & 31)) & 1u)) {
+            // an empty cell; when its whole coarse cell is empty, leave that instead
+            const int ci2 = ((cell[2] >> kOccGroupLog2) * Nc2 + (cell[1] >> kOccGroupLog2)) * Nc2 +
+                            (cell[0] >> kOccGroupLog2);
+            if ((ci2 >> 5) != occ2_w) {
+                occ2_w = ci2 >> 5;
+                occ2_bits = __ldg(b.occ2 + occ2_w);
+            }
+            const int lvl = ((occ2_bits >> (ci2 & 31)) & 1u) ? 0 : kOccGroupLog2;  // log2 cells per edge
+            // exit of the empty cell: cells of C << lvl voxels, the last one
+            // reaching the block's far face
+            const int Ce = C << lvl, last = lvl ? Nc2 - 1 : Nc - 1;
             float tx = 3.0e38f;
 #pragma unroll
             for (int a = 0; a < 3; a++) {
+                const int ce = cell[a] >> lvl;
                 if (d[a] > 0.f) {
-                    const float chi =
-                        cell[a] == Nc - 1 ? b.hi[a] : fmaf((float)((cell[a] + 1) * C), b.vox[a], b.lo[a]);
+                    const float chi = ce == last ? b.hi[a] : fmaf((float)((ce + 1) * Ce), b.vox[a], b.lo[a]);
                     tx = fminf(tx, (chi - m - o[a]) * inv_d[a]);
                 } else if (d[a] < 0.f) {
-                    const float clo = fmaf((float)(cell[a] * C), b.vox[a], b.lo[a]);
+                    const float clo = fmaf((float)(ce * Ce), b.vox[a], b.lo[a]);
                     tx = fminf(tx, (clo + m - o[a]) * inv_d[a]);
                 }
             }

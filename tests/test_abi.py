@@ -74,3 +74,63 @@ def test_calls_reject_null_context(L):
     assert L.cow_set_tile_order(None, 0) == 1
     assert b"null context" in L.cow_last_error()
     assert L.cow_free(None) == 0
+
+
+# --- residency-aware view order (host only) --------------------------------
+
+
+def _simulate(block_bytes, views, order, budget):
+    """The loading rule of cow_set_residency written out in Python: unload the
+    least recently used blocks a call does not need (ties: lowest index)
+    until the missing ones fit, then load them."""
+    res, last, clock, used, loaded = set(), {}, 0, 0, 0
+    for v in order:
+        need = set(views[v])
+        missing = sum(block_bytes[i] for i in need if i not in res)
+        clock += 1
+        for i in need:
+            last[i] = clock
+        while used + missing > budget:
+            victim = min((i for i in res if i not in need), key=lambda i: (last[i], i))
+            res.remove(victim)
+            used -= block_bytes[victim]
+        for i in sorted(need - res):
+            res.add(i)
+            used += block_bytes[i]
+        loaded += missing
+    return loaded
+
+
+def test_plan_view_order_hand_case(L):
+    """Views A = {0, 1}, B = {2, 3}, C = {0, 1} with room for two blocks:
+    A, B, C loads 6 blocks; the planner serves C right after A (4 blocks)."""
+    order, planned, given = cow.plan_view_order([10, 10, 10, 10], [[0, 1], [2, 3], [0, 1]], 20)
+    assert sorted(order.tolist()) == [0, 1, 2]
+    assert given == 60 and planned == 40
+    assert order.tolist() == [0, 2, 1]
+
+
+def test_plan_view_order_matches_simulation(L):
+    import numpy as np
+
+    rng = np.random.default_rng(3)
+    tot_planned = tot_given = 0
+    for trial in range(20):
+        nb = int(rng.integers(4, 40))
+        bb = rng.integers(1, 100, nb).tolist()
+        views = [sorted(rng.choice(nb, size=int(rng.integers(1, min(nb, 8) + 1)), replace=False).tolist())
+                 for _ in range(int(rng.integers(1, 25)))]
+        budget = max(sum(bb[i] for i in v) for v in views) + int(rng.integers(0, 200))
+        order, planned, given = cow.plan_view_order(bb, views, budget)
+        assert sorted(order.tolist()) == list(range(len(views)))
+        assert planned == _simulate(bb, views, order.tolist(), budget)
+        assert given == _simulate(bb, views, list(range(len(views))), budget)
+        tot_planned += planned
+        tot_given += given
+    # greedy is a heuristic (not optimal on every case) but loads less overall
+    assert tot_planned < tot_given
+    # a view over the budget and bad ids are rejected
+    with pytest.raises(cow.CowError):
+        cow.plan_view_order([10, 10], [[0, 1]], 15)
+    with pytest.raises(cow.CowError):
+        cow.plan_view_order([10, 10], [[0, 2]], 100)

@@ -59,6 +59,38 @@ def test_occupancy_bit_exact():
         assert ctx2.ztop(i) == oracle.OracleScene(city).ztop(i)
 
 
+def _coarse_bits(words, nc):
+    """Numpy OR over 4^3 groups of an occupancy bit array (z, y, x order)."""
+    n = nc ** 3
+    bits = ((words[np.arange(n) >> 5] >> (np.arange(n) & 31)) & 1).astype(bool).reshape(nc, nc, nc)
+    nc2 = -(-nc // 4)
+    pad = np.zeros((nc2 * 4,) * 3, bool)
+    pad[:nc, :nc, :nc] = bits
+    g = pad.reshape(nc2, 4, nc2, 4, nc2, 4).any(axis=(1, 3, 5)).ravel()
+    out = np.zeros((g.size + 31) // 32, np.uint32)
+    for c in np.nonzero(g)[0]:
+        out[c >> 5] |= np.uint32(1 << (int(c) & 31))
+    return out
+
+
+def test_coarse_occupancy_is_or_of_cells():
+    """The coarse level of the two-level occupancy grid: bit of a 4^3 group =
+    OR of the (oracle-exact) cell bits, clipped groups at the far faces."""
+    sc, _, _ = synth.workload_single_block(R=64, P=64)
+    ctx = cow.Context(sc, "fp32")
+    want = _coarse_bits(oracle.occupancy(sc.blocks[0].grid, 64, 4, 0.01), 16)
+    assert np.array_equal(ctx.occupancy_coarse(0), want)
+    city = synth.city_scene(8, 2, 2.0, [(33, 40)])
+    city.occ_cell = 3  # Nc = 11: the last group holds 3 cells per axis
+    ctx2 = cow.Context(city, "bf16")
+    n_on = []
+    for i, b in enumerate(city.blocks):
+        want = _coarse_bits(oracle.occupancy(b.grid, 33, 3, 0.01), 11)
+        assert np.array_equal(ctx2.occupancy_coarse(i), want)
+        n_on.append(int(np.unpackbits(want.view(np.uint8)).sum()))
+    assert max(n_on) > 0 and min(n_on) < 27  # both kinds of coarse cell occur
+
+
 @pytest.mark.parametrize("dtype", ["fp32", "fp16", "bf16", "fp8"])
 def test_packed_bits_exact(dtype):
     sc = synth.city_scene(9, 2, 2.0, [(17, 24)])
