@@ -75,6 +75,8 @@ def lib():
             "orc_block_ztop": (dbl, [P]),
             "orc_select_lod": (i32, [P, i32, P, P, i32, P, i32]),
             "orc_sort_view": (None, [P, P, i32, P, P]),
+            "orc_sparsity_loss_grad": (dbl, [P, i32, P, i32, P, i64, dbl, P, P]),
+            "orc_opacity_loss_grad": (dbl, [P, i32, P, i32, P, P, i64, dbl, P, P]),
             "orc_pe_dim": (i32, [i32]),
             "orc_block_mlp_nparam": (i32, [i32]),
             "orc_pe": (None, [P, i32, P]),
@@ -361,6 +363,41 @@ def render_rays_grad(osc: OracleScene, ids: Sequence[int], o, d, mlp, dL_drgb):
                                _ptr(g), C.cast(gptr, C.c_void_p), C.cast(pptr, C.c_void_p), _ptr(gm))
     planes = [gp[3 * i:3 * i + 3] for i in range(len(gg))]
     return gg, planes, gm
+
+
+def _grad_arrays(osc):
+    gg = [np.zeros(x.shape, np.float64) for x in osc.grids]
+    gp = [np.zeros(x.shape, np.float64) for pl in osc.planes for x in pl]
+    gptr = (C.c_void_p * len(gg))(*[x.ctypes.data for x in gg])
+    pptr = (C.c_void_p * len(gp))(*[x.ctypes.data for x in gp])
+    return gg, gp, gptr, pptr
+
+
+def sparsity_loss_grad(osc: OracleScene, ids: Sequence[int], points, weight: float = 1.0, grad: bool = True):
+    """Eq. 7 at the given FP32 points: returns (weight * loss, grid grads,
+    plane grads) (gradients None when grad is False)."""
+    pf = _np(points).reshape(-1, 3)
+    a = np.ascontiguousarray(ids, np.int32)
+    gg, gp, gptr, pptr = _grad_arrays(osc)
+    loss = lib().orc_sparsity_loss_grad(osc.ptr(), len(osc), _ptr(a), len(a), _ptr(pf), pf.shape[0], float(weight),
+                                        C.cast(gptr, C.c_void_p) if grad else None,
+                                        C.cast(pptr, C.c_void_p) if grad else None)
+    if not grad:
+        return loss, None, None
+    return loss, gg, [gp[3 * i:3 * i + 3] for i in range(len(gg))]
+
+
+def opacity_loss_grad(osc: OracleScene, ids: Sequence[int], o, d, weight: float = 1.0, grad: bool = True):
+    """Eq. 8 over ray batches (mean over rays of the sum over blocks)."""
+    of, df = _np(o).reshape(-1, 3), _np(d).reshape(-1, 3)
+    a = np.ascontiguousarray(ids, np.int32)
+    gg, gp, gptr, pptr = _grad_arrays(osc)
+    loss = lib().orc_opacity_loss_grad(osc.ptr(), len(osc), _ptr(a), len(a), _ptr(of), _ptr(df), of.shape[0],
+                                       float(weight), C.cast(gptr, C.c_void_p) if grad else None,
+                                       C.cast(pptr, C.c_void_p) if grad else None)
+    if not grad:
+        return loss, None, None
+    return loss, gg, [gp[3 * i:3 * i + 3] for i in range(len(gg))]
 
 
 def mlp(w, x) -> np.ndarray:

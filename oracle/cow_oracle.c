@@ -26,7 +26,9 @@
  *   - LOD selection, visibility and depth sorting of the real-time viewer
  *     (Appendix D);
  *   - the analytic gradient of the rendered colour with respect to grid,
- *     plane and MLP parameters (reverse mode through the steps above).
+ *     plane and MLP parameters (reverse mode through the steps above);
+ *   - the sparsity (Eq. 7) and block-opacity (Eq. 8) regularisers of
+ *     Sec. 4.3 with their gradients.
  *
  * Precision: every continuous quantity (interpolation, activations,
  * compositing, MLP, gradients) is FP64.  The discrete decisions -- which
@@ -1047,6 +1049,94 @@ void orc_render_rays_grad(const orc_block *blocks, int32_t nb, const int32_t *id
         free(Ck);
         free(gmlp);
     }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Training-stage regularisers of Sec. 4.3 on the baked representation, with
+ * their gradients (accumulated into the same arrays as above).
+ *
+ * Sparsity (Eq. 7): the mean over given points p of |alpha(p)|, alpha(p) =
+ * 1 - exp(-sigma(p) delta_b) with sigma from the block that contains p
+ * (Eq. 4 membership on the FP32 point; the first such block in ids) and that
+ * block's sample spacing delta_b; a point in no block contributes 0.
+ * d alpha / d f0 = sigma delta (1 - alpha).
+ *
+ * Opacity (Eq. 8): for every ray and every block with at least one occupied
+ * sample on it, the block opacity alpha^k = 1 - prod_i (1 - alpha_i) (Eq. 11)
+ * enters -[a log a + (1 - a) log(1 - a)] with a = alpha^k clamped to
+ * [1e-6, 1 - 1e-6]; the loss is the mean over rays of the sum over blocks.
+ * d alpha^k / d f0_i = sigma_i delta (1 - alpha^k); the clamp's derivative is
+ * 0 outside the interval.  No early termination.
+ *
+ * Both return weight * loss and add weight * dloss/dparam to the gradients. */
+
+static void scatter_ch0(const sample *s, double g0, double *const *grad_grid, double *const *grad_planes) {
+    const int32_t bi = s->block;
+    for (int q = 0; q < 8; q++) atomic_add(&grad_grid[bi][s->tp.gidx[q]], s->tp.gw[q] * g0);
+    for (int pl = 0; pl < 3; pl++)
+        for (int q = 0; q < 4; q++) atomic_add(&grad_planes[3 * bi + pl][s->tp.pidx[pl][q]], s->tp.pw[pl][q] * g0);
+}
+
+double orc_sparsity_loss_grad(const orc_block *blocks, int32_t nb, const int32_t *ids, int32_t n_ids,
+                              const float *pts, int64_t n_pts, double weight, double *const *grad_grid,
+                              double *const *grad_planes) {
+    (void)nb;
+    double loss = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : loss)
+    for (int64_t r = 0; r < n_pts; r++) {
+        const float *pf = pts + 3 * r;
+        int32_t bi = -1;
+        for (int k = 0; k < n_ids && bi < 0; k++)
+            if (inside_block(&blocks[ids[k]], pf)) bi = ids[k];
+        if (bi < 0) continue;
+        const orc_block *b = &blocks[bi];
+        sample s;
+        const double p[3] = {pf[0], pf[1], pf[2]};
+        make_taps(b, p, &s.tp);
+        double f[NCH];
+        eval_feature(b, &s.tp, f);
+        s.block = bi;
+        s.delta = (double)block_delta(b);
+        s.sigma = exp(f[0]);
+        s.alpha = -expm1(-s.sigma * s.delta);
+        loss += s.alpha;
+        if (grad_grid) scatter_ch0(&s, weight / (double)n_pts * s.sigma * s.delta * (1.0 - s.alpha), grad_grid, grad_planes);
+    }
+    return weight * loss / (double)(n_pts > 0 ? n_pts : 1);
+}
+
+double orc_opacity_loss_grad(const orc_block *blocks, int32_t nb, const int32_t *ids, int32_t n_ids,
+                             const float *o, const float *d, int64_t n_rays, double weight,
+                             double *const *grad_grid, double *const *grad_planes) {
+    (void)nb;
+    const double eps = 1e-6;
+    double loss = 0.0;
+#pragma omp parallel reduction(+ : loss)
+    {
+        sample_vec sv = {0, 0, 0};
+        int32_t *order = (int32_t *)malloc((size_t)(n_ids ? n_ids : 1) * sizeof(int32_t));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < n_rays; r++) {
+            sort_ids_for_ray(blocks, ids, n_ids, o + 3 * r, order);
+            for (int k = 0; k < n_ids; k++) {
+                sv.n = 0;
+                const int64_t nk = block_samples(blocks, order[k], o + 3 * r, d + 3 * r, &sv);
+                if (nk == 0) continue;
+                double T = 1.0;
+                for (int64_t i = 0; i < nk; i++) T *= 1.0 - sv.v[i].alpha;
+                const double a_raw = 1.0 - T;
+                const double a = a_raw < eps ? eps : a_raw > 1.0 - eps ? 1.0 - eps : a_raw;
+                loss += -(a * log(a) + (1.0 - a) * log(1.0 - a));
+                if (!grad_grid || !(a_raw > eps && a_raw < 1.0 - eps)) continue;
+                const double ga = -weight / (double)n_rays * log(a / (1.0 - a)); /* dL / d alpha^k */
+                for (int64_t i = 0; i < nk; i++)
+                    scatter_ch0(&sv.v[i], ga * sv.v[i].sigma * sv.v[i].delta * T, grad_grid, grad_planes);
+            }
+        }
+        free(sv.v);
+        free(order);
+    }
+    return weight * loss / (double)(n_rays > 0 ? n_rays : 1);
 }
 
 /* ------------------------------------------------------------------------- */
