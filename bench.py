@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--res-div", type=int, default=1, help="divide grid / plane resolutions (profiling runs)")
     ap.add_argument("--schedule", choices=["warp", "thread", "thread_const"], default="thread_const", help="marching schedule")
     ap.add_argument("--strip", type=int, default=0, help="tile order: 0 raster, k strips of k tile columns")
+    ap.add_argument("--reg", action="store_true",
+                    help="fit_2x2: add the sparsity (0.05) and opacity (0.001) regularisers to every step")
     return ap.parse_args()
 
 
@@ -389,7 +391,7 @@ def run_fit(args, ws, rank, local):
     tctx = cow.Context(tgt, "fp32")
     target = tctx.render_rays(o, d, [0, 1, 2, 3], mlp_t, aux=False)[0]
     tctx.close()
-    fit = train.Fitter(sc, mlp)
+    fit = train.Fitter(sc, mlp, lambda_sparsity=0.05 if args.reg else 0.0, lambda_opacity=0.001 if args.reg else 0.0)
     stream = torch.cuda.current_stream()
 
     def psnr_now():
@@ -418,7 +420,9 @@ def run_fit(args, ws, rank, local):
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "fit_2x2", "scene": f"2x2 blocks, {R}^3 grid + {P}^2 planes, FP32 parameters",
                        "rays": n, "adam_steps": args.warmup + args.steps, "lr_features": fit.lr_feat,
-                       "lr_mlp": fit.lr_mlp},
+                       "lr_mlp": fit.lr_mlp,
+                       "regularisers": ({"sparsity": 0.05, "sparsity_points": fit.n_sparsity_points,
+                                         "opacity": 0.001} if args.reg else None)},
             "fit_psnr_db": {"before": round(p0, 2), "after": round(p1, 2)}, "clocks": ck}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -331,6 +331,31 @@ cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, const float
 cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, const float *plane_xy,
                                const float *plane_xz, const float *plane_yz, void *stream);
 
+/* Training-stage regularisers of Sec. 4.3 on the loaded blocks, with their
+ * gradients with respect to the density channel of the grids and planes.
+ *   cow_sparsity_loss (Eq. 7): the mean over n_points points (device, FP32
+ *     x, y, z) of alpha(p) = 1 - exp(-sigma(p) delta), sigma from the first
+ *     block of ids that contains p (Eq. 4 membership), delta that block's
+ *     sample spacing; a point in no block counts 0.  The paper draws the
+ *     points uniformly in the scene's box (2^14 of them).
+ *   cow_opacity_loss (Eq. 8): for each ray (device o, d as cow_render_rays,
+ *     blocks ordered per ray) and each block with at least one occupied
+ *     sample, the binary entropy -(a log a + (1 - a) log(1 - a)) of the
+ *     block's opacity a = 1 - prod (1 - alpha_i) (Eq. 11), clamped to
+ *     [1e-6, 1 - 1e-6]; the mean over rays of the sum over blocks.  No early
+ *     termination.
+ * Both add weight * loss to *loss (a device float; NULL: not computed) and
+ * weight * d loss / d f0 into the FP32 gradient arrays, laid out as for
+ * cow_render_backward (grad_grid / grad_planes both NULL: no gradient;
+ * individual entries may be NULL).  ids: 1 .. 64 block ids.
+ * Errors: INVALID_ARG, OOM (residency budget), CUDA. */
+cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points, const int32_t *ids, int32_t n_ids,
+                             float weight, float *loss, float *const *grad_grid, float *const *grad_planes,
+                             void *stream);
+cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                            int32_t n_ids, float weight, float *loss, float *const *grad_grid,
+                            float *const *grad_planes, void *stream);
+
 /* One Adam step on n FP32 parameters (device arrays param, grad, m, v):
  *   m = b1 m + (1-b1) g;  v = b2 v + (1-b2) g^2;
  *   param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */

@@ -26,7 +26,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
-           "cow_get_residency", "cow_block_bytes", "cow_plan_view_order",
+           "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_sparsity_loss", "cow_opacity_loss",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune", "cow_last_error",
@@ -83,6 +83,8 @@ def lib():
             "cow_export_occupancy": [P, i32, P, i64],
             "cow_export_occupancy_coarse": [P, i32, P, i64],
             "cow_set_residency": [P, i64, P],
+            "cow_sparsity_loss": [P, P, i64, P, i32, flt, P, P, P, P],
+            "cow_opacity_loss": [P, P, P, i64, P, i32, flt, P, P, P, P],
             "cow_get_residency": [P, P],
             "cow_block_bytes": [P, i32, P],
             "cow_plan_view_order": [P, i32, P, P, i32, i64, P, P, P],
@@ -275,6 +277,42 @@ class Context:
         fn = lib().cow_render_backward_noalloc if noalloc else lib().cow_render_backward
         _check(fn(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a), len(a), _ptr(mlp),
                   float(ert_eps), _ptr(aux), _ptr(dL_drgb.contiguous()), gg, gp, _ptr(grad_mlp), _stream_ptr(stream)))
+
+    def _grad_tables(self, grads):
+        if grads is None:
+            return None, None
+        grad_grids, grad_planes = grads
+        nb = self.n_blocks
+        gg = (C.c_void_p * nb)(*[_ptr(g) if g is not None else None for g in grad_grids])
+        flat = []
+        for i in range(nb):
+            pl = grad_planes[i] if grad_planes[i] is not None else [None, None, None]
+            flat += [_ptr(t) if t is not None else None for t in pl]
+        return gg, (C.c_void_p * (3 * nb))(*flat)
+
+    def sparsity_loss(self, points, ids, weight: float = 1.0, loss=None, grads=None, stream=None):
+        """Eq. 7 at device points (n x 3): adds weight * loss to `loss` (a
+        1-element device tensor, created when None, returned) and, when
+        grads = (grad_grids, grad_planes) is given, the density gradient."""
+        a = np.ascontiguousarray(ids, np.int32)
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=points.device)
+        gg, gp = self._grad_tables(grads)
+        p = points.contiguous()
+        _check(lib().cow_sparsity_loss(self._ctx, _ptr(p), p.shape[0], _ptr(a), len(a), float(weight), _ptr(loss),
+                                       gg, gp, _stream_ptr(stream)))
+        return loss
+
+    def opacity_loss(self, o, d, ids, weight: float = 1.0, loss=None, grads=None, stream=None):
+        """Eq. 8 over a ray batch (device o, d): as sparsity_loss."""
+        a = np.ascontiguousarray(ids, np.int32)
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=o.device)
+        gg, gp = self._grad_tables(grads)
+        oc, dc = o.contiguous(), d.contiguous()
+        _check(lib().cow_opacity_loss(self._ctx, _ptr(oc), _ptr(dc), oc.shape[0], _ptr(a), len(a), float(weight),
+                                      _ptr(loss), gg, gp, _stream_ptr(stream)))
+        return loss
 
     def update_features(self, i: int, grid, planes, stream=None):
         """Re-pack block i's features from new FP32 arrays (occupancy kept)."""

@@ -239,6 +239,158 @@ __global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Training-stage regularisers (Sec. 4.3).
+//   Sparsity (Eq. 7): alpha(p) = 1 - exp(-sigma(p) delta_b) at given points,
+//     in the block containing p (Eq. 4, first in ids); loss += weight/n alpha,
+//     d alpha / d f0 = sigma delta (1 - alpha).
+//   Opacity (Eq. 8): per ray and block with occupied samples, alpha^k =
+//     1 - prod (1 - alpha_i); loss += weight/n H(clamp(alpha^k)) with H the
+//     binary entropy and the clamp to [1e-6, 1 - 1e-6];
+//     d alpha^k / d f0_i = sigma_i delta (1 - alpha^k).  The block is marched
+//     twice: once for alpha^k, once to scatter.
+// Gradients reach the density channel only: 20 scalar atomics per point or
+// sample (8 grid vertices, 4 texels of each plane).
+
+__device__ __forceinline__ void scatter_ch0(const BlockRec &b, float *gg, float *const gp[3], const float p[3],
+                                            const float g[3], float g0) {
+    if (gg) {
+        float fr[3];
+        int c0[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const int v = min(max(__float2int_rd(g[a]), 0), b.R - 2);
+            c0[a] = v;
+            fr[a] = fminf(fmaxf(g[a], 0.f), (float)(b.R - 1)) - (float)v;
+        }
+        const int64_t R = b.R;
+        const int64_t base = (c0[2] * R + c0[1]) * R + c0[0];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+            const float w = (dy ? fr[1] : 1.f - fr[1]) * (dz ? fr[2] : 1.f - fr[2]) * (dx ? fr[0] : 1.f - fr[0]);
+            atomicAdd(gg + 8 * (base + (dz * R + dy) * R + dx), w * g0);
+        }
+    }
+    float hf[3];
+    int h0[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        const int u = min(max(__float2int_rd(h), 0), b.P - 2);
+        h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
+        h0[a] = u;
+        hf[a] = h - (float)u;
+    }
+    const int64_t P = b.P;
+#pragma unroll
+    for (int pl = 0; pl < 3; pl++) {
+        if (!gp[pl]) continue;
+        const int ua = pl == 2 ? 1 : 0, va = pl == 0 ? 1 : 2;
+        const int64_t tb = (int64_t)h0[va] * P + h0[ua];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int du = q & 1, dv = q >> 1;
+            const float w = (dv ? hf[va] : 1.f - hf[va]) * (du ? hf[ua] : 1.f - hf[ua]);
+            atomicAdd(gp[pl] + 8 * (tb + dv * P + du), w * g0);
+        }
+    }
+}
+
+// sum of v over the CTA, added to *loss by one thread
+__device__ __forceinline__ void add_loss(float v, float *loss) {
+    __shared__ float s_part[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float w = threadIdx.x < (blockDim.x >> 5) ? s_part[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+        if (threadIdx.x == 0 && loss) atomicAdd(loss, w);
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a) {
+    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    float term = 0.f;
+    if (r < a.n) {
+        const float p[3] = {__ldg(a.pts + 3 * r), __ldg(a.pts + 3 * r + 1), __ldg(a.pts + 3 * r + 2)};
+        int id = -1;
+        for (int k = 0; k < a.n_ids && id < 0; k++) {
+            const int c = __ldg(a.ids + k);
+            if (inside_block(a.recs[c], p)) id = c;
+        }
+        if (id >= 0) {
+            const BlockRec &b = a.recs[id];
+            float g[3];
+#pragma unroll
+            for (int c = 0; c < 3; c++) g[c] = axis_coord(p[c], b.lo[c], b.kg[c]);
+            float2 f2[4];
+            accumulate_sample<DT>(b, p, g, f2);
+            const float sigma = expf(f2[0].x);
+            const float alpha = -expm1f(-sigma * b.delta);
+            const float scale = a.weight / (float)a.n;
+            term = scale * alpha;
+            if (a.grad_grid) {
+                float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
+                scatter_ch0(b, a.grad_grid[id], gp, p, g, scale * sigma * b.delta * (1.f - alpha));
+            }
+        }
+    }
+    add_loss(term, a.loss);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a) {
+    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    float term = 0.f;
+    if (r < a.n) {
+        float o[3], d[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            o[c] = __ldg(a.ray_o + 3 * r + c);
+            d[c] = __ldg(a.ray_d + 3 * r + c);
+        }
+        int order[kMaxRayIds];
+        const int n = sort_blocks_for_ray(a.recs, a.ids, a.n_ids, o, order);
+        float inv_d[3], omax;
+        ray_setup(d, o, inv_d, omax);
+        const float scale = a.weight / (float)a.n, eps = 1e-6f;
+        for (int k = 0; k < n; k++) {
+            const int id = order[k];
+            const BlockRec &b = a.recs[id];
+            const float delta = b.delta;
+            float T = 1.f;
+            int nk = 0;
+            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3]) {
+                float2 f2[4];
+                accumulate_sample<DT>(b, p, g, f2);
+                T *= expf(-expf(f2[0].x) * delta);
+                nk++;
+                return true;
+            });
+            if (nk == 0) continue;
+            const float a_raw = 1.f - T;
+            const float al = fminf(fmaxf(a_raw, eps), 1.f - eps);
+            term -= scale * (al * logf(al) + (1.f - al) * log1pf(-al));
+            if (!a.grad_grid || !(a_raw > eps && a_raw < 1.f - eps)) continue;
+            const float ga = -scale * (logf(al) - log1pf(-al));  // d loss / d alpha^k
+            float *gg = a.grad_grid[id];
+            float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
+            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3]) {
+                float2 f2[4];
+                accumulate_sample<DT>(b, p, g, f2);
+                scatter_ch0(b, gg, gp, p, g, ga * expf(f2[0].x) * delta * T);
+                return true;
+            });
+        }
+    }
+    add_loss(term, a.loss);
+}
+
 // grad_mlp[t] += sum over CTA rows, in row order
 __global__ void k_reduce_rows(const float *__restrict__ partials, int n_rows, float *grad_mlp) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,6 +448,32 @@ cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st) {
     case kF16: k_remarch_backward<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
     case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
     case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparsity(const RegArgs &a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    const int nb = (int)((a.n + kBwdThreads - 1) / kBwdThreads);
+    switch (a.dtype) {
+    case kF32: k_sparsity<kF32><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kF16: k_sparsity<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kBF16: k_sparsity<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kFP8: k_sparsity<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_opacity(const RegArgs &a, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    const int nb = (int)((a.n + kBwdThreads - 1) / kBwdThreads);
+    switch (a.dtype) {
+    case kF32: k_opacity<kF32><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kF16: k_opacity<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kBF16: k_opacity<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kFP8: k_opacity<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

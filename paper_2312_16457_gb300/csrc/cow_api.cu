@@ -855,6 +855,88 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     return COW_OK;
 }
 
+namespace {
+
+// Validate the ids and the per-block gradient arrays of a regulariser call,
+// load the blocks and upload the gradient pointer table.
+cow_status reg_prepare(cow_ctx *ctx, const int32_t *ids, int32_t n_ids, float *loss, float *const *grad_grid,
+                       float *const *grad_planes, cudaStream_t st, cow::RegArgs &a) {
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    const int32_t nb = (int32_t)ctx->blocks.size();
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    if (loss && !is_device_ptr(loss)) return fail(COW_ERR_INVALID_ARG, "loss must be device memory");
+    if ((grad_grid == nullptr) != (grad_planes == nullptr))
+        return fail(COW_ERR_INVALID_ARG, "pass both gradient tables or neither");
+    std::memset(&a, 0, sizeof(a));
+    cow_status rc = ensure_resident(ctx, ids, n_ids, st);
+    if (rc != COW_OK) return rc;
+    COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
+    COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (grad_grid) {
+        std::vector<float *> ptrs((size_t)nb * 4);
+        for (int32_t i = 0; i < nb; i++) {
+            ptrs[(size_t)i] = grad_grid[i];
+            for (int k = 0; k < 3; k++) ptrs[(size_t)nb + 3 * (size_t)i + k] = grad_planes[3 * i + k];
+            for (int k = 0; k < 4; k++) {
+                const float *q = k == 0 ? grad_grid[i] : grad_planes[3 * i + k - 1];
+                if (q && (((uintptr_t)q & 3u) || !is_device_ptr(q)))
+                    return fail(COW_ERR_INVALID_ARG, "block %d: gradient arrays must be aligned device memory", i);
+            }
+        }
+        COW_CUDA(ctx->gptrs.reserve(ptrs.size() * sizeof(float *)));
+        COW_CUDA(cudaMemcpyAsync(ctx->gptrs.p, ptrs.data(), ptrs.size() * sizeof(float *), cudaMemcpyHostToDevice, st));
+        a.grad_grid = (float *const *)ctx->gptrs.p;
+        a.grad_planes = (float *const *)ctx->gptrs.p + nb;
+    }
+    a.recs = ctx->d_blocks;
+    a.dtype = ctx->dtype;
+    a.n_ids = n_ids;
+    a.ids = (const int32_t *)ctx->ids.p;
+    a.loss = loss;
+    a.err = ctx->d_err;
+    return COW_OK;
+}
+
+}  // namespace
+
+cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points, const int32_t *ids, int32_t n_ids,
+                             float weight, float *loss, float *const *grad_grid, float *const *grad_planes,
+                             void *stream) {
+    g_last_error.clear();
+    if (!ctx || !points || n_points < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_sparsity_loss: null argument");
+    if (!is_device_ptr(points)) return fail(COW_ERR_INVALID_ARG, "points must be device memory");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cow::RegArgs a;
+    cow_status rc = reg_prepare(ctx, ids, n_ids, loss, grad_grid, grad_planes, st, a);
+    if (rc != COW_OK) return rc;
+    a.pts = points;
+    a.n = n_points;
+    a.weight = weight;
+    COW_CUDA(cow::launch_sparsity(a, st));
+    return COW_OK;
+}
+
+cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                            int32_t n_ids, float weight, float *loss, float *const *grad_grid,
+                            float *const *grad_planes, void *stream) {
+    g_last_error.clear();
+    if (!ctx || !o || !d || n_rays < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_opacity_loss: null argument");
+    if (!is_device_ptr(o) || !is_device_ptr(d)) return fail(COW_ERR_INVALID_ARG, "rays must be device memory");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cow::RegArgs a;
+    cow_status rc = reg_prepare(ctx, ids, n_ids, loss, grad_grid, grad_planes, st, a);
+    if (rc != COW_OK) return rc;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n = n_rays;
+    a.weight = weight;
+    COW_CUDA(cow::launch_opacity(a, st));
+    return COW_OK;
+}
+
 cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, const float *plane_xy,
                                const float *plane_xz, const float *plane_yz, void *stream) {
     g_last_error.clear();

@@ -62,6 +62,25 @@ struct BwdArgs {
     float *gcf;                   // scratch: n_rays x 8 (dL/dC_d, dL/dF per ray)
     unsigned *err;
 };
+
+// Training-stage regularisers (bwd.cu): sparsity (Eq. 7) over points,
+// block opacity (Eq. 8) over rays
+struct RegArgs {
+    const BlockRec *recs;         // every block of the context
+    int32_t dtype;
+    int32_t n_ids;
+    const int32_t *ids;           // the blocks that take part
+    const float *pts;             // sparsity: n x 3 points
+    const float *ray_o, *ray_d;   // opacity: n x 3 rays
+    int64_t n;
+    float weight;                 // the loss and its gradient are scaled by weight / n
+    float *loss;                  // device float, accumulated (may be null)
+    float *const *grad_grid;      // device pointer table as in BwdArgs (null: no gradient)
+    float *const *grad_planes;
+    unsigned *err;
+};
+cudaError_t launch_sparsity(const RegArgs &a, cudaStream_t st);
+cudaError_t launch_opacity(const RegArgs &a, cudaStream_t st);
 int backward_rows(int64_t n_rays);
 cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,

@@ -53,8 +53,20 @@ class Fitter:
     """Fit block features and the deferred MLP to target colours of a ray
     batch: forward, MSE gradient, backward, Adam, re-pack -- all in libcow."""
 
-    def __init__(self, scene, mlp, lr_feat=1e-2, lr_mlp=1e-3, device="cuda"):
+    def __init__(self, scene, mlp, lr_feat=1e-2, lr_mlp=1e-3, device="cuda", lambda_sparsity=0.0,
+                 lambda_opacity=0.0, n_sparsity_points=1 << 14, seed=0):
+        """lambda_sparsity / lambda_opacity weight the regularisers of Eq. 7
+        (mean alpha at n_sparsity_points uniform points of the scene box,
+        redrawn every step) and Eq. 8 (entropy of block opacities of the
+        step's rays); the paper trains with 0.05 and 0.001."""
         self.ctx = cow.Context(scene, "fp32")
+        self.box_lo = torch.tensor(scene.box_lo, dtype=torch.float32, device=device)
+        self.box_hi = torch.tensor(scene.box_hi, dtype=torch.float32, device=device)
+        self.lambda_sparsity, self.lambda_opacity = float(lambda_sparsity), float(lambda_opacity)
+        self.n_sparsity_points = int(n_sparsity_points)
+        self.gen = torch.Generator(device=device)
+        self.gen.manual_seed(seed)
+        self.reg_loss = None
         self.ids = list(range(len(scene.blocks)))
         self.params = []
         for b in scene.blocks:
@@ -66,14 +78,23 @@ class Fitter:
         self.t = 0
 
     def step(self, o, d, target, ert_eps: float = 0.0):
-        """One optimisation step; returns the loss (device tensor) before it."""
+        """One optimisation step; returns the colour loss (device tensor)
+        before it (the weighted regularisers are in self.reg_loss)."""
         nb = len(self.ids)
         rgb, aux, _ = self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps)
         g, loss = cow.mse_grad(rgb, target)
         grads = [torch.zeros_like(p) for p in self.params]
         gm = torch.zeros_like(self.mlp)
-        self.ctx.render_backward(o, d, self.ids, self.mlp, aux, g, [grads[4 * i] for i in range(nb)],
-                                 [grads[4 * i + 1:4 * i + 4] for i in range(nb)], gm, ert_eps=ert_eps)
+        gtab = ([grads[4 * i] for i in range(nb)], [grads[4 * i + 1:4 * i + 4] for i in range(nb)])
+        self.ctx.render_backward(o, d, self.ids, self.mlp, aux, g, gtab[0], gtab[1], gm, ert_eps=ert_eps)
+        if self.lambda_sparsity > 0.0 or self.lambda_opacity > 0.0:
+            self.reg_loss = torch.zeros(1, dtype=torch.float32, device=o.device)
+            if self.lambda_sparsity > 0.0:
+                u = torch.rand((self.n_sparsity_points, 3), generator=self.gen, device=o.device)
+                pts = self.box_lo + u * (self.box_hi - self.box_lo)
+                self.ctx.sparsity_loss(pts, self.ids, self.lambda_sparsity, loss=self.reg_loss, grads=gtab)
+            if self.lambda_opacity > 0.0:
+                self.ctx.opacity_loss(o, d, self.ids, self.lambda_opacity, loss=self.reg_loss, grads=gtab)
         self.t += 1
         for k, p in enumerate(self.params):
             cow.adam_step(p, grads[k], self.m[k], self.v[k], self.lr_feat, self.t)
