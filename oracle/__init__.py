@@ -41,7 +41,7 @@ class OrcBlock(C.Structure):
     _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3), ("R", C.c_int32), ("P", C.c_int32),
                 ("occ_cell", C.c_int32), ("level", C.c_int32), ("parent", C.c_int32),
                 ("is_f64", C.c_int32), ("grid", C.c_void_p), ("planes", C.c_void_p * 3),
-                ("occ", C.c_void_p)]
+                ("occ", C.c_void_p), ("unbounded", C.c_int32)]
 
 
 class OrcCamera(C.Structure):
@@ -71,6 +71,8 @@ def lib():
             "orc_render_rays": (None, [P, i32, P, i32, P, P, i64, P, i32, P, P, P]),
             "orc_sort_ids_for_ray": (None, [P, P, i32, P, P]),
             "orc_ray_samples": (i64, [P, P, i32, P, P, P, P, P, i64]),
+            "orc_ray_sample_steps": (i64, [P, P, i32, P, P, P, i64]),
+            "orc_contract": (None, [P, P]),
             "orc_render_rays_grad": (None, [P, i32, P, i32, P, P, i64, P, P, P, P, P]),
             "orc_block_ztop": (dbl, [P]),
             "orc_select_lod": (i32, [P, i32, P, P, i32, P, i32]),
@@ -226,6 +228,7 @@ class OracleScene:
             for k in range(3):
                 ob.planes[k] = pls[k].ctypes.data
             ob.occ = bits.ctypes.data
+            ob.unbounded = int(getattr(b, "unbounded", 0))
             self.grids.append(g)
             self.planes.append(pls)
             self.occ.append(bits)
@@ -344,6 +347,23 @@ def ray_samples(osc: OracleScene, order: Sequence[int], o, d, cap: int = 1 << 16
     n = lib().orc_ray_samples(osc.ptr(), _ptr(a), len(a), _ptr(of), _ptr(df), _ptr(t), _ptr(blk), _ptr(al), cap)
     n = min(n, cap)
     return t[:n], blk[:n], al[:n]
+
+
+def ray_sample_steps(osc: OracleScene, order: Sequence[int], o, d, cap: int = 1 << 16) -> np.ndarray:
+    """The step (delta) of each occupied sample of one ray, in ray_samples order."""
+    a = np.ascontiguousarray(order, np.int32)
+    of, df = _np(o).reshape(3), _np(d).reshape(3)
+    out = np.zeros(cap)
+    n = min(lib().orc_ray_sample_steps(osc.ptr(), _ptr(a), len(a), _ptr(of), _ptr(df), _ptr(out), cap), cap)
+    return out[:n]
+
+
+def contract(x) -> np.ndarray:
+    """Eq. 16 (FP64) of one normalised point."""
+    xx = np.ascontiguousarray(x, np.float64).reshape(3)
+    u = np.zeros(3)
+    lib().orc_contract(_ptr(xx), _ptr(u))
+    return u
 
 
 def render_rays_grad(osc: OracleScene, ids: Sequence[int], o, d, mlp, dL_drgb):

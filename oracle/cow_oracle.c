@@ -81,7 +81,17 @@ typedef struct orc_block {
     const void *grid;       /* R^3 x 8, index ((z*R + y)*R + x)*8 + c */
     const void *planes[3];  /* P^2 x 8 each, index (v*P + u)*8 + c; xy, xz, yz */
     const uint32_t *occ;    /* occupancy bits, NULL = every cell occupied */
+    int32_t unbounded;      /* 0, or ORC_CONTRACTED | the xy sides that extend to infinity */
 } orc_block;
+
+/* Unbounded boundary blocks (MERF scene contraction, Eq. 16). */
+#define ORC_EXT_XLO 1
+#define ORC_EXT_XHI 2
+#define ORC_EXT_YLO 4
+#define ORC_EXT_YHI 8
+#define ORC_CONTRACTED 16
+#define ORC_CONTRACT_MAX 1.0e4f   /* the march stops beyond ||x||_inf = 1e4 */
+#define ORC_CONTRACT_STEPS 65536  /* and after this many steps */
 
 typedef struct orc_camera {
     double c2w[12];   /* 3x4 row-major camera-to-world, OpenGL axes */
@@ -394,6 +404,16 @@ static void make_taps(const orc_block *b, const double p[3], taps *tp) {
     }
 }
 
+/* Taps of a contracted block at contracted coordinates u in [-2, 2]^3. */
+static void make_taps_u(const orc_block *b, const double u[3], taps *tp) {
+    orc_block v = *b;
+    for (int a = 0; a < 3; a++) {
+        v.lo[a] = -2.0f;
+        v.hi[a] = 2.0f;
+    }
+    make_taps(&v, u, tp);
+}
+
 static void eval_feature(const orc_block *b, const taps *tp, double f[NCH]) {
     for (int c = 0; c < NCH; c++) f[c] = 0.0;
     for (int k = 0; k < 8; k++)
@@ -477,11 +497,194 @@ static int candidate_range(const orc_block *b, const float of[3], const float df
     return 1;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Unbounded (contracted) boundary blocks.  Implementation details of the
+ * paper: blocks on the scene's boundary hold an unbounded representation
+ * with MERF's contraction (Eq. 16), which maps the space outside the unit
+ * cube of the block's normalised coordinates x = (p - c) / h (c the centre
+ * and h the half extents of its box) into the shell 1 < ||u||_inf < 2.  The
+ * grid and planes of such a block span u in [-2, 2]^3.
+ *
+ * The block owns its xy footprint extended to infinity across the sides
+ * flagged in `unbounded` (the sides on the scene's boundary), half-open as
+ * in Eq. 4, and every z.  A ray is marched through it from its first
+ * standard lattice point inside that region with the FP32 recurrence
+ * t_{k+1} = t_k + s_k, s_k = (delta m) m, m = max(1, ||x(t_k)||_inf): one
+ * lattice step inside the box and, outside, one lattice step of the
+ * dominant contracted coordinate (d/dm (2 - 1/m) = 1/m^2).  Sample k's
+ * opacity is 1 - exp(-sigma s_k).  The march stops when the point leaves
+ * the region, when ||x||_inf > 1e4, or after 65536 steps.  Decisions use the
+ * FP32 sequence below; interpolation is FP64 at the FP32 sample point. */
+
+static int owned_unbounded(const orc_block *b, const float p[3]) {
+    const int e = b->unbounded;
+    return ((e & ORC_EXT_XLO) || p[0] >= b->lo[0]) && ((e & ORC_EXT_XHI) || p[0] < b->hi[0]) &&
+           ((e & ORC_EXT_YLO) || p[1] >= b->lo[1]) && ((e & ORC_EXT_YHI) || p[1] < b->hi[1]);
+}
+
+/* FP32 normalised coordinates and their infinity norm. */
+static float contract_x32(const orc_block *b, const float p[3], float x[3]) {
+    float m = 0.0f;
+    for (int a = 0; a < 3; a++) {
+        const float c = (float)(0.5 * ((double)b->lo[a] + (double)b->hi[a]));
+        const float ih = (float)(2.0 / ((double)b->hi[a] - (double)b->lo[a]));
+        const float rel = p[a] - c;
+        x[a] = rel * ih;
+        const float ax = fabsf(x[a]);
+        if (ax > m) m = ax;
+    }
+    return m;
+}
+
+/* Eq. 16 in FP32: u_j = x_j inside the unit cube; outside, 2 - 1/|x_j| (with
+ * x_j's sign) on the coordinates that reach the norm, x_j / m on the rest. */
+static void contract_u32(const float x[3], float m, float u[3]) {
+    for (int a = 0; a < 3; a++) {
+        if (m <= 1.0f) {
+            u[a] = x[a];
+        } else if (fabsf(x[a]) == m) {
+            const float q = 1.0f / fabsf(x[a]);
+            const float v = 2.0f - q;
+            u[a] = x[a] < 0.0f ? -v : v;
+        } else {
+            u[a] = x[a] / m;
+        }
+    }
+}
+
+/* Eq. 16 in FP64 (interpolation). */
+void orc_contract(const double x[3], double u[3]) {
+    double m = 0.0;
+    for (int a = 0; a < 3; a++)
+        if (fabs(x[a]) > m) m = fabs(x[a]);
+    for (int a = 0; a < 3; a++) {
+        if (m <= 1.0) u[a] = x[a];
+        else if (fabs(x[a]) == m) u[a] = (2.0 - 1.0 / fabs(x[a])) * (x[a] < 0.0 ? -1.0 : 1.0);
+        else u[a] = x[a] / m;
+    }
+}
+
+static int occupied_unbounded(const orc_block *b, const float u[3]) {
+    if (!b->occ) return 1;
+    const int Nc = orc_occ_cells(b->R, b->occ_cell);
+    const float k = (float)((double)(b->R - 1) / 4.0);
+    int cell[3];
+    for (int a = 0; a < 3; a++) {
+        const float s = u[a] + 2.0f;
+        const float g = s * k;
+        int v = (int)floorf(g);
+        if (v < 0) v = 0;
+        if (v > b->R - 2) v = b->R - 2;
+        cell[a] = v / b->occ_cell;
+    }
+    const int64_t c = ((int64_t)cell[2] * Nc + cell[1]) * Nc + cell[0];
+    return (int)((b->occ[c >> 5] >> (c & 31)) & 1u);
+}
+
+static void make_taps(const orc_block *b, const double p[3], taps *tp);
+static void make_taps_u(const orc_block *b, const double u[3], taps *tp);
+
+/* First lattice index of the ray inside the block's region, or -1.  The
+ * region is convex and each FP32 lattice coordinate is monotone in the
+ * index, so the owned indices form one interval; its start is found from the
+ * FP32 entry estimate j = floor(t_in / delta - 1/2) of the bounded xy sides
+ * by stepping back while the previous point is owned, or forward (at most
+ * 64 points) until one is.  Every operation is FP32 round-to-nearest. */
+static int64_t first_owned_index(const orc_block *b, const float of[3], const float df[3], float delta) {
+    float tn = 0.0f;
+    for (int a = 0; a < 2; a++) {
+        const int elo = b->unbounded & (a == 0 ? ORC_EXT_XLO : ORC_EXT_YLO);
+        const int ehi = b->unbounded & (a == 0 ? ORC_EXT_XHI : ORC_EXT_YHI);
+        if (df[a] == 0.0f) {
+            if ((!elo && of[a] < b->lo[a]) || (!ehi && of[a] >= b->hi[a])) return -1;
+            continue;
+        }
+        const float inv = 1.0f / df[a];
+        const float bound = df[a] > 0.0f ? b->lo[a] : b->hi[a];
+        if (df[a] > 0.0f ? elo : ehi) continue;
+        const float rel = bound - of[a];
+        const float te = rel * inv;
+        if (te > tn) tn = te;
+    }
+    const float inv_delta = 1.0f / delta;
+    const float xq = tn * inv_delta;
+    const float xs = xq - 0.5f;
+    if (!(xs < 16777216.0f)) return -1;
+    int64_t j = (int64_t)floorf(xs);
+    if (j < 0) j = 0;
+    float p[3];
+    lattice_point(of, df, delta, j, p);
+    if (owned_unbounded(b, p)) {
+        for (int k = 0; k < 64 && j > 0; k++) {
+            lattice_point(of, df, delta, j - 1, p);
+            if (!owned_unbounded(b, p)) break;
+            j--;
+        }
+        return j;
+    }
+    for (int k = 1; k <= 64; k++) {
+        lattice_point(of, df, delta, j + k, p);
+        if (owned_unbounded(b, p)) return j + k;
+    }
+    return -1;
+}
+
+static int64_t unbounded_samples(const orc_block *blocks, int32_t bi, const float of[3], const float df[3],
+                                 sample_vec *out) {
+    const orc_block *b = &blocks[bi];
+    const float delta = block_delta(b);
+    const int64_t i0 = first_owned_index(b, of, df, delta);
+    if (i0 < 0) return 0;
+    float t = ((float)i0 + 0.5f) * delta;
+    int64_t n = 0;
+    for (int k = 0; k < ORC_CONTRACT_STEPS; k++) {
+        float pf[3];
+        for (int a = 0; a < 3; a++) {
+            const float td = t * df[a];
+            pf[a] = of[a] + td;
+        }
+        if (!owned_unbounded(b, pf)) break;
+        float x[3];
+        const float m = contract_x32(b, pf, x);
+        if (m > ORC_CONTRACT_MAX) break;
+        const float m1 = m > 1.0f ? m : 1.0f;
+        const float dm = delta * m1;
+        const float step = dm * m1;
+        float u[3];
+        contract_u32(x, m, u);
+        if (occupied_unbounded(b, u)) {
+            sample s;
+            double x64[3], u64[3];
+            for (int a = 0; a < 3; a++) {
+                const double c = 0.5 * ((double)b->lo[a] + (double)b->hi[a]);
+                const double h = 0.5 * ((double)b->hi[a] - (double)b->lo[a]);
+                x64[a] = ((double)pf[a] - c) / h;
+            }
+            orc_contract(x64, u64);
+            make_taps_u(b, u64, &s.tp);
+            double f[NCH];
+            eval_feature(b, &s.tp, f);
+            s.t = (double)t;
+            s.delta = (double)step;
+            s.sigma = exp(f[0]);
+            s.alpha = -expm1(-s.sigma * s.delta);
+            for (int c = 0; c < 3; c++) s.c[c] = sigmoid(f[1 + c]);
+            for (int c = 0; c < 4; c++) s.s[c] = sigmoid(f[4 + c]);
+            s.block = bi;
+            push_sample(out, &s);
+            n++;
+        }
+        t = t + step;
+    }
+    return n;
+}
+
 /* Append the occupied samples of block bi along the ray, in lattice order;
  * returns the number appended. */
 static int64_t block_samples(const orc_block *blocks, int32_t bi, const float of[3], const float df[3],
                              sample_vec *out) {
     const orc_block *b = &blocks[bi];
+    if (b->unbounded & ORC_CONTRACTED) return unbounded_samples(blocks, bi, of, df, out);
     const float delta = block_delta(b);
     int64_t i0, i1, n = 0;
     if (!candidate_range(b, of, df, delta, &i0, &i1)) return 0;
@@ -902,6 +1105,19 @@ int64_t orc_ray_samples(const orc_block *blocks, const int32_t *order, int32_t n
     return n;
 }
 
+/* The step (delta of Eq. 1) of every occupied sample of one ray, as
+ * orc_ray_samples orders them: the block's lattice spacing, or the
+ * recurrence's step in an unbounded block. */
+int64_t orc_ray_sample_steps(const orc_block *blocks, const int32_t *order, int32_t n_order, const float *o,
+                             const float *d, double *out_delta, int64_t cap) {
+    sample_vec sv = {0, 0, 0};
+    for (int k = 0; k < n_order; k++) block_samples(blocks, order[k], o, d, &sv);
+    int64_t n = sv.n;
+    for (int64_t i = 0; i < n && i < cap; i++) out_delta[i] = sv.v[i].delta;
+    free(sv.v);
+    return n;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Gradient: reverse mode through MLP, Eq. 12 blend, Eq. 11 accumulation,
  * activations and interpolation taps, for rays rendered block-wise (mode 0).
@@ -1057,8 +1273,9 @@ void orc_render_rays_grad(const orc_block *blocks, int32_t nb, const int32_t *id
  *
  * Sparsity (Eq. 7): the mean over given points p of |alpha(p)|, alpha(p) =
  * 1 - exp(-sigma(p) delta_b) with sigma from the block that contains p
- * (Eq. 4 membership on the FP32 point; the first such block in ids) and that
- * block's sample spacing delta_b; a point in no block contributes 0.
+ * (Eq. 4 membership on the FP32 point, the extended region of an unbounded
+ * block; the first such block in ids) and that block's lattice spacing
+ * delta_b; a point in no block contributes 0.
  * d alpha / d f0 = sigma delta (1 - alpha).
  *
  * Opacity (Eq. 8): for every ray and every block with at least one occupied
@@ -1086,13 +1303,23 @@ double orc_sparsity_loss_grad(const orc_block *blocks, int32_t nb, const int32_t
     for (int64_t r = 0; r < n_pts; r++) {
         const float *pf = pts + 3 * r;
         int32_t bi = -1;
-        for (int k = 0; k < n_ids && bi < 0; k++)
-            if (inside_block(&blocks[ids[k]], pf)) bi = ids[k];
+        for (int k = 0; k < n_ids && bi < 0; k++) {
+            const orc_block *c = &blocks[ids[k]];
+            if ((c->unbounded & ORC_CONTRACTED) ? owned_unbounded(c, pf) : inside_block(c, pf)) bi = ids[k];
+        }
         if (bi < 0) continue;
         const orc_block *b = &blocks[bi];
         sample s;
         const double p[3] = {pf[0], pf[1], pf[2]};
-        make_taps(b, p, &s.tp);
+        if (b->unbounded & ORC_CONTRACTED) {
+            double x64[3], u64[3];
+            for (int a = 0; a < 3; a++)
+                x64[a] = (p[a] - 0.5 * ((double)b->lo[a] + (double)b->hi[a])) / (0.5 * ((double)b->hi[a] - (double)b->lo[a]));
+            orc_contract(x64, u64);
+            make_taps_u(b, u64, &s.tp);
+        } else {
+            make_taps(b, p, &s.tp);
+        }
         double f[NCH];
         eval_feature(b, &s.tp, f);
         s.block = bi;

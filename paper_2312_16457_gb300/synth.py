@@ -32,6 +32,8 @@ import torch
 
 NCH = 8
 MLP_NPARAM = 499
+# unbounded boundary blocks: the xy sides that extend to infinity, and the flag
+EXT_XLO, EXT_XHI, EXT_YLO, EXT_YHI, CONTRACTED = 1, 2, 4, 8, 16
 _MASK32 = 0xFFFFFFFF
 
 
@@ -51,10 +53,11 @@ class Block:
     parent: int = -1
     grid: Optional[torch.Tensor] = None  # [R, R, R, 8] float32, [z][y][x][c]
     planes: List[torch.Tensor] = field(default_factory=list)  # 3 x [P, P, 8]
+    unbounded: int = 0  # 0, or CONTRACTED | the xy sides (EXT_*) that extend to infinity
 
     def to(self, device) -> "Block":
         return Block(self.lo, self.hi, self.R, self.P, self.level, self.parent,
-                     self.grid.to(device), [p.to(device) for p in self.planes])
+                     self.grid.to(device), [p.to(device) for p in self.planes], self.unbounded)
 
 
 @dataclass
@@ -179,14 +182,32 @@ def _axis(lo: float, hi: float, n: int, device) -> torch.Tensor:
     return lo + i * ((hi - lo) / (n - 1))
 
 
+def _vertex_world(us, lo, hi):
+    """World positions of the vertices of an unbounded block, whose grid spans
+    contracted coordinates u in [-2, 2]^3: the point whose contraction is u
+    (for u in the shell, |x| = 1 / (2 - ||u||_inf) on the coordinates that
+    reach the norm and u_i times that on the others; ||u|| is capped at
+    2 - 1e-3, i.e. 1000 half extents from the centre)."""
+    uu = torch.stack(us, 0)
+    m = uu.abs().amax(0).clamp(max=2.0 - 1e-3)
+    big = 1.0 / (2.0 - m)
+    x = torch.where(m <= 1.0, uu, torch.where(uu.abs() >= m, torch.sign(uu) * big, uu * big))
+    return [0.5 * (lo[a] + hi[a]) + 0.5 * (hi[a] - lo[a]) * x[a] for a in range(3)]
+
+
 def bake_block(fld: WorldField, lo, hi, R: int, P: int, key: int, level=1, parent=-1,
-               device="cpu") -> Block:
-    """Sample the world field at the block's vertices (vertex 0 at lo, R-1 at hi)."""
+               device="cpu", unbounded=0) -> Block:
+    """Sample the world field at the block's vertices (vertex 0 at lo, R-1 at
+    hi; for an unbounded block vertex 0 at u = -2, R-1 at u = 2)."""
     lo = tuple(float(np.float32(v)) for v in lo)
     hi = tuple(float(np.float32(v)) for v in hi)
-    xs, ys, zs = (_axis(lo[a], hi[a], R, device) for a in range(3))
+    if unbounded & CONTRACTED:
+        us = torch.meshgrid(*(_axis(-2.0, 2.0, R, device),) * 3, indexing="ij")  # (z, y, x)
+        xx, yy, zz = _vertex_world([us[2], us[1], us[0]], lo, hi)
+    else:
+        xs, ys, zs = (_axis(lo[a], hi[a], R, device) for a in range(3))
+        zz, yy, xx = torch.meshgrid(zs, ys, xs, indexing="ij")
     grid = torch.empty((R, R, R, NCH), dtype=torch.float32, device=device)
-    zz, yy, xx = torch.meshgrid(zs, ys, xs, indexing="ij")
     grid[..., 0] = fld.log_density(xx, yy, zz).to(torch.float32)
     n = R * R * R
     for ch in range(1, NCH):
@@ -199,7 +220,7 @@ def bake_block(fld: WorldField, lo, hi, R: int, P: int, key: int, level=1, paren
         nz = uniform_noise(P * P * NCH, -fld.plane_noise, fld.plane_noise, fld.seed, key, 1 + pl,
                            device=device)
         planes.append(nz.view(P, P, NCH).contiguous())
-    return Block(lo, hi, R, P, level, parent, grid.contiguous(), planes)
+    return Block(lo, hi, R, P, level, parent, grid.contiguous(), planes, unbounded)
 
 
 # --------------------------------------------------------------------------
@@ -215,12 +236,16 @@ def single_block_scene(seed=1, R=64, P=256, device="cpu") -> Scene:
 
 
 def city_scene(seed: int, M: int, side: float, res: Sequence[tuple], height=2.0,
-               blobs_per_area=2.0, lod_thresh=None, device="cpu", levels=None) -> Scene:
+               blobs_per_area=2.0, lod_thresh=None, device="cpu", levels=None, unbounded=False) -> Scene:
     """M x M ground blocks of the given side at LOD 1, merged 2x2 per level.
 
     res[l] = (R, P) of level l+1.  Blob centres are uniform over the ground
-    and the lower half of the height so that they cross block borders."""
+    and the lower half of the height so that they cross block borders.
+    unbounded=True (one level only) makes the blocks on the scene's boundary
+    unbounded: contracted, extending to infinity across their boundary sides
+    (the ground slab then continues to the horizon)."""
     L = len(res) if levels is None else levels
+    assert not unbounded or L == 1
     half = 0.5 * M * side
     box_lo = (-half, -half, -0.5 * height)
     box_hi = (half, half, 0.5 * height)
@@ -240,7 +265,12 @@ def city_scene(seed: int, M: int, side: float, res: Sequence[tuple], height=2.0,
                 hi = (-half + (i + 1) * s, -half + (j + 1) * s, box_hi[2])
                 parent = level_index.get((lev + 1, i // 2, j // 2), -1)
                 key = lev * 100000 + j * 1000 + i
-                blocks.append(bake_block(fld, lo, hi, R, P, key, lev, parent, device))
+                ext = 0
+                if unbounded:
+                    ext = (EXT_XLO if i == 0 else 0) | (EXT_XHI if i == m - 1 else 0) | \
+                          (EXT_YLO if j == 0 else 0) | (EXT_YHI if j == m - 1 else 0)
+                    ext = ext | CONTRACTED if ext else 0
+                blocks.append(bake_block(fld, lo, hi, R, P, key, lev, parent, device, ext))
                 level_index[(lev, i, j)] = len(blocks) - 1
     thr = list(lod_thresh) if lod_thresh is not None else [2.0 * side * 2 ** l for l in range(L)]
     return Scene(blocks, box_lo, box_hi, thr)
@@ -328,6 +358,15 @@ def block_mlp_weights(seed: int, n_blocks: int, n_freq: int, std=0.3, spread=0.1
 
 # --------------------------------------------------------------------------
 # the five workloads (full sizes; tests pass smaller resolutions)
+
+
+def workload_unbounded(R=64, P=256, device="cpu", width=160, height=90):
+    """2x2 blocks of side 2, all on the scene's boundary and unbounded
+    (contracted), one camera low inside the scene looking out at the horizon;
+    scene seed 6, per-block MLP seed 106."""
+    sc = city_scene(6, 2, 2.0, [(R, P)], device=device, unbounded=True)
+    cam = camera((-0.3, -0.2, 0.4), (6.0, 3.5, -0.6), width, height, 70.0)
+    return sc, [cam], mlp_weights(106)
 
 
 def workload_single_block(R=64, P=256, device="cpu", width=128, height=128):
