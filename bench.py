@@ -37,7 +37,7 @@ METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
 # DRAM bytes (read + write) of one k_march_views launch from an ncu capture of
 # the default workload (profiles/march_views_city_lod_1080p_traffic.md); valid
 # for the marcher revision named here and null for any other configuration.
-MARCH_REVISION = "v7-occpyramid"
+MARCH_REVISION = "v8-unbounded"
 MEASURED_TRAFFIC = {}
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}

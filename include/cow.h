@@ -169,6 +169,28 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
                       const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                       float *out_aux, int32_t *out_nsamp, void *stream);
 
+/* Unbounded boundary blocks (implementation details of the paper: blocks on
+ * the scene's boundary use MERF's scene contraction, Eq. 16).  A contracted
+ * block's grid and planes span u = contract(x) in [-2, 2]^3, x = (p - c) / h
+ * with c the centre and h the half extents of its box: contract(x) = x
+ * inside the unit cube; outside, 2 - 1/|x_j| (sign of x_j) on the
+ * coordinates that reach ||x||_inf and x_j / ||x||_inf on the others.  The
+ * block owns its xy footprint extended to infinity across the flagged sides
+ * (half-open as Eq. 4) and every z.  A ray marches it from its first owned
+ * lattice point (t = (i + 1/2) delta) with steps s = delta m^2,
+ * m = max(1, ||x||_inf), until it leaves the region, ||x||_inf > 1e4 or 65536
+ * steps; a sample's alpha is 1 - exp(-sigma s).
+ *   flags : 0 (bounded, the default) or COW_UNBOUNDED_CONTRACTED | sides.
+ * The grid and planes given at load time are read in u (vertex 0 at u = -2,
+ * vertex R-1 at u = 2); occupancy is built from them as for any block.
+ * Errors: INVALID_ARG. */
+#define COW_UNBOUNDED_XLO 1
+#define COW_UNBOUNDED_XHI 2
+#define COW_UNBOUNDED_YLO 4
+#define COW_UNBOUNDED_YHI 8
+#define COW_UNBOUNDED_CONTRACTED 16
+cow_status cow_set_block_unbounded(cow_ctx *ctx, int32_t block, int32_t flags, void *stream);
+
 /* Per-block deferred MLPs (Sec. 4.1: each block k of LOD l carries its own
  * tiny MLP Phi^{k,l}; Sec. 4.2, Eq. 5: the block colours of Eq. 3 are
  * blended by opacity) with a multi-frequency encoding of the view direction.

@@ -26,6 +26,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
+           "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_sparsity_loss", "cow_opacity_loss",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
@@ -83,6 +84,7 @@ def lib():
             "cow_export_occupancy": [P, i32, P, i64],
             "cow_export_occupancy_coarse": [P, i32, P, i64],
             "cow_set_residency": [P, i64, P],
+            "cow_set_block_unbounded": [P, i32, i32, P],
             "cow_sparsity_loss": [P, P, i64, P, i32, flt, P, P, P, P],
             "cow_opacity_loss": [P, P, P, i64, P, i32, flt, P, P, P, P],
             "cow_get_residency": [P, P],
@@ -174,6 +176,9 @@ class Context:
                                      _stream_ptr(stream)))
         self.n_blocks = n
         self.schedule = "thread_const"  # the library default
+        for i, b in enumerate(scene.blocks):
+            if getattr(b, "unbounded", 0):
+                self.set_unbounded(i, b.unbounded, stream)
         del keep
 
     def close(self):
@@ -343,6 +348,12 @@ class Context:
         out = np.zeros(words, np.uint32)
         _check(lib().cow_export_occupancy(self._ctx, int(i), _ptr(out), words))
         return out
+
+    def set_unbounded(self, i: int, flags: int, stream=None):
+        """Block i becomes an unbounded (contracted) boundary block: flags =
+        16 | the xy sides extended to infinity (1 -x, 2 +x, 4 -y, 8 +y); 0
+        makes it bounded again."""
+        _check(lib().cow_set_block_unbounded(self._ctx, int(i), int(flags), _stream_ptr(stream)))
 
     # --- dynamic loading ---------------------------------------------------
     def set_residency(self, budget_bytes: int, stream=None):

@@ -56,6 +56,7 @@ __device__ __forceinline__ float norm1(const float a[3]) { return fabsf(a[0]) + 
 // constrain nothing.
 __device__ __forceinline__ bool culled(const BlockRec &b, const float o[3], const float n[4][3], const bool use[4],
                                        const float fwd[3]) {
+    if (b.unb) return false;  // an unbounded block has no box to cull
     for (int k = 0; k < 5; k++) {
         if (k < 4 && !use[k]) continue;
         const float *nk = k < 4 ? n[k] : fwd;

@@ -62,7 +62,7 @@ __device__ __forceinline__ void scatter_taps(const BlockRec &b, float *gg, float
     int h0[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        float h = axis_coord(p[a], b.plo[a], b.kp[a]);
         const int u = min(max(__float2int_rd(h), 0), b.P - 2);
         h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
         h0[a] = u;
@@ -201,8 +201,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a) {
         const BlockRec &b = a.recs[id];
         float *gg = a.grad_grid[id];
         float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
-        const float delta = b.delta;
-        const bool more = for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3]) {
+        const bool more = for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3],
+                                                                           float delta) {
             float2 f2[4];
             accumulate_sample<DT>(b, p, g, f2);
             const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
@@ -276,7 +276,7 @@ __device__ __forceinline__ void scatter_ch0(const BlockRec &b, float *gg, float 
     int h0[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        float h = axis_coord(p[a], b.plo[a], b.kp[a]);
         const int u = min(max(__float2int_rd(h), 0), b.P - 2);
         h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
         h0[a] = u;
@@ -321,22 +321,22 @@ __global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a) {
         int id = -1;
         for (int k = 0; k < a.n_ids && id < 0; k++) {
             const int c = __ldg(a.ids + k);
-            if (inside_block(a.recs[c], p)) id = c;
+            const BlockRec &bc = a.recs[c];
+            if ((bc.unb & kUnbContracted) ? owned_unbounded(bc, p) : inside_block(bc, p)) id = c;
         }
         if (id >= 0) {
             const BlockRec &b = a.recs[id];
-            float g[3];
-#pragma unroll
-            for (int c = 0; c < 3; c++) g[c] = axis_coord(p[c], b.lo[c], b.kg[c]);
+            float q[3], g[3];
+            lookup_coords(b, p, q, g);
             float2 f2[4];
-            accumulate_sample<DT>(b, p, g, f2);
+            accumulate_sample<DT>(b, q, g, f2);
             const float sigma = expf(f2[0].x);
             const float alpha = -expm1f(-sigma * b.delta);
             const float scale = a.weight / (float)a.n;
             term = scale * alpha;
             if (a.grad_grid) {
                 float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
-                scatter_ch0(b, a.grad_grid[id], gp, p, g, scale * sigma * b.delta * (1.f - alpha));
+                scatter_ch0(b, a.grad_grid[id], gp, q, g, scale * sigma * b.delta * (1.f - alpha));
             }
         }
     }
@@ -362,10 +362,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a) {
         for (int k = 0; k < n; k++) {
             const int id = order[k];
             const BlockRec &b = a.recs[id];
-            const float delta = b.delta;
             float T = 1.f;
             int nk = 0;
-            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3]) {
+            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
                 float2 f2[4];
                 accumulate_sample<DT>(b, p, g, f2);
                 T *= expf(-expf(f2[0].x) * delta);
@@ -380,7 +379,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a) {
             const float ga = -scale * (logf(al) - log1pf(-al));  // d loss / d alpha^k
             float *gg = a.grad_grid[id];
             float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
-            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3]) {
+            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
                 float2 f2[4];
                 accumulate_sample<DT>(b, p, g, f2);
                 scatter_ch0(b, gg, gp, p, g, ga * expf(f2[0].x) * delta * T);

@@ -241,6 +241,20 @@ cow::BlockRec make_rec(const cow_ctx *c, const BlockHost &b) {
     r.scale = b.scale;
     r.occ2 = b.occ2;
     r.Nc2 = (r.Nc + cow::kOccGroup - 1) / cow::kOccGroup;
+    r.unb = b.unb;
+    for (int a = 0; a < 3; a++) {
+        r.cc[a] = (float)(0.5 * ((double)b.lo[a] + (double)b.hi[a]));
+        r.ih[a] = (float)(2.0 / ((double)b.hi[a] - (double)b.lo[a]));
+        r.plo[a] = r.lo[a];
+    }
+    if (b.unb & cow::kUnbContracted) {
+        // lookups index the contracted coordinate u in [-2, 2]
+        for (int a = 0; a < 3; a++) {
+            r.plo[a] = -2.0f;
+            r.kg[a] = (float)((double)(b.R - 1) / 4.0);
+            r.kp[a] = (float)((double)(b.P - 1) / 4.0);
+        }
+    }
     return r;
 }
 
@@ -731,6 +745,8 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     int32_t max_blk = 0;
     for (const auto &r : plan.recs) max_blk = std::max(max_blk, r.ids_count);
     a.smem_recs = max_blk <= 96 ? max_blk : 0;  // views with more records read them from global memory
+    bool any_unbounded = false;
+    for (int32_t k = 0; k < n_ids; k++) any_unbounded |= ctx->blocks[(size_t)ids[k]].unb != 0;
     if (ctx->schedule == COW_SCHED_THREAD_CONST && n_ids <= cow::kParamRecs) {
         // the records travel in the launch's parameter buffer
         cow::ParamRecs pr;
@@ -738,8 +754,10 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
         std::copy(vrecs.begin(), vrecs.begin() + n_ids, pr.r);
         COW_CUDA(cow::launch_march_views(a, plan.n_tiles, cow::kSchedThreadConst, st, &pr));
     } else {
-        COW_CUDA(cow::launch_march_views(a, plan.n_tiles, ctx->schedule == COW_SCHED_WARP ? cow::kSchedWarp
-                                                                                          : cow::kSchedThread, st));
+        // the warp schedule marches bounded blocks only
+        COW_CUDA(cow::launch_march_views(a, plan.n_tiles,
+                                         ctx->schedule == COW_SCHED_WARP && !any_unbounded ? cow::kSchedWarp
+                                                                                           : cow::kSchedThread, st));
     }
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)plan.n_pix * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)plan.n_pix * 32, cudaMemcpyDeviceToHost, st));
@@ -1001,6 +1019,20 @@ cow_status cow_set_block_mlps(cow_ctx *ctx, const float *mlps, int32_t n_mlps, i
     ctx->n_freq = n_freq;
     ctx->block_mlp_nparam = stride;
     return COW_OK;
+}
+
+cow_status cow_set_block_unbounded(cow_ctx *ctx, int32_t block, int32_t flags, void *stream) {
+    g_last_error.clear();
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
+    if (flags & ~31) return fail(COW_ERR_INVALID_ARG, "unknown unbounded flags %d", flags);
+    if (flags && !(flags & COW_UNBOUNDED_CONTRACTED))
+        return fail(COW_ERR_INVALID_ARG, "extended sides need COW_UNBOUNDED_CONTRACTED");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    COW_CUDA(cudaStreamSynchronize(st));  // earlier calls may still read the record
+    ctx->blocks[(size_t)block].unb = flags;
+    return refresh_rec(ctx, block, st);
 }
 
 cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {

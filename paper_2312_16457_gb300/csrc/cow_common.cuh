@@ -28,6 +28,11 @@ constexpr unsigned kErrArg = 4u;      // a kernel met an argument it cannot hand
 
 enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3 };
 
+// Unbounded boundary blocks (scene contraction, Eq. 16)
+constexpr int kUnbXLo = 1, kUnbXHi = 2, kUnbYLo = 4, kUnbYHi = 8, kUnbContracted = 16;
+constexpr float kContractMax = 1.0e4f;  // the march of an unbounded block stops beyond ||x||_inf = 1e4
+constexpr int kContractSteps = 65536;   // and after this many steps
+
 // Occupancy cells per coarse cell along each axis (the second level of the
 // multi-level occupancy grid).
 constexpr int kOccGroupLog2 = 2;
@@ -52,9 +57,15 @@ struct alignas(16) BlockRec {
     const float *scale;      // 32 floats: per-channel scale of grid, xy, xz, yz
     const uint32_t *occ2;    // coarse occupancy: one bit per kOccGroup^3 cells (OR of their bits)
     int32_t Nc2;             // coarse cells per axis, ceil(Nc / kOccGroup)
-    int32_t pad_;
+    int32_t unb;             // 0, or kUnbContracted | the xy sides (kUnbX/YLo/Hi) extended to infinity
+    float cc[3];             // unbounded: (float)((lo + hi) / 2), computed in double
+    float ih[3];             // unbounded: (float)(2 / (hi - lo)), computed in double
+    float plo[3];            // origin of the lookup coordinates: lo, or -2 (contracted u) when unbounded
+    int32_t pad_[3];
+    // when unbounded, kg and kp hold (R-1)/4 and (P-1)/4: lookups index u in [-2, 2]
 };
 static_assert(sizeof(BlockRec) % 16 == 0, "BlockRec must be a multiple of 16 bytes");
+static_assert(sizeof(BlockRec) * 96 + 512 <= 32764, "96 records fit the kernel parameter space");
 
 // Block records passed by value in a launch's parameter buffer (a kernel's
 // parameters may take up to 32764 bytes).
@@ -133,6 +144,57 @@ __device__ __forceinline__ bool inside_block(const BlockRec &b, const float p[3]
 
 // Continuous vertex coordinate along one axis: (p - lo) * k.
 __device__ __forceinline__ float axis_coord(float p, float lo, float k) { return __fmul_rn(__fsub_rn(p, lo), k); }
+
+// --- unbounded blocks: the region they own and the contraction (Eq. 16) -----
+// The block owns its xy footprint extended to infinity across the sides in
+// b.unb (half-open as Eq. 4) and every z.
+__device__ __forceinline__ bool owned_unbounded(const BlockRec &b, const float p[3]) {
+    const int e = b.unb;
+    return ((e & kUnbXLo) || p[0] >= b.lo[0]) && ((e & kUnbXHi) || p[0] < b.hi[0]) &&
+           ((e & kUnbYLo) || p[1] >= b.lo[1]) && ((e & kUnbYHi) || p[1] < b.hi[1]);
+}
+
+// x = (p - c) * (2 / (hi - lo)) and ||x||_inf, then u = contract(x): x inside
+// the unit cube; outside, 2 - 1/|x_j| (sign of x_j) on the coordinates that
+// reach the norm and x_j / ||x|| on the rest.  FP32, round to nearest.
+__device__ __forceinline__ float unbounded_x(const BlockRec &b, const float p[3], float x[3]) {
+    float m = 0.f;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        x[a] = __fmul_rn(__fsub_rn(p[a], b.cc[a]), b.ih[a]);
+        m = fmaxf(m, fabsf(x[a]));
+    }
+    return m;
+}
+
+__device__ __forceinline__ void contract_u(const float x[3], float m, float u[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (m <= 1.f) {
+            u[a] = x[a];
+        } else if (fabsf(x[a]) == m) {
+            const float v = __fsub_rn(2.f, __fdiv_rn(1.f, fabsf(x[a])));
+            u[a] = x[a] < 0.f ? -v : v;
+        } else {
+            u[a] = __fdiv_rn(x[a], m);
+        }
+    }
+}
+
+// Lookup coordinates of a point for the feature gathers: q (the point, or
+// its contraction u for an unbounded block) and the grid coordinate g.
+__device__ __forceinline__ void lookup_coords(const BlockRec &b, const float p[3], float q[3], float g[3]) {
+    if (b.unb & kUnbContracted) {
+        float x[3];
+        const float m = unbounded_x(b, p, x);
+        contract_u(x, m, q);
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; a++) q[a] = p[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) g[a] = axis_coord(q[a], b.plo[a], b.kg[a]);
+}
 
 // Candidate lattice range of a ray in a block: FP32 slab test on the grown
 // box, widened by two indices at each end.  Returns false on a miss.

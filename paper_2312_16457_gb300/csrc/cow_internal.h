@@ -73,6 +73,7 @@ struct BlockHost {
     // dynamic loading (cow_set_residency): the packed grid and planes may live
     // only in pinned host memory while the block is unloaded
     void *host_feat[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t unb = 0;           // cow_set_block_unbounded flags
     bool resident = true;
     bool dirty = false;        // device copy newer than host_feat (cow_update_features)
     bool async_alloc = false;  // device tensors from cudaMallocAsync

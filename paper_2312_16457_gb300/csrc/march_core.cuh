@@ -81,7 +81,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
     int h0[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        float h = axis_coord(p[a], b.lo[a], b.kp[a]);
+        float h = axis_coord(p[a], b.plo[a], b.kp[a]);
         const int u = min(max(__float2int_rd(h), 0), b.P - 2);
         h = fminf(fmaxf(h, 0.f), (float)(b.P - 1));
         h0[a] = u;
@@ -131,8 +131,10 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
 }
 
 // Visit the occupied lattice samples of one ray inside one block, in order
-// (Eq. 4 membership, occupancy skip); fn(p, g) is called for each and
-// returns false to stop the ray.  Returns false when fn stopped it.
+// (Eq. 4 membership, occupancy skip); fn(p, g, s) is called for each with
+// the lookup point, the grid coordinate and the sample's step s (delta of
+// Eq. 1), and returns false to stop the ray.  Returns false when fn stopped
+// it.
 //
 // Two-level occupancy (Sec. 4.1's multi-level occupancy grid): a sample
 // tests its own cell; when that is empty it tests the coarse cell around it
@@ -144,9 +146,95 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
 // the empty cell -- shrunk by a margin m far above the FP32 position and
 // coordinate error -- decides an empty cell and would be skipped anyway.
 // The jump lands one lattice step short of that exit.
+// First lattice index of the ray inside an unbounded block's region, or -1.
+// The owned indices form one interval (convex region, monotone FP32 lattice
+// coordinates); its start is found from the FP32 entry estimate
+// j = floor(t_in / delta - 1/2) over the bounded xy sides by stepping back
+// while the previous point is owned, or forward (at most 64 points) until one
+// is.  The same FP32 sequence as the oracle's, so both find the same index.
+__device__ __forceinline__ int first_owned_index(const BlockRec &b, const float o[3], const float d[3]) {
+    float tn = 0.f;
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        const bool elo = b.unb & (a == 0 ? kUnbXLo : kUnbYLo), ehi = b.unb & (a == 0 ? kUnbXHi : kUnbYHi);
+        if (d[a] == 0.f) {
+            if ((!elo && o[a] < b.lo[a]) || (!ehi && o[a] >= b.hi[a])) return -1;
+            continue;
+        }
+        if (d[a] > 0.f ? elo : ehi) continue;
+        const float inv = __fdiv_rn(1.f, d[a]);
+        const float bound = d[a] > 0.f ? b.lo[a] : b.hi[a];
+        tn = fmaxf(tn, __fmul_rn(__fsub_rn(bound, o[a]), inv));
+    }
+    const float xs = __fsub_rn(__fmul_rn(tn, __fdiv_rn(1.f, b.delta)), 0.5f);
+    if (!(xs < 16777216.f)) return -1;
+    int j = max(__float2int_rd(xs), 0);
+    float p[3];
+    lattice_point(o, d, b.delta, j, p);
+    if (owned_unbounded(b, p)) {
+        for (int k = 0; k < 64 && j > 0; k++) {
+            lattice_point(o, d, b.delta, j - 1, p);
+            if (!owned_unbounded(b, p)) break;
+            j--;
+        }
+        return j;
+    }
+    for (int k = 1; k <= 64; k++) {
+        lattice_point(o, d, b.delta, j + k, p);
+        if (owned_unbounded(b, p)) return j + k;
+    }
+    return -1;
+}
+
+// Samples of an unbounded (contracted) block: from its first owned lattice
+// point the ray advances by s = (delta m) m, m = max(1, ||x||_inf) -- one
+// lattice step inside the box, one lattice step of the dominant contracted
+// coordinate outside -- until it leaves the region, ||x|| exceeds 1e4 or
+// 65536 steps were taken.  Each occupied point calls fn(u, g, s).
+template <typename Fn>
+__device__ __forceinline__ bool for_each_sample_unbounded(const BlockRec &b, const float o[3], const float d[3],
+                                                          Fn &&fn) {
+    const int i0 = first_owned_index(b, o, d);
+    if (i0 < 0) return true;
+    const int Nc = b.Nc, C = b.C, R = b.R;
+    float t = __fmul_rn(__fadd_rn(__int2float_rn(i0), 0.5f), b.delta);
+    int occ_w = -1;
+    uint32_t occ_bits = 0u;
+    for (int k = 0; k < kContractSteps; k++) {
+        float p[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) p[a] = __fadd_rn(o[a], __fmul_rn(t, d[a]));
+        if (!owned_unbounded(b, p)) break;
+        float x[3];
+        const float m = unbounded_x(b, p, x);
+        if (m > kContractMax) break;
+        const float m1 = fmaxf(m, 1.f);
+        const float s = __fmul_rn(__fmul_rn(b.delta, m1), m1);
+        float u[3], g[3];
+        contract_u(x, m, u);
+        int cell[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            g[a] = axis_coord(u[a], b.plo[a], b.kg[a]);
+            const int v = min(max(__float2int_rd(g[a]), 0), R - 2);
+            cell[a] = C == 1 ? v : (int)__umulhi((unsigned)v, b.cdiv);
+        }
+        const int ci = (cell[2] * Nc + cell[1]) * Nc + cell[0];
+        if ((ci >> 5) != occ_w) {
+            occ_w = ci >> 5;
+            occ_bits = __ldg(b.occ + occ_w);
+        }
+        if ((occ_bits >> (ci & 31)) & 1u)
+            if (!fn(u, g, s)) return false;
+        t = __fadd_rn(t, s);
+    }
+    return true;
+}
+
 template <typename Fn>
 __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o[3], const float d[3],
                                                 const float inv_d[3], float omax, unsigned *err, Fn &&fn) {
+    if (b.unb & kUnbContracted) return for_each_sample_unbounded(b, o, d, fn);
     int i0, i1;
     float tfar;
     if (!candidate_range(b, o, d, inv_d, i0, i1, tfar)) return true;
@@ -206,7 +294,7 @@ __device__ __forceinline__ bool for_each_sample(const BlockRec &b, const float o
             if (j > i) i = min(j, i1);
             continue;
         }
-        if (!fn(p, g)) return false;
+        if (!fn(p, g, delta)) return false;
     }
     return true;
 }
@@ -251,13 +339,12 @@ template <int DT>
 __device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3],
                                             const float inv_d[3], float omax, float ert_eps, RayState &s,
                                             unsigned *err) {
-    const float delta = b.delta;
-    const bool more = for_each_sample(b, o, d, inv_d, omax, err, [&](const float p[3], const float g[3]) {
+    const bool more = for_each_sample(b, o, d, inv_d, omax, err, [&](const float p[3], const float g[3], float dt) {
         float2 f2[4];
         accumulate_sample<DT>(b, p, g, f2);
         const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
         const float sigma = __expf(f[0]);
-        const float e = __expf(-sigma * delta);
+        const float e = __expf(-sigma * dt);
         const float w = s.T * (1.f - e);
 #pragma unroll
         for (int c = 0; c < 3; c++) s.Cd[c] = fmaf(w, sigmoidf_fast(f[1 + c]), s.Cd[c]);
