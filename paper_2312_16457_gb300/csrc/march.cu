@@ -22,12 +22,18 @@
 #ifndef COW_MARCH_MIN_BLOCKS_W
 #define COW_MARCH_MIN_BLOCKS_W 4
 #endif
+#ifndef COW_WARP_W
+#define COW_WARP_W 8  // pixels per warp row (the warp covers COW_WARP_W x 32/COW_WARP_W pixels)
+#endif
 
 namespace cow {
 
 namespace {
 
 constexpr int kTileW = 16, kTileH = 8, kThreads = 128;
+constexpr int kWarpW = COW_WARP_W, kWarpH = 32 / kWarpW;  // one ray per thread: a warp's pixel patch
+static_assert(kTileW % kWarpW == 0 && kTileH % kWarpH == 0 && (kTileW / kWarpW) * (kTileH / kWarpH) == kThreads / 32,
+              "the CTA tile is an exact grid of warp patches");
 constexpr int kMinBlocks = COW_MARCH_MIN_BLOCKS;  // CTAs per SM the register budget is sized for
 constexpr int kMinBlocksW = COW_MARCH_MIN_BLOCKS_W;
 constexpr int kMaxSmemRecs = 96;                  // block records a CTA stages in shared memory
@@ -114,8 +120,9 @@ __device__ __forceinline__ void march_tile_rays(const MarchArgs &a, const ViewRe
     int tx, ty;
     tile_xy(v, t, kTileH, tx, ty);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = tx * kTileW + (warp & 1) * 8 + (lane & 7);
-    const int py = ty * kTileH + (warp >> 1) * 4 + (lane >> 3);
+    constexpr int kWarpsX = kTileW / kWarpW;
+    const int px = tx * kTileW + (warp % kWarpsX) * kWarpW + (lane % kWarpW);
+    const int py = ty * kTileH + (warp / kWarpsX) * kWarpH + (lane / kWarpW);
     if (px >= v.W || py >= v.H) return;
     float o[3], d[3], inv_d[3], omax;
     pixel_ray(v, px, py, o, d);
