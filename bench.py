@@ -38,7 +38,7 @@ METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
 # the default workload (profiles/march_views_city_lod_1080p_traffic.md); valid
 # for the marcher revision named here and null for any other configuration.
 MARCH_REVISION = "v8-unbounded"
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("city_lod_1080p", "bf16", "thread_const", 1): 49487934976}
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}
 GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160}  # per occupied sample: 20 texels x 8 ch
