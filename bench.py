@@ -339,6 +339,14 @@ def run_cow(args, ws, rank, local):
     gb = GATHER_BYTES[storage] * n_samples / 1e9
     hbm = peaks.get("hbm_gbs")
     achieved = gb / (ms / 1000.0)
+    # the HBM level: the launch's measured DRAM bytes (ncu, one capture of
+    # this configuration) over the live step time, against the measured copy peak
+    traffic = MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div))
+    hbm_level = None
+    if traffic and hbm:
+        dram_gbs = traffic / 1e9 / (ms / 1000.0)
+        hbm_level = {"achieved": round(dram_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(dram_gbs / hbm, 3),
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
@@ -356,13 +364,14 @@ def run_cow(args, ws, rank, local):
         **fp32,
         "roofline": {"bound": "gather", "kernel": KERNEL_OF_SCHEDULE[args.schedule], "achieved": round(achieved, 1),
                      "peak": round(peak_l1, 1), "unit": "GB/s", "frac": round(achieved / peak_l1, 3),
-                     "traffic": MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div)),
+                     "traffic": traffic,
                      "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, marcher "
                                        f"{MARCH_REVISION}",
                      "peak_source": f"measured live: random {width}-byte gathers from a 64 KiB (L1-resident) "
                                     "buffer, cow_gather_peak",
                      "levels_gbs": {"l1_gather": round(peak_l1, 1), "l2_gather": round(peak_l2, 1),
                                     "hbm_gather": round(peak_hbm, 1), "hbm_copy_measured": hbm},
+                     "hbm_level": hbm_level,
                      "algorithmic_bytes_per_launch": int(GATHER_BYTES[storage] * n_samples),
                      "unit_note": f"{GATHER_BYTES[storage]} B per occupied sample (8 grid vertices + 12 plane "
                                   "texels x 8 channels) x occupied samples of the frame"},
