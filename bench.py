@@ -328,6 +328,15 @@ def run_cow(args, ws, rank, local):
                "mrays_per_s": round(n_pix / dt / 1e6, 6),
                "psnr_vs_oracle_db": round(psnr(rgb_main[pix], rgb_o), 2),
                "max_abs_drgb_vs_oracle": float(np.abs(rgb_main[pix] - rgb_o).max())}
+        # the same oracle on one core, on 1/64 of the pixels
+        import oracle
+
+        oracle.set_threads(1)
+        n1 = max(1, n_pix // 64)
+        _, _, dt1 = oracle_sample(sc, cam, ids, mlp, n1, seed=1)
+        oracle.set_threads(os.cpu_count())
+        cpu["one_core"] = {"value": round((n1 / dt1) / npix, 6), "unit": "frames/s", "cores": 1,
+                           "sample": f"{n1} pixels, {dt1:.2f} s", "mrays_per_s": round(n1 / dt1 / 1e6, 6)}
 
     # gather roofline: the marcher's algorithmic gather bytes against the
     # measured random-gather rate of the same load width from an L1-resident
@@ -349,7 +358,8 @@ def run_cow(args, ws, rank, local):
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "ms_median": round(float(np.median(times)), 4),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "scene": desc, "storage": storage, "n_blocks_selected": int(len(ids)),
                    "schedule": args.schedule, "tile_strip": args.strip,

@@ -64,6 +64,7 @@ def lib():
             "orc_quantize": (None, [P, i64, i32, P, P, P]),
             "orc_pixel_ray": (None, [P, i32, i32, P, P]),
             "orc_occ_cells": (i32, [i32, i32]),
+            "orc_set_threads": (i32, [i32]),
             "orc_occupancy": (None, [P, i32, i32, flt, P]),
             "orc_feature_at": (dbl, [P, P, P]),
             "orc_mlp": (None, [P, P, i64, P]),
@@ -100,6 +101,11 @@ def _np(x, dtype=np.float32) -> np.ndarray:
     if hasattr(x, "detach"):
         x = x.detach().cpu().numpy()
     return np.ascontiguousarray(x, dtype=dtype)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops; returns the new maximum."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def make_camera(cam) -> OrcCamera:

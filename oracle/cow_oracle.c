@@ -49,6 +49,7 @@
  */
 #include <float.h>
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -299,6 +300,13 @@ static int inside_block(const orc_block *b, const float p[3]) {
 }
 
 int32_t orc_occ_cells(int32_t R, int32_t C) { return (R - 1 + C - 1) / C; }
+
+/* Threads of the oracle's parallel loops (for timing it on one core);
+ * returns the new maximum. */
+int32_t orc_set_threads(int32_t n) {
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 /* Occupancy cell of a point inside block b: the voxel v = floor(g) of the
  * continuous grid coordinate g = (p - lo) * ((R-1)/(hi-lo)), clamped to
