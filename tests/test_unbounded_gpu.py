@@ -101,3 +101,30 @@ def test_batched_and_block_mlp_forms():
     r_o, _, n_o = oracle.render_view_block_mlp(oracle.OracleScene(sc), cams[0], order, w, L)
     assert np.array_equal(ns.cpu().numpy(), n_o)
     assert np.abs(rgb.cpu().numpy() - r_o).max() <= TOL
+
+
+def test_regularisers_through_unbounded_blocks():
+    """Sparsity points beyond the scene's box fall in the extended regions;
+    opacity rays leave through the contracted shells."""
+    sc, _, _ = synth.workload_unbounded(R=24, P=64)
+    ctx = cow.Context(sc, "fp32")
+    ids = list(range(4))
+    rng = np.random.default_rng(4)
+    pts = rng.uniform([-6, -6, -3], [6, 6, 3], size=(1 << 13, 3)).astype(np.float32)
+    _, d = synth.random_rays(1024, 12, sc.box_lo, sc.box_hi)
+    o = torch.tensor([-0.5, 0.3, 0.2]).expand(1024, 3).contiguous()
+    gg = [torch.zeros(b.grid.shape, device="cuda") for b in sc.blocks]
+    gp = [[torch.zeros(p.shape, device="cuda") for p in b.planes] for b in sc.blocks]
+    ls = ctx.sparsity_loss(torch.from_numpy(pts).cuda(), ids, 0.05, grads=(gg, gp))
+    lo = ctx.opacity_loss(o.cuda(), d.cuda(), ids, 0.001, grads=(gg, gp))
+    ctx.sync_check()
+    osc = oracle.OracleScene(sc)
+    ols, sg, sp = oracle.sparsity_loss_grad(osc, ids, pts, weight=0.05)
+    olo, og, op = oracle.opacity_loss_grad(osc, ids, o, d, weight=0.001)
+    assert ols > 1e-3 and olo > 1e-5
+    assert abs(float(ls.item()) - ols) <= 1e-4 * ols
+    assert abs(float(lo.item()) - olo) <= 1e-4 * olo
+    for b in range(4):
+        assert _rel(gg[b].cpu().numpy(), sg[b] + og[b]) <= 1e-3
+        for k in range(3):
+            assert _rel(gp[b][k].cpu().numpy(), sp[b][k] + op[b][k]) <= 1e-3
