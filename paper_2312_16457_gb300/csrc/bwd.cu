@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(BwdArgs a) {
 
 // K6: re-march and scatter the feature gradients.
 template <int DT>
-__global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a, const __grid_constant__ RayRecs rr) {
     const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     if (r >= a.n_rays) return;
     float o[3], d[3], Cf[3], Ff[4], gC[3], gF[4];
@@ -192,13 +192,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a) {
         gF[c] = __ldg(a.gcf + 8 * r + 3 + c);
     }
     int order[kMaxRayIds];
-    const int n = sort_blocks_for_ray(a.recs, a.ids, a.n_ray_ids, o, order);
+    const int n = sort_blocks_for_ray(rr, o, order);
     float inv_d[3], omax;
     ray_setup(d, o, inv_d, omax);
     float T = 1.f, PC[3] = {0.f, 0.f, 0.f}, PF[4] = {0.f, 0.f, 0.f, 0.f};
     for (int k = 0; k < n; k++) {
-        const int id = order[k];
-        const BlockRec &b = a.recs[id];
+        const int id = rr.id[order[k]];
+        const BlockRec &b = rr.r[order[k]];
         float *gg = a.grad_grid[id];
         float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
         const bool more = for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3],
@@ -313,19 +313,19 @@ __device__ __forceinline__ void add_loss(float v, float *loss) {
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a) {
+__global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a, const __grid_constant__ RayRecs rr) {
     const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     float term = 0.f;
     if (r < a.n) {
         const float p[3] = {__ldg(a.pts + 3 * r), __ldg(a.pts + 3 * r + 1), __ldg(a.pts + 3 * r + 2)};
-        int id = -1;
-        for (int k = 0; k < a.n_ids && id < 0; k++) {
-            const int c = __ldg(a.ids + k);
-            const BlockRec &bc = a.recs[c];
-            if ((bc.unb & kUnbContracted) ? owned_unbounded(bc, p) : inside_block(bc, p)) id = c;
+        int pos = -1;
+        for (int k = 0; k < rr.n && pos < 0; k++) {
+            const BlockRec &bc = rr.r[k];
+            if ((bc.unb & kUnbContracted) ? owned_unbounded(bc, p) : inside_block(bc, p)) pos = k;
         }
-        if (id >= 0) {
-            const BlockRec &b = a.recs[id];
+        if (pos >= 0) {
+            const int id = rr.id[pos];
+            const BlockRec &b = rr.r[pos];
             float q[3], g[3];
             lookup_coords(b, p, q, g);
             float2 f2[4];
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a) {
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a) {
+__global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a, const __grid_constant__ RayRecs rr) {
     const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     float term = 0.f;
     if (r < a.n) {
@@ -355,13 +355,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a) {
             d[c] = __ldg(a.ray_d + 3 * r + c);
         }
         int order[kMaxRayIds];
-        const int n = sort_blocks_for_ray(a.recs, a.ids, a.n_ids, o, order);
+        const int n = sort_blocks_for_ray(rr, o, order);
         float inv_d[3], omax;
         ray_setup(d, o, inv_d, omax);
         const float scale = a.weight / (float)a.n, eps = 1e-6f;
         for (int k = 0; k < n; k++) {
-            const int id = order[k];
-            const BlockRec &b = a.recs[id];
+            const int id = rr.id[order[k]];
+            const BlockRec &b = rr.r[order[k]];
             float T = 1.f;
             int nk = 0;
             for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
@@ -435,7 +435,7 @@ __global__ void k_mse_grad(const float *__restrict__ rgb, const float *__restric
 
 int backward_rows(int64_t n_rays) { return (int)((n_rays + kBwdThreads - 1) / kBwdThreads); }
 
-cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st) {
+cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n_rays <= 0) return cudaSuccess;
     const int nb = backward_rows(a.n_rays);
     k_mlp_backward<<<nb, kBwdThreads, 0, st>>>(a);
@@ -443,36 +443,36 @@ cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     k_reduce_rows<<<(kMlpParams + 127) / 128, 128, 0, st>>>(a.partials, nb, a.grad_mlp);
     switch (a.dtype) {
-    case kF32: k_remarch_backward<kF32><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kF16: k_remarch_backward<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kF32: k_remarch_backward<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kF16: k_remarch_backward<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_sparsity(const RegArgs &a, cudaStream_t st) {
+cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const int nb = (int)((a.n + kBwdThreads - 1) / kBwdThreads);
     switch (a.dtype) {
-    case kF32: k_sparsity<kF32><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kF16: k_sparsity<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kBF16: k_sparsity<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kFP8: k_sparsity<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kF32: k_sparsity<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kF16: k_sparsity<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_sparsity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_sparsity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_opacity(const RegArgs &a, cudaStream_t st) {
+cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const int nb = (int)((a.n + kBwdThreads - 1) / kBwdThreads);
     switch (a.dtype) {
-    case kF32: k_opacity<kF32><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kF16: k_opacity<kF16><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kBF16: k_opacity<kBF16><<<nb, kBwdThreads, 0, st>>>(a); break;
-    case kFP8: k_opacity<kFP8><<<nb, kBwdThreads, 0, st>>>(a); break;
+    case kF32: k_opacity<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kF16: k_opacity<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_opacity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_opacity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

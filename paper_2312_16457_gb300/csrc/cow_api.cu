@@ -394,6 +394,17 @@ cow_status resolve_mlp(cow_ctx *c, const float *mlp, cudaStream_t st, const floa
     return COW_OK;
 }
 
+// The records of a ray-batch call's blocks, for the launch's parameter buffer
+// (call after the blocks are loaded: the records carry their pointers).
+void make_ray_recs(const cow_ctx *c, const int32_t *ids, int32_t n, cow::RayRecs &rr) {
+    std::memset(&rr, 0, sizeof(rr));
+    rr.n = n;
+    for (int32_t k = 0; k < n; k++) {
+        rr.r[k] = c->recs[(size_t)ids[k]];
+        rr.id[k] = ids[k];
+    }
+}
+
 // --- dynamic loading / unloading under a device-memory budget (App. D) -----
 // The packed grid and planes of a block are its loadable resources; the
 // occupancy levels, scales and records stay resident (a few KB per block).
@@ -808,7 +819,9 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     a.ray_d = d;
     a.n_rays = n_rays;
     a.n_ray_ids = n_ids;
-    COW_CUDA(cow::launch_march_rays(a, st));
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_march_rays(a, rr, st));
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)n_rays * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)n_rays * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)n_rays * 4, cudaMemcpyDeviceToHost, st));
@@ -869,7 +882,9 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     a.partials = (float *)ctx->partials.p;
     a.gcf = (float *)((unsigned char *)ctx->partials.p + part_bytes);
     a.err = ctx->d_err;
-    COW_CUDA(cow::launch_backward_rays(a, st));
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_backward_rays(a, rr, st));
     return COW_OK;
 }
 
@@ -932,7 +947,9 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
     a.pts = points;
     a.n = n_points;
     a.weight = weight;
-    COW_CUDA(cow::launch_sparsity(a, st));
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_sparsity(a, rr, st));
     return COW_OK;
 }
 
@@ -951,7 +968,9 @@ cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_
     a.ray_d = d;
     a.n = n_rays;
     a.weight = weight;
-    COW_CUDA(cow::launch_opacity(a, st));
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_opacity(a, rr, st));
     return COW_OK;
 }
 
@@ -1424,6 +1443,8 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     a.partials = rows;
     a.gcf = gcf;
     a.err = ctx->d_err;
-    COW_CUDA(cow::launch_backward_rays(a, st));
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_backward_rays(a, rr, st));
     return COW_OK;
 }

@@ -67,6 +67,16 @@ struct alignas(16) BlockRec {
 static_assert(sizeof(BlockRec) % 16 == 0, "BlockRec must be a multiple of 16 bytes");
 static_assert(sizeof(BlockRec) * 96 + 512 <= 32764, "96 records fit the kernel parameter space");
 
+// The blocks of a ray-batch call (at most kMaxRayIds), passed by value in the
+// launch's parameter buffer like ParamRecs: record k is block id[k].
+struct RayRecs {
+    BlockRec r[kMaxRayIds];
+    int32_t id[kMaxRayIds];
+    int32_t n;
+    int32_t pad_[3];
+};
+static_assert(sizeof(RayRecs) + 512 <= 32764, "the ray-batch records fit the kernel parameter space");
+
 // Block records passed by value in a launch's parameter buffer (a kernel's
 // parameters may take up to 32764 bytes).
 constexpr int kParamRecs = 96;

@@ -8,6 +8,7 @@ namespace cow {
 
 struct BlockRec;
 struct ViewRec;
+struct RayRecs;
 
 struct MarchArgs {
     const BlockRec *recs;  // view mode: the views' block records, near to far, by ViewRec::ids_begin;
@@ -39,7 +40,7 @@ constexpr int kSchedThreadConst = 2;  // one ray per thread, records in the para
 struct ParamRecs;
 cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st,
                                const ParamRecs *pr = nullptr);
-cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st);
+cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
 int march_tile_w();
 int march_tile_h();
 
@@ -79,10 +80,10 @@ struct RegArgs {
     float *const *grad_planes;
     unsigned *err;
 };
-cudaError_t launch_sparsity(const RegArgs &a, cudaStream_t st);
-cudaError_t launch_opacity(const RegArgs &a, cudaStream_t st);
+cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st);
+cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st);
 int backward_rows(int64_t n_rays);
-cudaError_t launch_backward_rays(const BwdArgs &a, cudaStream_t st);
+cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
                         float eps, int step, cudaStream_t st);
 cudaError_t launch_mse_grad(const float *rgb, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);

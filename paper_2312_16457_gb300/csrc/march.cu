@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchAr
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a, const __grid_constant__ RayRecs rr) {
     __shared__ float s_mlp[kMlpParams + 1];
     load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
@@ -369,12 +369,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a
     }
     // per-ray depth order: xy distance of block centres to this origin (App. D)
     int order[kMaxRayIds];
-    const int n = sort_blocks_for_ray(a.recs, a.ids, a.n_ray_ids, o, order);
+    const int n = sort_blocks_for_ray(rr, o, order);
     float inv_d[3], omax;
     ray_setup(d, o, inv_d, omax);
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
     for (int k = 0; k < n && !s.done; k++)
-        march_block<DT>(a.recs[order[k]], o, d, inv_d, omax, a.ert_eps, s, a.err);
+        march_block<DT>(rr.r[order[k]], o, d, inv_d, omax, a.ert_eps, s, a.err);
     write_outputs(a, r, s, d, s_mlp);
 }
 
@@ -425,14 +425,14 @@ cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cu
                      : launch_thread_dt<false>(a, n_tiles, in_params, st, pr);
 }
 
-cudaError_t launch_march_rays(const MarchArgs &a, cudaStream_t st) {
+cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n_rays <= 0) return cudaSuccess;
     const int64_t nb = (a.n_rays + kThreads - 1) / kThreads;
     switch (a.dtype) {
-    case kF32: k_march_rays<kF32><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
-    case kF16: k_march_rays<kF16><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
-    case kBF16: k_march_rays<kBF16><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
-    case kFP8: k_march_rays<kFP8><<<(unsigned)nb, kThreads, 0, st>>>(a); break;
+    case kF32: k_march_rays<kF32><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kF16: k_march_rays<kF16><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_march_rays<kBF16><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_march_rays<kFP8><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -307,22 +307,23 @@ __device__ __forceinline__ void ray_setup(const float d[3], const float o[3], fl
 
 // Per-ray depth order of the ray-batch form: xy distance of block centres to
 // this ray's origin (App. D) as the FP32 key dx*dx + dy*dy, ties by id.
-__device__ __forceinline__ int sort_blocks_for_ray(const BlockRec *recs, const int32_t *ids, int n, const float o[3],
-                                                   int order[kMaxRayIds]) {
+// order[] receives positions into rr (block rr.id[k] is record rr.r[k]).
+__device__ __forceinline__ int sort_blocks_for_ray(const RayRecs &rr, const float o[3], int order[kMaxRayIds]) {
     float key[kMaxRayIds];
+    const int n = rr.n;
     for (int i = 0; i < n; i++) {
-        const int id = __ldg(ids + i);
-        const BlockRec &b = recs[id];
+        const BlockRec &b = rr.r[i];
+        const int id = rr.id[i];
         const float dx = __fsub_rn(b.cx, o[0]), dy = __fsub_rn(b.cy, o[1]);
         const float kk = __fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy));
         int j = i - 1;
-        while (j >= 0 && (key[j] > kk || (key[j] == kk && order[j] > id))) {
+        while (j >= 0 && (key[j] > kk || (key[j] == kk && rr.id[order[j]] > id))) {
             key[j + 1] = key[j];
             order[j + 1] = order[j];
             j--;
         }
         key[j + 1] = kk;
-        order[j + 1] = id;
+        order[j + 1] = i;
     }
     return n;
 }
