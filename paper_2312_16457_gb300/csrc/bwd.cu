@@ -29,6 +29,13 @@ namespace cow {
 
 namespace {
 
+#ifndef COW_BWD_MIN_BLOCKS
+// CTAs per SM the re-march's register budget is sized for: 2 lets it keep its
+// ~168 live registers (the compiler's own choice, 128, spills); measured on
+// the 2x2-block fit: 2 -> 296 ms a step, 3 -> 300, 4 or unset -> 312
+#define COW_BWD_MIN_BLOCKS 2
+#endif
+
 constexpr int kBwdThreads = 128;
 constexpr int kVec = 77;  // x (10), dz1 (16), h1 (16), dz2 (16), h2 (16), dz3 (3)
 
@@ -175,7 +182,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(BwdArgs a) {
 
 // K6: re-march and scatter the feature gradients.
 template <int DT>
-__global__ void __launch_bounds__(kBwdThreads) k_remarch_backward(BwdArgs a, const __grid_constant__ RayRecs rr) {
+__global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_remarch_backward(BwdArgs a,
+                                                                                const __grid_constant__ RayRecs rr) {
     const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     if (r >= a.n_rays) return;
     float o[3], d[3], Cf[3], Ff[4], gC[3], gF[4];
