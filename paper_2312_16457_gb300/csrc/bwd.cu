@@ -36,6 +36,12 @@ namespace {
 #define COW_BWD_MIN_BLOCKS 2
 #endif
 
+#ifndef COW_REG_MIN_BLOCKS
+// the same for the opacity regulariser's double march: 2 CTAs per SM took a
+// regularised fit step from ~496 to ~473 ms
+#define COW_REG_MIN_BLOCKS 2
+#endif
+
 constexpr int kBwdThreads = 128;
 constexpr int kVec = 77;  // x (10), dz1 (16), h1 (16), dz2 (16), h2 (16), dz3 (3)
 
@@ -352,7 +358,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a, const __gri
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kBwdThreads) k_opacity(RegArgs a, const __grid_constant__ RayRecs rr) {
+__global__ void __launch_bounds__(kBwdThreads, COW_REG_MIN_BLOCKS) k_opacity(RegArgs a,
+                                                                          const __grid_constant__ RayRecs rr) {
     const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     float term = 0.f;
     if (r < a.n) {

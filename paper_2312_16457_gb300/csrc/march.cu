@@ -22,6 +22,9 @@
 #ifndef COW_MARCH_MIN_BLOCKS_W
 #define COW_MARCH_MIN_BLOCKS_W 4
 #endif
+#ifndef COW_RAYS_MIN_BLOCKS
+#define COW_RAYS_MIN_BLOCKS COW_MARCH_MIN_BLOCKS  // 2 or 3 measured slower on the 2x2-block fit
+#endif
 #ifndef COW_WARP_W
 #define COW_WARP_W 8  // pixels per warp row (the warp covers COW_WARP_W x 32/COW_WARP_W pixels)
 #endif
@@ -355,7 +358,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchAr
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_rays(MarchArgs a, const __grid_constant__ RayRecs rr) {
+__global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(MarchArgs a,
+                                                                          const __grid_constant__ RayRecs rr) {
     __shared__ float s_mlp[kMlpParams + 1];
     load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
