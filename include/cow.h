@@ -296,7 +296,10 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
  * the given blocks in the xy-distance order of its own origin, App. D).
  *   o, d        : device float32 n_rays x 3 origins and unit directions.
  *   ids, n_ids  : host array of the blocks to composite (1..64).
- *   other arguments as cow_render; outputs have n_rays rows. */
+ *   other arguments as cow_render; outputs have n_rays rows.
+ * n_rays = 0 returns COW_OK at once (the arrays may then be NULL); the same
+ * holds for cow_render_backward(_noalloc), cow_opacity_loss and, with
+ * n_points = 0, cow_sparsity_loss. */
 cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);

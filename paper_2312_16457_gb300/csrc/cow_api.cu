@@ -780,6 +780,7 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream) {
     g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !out_rgb)
         return fail(COW_ERR_INVALID_ARG, "cow_render_rays: null argument");
     if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
@@ -832,6 +833,7 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
                                int32_t n_ids, const float *mlp, float ert_eps, const float *aux, const float *dL_drgb,
                                float *const *grad_grid, float *const *grad_planes, float *grad_mlp, void *stream) {
     g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !aux || !dL_drgb || !grad_grid || !grad_planes || !grad_mlp)
         return fail(COW_ERR_INVALID_ARG, "cow_render_backward: null argument");
     if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
@@ -937,6 +939,7 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
                              float weight, float *loss, float *const *grad_grid, float *const *grad_planes,
                              void *stream) {
     g_last_error.clear();
+    if (ctx && n_points == 0) return COW_OK;  // nothing to add (the arrays may be NULL)
     if (!ctx || !points || n_points < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_sparsity_loss: null argument");
     if (!is_device_ptr(points)) return fail(COW_ERR_INVALID_ARG, "points must be device memory");
     DeviceGuard dg(ctx->device);
@@ -957,6 +960,7 @@ cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_
                             int32_t n_ids, float weight, float *loss, float *const *grad_grid,
                             float *const *grad_planes, void *stream) {
     g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // nothing to add (the arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_opacity_loss: null argument");
     if (!is_device_ptr(o) || !is_device_ptr(d)) return fail(COW_ERR_INVALID_ARG, "rays must be device memory");
     DeviceGuard dg(ctx->device);
@@ -1383,6 +1387,7 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
                                                   float *const *grad_grid, float *const *grad_planes,
                                                   float *grad_mlp, void *stream) {
     g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !aux || !dL_drgb || !grad_grid || !grad_planes || !grad_mlp)
         return fail(COW_ERR_INVALID_ARG, "cow_render_backward_noalloc: null argument");
     if (n_rays > kNoAllocMaxRays)
