@@ -134,3 +134,19 @@ def test_plan_view_order_matches_simulation(L):
         cow.plan_view_order([10, 10], [[0, 1]], 15)
     with pytest.raises(cow.CowError):
         cow.plan_view_order([10, 10], [[0, 2]], 100)
+
+
+def test_header_and_library_from_plain_c(L, tmp_path):
+    """include/cow.h is C; a C program links libcow.so and runs host-only calls."""
+    import subprocess
+
+    from paper_2312_16457_gb300 import build
+
+    exe = tmp_path / "abi_from_c"
+    src = os.path.join(ROOT, "tests", "c", "abi_from_c.c")
+    libdir = os.path.dirname(build.LIB)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), src, "-o", str(exe),
+                    "-L", libdir, "-lcow", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.strip() == "ok 2 40 60"
