@@ -98,3 +98,62 @@ def test_fit_reduces_loss():
     fit.ctx.sync_check()
     assert losses[-1] < 0.6 * losses[0], losses[::8]
     assert all(np.isfinite(losses))
+
+
+def test_backward_matches_gpu_finite_differences():
+    """Central differences of the GPU render itself (FP32 renders, the loss
+    summed in FP64) against the analytic backward, on the entries with the
+    largest gradients; h = 1e-2 keeps FP32 rounding well below the signal."""
+    sc = synth.city_scene(21, 2, 2.0, [(12, 32)])
+    o, d = synth.random_rays(4096, 13, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    mlp = torch.from_numpy(synth.mlp_weights(5)).cuda()
+    w = torch.randn(4096, 3, device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
+    ctx = cow.Context(sc, "fp32")
+    ids = list(range(4))
+    _, _, gg, gp, gm = _gpu_grads(ctx, sc, o, d, ids, mlp, w)
+    grids = [b.grid.cuda().clone() for b in sc.blocks]
+    planes = [[p.cuda().clone() for p in b.planes] for b in sc.blocks]
+
+    def loss():
+        rgb = ctx.render_rays(o, d, ids, mlp, aux=False)[0]
+        return float((rgb.double() * w.double()).sum())
+
+    cands = []
+    for b in range(4):
+        cands.append((b, -1, gg[b]))
+        cands += [(b, k, gp[b][k]) for k in range(3)]
+    picks = []
+    for b, k, g in cands:
+        flat = g.reshape(-1)
+        j = int(flat.abs().argmax())
+        picks.append((b, k, j, float(flat[j])))
+    h = 1e-2
+    checked = 0
+    for b, k, j, gval in picks:
+        if abs(gval) < 0.05:
+            continue
+        arr = grids[b] if k < 0 else planes[b][k]
+        flat = arr.view(-1)
+        x0 = float(flat[j])
+        vals = []
+        for s in (1.0, -1.0):
+            flat[j] = x0 + s * h
+            ctx.update_features(b, grids[b], planes[b])
+            vals.append(loss())
+        flat[j] = x0
+        ctx.update_features(b, grids[b], planes[b])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - gval) <= 0.03 * abs(gval) + 2e-3, (b, k, j, fd, gval)
+        checked += 1
+    for j in gm.abs().argsort(descending=True)[:3].tolist():  # the deferred MLP
+        x0 = float(mlp[j])
+        vals = []
+        for s in (1.0, -1.0):
+            mlp[j] = x0 + s * h
+            vals.append(loss())
+        mlp[j] = x0
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - float(gm[j])) <= 0.03 * abs(float(gm[j])) + 2e-3, ("mlp", j, fd, float(gm[j]))
+        checked += 1
+    assert checked >= 8
