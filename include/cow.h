@@ -298,11 +298,20 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
  *   ids, n_ids  : host array of the blocks to composite (1..64).
  *   other arguments as cow_render; outputs have n_rays rows.
  * n_rays = 0 returns COW_OK at once (the arrays may then be NULL); the same
- * holds for cow_render_backward(_noalloc), cow_opacity_loss and, with
- * n_points = 0, cow_sparsity_loss. */
+ * holds for cow_render_rays_block_t, cow_render_backward(_noalloc),
+ * cow_opacity_loss and, with n_points = 0, cow_sparsity_loss. */
 cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);
+
+/* cow_render_rays without early termination that also writes every block's
+ * own transmittance prod (1 - alpha_i) over its occupied samples (Eq. 11),
+ * -1 for a block without one: out_block_T is device float32 n_rays x n_ids,
+ * row r, column k for ids[k].  cow_opacity_loss reads it instead of marching
+ * each block a second time. */
+cow_status cow_render_rays_block_t(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                                   int32_t n_ids, const float *mlp, uint32_t flags, float *out_rgb, float *out_aux,
+                                   int32_t *out_nsamp, float *out_block_T, void *stream);
 
 /* Gradients of the ray-batch render (differentiation form): the analytic
  * adjoint of cow_render_rays with respect to every grid and plane feature and
@@ -368,7 +377,9 @@ cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, c
  *     sample, the binary entropy -(a log a + (1 - a) log(1 - a)) of the
  *     block's opacity a = 1 - prod (1 - alpha_i) (Eq. 11), clamped to
  *     [1e-6, 1 - 1e-6]; the mean over rays of the sum over blocks.  No early
- *     termination.
+ *     termination.  block_T: NULL (every block is marched once for its
+ *     opacity and once to scatter), or the out_block_T of a
+ *     cow_render_rays_block_t call on the same rays and ids (one march).
  * Both add weight * loss to *loss (a device float; NULL: not computed) and
  * weight * d loss / d f0 into the FP32 gradient arrays, laid out as for
  * cow_render_backward (grad_grid / grad_planes both NULL: no gradient;
@@ -378,7 +389,7 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
                              float weight, float *loss, float *const *grad_grid, float *const *grad_planes,
                              void *stream);
 cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
-                            int32_t n_ids, float weight, float *loss, float *const *grad_grid,
+                            int32_t n_ids, const float *block_T, float weight, float *loss, float *const *grad_grid,
                             float *const *grad_planes, void *stream);
 
 /* One Adam step on n FP32 parameters (device arrays param, grad, m, v):

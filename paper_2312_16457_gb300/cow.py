@@ -24,7 +24,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
-           "cow_render", "cow_render_rays", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
+           "cow_render", "cow_render_rays", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_sparsity_loss", "cow_opacity_loss",
@@ -86,7 +86,8 @@ def lib():
             "cow_set_residency": [P, i64, P],
             "cow_set_block_unbounded": [P, i32, i32, P],
             "cow_sparsity_loss": [P, P, i64, P, i32, flt, P, P, P, P],
-            "cow_opacity_loss": [P, P, P, i64, P, i32, flt, P, P, P, P],
+            "cow_opacity_loss": [P, P, P, i64, P, i32, P, flt, P, P, P, P],
+            "cow_render_rays_block_t": [P, P, P, i64, P, i32, P, u32, P, P, P, P, P],
             "cow_get_residency": [P, P],
             "cow_block_bytes": [P, i32, P],
             "cow_plan_view_order": [P, i32, P, P, i32, i64, P, P, P],
@@ -308,16 +309,34 @@ class Context:
                                        gg, gp, _stream_ptr(stream)))
         return loss
 
-    def opacity_loss(self, o, d, ids, weight: float = 1.0, loss=None, grads=None, stream=None):
-        """Eq. 8 over a ray batch (device o, d): as sparsity_loss."""
+    def opacity_loss(self, o, d, ids, weight: float = 1.0, loss=None, grads=None, block_T=None, stream=None):
+        """Eq. 8 over a ray batch (device o, d): as sparsity_loss.  block_T:
+        the in-block transmittances of render_rays_block_t on the same rays
+        and ids (each block is then marched once instead of twice)."""
         a = np.ascontiguousarray(ids, np.int32)
         if loss is None:
             loss = torch.zeros(1, dtype=torch.float32, device=o.device)
         gg, gp = self._grad_tables(grads)
         oc, dc = o.contiguous(), d.contiguous()
-        _check(lib().cow_opacity_loss(self._ctx, _ptr(oc), _ptr(dc), oc.shape[0], _ptr(a), len(a), float(weight),
-                                      _ptr(loss), gg, gp, _stream_ptr(stream)))
+        _check(lib().cow_opacity_loss(self._ctx, _ptr(oc), _ptr(dc), oc.shape[0], _ptr(a), len(a), _ptr(block_T),
+                                      float(weight), _ptr(loss), gg, gp, _stream_ptr(stream)))
         return loss
+
+    def render_rays_block_t(self, o, d, ids, mlp, mlp_bf16: bool = False, stream=None):
+        """render_rays without early termination; returns (rgb, aux, block_T)
+        with block_T[r, k] the transmittance of block ids[k] alone (-1: no
+        occupied sample)."""
+        n = o.shape[0]
+        a = np.ascontiguousarray(ids, np.int32)
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
+        ax = torch.empty((n, 8), dtype=torch.float32, device=o.device)
+        bt = torch.empty((n, len(a)), dtype=torch.float32, device=o.device)
+        m = mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp)
+        oc, dc = o.contiguous(), d.contiguous()
+        _check(lib().cow_render_rays_block_t(self._ctx, _ptr(oc), _ptr(dc), n, _ptr(a), len(a), _ptr(m),
+                                             FLAG_MLP_BF16 if mlp_bf16 else 0, _ptr(rgb), _ptr(ax), None, _ptr(bt),
+                                             _stream_ptr(stream)))
+        return rgb, ax, bt
 
     def update_features(self, i: int, grid, planes, stream=None):
         """Re-pack block i's features from new FP32 arrays (occupancy kept)."""

@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_remarch_bac
 //     1 - prod (1 - alpha_i); loss += weight/n H(clamp(alpha^k)) with H the
 //     binary entropy and the clamp to [1e-6, 1 - 1e-6];
 //     d alpha^k / d f0_i = sigma_i delta (1 - alpha^k).  The block is marched
-//     twice: once for alpha^k, once to scatter.
+//     once for alpha^k -- or alpha^k comes from the forward's in-block
+//     transmittance -- and once to scatter.
 // Gradients reach the density channel only: 20 scalar atomics per point or
 // sample (8 grid vertices, 4 texels of each plane).
 
@@ -378,15 +379,20 @@ __global__ void __launch_bounds__(kBwdThreads, COW_REG_MIN_BLOCKS) k_opacity(Reg
             const int id = rr.id[order[k]];
             const BlockRec &b = rr.r[order[k]];
             float T = 1.f;
-            int nk = 0;
-            for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
-                float2 f2[4];
-                accumulate_sample<DT>(b, p, g, f2);
-                T *= expf(-expf(f2[0].x) * delta);
-                nk++;
-                return true;
-            });
-            if (nk == 0) continue;
+            if (a.block_T) {  // the forward's in-block transmittance
+                T = __ldg(a.block_T + r * rr.n + order[k]);
+                if (T < 0.f) continue;  // no occupied sample
+            } else {
+                int nk = 0;
+                for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
+                    float2 f2[4];
+                    accumulate_sample<DT>(b, p, g, f2);
+                    T *= expf(-expf(f2[0].x) * delta);
+                    nk++;
+                    return true;
+                });
+                if (nk == 0) continue;
+            }
             const float a_raw = 1.f - T;
             const float al = fminf(fmaxf(a_raw, eps), 1.f - eps);
             term -= scale * (al * logf(al) + (1.f - al) * log1pf(-al));

@@ -776,9 +776,9 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     return COW_OK;
 }
 
-cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
-                           int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
-                           float *out_aux, int32_t *out_nsamp, void *stream) {
+static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                                   int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                                   float *out_aux, int32_t *out_nsamp, float *out_block_T, void *stream) {
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !out_rgb)
@@ -820,6 +820,7 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     a.ray_d = d;
     a.n_rays = n_rays;
     a.n_ray_ids = n_ids;
+    a.out_block_T = out_block_T;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_march_rays(a, rr, st));
@@ -827,6 +828,24 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)n_rays * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)n_rays * 4, cudaMemcpyDeviceToHost, st));
     return COW_OK;
+}
+
+cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                           int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
+                           float *out_aux, int32_t *out_nsamp, void *stream) {
+    return render_rays_impl(ctx, o, d, n_rays, ids, n_ids, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, nullptr,
+                            stream);
+}
+
+cow_status cow_render_rays_block_t(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                                   int32_t n_ids, const float *mlp, uint32_t flags, float *out_rgb, float *out_aux,
+                                   int32_t *out_nsamp, float *out_block_T, void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;
+    if (!out_block_T || !is_device_ptr(out_block_T))
+        return fail(COW_ERR_INVALID_ARG, "out_block_T must be device memory (n_rays x n_ids floats)");
+    return render_rays_impl(ctx, o, d, n_rays, ids, n_ids, mlp, 0.0f, flags, out_rgb, out_aux, out_nsamp, out_block_T,
+                            stream);
 }
 
 cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
@@ -957,7 +976,7 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
 }
 
 cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
-                            int32_t n_ids, float weight, float *loss, float *const *grad_grid,
+                            int32_t n_ids, const float *block_T, float weight, float *loss, float *const *grad_grid,
                             float *const *grad_planes, void *stream) {
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // nothing to add (the arrays may be NULL)
@@ -968,10 +987,12 @@ cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_
     cow::RegArgs a;
     cow_status rc = reg_prepare(ctx, ids, n_ids, loss, grad_grid, grad_planes, st, a);
     if (rc != COW_OK) return rc;
+    if (block_T && !is_device_ptr(block_T)) return fail(COW_ERR_INVALID_ARG, "block_T must be device memory");
     a.ray_o = o;
     a.ray_d = d;
     a.n = n_rays;
     a.weight = weight;
+    a.block_T = block_T;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_opacity(a, rr, st));

@@ -31,6 +31,7 @@ struct MarchArgs {
     int32_t smem_recs;     // view mode, thread schedule: block records the launch's shared memory holds
     const float *const *block_mlps;  // view mode, per-block MLPs: weights of record k, parallel to recs
     int32_t n_freq;                  // PE frequencies of the per-block MLPs
+    float *out_block_T;              // ray mode, may be null: n_rays x n_ray_ids in-block transmittances
 };
 
 // marching schedules of the view kernel
@@ -75,6 +76,8 @@ struct RegArgs {
     const float *ray_o, *ray_d;   // opacity: n x 3 rays
     int64_t n;
     float weight;                 // the loss and its gradient are scaled by weight / n
+    const float *block_T;         // opacity: the forward's n x n_ids in-block transmittances (-1: no
+                                  // sample), or null to march every block twice
     float *loss;                  // device float, accumulated (may be null)
     float *const *grad_grid;      // device pointer table as in BwdArgs (null: no gradient)
     float *const *grad_planes;

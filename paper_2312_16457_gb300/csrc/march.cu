@@ -377,8 +377,21 @@ __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(Ma
     float inv_d[3], omax;
     ray_setup(d, o, inv_d, omax);
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
-    for (int k = 0; k < n && !s.done; k++)
-        march_block<DT>(rr.r[order[k]], o, d, inv_d, omax, a.ert_eps, s, a.err);
+    if (a.out_block_T) {
+        // also every block's own transmittance, at its position in ids; -1
+        // for a block without occupied samples (the call has no early
+        // termination, so every block is marched)
+        float *bt = a.out_block_T + r * n;
+        for (int k = 0; k < n; k++) {
+            float tb = 1.f;
+            const int n0 = s.nsamp;
+            march_block<DT>(rr.r[order[k]], o, d, inv_d, omax, a.ert_eps, s, a.err, &tb);
+            bt[order[k]] = s.nsamp > n0 ? tb : -1.f;
+        }
+    } else {
+        for (int k = 0; k < n && !s.done; k++)
+            march_block<DT>(rr.r[order[k]], o, d, inv_d, omax, a.ert_eps, s, a.err);
+    }
     write_outputs(a, r, s, d, s_mlp);
 }
 

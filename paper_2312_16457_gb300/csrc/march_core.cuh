@@ -335,11 +335,13 @@ struct RayState {
     bool done;
 };
 
-// March one ray through one block, updating its state (Eq. 1-2).
+// March one ray through one block, updating its state (Eq. 1-2); when tb
+// is given it is multiplied by every sample's 1 - alpha (the block's own
+// transmittance, Eq. 11).
 template <int DT>
 __device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3],
                                             const float inv_d[3], float omax, float ert_eps, RayState &s,
-                                            unsigned *err) {
+                                            unsigned *err, float *tb = nullptr) {
     const bool more = for_each_sample(b, o, d, inv_d, omax, err, [&](const float p[3], const float g[3], float dt) {
         float2 f2[4];
         accumulate_sample<DT>(b, p, g, f2);
@@ -352,6 +354,7 @@ __device__ __forceinline__ void march_block(const BlockRec &b, const float o[3],
 #pragma unroll
         for (int c = 0; c < 4; c++) s.F[c] = fmaf(w, sigmoidf_fast(f[4 + c]), s.F[c]);
         s.T *= e;
+        if (tb) *tb *= e;
         s.nsamp++;
         return !(s.T < ert_eps);
     });

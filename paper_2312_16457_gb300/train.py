@@ -81,7 +81,12 @@ class Fitter:
         """One optimisation step; returns the colour loss (device tensor)
         before it (the weighted regularisers are in self.reg_loss)."""
         nb = len(self.ids)
-        rgb, aux, _ = self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps)
+        block_T = None
+        if self.lambda_opacity > 0.0 and ert_eps == 0.0:
+            # the forward also keeps every block's transmittance for the opacity term
+            rgb, aux, block_T = self.ctx.render_rays_block_t(o, d, self.ids, self.mlp)
+        else:
+            rgb, aux, _ = self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps)
         g, loss = cow.mse_grad(rgb, target)
         grads = [torch.zeros_like(p) for p in self.params]
         gm = torch.zeros_like(self.mlp)
@@ -94,7 +99,8 @@ class Fitter:
                 pts = self.box_lo + u * (self.box_hi - self.box_lo)
                 self.ctx.sparsity_loss(pts, self.ids, self.lambda_sparsity, loss=self.reg_loss, grads=gtab)
             if self.lambda_opacity > 0.0:
-                self.ctx.opacity_loss(o, d, self.ids, self.lambda_opacity, loss=self.reg_loss, grads=gtab)
+                self.ctx.opacity_loss(o, d, self.ids, self.lambda_opacity, loss=self.reg_loss, grads=gtab,
+                                      block_T=block_T)
         self.t += 1
         for k, p in enumerate(self.params):
             cow.adam_step(p, grads[k], self.m[k], self.v[k], self.lr_feat, self.t)

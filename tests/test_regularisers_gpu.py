@@ -76,6 +76,16 @@ def test_opacity_matches_oracle(storage):
     assert ol > 1e-5
     assert abs(float(loss.item()) - ol) <= 1e-4 * ol
     _check_grads(gg, gp, og, op)
+    # the same from the forward's in-block transmittances (one march a block)
+    rgb, _, bt = ctx.render_rays_block_t(o.cuda(), d.cuda(), ids, synth.mlp_weights(3))
+    rgb2 = ctx.render_rays(o.cuda(), d.cuda(), ids, synth.mlp_weights(3), aux=False)[0]
+    assert (rgb - rgb2).abs().max().item() <= 1e-6
+    assert bool(((bt == -1) | ((bt > 0) & (bt <= 1))).all()) and bool((bt == -1).any()) and bool((bt > 0).any())
+    gg2, gp2 = _zeros(sc)
+    loss2 = ctx.opacity_loss(o.cuda(), d.cuda(), ids, 0.001, grads=(gg2, gp2), block_T=bt)
+    ctx.sync_check()
+    assert abs(float(loss2.item()) - ol) <= 1e-4 * ol
+    _check_grads(gg2, gp2, og, op)
 
 
 def test_fitter_with_regularisers():
