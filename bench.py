@@ -41,7 +41,8 @@ MARCH_REVISION = "v8-unbounded"
 MEASURED_TRAFFIC = {("city_lod_1080p", "bf16", "thread_const", 1): 49487934976}
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}
-GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160}  # per occupied sample: 20 texels x 8 ch
+# per occupied sample: 20 texels x 8 channels (8 grid vertices + 12 plane texels)
+GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160, "bf16_fp8": 8 * 16 + 12 * 8}
 
 
 def parse():
@@ -341,7 +342,7 @@ def run_cow(args, ws, rank, local):
     # gather roofline: the marcher's algorithmic gather bytes against the
     # measured random-gather rate of the same load width from an L1-resident
     # buffer (L2- and HBM-resident levels reported beside it)
-    width = 32 if storage in ("fp32", "fp16", "bf16") else 16
+    width = 32 if storage in ("fp32", "fp16", "bf16", "bf16_fp8") else 16
     peak_l1 = cow.gather_peak(width, 64 << 10)
     peak_l2 = cow.gather_peak(width, 32 << 20)
     peak_hbm = cow.gather_peak(width, 8 << 30, iters=64)

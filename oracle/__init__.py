@@ -204,8 +204,9 @@ class OracleScene:
     computed by the oracle itself.
 
     values: "master" (FP32 arrays as given), or a storage format name
-    ("fp16", "bf16", "fp8") to run on the oracle's own dequantisation of the
-    master, or "f64" to hold float64 copies (finite differences)."""
+    ("fp16", "bf16", "fp8", or "bf16_fp8" for a BF16 grid with FP8 planes) to
+    run on the oracle's own dequantisation of the master, or "f64" to hold
+    float64 copies (finite differences)."""
 
     def __init__(self, scene, values: str = "master", occupancy_from=None):
         self.scene = scene
@@ -222,9 +223,10 @@ class OracleScene:
             pls = [_np(p, np.float64 if f64 else np.float32) for p in b.planes]
             occ_src = _np(b.grid) if occupancy_from is None else _np(occupancy_from[i])
             bits = occupancy(occ_src, b.R, scene.occ_cell, scene.occ_thresh)
-            if values in ("fp16", "bf16", "fp8"):
-                g = quantize(g, values, channel_scale_exps(g, values))[1].reshape(g.shape)
-                pls = [quantize(p, values, channel_scale_exps(p, values))[1].reshape(p.shape) for p in pls]
+            if values in ("fp16", "bf16", "fp8", "bf16_fp8"):
+                gv, pv = (values, values) if values != "bf16_fp8" else ("bf16", "fp8")
+                g = quantize(g, gv, channel_scale_exps(g, gv))[1].reshape(g.shape)
+                pls = [quantize(p, pv, channel_scale_exps(p, pv))[1].reshape(p.shape) for p in pls]
             ob = self.blocks[i]
             ob.lo[:] = [float(v) for v in b.lo]
             ob.hi[:] = [float(v) for v in b.hi]

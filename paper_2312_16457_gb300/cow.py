@@ -16,8 +16,16 @@ import torch
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcow.so")
 _lib = None
 
-DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
+# "bf16_fp8": BF16 grid, FP8-E4M3 planes (quad layout)
+DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3, "bf16_fp8": 4}
 ELEM_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp8": 1}
+
+
+def tensor_storage(storage: str, tensor: int) -> str:
+    """Storage of tensor 0 (grid) or 1-3 (planes) of a context."""
+    if storage == "bf16_fp8":
+        return "bf16" if tensor == 0 else "fp8"
+    return storage
 FLAG_MLP_BF16 = 1
 FLAG_BLOCK_MLPS = 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE_ASSERT"}
@@ -402,7 +410,8 @@ class Context:
     def packed(self, i: int, tensor: int):
         b = self.scene.blocks[i]
         n = (b.R ** 3 if tensor == 0 else b.P ** 2) * 8
-        dt = {"fp32": np.float32, "fp16": np.uint16, "bf16": np.uint16, "fp8": np.uint8}[self.storage]
+        dt = {"fp32": np.float32, "fp16": np.uint16, "bf16": np.uint16,
+              "fp8": np.uint8}[tensor_storage(self.storage, tensor)]
         out = np.zeros(n, dt)
         se = np.zeros(8, np.int32)
         _check(lib().cow_export_packed(self._ctx, int(i), int(tensor), _ptr(out), out.nbytes, _ptr(se)))

@@ -225,6 +225,7 @@ cudaError_t launch_march_batch(const BatchArgs &a, int tile_cfg, int grid, cudaS
     case kF16: return launch_dt<kF16>(a, tile_cfg, grid, st);
     case kBF16: return launch_dt<kBF16>(a, tile_cfg, grid, st);
     case kFP8: return launch_dt<kFP8>(a, tile_cfg, grid, st);
+    case kMixed: return launch_dt<kMixed>(a, tile_cfg, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -468,6 +468,7 @@ cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream
     case kF16: k_remarch_backward<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_remarch_backward<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -481,6 +482,7 @@ cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st
     case kF16: k_sparsity<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kBF16: k_sparsity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_sparsity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_sparsity<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -494,6 +496,7 @@ cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st)
     case kF16: k_opacity<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kBF16: k_opacity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_opacity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_opacity<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -43,10 +43,22 @@ using namespace cowi;
 
 namespace {
 
+// storage of tensor t (0 grid, 1-3 planes) of a context: the mixed format
+// keeps the grid in BF16 and the planes in FP8
+int tensor_dtype(int dtype, int t) {
+    if (dtype == COW_BF16_FP8) return t == 0 ? COW_BF16 : COW_FP8_E4M3;
+    return dtype;
+}
+
 int elem_bytes(int dtype) { return dtype == COW_FP32 ? 4 : dtype == COW_FP8_E4M3 ? 1 : 2; }
 
 // bytes of one packed element (a vertex, or a vertex pair in the pair layout)
-int64_t packed_elem_bytes(int dtype) { return dtype == COW_FP32 ? 32 : 2 * 8 * elem_bytes(dtype); }
+// bytes of one packed element: an FP32 vertex, a pair of 16- or 8-bit
+// vertices, or (mixed planes) a 2x2 quad of FP8 texels -- 32 bytes for the
+// mixed format's grid and planes alike
+int64_t packed_elem_bytes(int dtype) {
+    return dtype == COW_FP32 || dtype == COW_BF16_FP8 ? 32 : 2 * 8 * elem_bytes(dtype);
+}
 
 // smallest e with amax <= 448 * 2^e (e = 0 for an all-zero channel)
 int fp8_exponent(float amax) {
@@ -117,7 +129,7 @@ cow_status repack_block(cow_ctx *c, BlockHost &b, const float *const src_in[4], 
             s = (const float *)staging;
         }
         int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (c->dtype == COW_FP8_E4M3) {
+        if (tensor_dtype(c->dtype, t) == COW_FP8_E4M3) {
             COW_CUDA(cow::launch_amax8(s, nv[t], d_amax, st));
             unsigned amax_bits[8];
             COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
@@ -135,7 +147,8 @@ cow_status repack_block(cow_ctx *c, BlockHost &b, const float *const src_in[4], 
             scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
         }
         COW_CUDA(cudaMemcpyAsync(d_inv + 8 * t, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
-        COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? b.R : b.P, c->dtype, d_inv + 8 * t, dst[t], st));
+        if (c->dtype == COW_BF16_FP8 && t > 0) COW_CUDA(cow::launch_pack_quad8(s, b.P, d_inv + 8 * t, dst[t], st));
+        else COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? b.R : b.P, tensor_dtype(c->dtype, t), d_inv + 8 * t, dst[t], st));
     }
     COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
     return COW_OK;
@@ -160,7 +173,7 @@ cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *sta
             s = (const float *)staging;
         }
         int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (c->dtype == COW_FP8_E4M3) {
+        if (tensor_dtype(c->dtype, t) == COW_FP8_E4M3) {
             COW_CUDA(cow::launch_amax8(s, nv[t], d_amax, st));
             unsigned amax_bits[8];
             COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
@@ -178,7 +191,9 @@ cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *sta
             scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
         }
         COW_CUDA(cudaMemcpyAsync(d_inv, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
-        COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? d.grid_res : d.plane_res, c->dtype, d_inv, *dst[t], st));
+        if (c->dtype == COW_BF16_FP8 && t > 0) COW_CUDA(cow::launch_pack_quad8(s, d.plane_res, d_inv, *dst[t], st));
+        else COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? d.grid_res : d.plane_res, tensor_dtype(c->dtype, t), d_inv,
+                                       *dst[t], st));
         if (t == 0) COW_CUDA(cow::launch_occupancy(s, d.grid_res, c->occ_cell, log_thresh, b.occ, st));
         // the staging buffer and d_inv are reused by the next tensor: the
         // stream orders the next copies after these kernels
@@ -532,7 +547,7 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
     g_last_error.clear();
     if (!out || !blocks || n < 1) return fail(COW_ERR_INVALID_ARG, "cow_load_blocks: null pointer or n < 1");
     *out = nullptr;
-    if ((int)storage < 0 || (int)storage > 3) return fail(COW_ERR_INVALID_ARG, "unknown storage dtype %d", (int)storage);
+    if ((int)storage < 0 || (int)storage > 4) return fail(COW_ERR_INVALID_ARG, "unknown storage dtype %d", (int)storage);
     if (occ_cell < 1 || occ_cell > 4096) return fail(COW_ERR_INVALID_ARG, "occ_cell must be in [1, 4096]");
     if (!(occ_thresh > 0.0f)) return fail(COW_ERR_INVALID_ARG, "occ_thresh must be > 0");
     size_t max_vec = 0;
@@ -1322,7 +1337,8 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
         return fail(COW_ERR_INVALID_ARG, "block or tensor out of range");
     const BlockHost &b = ctx->blocks[(size_t)block];
     const int64_t nv = tensor == 0 ? (int64_t)b.R * b.R * b.R : (int64_t)b.P * b.P;
-    const int64_t need = nv * cow::kNch * elem_bytes(ctx->dtype);
+    const int tdt = tensor_dtype(ctx->dtype, tensor);
+    const int64_t need = nv * cow::kNch * elem_bytes(tdt);
     if (nbytes < need) return fail(COW_ERR_INVALID_ARG, "need %lld bytes", (long long)need);
     DeviceGuard dg(ctx->device);
     // an unloaded block is read from its pinned host copy
@@ -1331,7 +1347,8 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
         COW_CUDA(cudaMemcpy(out, src, (size_t)need, cudaMemcpyDefault));
     } else {
         // pair layout on the device: keep the first vertex of every pair
-        const int64_t pe = packed_elem_bytes(ctx->dtype), ve = pe / 2;
+        // (the first texel of a mixed-format quad)
+        const int64_t pe = packed_elem_bytes(ctx->dtype), ve = cow::kNch * elem_bytes(tdt);
         std::vector<unsigned char> raw((size_t)(nv * pe));
         COW_CUDA(cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDefault));
         for (int64_t i = 0; i < nv; i++) std::memcpy((unsigned char *)out + i * ve, raw.data() + i * pe, (size_t)ve);

@@ -26,7 +26,9 @@ constexpr unsigned kErrRange = 1u;    // a (ray, block) candidate range exceeded
 constexpr unsigned kErrTimeout = 2u;  // a bounded wait ran out
 constexpr unsigned kErrArg = 4u;      // a kernel met an argument it cannot handle
 
-enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3 };
+// kMixed: BF16 grid (pair layout) with FP8-E4M3 planes (quad layout: element
+// (u, v) holds texels (u, v), (u+1, v), (u, v+1), (u+1, v+1), 8 bytes each)
+enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3, kMixed = 4 };
 
 // Unbounded boundary blocks (scene contraction, Eq. 16)
 constexpr int kUnbXLo = 1, kUnbXHi = 2, kUnbYLo = 4, kUnbYHi = 8, kUnbContracted = 16;
@@ -400,6 +402,10 @@ struct Store<kFP8> {
         hi[3] = fp8x2_to_float2(q.w >> 16);
     }
 };
+
+// BF16 grid of the mixed format (its planes are read by accumulate_sample)
+template <>
+struct Store<kMixed> : Store<kBF16> {};
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 

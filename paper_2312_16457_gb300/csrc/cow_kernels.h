@@ -118,5 +118,6 @@ cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cud
 cudaError_t launch_pack(const float *x, int64_t n_vec, int row, int dtype, const float *inv_scale8, void *out,
                         cudaStream_t st);
 cudaError_t launch_occupancy(const float *grid, int R, int C, double log_thresh, uint32_t *bits, cudaStream_t st);
+cudaError_t launch_pack_quad8(const float *x, int P, const float *inv_scale8, void *out, cudaStream_t st);
 
 }  // namespace cow

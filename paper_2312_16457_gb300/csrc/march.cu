@@ -416,6 +416,7 @@ cudaError_t launch_thread_dt(const MarchArgs &a, int n_tiles, bool in_params, cu
     case kF16: return launch_thread<kF16, kBlockMlp>(a, n_tiles, in_params, st, pr);
     case kBF16: return launch_thread<kBF16, kBlockMlp>(a, n_tiles, in_params, st, pr);
     case kFP8: return launch_thread<kFP8, kBlockMlp>(a, n_tiles, in_params, st, pr);
+    case kMixed: return launch_thread<kMixed, kBlockMlp>(a, n_tiles, in_params, st, pr);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -432,6 +433,7 @@ cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cu
         case kF16: k_march_views_w<kF16><<<n_tiles, kThreads, 0, st>>>(a); break;
         case kBF16: k_march_views_w<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
         case kFP8: k_march_views_w<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kMixed: k_march_views_w<kMixed><<<n_tiles, kThreads, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
@@ -450,6 +452,7 @@ cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_
     case kF16: k_march_rays<kF16><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     case kBF16: k_march_rays<kBF16><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     case kFP8: k_march_rays<kFP8><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_march_rays<kMixed><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -118,6 +118,34 @@ __global__ void k_occupancy(const float *__restrict__ grid, int R, int C, int Nc
     }
 }
 
+// FP8 quad layout (planes of the mixed format): element (u, v) of a P x P
+// plane holds the FP8 texels (u, v), (u+1, v), (u, v+1), (u+1, v+1), clamped
+// at the last row and column, 8 bytes each.
+__global__ void k_pack_quad8(const float *__restrict__ x, int P, const float *__restrict__ inv_scale, void *out) {
+    float s[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) s[c] = inv_scale[c];
+    const int64_t n = (int64_t)P * P;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int u = (int)(i % P), v = (int)(i / P);
+        const int u1 = min(u + 1, P - 1), v1 = min(v + 1, P - 1);
+        const int64_t t[4] = {(int64_t)v * P + u, (int64_t)v * P + u1, (int64_t)v1 * P + u, (int64_t)v1 * P + u1};
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            float val[8];
+            load_scaled(x, t[q], s, val);
+            uint32_t e[4];
+            encode8<kFP8>(val, e);
+            w[2 * q] = e[0];
+            w[2 * q + 1] = e[1];
+        }
+        uint4 *o = reinterpret_cast<uint4 *>(out) + 2 * i;
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
 int grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b > 152 * 64) b = 152 * 64;
@@ -143,6 +171,11 @@ cudaError_t launch_pack(const float *x, int64_t n_vec, int row, int dtype, const
     case kFP8: k_pack<kFP8><<<g, 256, 0, st>>>(x, n_vec, row, inv_scale8, out); break;
     default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_quad8(const float *x, int P, const float *inv_scale8, void *out, cudaStream_t st) {
+    k_pack_quad8<<<grid_for((int64_t)P * P, 256), 256, 0, st>>>(x, P, inv_scale8, out);
     return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ def _gpu_grads(ctx, sc, o, d, ids, mlp, g):
     return rgb, ns, gg, gp, gm
 
 
-@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+@pytest.mark.parametrize("storage", ["fp32", "bf16", "bf16_fp8"])
 def test_backward_matches_oracle_gradient(storage):
     sc = synth.city_scene(17, 2, 2.0, [(16, 40)])
     o, d = synth.random_rays(4096, 7, sc.box_lo, sc.box_hi)
