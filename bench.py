@@ -235,6 +235,8 @@ def run_cow(args, ws, rank, local):
     ctx32 = cow.Context(sc, "fp32") if (not args.no_fp32 and storage != "fp32") else None
     if ctx32 is not None:
         ctx32.set_schedule(args.schedule)
+    # the mixed precision form (BF16 grid, FP8 planes) on the same frame
+    ctxm = cow.Context(sc, "bf16_fp8") if (not args.no_fp32 and storage == "bf16") else None
     need_master = rank == 0 and ws == 1 and not args.no_cpu
     if not need_master:  # the contexts hold packed copies; drop the FP32 masters
         for b in sc.blocks:
@@ -306,6 +308,15 @@ def run_cow(args, ws, rank, local):
     block_mlp_form = {"frames_per_s": round(1000.0 / float(np.mean(tbm)), 3), "n_freq": 4,
                       "mlp_params_per_block": synth.block_mlp_nparam(4)}
 
+    mixed = {}
+    if ctxm is not None:
+        outm = (torch.empty((npix, 3), device=dev), None, None)
+        tm = time_steps(lambda: ctxm.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=outm),
+                        max(5, args.steps // 2), 3, flush, stream)
+        ctxm.sync_check()
+        mixed = {"frames_per_s": round(1000.0 / float(np.mean(tm)), 3), "rgb": outm[0].cpu().numpy()}
+        ctxm.close()
+
     # plain FP32 storage, same frame
     fp32 = {}
     if ctx32 is not None:
@@ -316,6 +327,10 @@ def run_cow(args, ws, rank, local):
         rgb32 = out32[0].cpu().numpy()
         fp32 = {"plain_fp32_frames_per_s": round(1000.0 / float(np.mean(t32)), 3),
                 "psnr_vs_plain_fp32_db": round(psnr(rgb_main, rgb32), 2)}
+        if mixed:
+            fp32["bf16_grid_fp8_planes_same_frame"] = {
+                "frames_per_s": mixed["frames_per_s"], "psnr_vs_plain_fp32_db": round(psnr(mixed["rgb"], rgb32), 2),
+                "storage": "BF16 grid, FP8-E4M3 planes (quad layout, per-channel scales)"}
         ctx32.close()
 
     # oracle on a bounded sample of this frame (rank 0, N = 1 only)
