@@ -45,9 +45,21 @@ namespace {
 constexpr int kBwdThreads = 128;
 constexpr int kVec = 77;  // x (10), dz1 (16), h1 (16), dz2 (16), h2 (16), dz3 (3)
 
+// Vector reduction without a returned value (red, not atom: a float4
+// atomicAdd compiles to an atomic that returns the old value through L1, and
+// those returns kept the backward's L1 pipe saturated).  16-byte aligned.
+__device__ __forceinline__ void red_add4(float *dst, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void red_add1(float *dst, float a) {
+    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(dst), "f"(a) : "memory");
+}
+
 __device__ __forceinline__ void red_add8(float *dst, float s, const float gf[8]) {
-    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(s * gf[0], s * gf[1], s * gf[2], s * gf[3]));
-    atomicAdd(reinterpret_cast<float4 *>(dst) + 1, make_float4(s * gf[4], s * gf[5], s * gf[6], s * gf[7]));
+    red_add4(dst, s * gf[0], s * gf[1], s * gf[2], s * gf[3]);
+    red_add4(dst + 4, s * gf[4], s * gf[5], s * gf[6], s * gf[7]);
 }
 
 // Scatter an 8-channel feature gradient to the taps of the lookup at (p, g).
@@ -284,7 +296,7 @@ __device__ __forceinline__ void scatter_ch0(const BlockRec &b, float *gg, float 
         for (int k = 0; k < 8; k++) {
             const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
             const float w = (dy ? fr[1] : 1.f - fr[1]) * (dz ? fr[2] : 1.f - fr[2]) * (dx ? fr[0] : 1.f - fr[0]);
-            atomicAdd(gg + 8 * (base + (dz * R + dy) * R + dx), w * g0);
+            red_add1(gg + 8 * (base + (dz * R + dy) * R + dx), w * g0);
         }
     }
     float hf[3];
@@ -307,7 +319,7 @@ __device__ __forceinline__ void scatter_ch0(const BlockRec &b, float *gg, float 
         for (int q = 0; q < 4; q++) {
             const int du = q & 1, dv = q >> 1;
             const float w = (dv ? hf[va] : 1.f - hf[va]) * (du ? hf[ua] : 1.f - hf[ua]);
-            atomicAdd(gp[pl] + 8 * (tb + dv * P + du), w * g0);
+            red_add1(gp[pl] + 8 * (tb + dv * P + du), w * g0);
         }
     }
 }
