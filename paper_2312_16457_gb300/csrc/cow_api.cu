@@ -89,7 +89,6 @@ void destroy(cow_ctx *c) {
     cudaFree(c->d_err);
     cudaFree(c->d_mlp);
     c->views.release();
-    c->ids.release();
     c->out_rgb.release();
     c->out_aux.release();
     c->out_nsamp.release();
@@ -809,8 +808,6 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     cudaStream_t st = (cudaStream_t)stream;
     cow_status rc;
     if ((rc = ensure_resident(ctx, ids, n_ids, st)) != COW_OK) return rc;
-    COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
-    COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const float *d_mlp = nullptr;
     if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
     float *rgb, *aux;
@@ -821,9 +818,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     if ((rc = resolve_out(out_nsamp, (size_t)n_rays * 4, ctx->out_nsamp, &ns, &h_ns)) != COW_OK) return rc;
     cow::MarchArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.recs = ctx->d_blocks;
     a.dtype = ctx->dtype;
-    a.ids = (const int32_t *)ctx->ids.p;
     a.mlp = d_mlp;
     a.ert_eps = ert_eps;
     a.flags = flags;
@@ -834,7 +829,6 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     a.ray_o = o;
     a.ray_d = d;
     a.n_rays = n_rays;
-    a.n_ray_ids = n_ids;
     a.out_block_T = out_block_T;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
@@ -894,17 +888,12 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     if (rc != COW_OK) return rc;
     COW_CUDA(ctx->gptrs.reserve(ptrs.size() * sizeof(float *)));
     COW_CUDA(cudaMemcpyAsync(ctx->gptrs.p, ptrs.data(), ptrs.size() * sizeof(float *), cudaMemcpyHostToDevice, st));
-    COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
-    COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const int rows = cow::backward_rows(n_rays);
     const size_t part_bytes = ((size_t)std::max(rows, 1) * cow::kMlpParams * sizeof(float) + 255) & ~(size_t)255;
     COW_CUDA(ctx->partials.reserve(part_bytes + (size_t)std::max<int64_t>(n_rays, 1) * 8 * sizeof(float)));
     cow::BwdArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.recs = ctx->d_blocks;
     a.dtype = ctx->dtype;
-    a.n_ray_ids = n_ids;
-    a.ids = (const int32_t *)ctx->ids.p;
     a.mlp = mlp;
     a.ert_eps = ert_eps;
     a.ray_o = o;
@@ -940,8 +929,6 @@ cow_status reg_prepare(cow_ctx *ctx, const int32_t *ids, int32_t n_ids, float *l
     std::memset(&a, 0, sizeof(a));
     cow_status rc = ensure_resident(ctx, ids, n_ids, st);
     if (rc != COW_OK) return rc;
-    COW_CUDA(ctx->ids.reserve((size_t)n_ids * sizeof(int32_t)));
-    COW_CUDA(cudaMemcpyAsync(ctx->ids.p, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     if (grad_grid) {
         std::vector<float *> ptrs((size_t)nb * 4);
         for (int32_t i = 0; i < nb; i++) {
@@ -958,10 +945,7 @@ cow_status reg_prepare(cow_ctx *ctx, const int32_t *ids, int32_t n_ids, float *l
         a.grad_grid = (float *const *)ctx->gptrs.p;
         a.grad_planes = (float *const *)ctx->gptrs.p + nb;
     }
-    a.recs = ctx->d_blocks;
     a.dtype = ctx->dtype;
-    a.n_ids = n_ids;
-    a.ids = (const int32_t *)ctx->ids.p;
     a.loss = loss;
     a.err = ctx->d_err;
     return COW_OK;
@@ -1387,8 +1371,7 @@ constexpr int32_t kNoAllocMaxBlocks = 1024;
 constexpr size_t kNaRowsBytes = (size_t)(kNoAllocMaxRays / 128) * cow::kMlpParams * sizeof(float);  // 1021952
 constexpr size_t kNaGcfBytes = (size_t)kNoAllocMaxRays * 8 * sizeof(float);                           // 2 MiB
 constexpr size_t kNaPtrBytes = (size_t)kNoAllocMaxBlocks * 4 * sizeof(float *);                        // 32 KiB
-constexpr size_t kNaIdsBytes = (size_t)cow::kMaxRayIds * sizeof(int32_t);
-constexpr size_t kNaTotalBytes = kNaRowsBytes + kNaGcfBytes + kNaPtrBytes + kNaIdsBytes;
+constexpr size_t kNaTotalBytes = kNaRowsBytes + kNaGcfBytes + kNaPtrBytes;
 static_assert(kNaRowsBytes % 256 == 0 && kNaGcfBytes % 256 == 0 && kNaPtrBytes % 256 == 0,
               "scratch sections must keep 256-byte alignment");
 
@@ -1463,16 +1446,11 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     float *rows = (float *)scratch;
     float *gcf = (float *)(scratch + kNaRowsBytes);
     float **dptrs = (float **)(scratch + kNaRowsBytes + kNaGcfBytes);
-    int32_t *dids = (int32_t *)(scratch + kNaRowsBytes + kNaGcfBytes + kNaPtrBytes);
     cudaStream_t st = (cudaStream_t)stream;
     COW_CUDA(cudaMemcpyAsync(dptrs, table, (size_t)nb * 4 * sizeof(float *), cudaMemcpyHostToDevice, st));
-    COW_CUDA(cudaMemcpyAsync(dids, ids, (size_t)n_ids * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     cow::BwdArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.recs = ctx->d_blocks;
     a.dtype = ctx->dtype;
-    a.n_ray_ids = n_ids;
-    a.ids = dids;
     a.mlp = mlp;
     a.ert_eps = ert_eps;
     a.ray_o = o;

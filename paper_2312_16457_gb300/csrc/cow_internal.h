@@ -103,7 +103,7 @@ struct cow_ctx {
     std::vector<cow::BlockRec> recs;  // host copy of d_blocks
     unsigned *d_err = nullptr;
     float *d_mlp = nullptr;
-    cowi::DevBuf views, ids, out_rgb, out_aux, out_nsamp;
+    cowi::DevBuf views, out_rgb, out_aux, out_nsamp;
     cowi::DevBuf gptrs, partials;  // backward: per-block gradient pointers, per-CTA MLP-gradient rows
     cowi::DevBuf staging;          // host masters of cow_update_features
     cowi::DevBuf block_mlps;       // cow_set_block_mlps: n_blocks x block_mlp_nparam FP32

@@ -11,12 +11,11 @@ struct ViewRec;
 struct RayRecs;
 
 struct MarchArgs {
-    const BlockRec *recs;  // view mode: the views' block records, near to far, by ViewRec::ids_begin;
-                           // ray mode: every block of the context, indexed by ids
+    const BlockRec *recs;  // view mode: the views' block records, near to far, by ViewRec::ids_begin
+                           // (ray mode takes its records by value, RayRecs)
     const ViewRec *views;
     int32_t n_views;
     int32_t dtype;
-    const int32_t *ids;    // ray mode: the blocks to composite
     const float *mlp;      // 499 FP32 (device)
     float ert_eps;
     uint32_t flags;
@@ -27,7 +26,6 @@ struct MarchArgs {
     const float *ray_o;    // ray mode
     const float *ray_d;
     int64_t n_rays;
-    int32_t n_ray_ids;
     int32_t smem_recs;     // view mode, thread schedule: block records the launch's shared memory holds
     const float *const *block_mlps;  // view mode, per-block MLPs: weights of record k, parallel to recs
     int32_t n_freq;                  // PE frequencies of the per-block MLPs
@@ -46,11 +44,8 @@ int march_tile_w();
 int march_tile_h();
 
 // K6 / K7: gradients of the ray-batch form (bwd.cu)
-struct BwdArgs {
-    const BlockRec *recs;         // every block of the context
+struct BwdArgs {                  // the call's block records come by value (RayRecs)
     int32_t dtype;
-    int32_t n_ray_ids;
-    const int32_t *ids;           // the blocks to composite
     const float *mlp;             // 499 FP32 (device)
     float ert_eps;
     const float *ray_o, *ray_d;   // n_rays x 3
@@ -67,11 +62,8 @@ struct BwdArgs {
 
 // Training-stage regularisers (bwd.cu): sparsity (Eq. 7) over points,
 // block opacity (Eq. 8) over rays
-struct RegArgs {
-    const BlockRec *recs;         // every block of the context
+struct RegArgs {                  // the blocks that take part come by value (RayRecs)
     int32_t dtype;
-    int32_t n_ids;
-    const int32_t *ids;           // the blocks that take part
     const float *pts;             // sparsity: n x 3 points
     const float *ray_o, *ray_d;   // opacity: n x 3 rays
     int64_t n;
