@@ -68,10 +68,15 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
             for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
         }
     }
+    // per-channel scales: 8 floats of one tensor as two 16-byte loads (the
+    // scale array is its own allocation, so 16-byte aligned)
+    const float4 *scale4 = reinterpret_cast<const float4 *>(b.scale);
     if (DT == kFP8) {
-#pragma unroll
-        for (int c = 0; c < 4; c++)
-            f[c] = make_float2(acc[c].x * b.scale[2 * c], acc[c].y * b.scale[2 * c + 1]);
+        const float4 sa = __ldg(scale4), sb = __ldg(scale4 + 1);
+        f[0] = make_float2(acc[0].x * sa.x, acc[0].y * sa.y);
+        f[1] = make_float2(acc[1].x * sa.z, acc[1].y * sa.w);
+        f[2] = make_float2(acc[2].x * sb.x, acc[2].y * sb.y);
+        f[3] = make_float2(acc[3].x * sb.z, acc[3].y * sb.w);
     } else {
 #pragma unroll
         for (int c = 0; c < 4; c++) f[c] = acc[c];
@@ -134,10 +139,11 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
             }
         }
         if (DT == kFP8 || DT == kMixed) {
-            const float *sc = b.scale + 8 * (pl + 1);
-#pragma unroll
-            for (int c = 0; c < 4; c++)
-                f[c] = __ffma2_rn(pacc[c], make_float2(sc[2 * c], sc[2 * c + 1]), f[c]);
+            const float4 sa = __ldg(scale4 + 2 * (pl + 1)), sb = __ldg(scale4 + 2 * (pl + 1) + 1);
+            f[0] = __ffma2_rn(pacc[0], make_float2(sa.x, sa.y), f[0]);
+            f[1] = __ffma2_rn(pacc[1], make_float2(sa.z, sa.w), f[1]);
+            f[2] = __ffma2_rn(pacc[2], make_float2(sb.x, sb.y), f[2]);
+            f[3] = __ffma2_rn(pacc[3], make_float2(sb.z, sb.w), f[3]);
         } else {
 #pragma unroll
             for (int c = 0; c < 4; c++) f[c] = __fadd2_rn(f[c], pacc[c]);
