@@ -121,3 +121,32 @@ def test_argument_errors():
     # the global form is unaffected
     ctx.render(cams, [[0]], mlp)
     ctx.sync_check()
+
+
+def test_identical_block_mlps_seam_only_where_blocks_meet():
+    """The library's per-block form with the same MLP in every block against
+    its global form: equal colours on rays whose occupied samples lie in one
+    block, different colours on rays with samples in two or more blocks (the
+    per-block form's seam for view-dependent colour); the blended C_d, F and
+    T agree everywhere."""
+    sc = synth.city_scene(6, 2, 2.0, [(24, 64)])
+    n = len(sc.blocks)
+    mlp = synth.mlp_weights(106)
+    ctx = cow.Context(sc, "fp32")
+    ctx.set_block_mlps(np.repeat(mlp[None, :], n, axis=0), 0)
+    cam = synth.camera((-0.6, -4.0, 3.0), (0.2, 0.3, -0.5), 80, 60, 70.0)
+    order = ctx.sort_blocks(cam, list(range(n)))
+    r_b, a_b, n_b = _render(ctx, [cam], [order])
+    rg, ag, ng = ctx.render([cam], [order], torch.from_numpy(mlp).cuda(), nsamp=True)
+    ctx.sync_check()
+    r_g, a_g, n_g = rg.cpu().numpy(), ag.cpu().numpy(), ng.cpu().numpy()
+    assert np.array_equal(n_b, n_g)
+    assert np.abs(a_b - a_g).max() <= 1e-5
+    blocks_hit = np.zeros_like(n_b)
+    for k in order:
+        _, _, n_k = _render(ctx, [cam], [[k]])
+        blocks_hit += n_k > 0
+    one, many = blocks_hit == 1, blocks_hit >= 2
+    assert one.mean() > 0.15 and many.mean() > 0.05
+    assert np.abs(r_b[one] - r_g[one]).max() <= 1e-5
+    assert np.abs(r_b[many] - r_g[many]).max() > 1e-2

@@ -156,3 +156,33 @@ def test_block_without_samples_takes_no_part(orc):
     assert np.array_equal(rgb, rgb2) and np.array_equal(aux, aux2)
     r1, _, n1 = orc.render_view_block_mlp(osc, cam, [1], w, L)
     assert np.all(n1 == 0) and np.all(r1 == 0.0)
+
+
+def test_identical_block_mlps_seam_only_where_blocks_meet(orc):
+    """The per-block form with the same MLP in every block (L = 0, the global
+    MLP's layout) against the global form: a ray whose occupied samples all
+    lie in one block gets the same colour (Eq. 5 with one term is Eq. 3),
+    while a ray with samples in two or more blocks does not, because the MLP
+    is not linear in (C_d, F).  This is the seam of the per-block form for
+    view-dependent colour, which the global form does not have."""
+    sc = synth.city_scene(6, 2, 2.0, [(12, 32)])
+    n = len(sc.blocks)
+    mlp = synth.mlp_weights(106)
+    w = np.repeat(mlp[None, :].astype(np.float64), n, axis=0)
+    osc = orc.OracleScene(sc)
+    cam = synth.camera((-0.6, -4.0, 3.0), (0.2, 0.3, -0.5), 40, 30, 70.0)
+    order = orc.sort_view(osc, list(range(n)), cam)
+    r_b, a_b, n_b = orc.render_view_block_mlp(osc, cam, order, w, 0)
+    r_g, a_g, n_g = orc.render_view(osc, cam, order, mlp)
+    assert np.array_equal(n_b, n_g)
+    np.testing.assert_allclose(a_b, a_g, rtol=0, atol=1e-13)  # the blended C_d, F, T are the same
+    blocks_hit = np.zeros_like(n_b)
+    for k in order:
+        _, _, n_k = orc.render_view_block_mlp(osc, cam, [k], w, 0)
+        blocks_hit += n_k > 0
+    one = blocks_hit == 1
+    many = blocks_hit >= 2
+    assert one.mean() > 0.15 and many.mean() > 0.05
+    np.testing.assert_allclose(r_b[one], r_g[one], rtol=0, atol=1e-13)
+    seam = np.abs(r_b[many] - r_g[many]).max(axis=1)
+    assert seam.max() > 1e-2 and np.median(seam) > 1e-4
