@@ -229,9 +229,9 @@ cow_status cow_set_block_mlps(cow_ctx *ctx, const float *mlps, int32_t n_mlps, i
  *       copied back to the host copy before their block is unloaded.
  *       Loads are ordered on the calling stream; the host waits for them
  *       before the call returns (a context serves one stream at a time in
- *       this mode).  The batched form and this mode exclude each other
- *       (COW_ERR_UNSUPPORTED); cow_render_backward_noalloc loads nothing and
- *       rejects unloaded blocks (INVALID_ARG).
+ *       this mode).  The batched form serves its views in runs whose blocks
+ *       fit the budget together (cow_batch_render); cow_render_backward_noalloc
+ *       loads nothing and rejects unloaded blocks (INVALID_ARG).
  *   cow_get_residency : the budget, the bytes and blocks now on the device
  *       and the load / unload counters since the context was created.
  *   cow_block_bytes   : bytes of block's packed grid and planes on the device. */
@@ -280,6 +280,18 @@ cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, con
  * cow_batch_render : outputs as cow_render but device memory only; use_graph
  *                    != 0 replays a CUDA graph captured on the first call (and
  *                    again whenever the arguments or the configuration change).
+ *                    Under a residency budget (cow_set_residency) the views
+ *                    are cut, in the order set, into runs: a view joins the
+ *                    current run while the run's distinct blocks plus its own
+ *                    fit the budget, else it starts the next run.  Each run's
+ *                    blocks are made resident by the cow_render rule (LRU
+ *                    unloading of the others) and the run is one persistent
+ *                    launch; use_graph is then ignored and the host waits
+ *                    for each run's loads.  Pixels equal the all-resident
+ *                    batch's.  A view whose own blocks exceed the budget
+ *                    fails with OOM (runs cut before it may have rendered).
+ *                    cow_plan_view_order gives an order that loads few bytes.
+ * cow_batch_last_groups : launches (runs) of the last cow_batch_render.
  * cow_batch_set_config : tile_cfg 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8
  *                    pixels per CTA; ctas_per_sm resident CTAs per SM (1..32).
  * cow_batch_tune   : times every (tile_cfg, ctas_per_sm in {2,3,4,6,8}) on the
@@ -293,6 +305,7 @@ cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_v
                                const int32_t *ids_offsets, int64_t *out_pixels);
 cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                             float *out_aux, int32_t *out_nsamp, int32_t use_graph, void *stream);
+cow_status cow_batch_last_groups(const cow_batch *b, int32_t *out_groups);
 cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm);
 cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb, int32_t reps,
                           void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms);

@@ -38,7 +38,8 @@ EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "c
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_sparsity_loss", "cow_opacity_loss",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
-           "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune", "cow_last_error",
+           "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
+           "cow_batch_last_groups", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
@@ -111,6 +112,7 @@ def lib():
             "cow_batch_set_views": [P, P, i32, P, P, P],
             "cow_batch_render": [P, P, flt, u32, P, P, P, i32, P],
             "cow_batch_set_config": [P, i32, i32],
+            "cow_batch_last_groups": [P, P],
             "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
         }
         for name, args in sig.items():
@@ -500,6 +502,13 @@ class Batch:
         _check(lib().cow_batch_render(self._b, _ptr(mlp), float(ert_eps), FLAG_MLP_BF16 if mlp_bf16 else 0,
                                       _ptr(out_rgb), _ptr(out_aux), _ptr(out_nsamp), 1 if graph else 0,
                                       _stream_ptr(stream)))
+
+    def last_groups(self) -> int:
+        """Launches of the last render: 1, or the runs of views served one
+        after another under a residency budget."""
+        n = C.c_int32()
+        _check(lib().cow_batch_last_groups(self._b, C.byref(n)))
+        return n.value
 
     def set_config(self, tile_cfg: int, ctas_per_sm: int):
         _check(lib().cow_batch_set_config(self._b, int(tile_cfg), int(ctas_per_sm)))

@@ -1,7 +1,9 @@
 // batch_api.cu -- C ABI of the batched form: many cameras of uneven size and
 // LOD set served by one persistent launch (K8), optionally replayed from a
 // CUDA graph, with the tile shape and the number of resident CTAs picked by
-// an autotuner that times the candidates on the batch itself.
+// an autotuner that times the candidates on the batch itself.  Under a
+// residency budget the views are served in groups whose blocks fit the
+// budget together: one launch per group, its blocks made resident first.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -27,6 +29,8 @@ struct cow_batch {
     int32_t n_items = 0;
     int32_t max_blk = 0;               // longest block list of a view
     bool dirty = true;                 // staging must be rebuilt
+    uint64_t rec_gen = 0;              // the context's record generation the staging holds
+    int32_t last_groups = 0;           // launches of the last render (groups under a budget)
     int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
     int sms = 0;
     // captured graph and the arguments it was captured with
@@ -50,8 +54,9 @@ void batch_destroy(cow_batch *b) {
 }
 
 // Build the pinned staging (header, view records, block records) for the
-// current cameras and tile shape.
-cow_status build_stage(cow_batch *b) {
+// views first .. last-1 of the current cameras and the tile shape.  A view's
+// pixels keep their place in the whole batch's output.
+cow_status build_stage(cow_batch *b, int32_t first, int32_t last) {
     cudaError_t e = cudaEventSynchronize(b->copied);  // the previous copy has read h_stage
     if (e != cudaSuccess) return fail(COW_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
     int tw, th;
@@ -61,10 +66,12 @@ cow_status build_stage(cow_batch *b) {
     cow::BlockRec *br = (cow::BlockRec *)(b->h_stage + b->recs_off);
     int64_t tiles = 0, pix = 0;
     b->max_blk = 0;
-    for (int32_t v = 0; v < nv; v++) {
+    for (int32_t v = 0; v < first; v++) pix += (int64_t)b->cams[(size_t)v].width * b->cams[(size_t)v].height;
+    const int32_t id0 = b->offs[(size_t)first];
+    for (int32_t v = first; v < last; v++) {
         b->max_blk = std::max(b->max_blk, b->offs[(size_t)v + 1] - b->offs[(size_t)v]);
         const cow_camera &cam = b->cams[(size_t)v];
-        cow::ViewRec &r = vr[v];
+        cow::ViewRec &r = vr[v - first];
         std::memset(&r, 0, sizeof(r));
         for (int rr = 0; rr < 3; rr++) {
             for (int k = 0; k < 3; k++) r.Rm[3 * rr + k] = (float)cam.c2w[4 * rr + k];
@@ -75,20 +82,22 @@ cow_status build_stage(cow_batch *b) {
         r.H = cam.height;
         r.tiles_x = (cam.width + tw - 1) / tw;
         r.tile_begin = (int32_t)tiles;
-        r.ids_begin = b->offs[(size_t)v];
+        r.ids_begin = b->offs[(size_t)v] - id0;
         r.ids_count = b->offs[(size_t)v + 1] - b->offs[(size_t)v];
         r.pix_offset = pix;
         tiles += (int64_t)r.tiles_x * ((cam.height + th - 1) / th);
         pix += (int64_t)cam.width * cam.height;
     }
     if (tiles > 0x7fffffff) return fail(COW_ERR_INVALID_ARG, "too many tiles in one batch");
-    for (size_t k = 0; k < b->ids.size(); k++) br[k] = b->ctx->recs[(size_t)b->ids[k]];
+    for (int32_t k = id0; k < b->offs[(size_t)last]; k++) br[k - id0] = b->ctx->recs[(size_t)b->ids[(size_t)k]];
     int32_t *hdr = (int32_t *)b->h_stage;
-    hdr[0] = nv;
+    hdr[0] = last - first;
     hdr[1] = (int32_t)tiles;
     b->n_items = (int32_t)tiles;
-    b->n_pixels = pix;
-    b->dirty = false;
+    b->n_pixels = 0;
+    for (int32_t v = 0; v < nv; v++) b->n_pixels += (int64_t)b->cams[(size_t)v].width * b->cams[(size_t)v].height;
+    b->rec_gen = b->ctx->rec_gen;
+    b->dirty = first != 0 || last != nv;  // a group's staging: the whole batch must be rebuilt later
     return COW_OK;
 }
 
@@ -124,6 +133,67 @@ cudaError_t enqueue(cow_batch *b, const cow::BatchArgs &a, int tile_cfg, int gri
     return e;
 }
 
+// Under a residency budget: cut the views, in the batch's order, into runs
+// whose blocks fit the budget together (a view joins the current run while
+// the run's distinct blocks plus its own still fit), make each run's blocks
+// resident (LRU unloading of the others) and launch the persistent kernel on
+// that run.  Runs are launched eagerly on the caller's stream, never from the
+// graph: each one rewrites the staging and the block records.
+cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *rgb, float *aux,
+                         int32_t *ns, cudaStream_t st) {
+    cow_ctx *c = b->ctx;
+    const int32_t nv = (int32_t)b->cams.size();
+    const int32_t nb = (int32_t)c->blocks.size();
+    std::vector<char> in((size_t)nb, 0);
+    std::vector<int32_t> run_ids;
+    int64_t run_bytes = 0;
+    int32_t first = 0, groups = 0;
+    auto launch = [&](int32_t last) -> cow_status {
+        cow_status rc = make_resident(c, run_ids.data(), (int64_t)run_ids.size(), st);
+        if (rc != COW_OK) return rc;
+        if ((rc = build_stage(b, first, last)) != COW_OK) return rc;
+        const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, rgb, aux, ns);
+        COW_CUDA(enqueue(b, a, b->tile_cfg, std::max(1, b->sms * b->ctas_per_sm), st, true));
+        groups++;
+        return COW_OK;
+    };
+    for (int32_t v = 0; v < nv; v++) {
+        // the view's distinct blocks, and the bytes it adds to the current run
+        std::vector<int32_t> own;
+        int64_t own_bytes = 0, add = 0;
+        for (int32_t k = b->offs[(size_t)v]; k < b->offs[(size_t)v + 1]; k++) {
+            const int32_t id = b->ids[(size_t)k];
+            if (std::find(own.begin(), own.end(), id) != own.end()) continue;
+            own.push_back(id);
+            const int64_t by = block_feature_bytes(c, id);
+            own_bytes += by;
+            if (!in[(size_t)id]) add += by;
+        }
+        if (own_bytes > c->budget)
+            return fail(COW_ERR_OOM, "batch view %d needs %lld bytes, over the residency budget of %lld", v,
+                        (long long)own_bytes, (long long)c->budget);
+        if (v > first && run_bytes + add > c->budget) {
+            cow_status rc = launch(v);
+            if (rc != COW_OK) return rc;
+            for (int32_t id : run_ids) in[(size_t)id] = 0;
+            run_ids.clear();
+            run_bytes = 0;
+            first = v;
+            add = own_bytes;
+        }
+        for (int32_t id : own)
+            if (!in[(size_t)id]) {
+                in[(size_t)id] = 1;
+                run_ids.push_back(id);
+            }
+        run_bytes += add;
+    }
+    cow_status rc = launch(nv);
+    if (rc != COW_OK) return rc;
+    b->last_groups = groups;
+    return COW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -133,8 +203,6 @@ cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, co
     if (!ctx || !out || max_views < 1 || max_ids < 0 || max_views > (1 << 16) || max_ids > (1 << 22))
         return fail(COW_ERR_INVALID_ARG, "cow_batch_create: bad argument");
     *out = nullptr;
-    if (ctx->budget > 0)
-        return fail(COW_ERR_UNSUPPORTED, "the batched form needs every block resident (residency budget is set)");
     DeviceGuard dg(ctx->device);
     cow_batch *b = new cow_batch();
     b->ctx = ctx;
@@ -187,7 +255,7 @@ cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_v
     b->cams.assign(cams, cams + n_views);
     b->ids.assign(ids, ids + n_ids);
     b->offs.assign(ids_offsets, ids_offsets + n_views + 1);
-    cow_status rc = build_stage(b);
+    cow_status rc = build_stage(b, 0, n_views);
     if (rc != COW_OK) return rc;
     if (out_pixels) *out_pixels = b->n_pixels;
     return COW_OK;
@@ -206,10 +274,12 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
         return fail(COW_ERR_INVALID_ARG, "aux / nsamp must be device memory (aux 16-byte aligned)");
     DeviceGuard dg(b->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (b->dirty) {
-        cow_status rc = build_stage(b);
+    if (b->ctx->budget > 0) return render_groups(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
+    if (b->dirty || b->rec_gen != b->ctx->rec_gen) {  // new views, tile shape, or block records
+        cow_status rc = build_stage(b, 0, (int32_t)b->cams.size());
         if (rc != COW_OK) return rc;
     }
+    b->last_groups = 1;
     const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp);
     const int grid = std::max(1, b->sms * b->ctas_per_sm);
     if (!use_graph) {
@@ -241,6 +311,12 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     }
     COW_CUDA(cudaGraphLaunch(b->exec, st));
     COW_CUDA(cudaEventRecord(b->copied, st));
+    return COW_OK;
+}
+
+cow_status cow_batch_last_groups(const cow_batch *b, int32_t *out_groups) {
+    if (!b || !out_groups) return fail(COW_ERR_INVALID_ARG, "cow_batch_last_groups: null argument");
+    *out_groups = b->last_groups;
     return COW_OK;
 }
 

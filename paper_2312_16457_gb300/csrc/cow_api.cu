@@ -439,6 +439,7 @@ void **tensor_slot(BlockHost &b, int t) { return t == 0 ? &b.grid : &b.planes[t 
 // Write the host record of block i and its entry of the device record table.
 cow_status refresh_rec(cow_ctx *c, int32_t i, cudaStream_t st) {
     c->recs[(size_t)i] = make_rec(c, c->blocks[(size_t)i]);
+    c->rec_gen++;
     COW_CUDA(cudaMemcpyAsync(c->d_blocks + i, &c->recs[(size_t)i], sizeof(cow::BlockRec), cudaMemcpyHostToDevice, st));
     COW_CUDA(cudaStreamSynchronize(st));  // the host record is the copy's source
     return COW_OK;
@@ -534,6 +535,16 @@ cow_status ensure_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream
 }
 
 }  // namespace
+
+namespace cowi {
+
+int64_t block_feature_bytes(const cow_ctx *c, int32_t i) { return feature_bytes(c, c->blocks[(size_t)i]); }
+
+cow_status make_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) {
+    return ensure_resident(c, ids, n, st);
+}
+
+}  // namespace cowi
 
 extern "C" {
 
@@ -1081,8 +1092,6 @@ cow_status cow_set_block_unbounded(cow_ctx *ctx, int32_t block, int32_t flags, v
 cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
     g_last_error.clear();
     if (!ctx || budget_bytes < 0) return fail(COW_ERR_INVALID_ARG, "cow_set_residency: null context or budget < 0");
-    if (budget_bytes > 0 && ctx->n_batches > 0)
-        return fail(COW_ERR_UNSUPPORTED, "the batched form needs every block resident: free its batches first");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     COW_CUDA(cudaStreamSynchronize(st));

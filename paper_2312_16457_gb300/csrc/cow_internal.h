@@ -91,6 +91,20 @@ inline double focal_length(int32_t H, double fov_y_deg) {
 
 }  // namespace cowi
 
+struct cow_ctx;
+
+namespace cowi {
+
+// Device bytes of block i's packed features (what the residency budget counts).
+int64_t block_feature_bytes(const cow_ctx *c, int32_t i);
+
+// Make the blocks ids[0 .. n) resident under the context's budget (LRU
+// unloading of the others); a no-op without a budget.  Block records of
+// loaded or unloaded blocks are rewritten (cow_ctx::rec_gen advances).
+cow_status make_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st);
+
+}  // namespace cowi
+
 struct cow_ctx {
     int device = 0;
     int dtype = 0;
@@ -116,4 +130,5 @@ struct cow_ctx {
     int64_t resident_bytes = 0;
     int64_t n_uploads = 0, upload_bytes = 0, n_evictions = 0;
     int32_t n_batches = 0;  // live cow_batch objects on this context
+    uint64_t rec_gen = 0;   // advances whenever a block record is rewritten
 };

@@ -105,19 +105,118 @@ def test_updated_features_survive_unloading():
     assert np.array_equal(ctx.packed(k, 1)[0], ref.packed(k, 1)[0])
 
 
-def test_ray_form_and_batch_exclusion():
+def test_ray_form_under_budget():
     sc, cams, mlp = _scene()
     ctx = cow.Context(sc, "bf16")
     ids = list(range(4))
     o, d = synth.random_rays(4096, 3, sc.box_lo, sc.box_hi, device="cuda")
     want = ctx.render_rays(o, d, ids, mlp)[0]
-    batch = cow.Batch(ctx, 2, 64)
-    with pytest.raises(cow.CowError):
-        ctx.set_residency(1 << 30)  # a live batch needs every block resident
-    batch.close()
     ctx.set_residency(sum(ctx.block_bytes(i) for i in ids))
     got = ctx.render_rays(o, d, ids, mlp)[0]
     ctx.sync_check()
     assert torch.equal(got, want)
-    with pytest.raises(cow.CowError):
-        cow.Batch(ctx, 2, 64)
+
+
+def _runs(bb, ids, budget):
+    """The batch's cut of its views, in order, into runs whose distinct
+    blocks fit the budget together."""
+    runs, run, first = [], set(), 0
+    for v, iv in enumerate(ids):
+        own = set(int(i) for i in iv)
+        add = sum(bb[i] for i in own - run)
+        if v > first and sum(bb[i] for i in run) + add > budget:
+            runs.append(run)
+            run, first = set(), v
+        run |= own
+    runs.append(run)
+    return runs
+
+
+def _lru_uploads(bb, runs, budget, resident=()):
+    """Bytes loaded when each run's blocks are made resident in turn by the
+    context's rule: unload the least recently used blocks the run does not
+    use (ties: lowest index) until the missing ones fit, then load them."""
+    res, last, clock, up = set(resident), {}, 0, 0
+    for run in runs:
+        clock += 1
+        for i in run:
+            last[i] = clock
+        missing = sum(bb[i] for i in run if i not in res)
+        cur = sum(bb[i] for i in res)
+        while cur + missing > budget:
+            victim = min((i for i in res if i not in run), key=lambda i: (last.get(i, 0), i))
+            res.remove(victim)
+            cur -= bb[victim]
+        for i in sorted(run):
+            if i not in res:
+                res.add(i)
+                up += bb[i]
+    return up, res
+
+
+def test_batch_under_budget_equals_all_resident():
+    """The batched form under a residency budget: the views run in groups
+    whose blocks fit together, the pixels equal the all-resident batch's bit
+    for bit, the loads equal a re-statement of the rule, the budget holds,
+    and leaving the budget serves the whole batch in one launch again."""
+    sc, cams, mlp = _scene()
+    ref = cow.Context(sc, "bf16")
+    ctx = cow.Context(sc, "bf16")
+    ids = [ref.select_lod(c, sc.lod_thresh) for c in cams]
+    mlp_d = torch.from_numpy(mlp).cuda()
+    n_ids = sum(len(i) for i in ids)
+
+    def outs(n):
+        return (torch.empty((n, 3), device="cuda"), torch.empty((n, 8), device="cuda"),
+                torch.empty(n, dtype=torch.int32, device="cuda"))
+
+    rb = cow.Batch(ref, len(cams), n_ids)
+    npix = rb.set_views(cams, ids)
+    want = outs(npix)
+    rb.render(mlp_d, *want)
+    ref.sync_check()
+    bb = [ctx.block_bytes(i) for i in range(len(sc.blocks))]
+    need = [sum(bb[i] for i in set(v.tolist())) for v in ids]
+    budget = int(1.25 * max(need))
+    batch = cow.Batch(ctx, len(cams), n_ids)  # created before the budget is set
+    assert batch.set_views(cams, ids) == npix
+    got = outs(npix)
+    batch.render(mlp_d, *got, graph=True)
+    assert batch.last_groups() == 1
+    ctx.set_residency(budget)
+    r0 = ctx.residency()
+    runs = _runs(bb, ids, budget)
+    assert len(runs) > 2
+    for step in range(2):  # the second render starts from what the first left resident
+        for t in got:
+            t.zero_()
+        before = ctx.residency()
+        batch.render(mlp_d, *got, graph=True)
+        ctx.sync_check()
+        assert batch.last_groups() == len(runs)
+        after = ctx.residency()
+        assert after["resident_bytes"] <= budget
+        for g, w in zip(got, want):
+            assert torch.equal(g, w)
+        if step == 0:
+            up, left = _lru_uploads(bb, runs, budget)
+            assert after["upload_bytes"] - r0["upload_bytes"] == up
+            assert after["resident_bytes"] == sum(bb[i] for i in left)
+        assert after["upload_bytes"] > before["upload_bytes"]  # the first run's blocks were unloaded meanwhile
+    # back to all resident: new block records, one launch (graph replay)
+    ctx.set_residency(0)
+    for t in got:
+        t.zero_()
+    batch.render(mlp_d, *got, graph=True)
+    ctx.sync_check()
+    assert batch.last_groups() == 1
+    for g, w in zip(got, want):
+        assert torch.equal(g, w)
+    # a view whose blocks alone exceed the budget
+    ctx.set_residency(max(need) - 1)
+    with pytest.raises(cow.CowError) as e:
+        batch.render(mlp_d, got[0])
+    assert e.value.status == 3  # OOM
+    assert ctx.residency()["resident_bytes"] <= max(need) - 1
+    batch.close()
+    rb.close()
