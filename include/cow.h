@@ -227,9 +227,10 @@ cow_status cow_set_block_mlps(cow_ctx *ctx, const float *mlps, int32_t n_mlps, i
  *       unloads least recently used blocks; 0 loads every block back and
  *       frees the host copies.  Features changed by cow_update_features are
  *       copied back to the host copy before their block is unloaded.
- *       Loads are ordered on the calling stream; the host waits for them
- *       before the call returns (a context serves one stream at a time in
- *       this mode).  The batched form serves its views in runs whose blocks
+ *       Loads and unloads are ordered on the calling stream and the call
+ *       returns without waiting for them (a context serves one stream at a
+ *       time in this mode); the host waits only to copy changed features
+ *       back and to free the allocations made when the blocks were loaded.  The batched form serves its views in runs whose blocks
  *       fit the budget together (cow_batch_render); cow_render_backward_noalloc
  *       loads nothing and rejects unloaded blocks (INVALID_ARG).
  *   cow_get_residency : the budget, the bytes and blocks now on the device
@@ -283,11 +284,14 @@ cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, con
  *                    Under a residency budget (cow_set_residency) the views
  *                    are cut, in the order set, into runs: a view joins the
  *                    current run while the run's distinct blocks plus its own
- *                    fit the budget, else it starts the next run.  Each run's
+ *                    fit the budget, else it starts the next run.  Successive
+ *                    renders walk the views first to last, then last to
+ *                    first, and so on (cow_batch_set_views restarts at first
+ *                    to last), so each render begins with the blocks the
+ *                    previous one left resident.  Each run's
  *                    blocks are made resident by the cow_render rule (LRU
  *                    unloading of the others) and the run is one persistent
- *                    launch; use_graph is then ignored and the host waits
- *                    for each run's loads.  Pixels equal the all-resident
+ *                    launch; use_graph is then ignored.  Pixels equal the all-resident
  *                    batch's.  A view whose own blocks exceed the budget
  *                    fails with OOM (runs cut before it may have rendered).
  *                    cow_plan_view_order gives an order that loads few bytes.

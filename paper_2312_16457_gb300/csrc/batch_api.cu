@@ -31,6 +31,7 @@ struct cow_batch {
     bool dirty = true;                 // staging must be rebuilt
     uint64_t rec_gen = 0;              // the context's record generation the staging holds
     int32_t last_groups = 0;           // launches of the last render (groups under a budget)
+    bool backward = false;             // under a budget: the next render serves the views last to first
     int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
     int sms = 0;
     // captured graph and the arguments it was captured with
@@ -137,27 +138,33 @@ cudaError_t enqueue(cow_batch *b, const cow::BatchArgs &a, int tile_cfg, int gri
 // whose blocks fit the budget together (a view joins the current run while
 // the run's distinct blocks plus its own still fit), make each run's blocks
 // resident (LRU unloading of the others) and launch the persistent kernel on
-// that run.  Runs are launched eagerly on the caller's stream, never from the
-// graph: each one rewrites the staging and the block records.
+// that run.  Successive renders walk the views in alternating directions, so
+// a render starts with the blocks the previous one left resident.  Runs are
+// launched eagerly on the caller's stream, never from the graph: each one
+// rewrites the staging and the block records.
 cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *rgb, float *aux,
                          int32_t *ns, cudaStream_t st) {
     cow_ctx *c = b->ctx;
     const int32_t nv = (int32_t)b->cams.size();
     const int32_t nb = (int32_t)c->blocks.size();
+    const bool back = b->backward;
     std::vector<char> in((size_t)nb, 0);
     std::vector<int32_t> run_ids;
     int64_t run_bytes = 0;
-    int32_t first = 0, groups = 0;
-    auto launch = [&](int32_t last) -> cow_status {
+    int32_t first = 0, groups = 0;  // first: the run's first view in walking order (step index)
+    auto view_at = [&](int32_t k) { return back ? nv - 1 - k : k; };
+    auto launch = [&](int32_t last) -> cow_status {  // steps first .. last-1
         cow_status rc = make_resident(c, run_ids.data(), (int64_t)run_ids.size(), st);
         if (rc != COW_OK) return rc;
-        if ((rc = build_stage(b, first, last)) != COW_OK) return rc;
+        const int32_t lo = back ? nv - last : first, hi = back ? nv - first : last;
+        if ((rc = build_stage(b, lo, hi)) != COW_OK) return rc;
         const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, rgb, aux, ns);
         COW_CUDA(enqueue(b, a, b->tile_cfg, std::max(1, b->sms * b->ctas_per_sm), st, true));
         groups++;
         return COW_OK;
     };
-    for (int32_t v = 0; v < nv; v++) {
+    for (int32_t k = 0; k < nv; k++) {
+        const int32_t v = view_at(k);
         // the view's distinct blocks, and the bytes it adds to the current run
         std::vector<int32_t> own;
         int64_t own_bytes = 0, add = 0;
@@ -172,13 +179,13 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
         if (own_bytes > c->budget)
             return fail(COW_ERR_OOM, "batch view %d needs %lld bytes, over the residency budget of %lld", v,
                         (long long)own_bytes, (long long)c->budget);
-        if (v > first && run_bytes + add > c->budget) {
-            cow_status rc = launch(v);
+        if (k > first && run_bytes + add > c->budget) {
+            cow_status rc = launch(k);
             if (rc != COW_OK) return rc;
             for (int32_t id : run_ids) in[(size_t)id] = 0;
             run_ids.clear();
             run_bytes = 0;
-            first = v;
+            first = k;
             add = own_bytes;
         }
         for (int32_t id : own)
@@ -191,6 +198,7 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
     cow_status rc = launch(nv);
     if (rc != COW_OK) return rc;
     b->last_groups = groups;
+    b->backward = !back;
     return COW_OK;
 }
 
@@ -255,6 +263,7 @@ cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_v
     b->cams.assign(cams, cams + n_views);
     b->ids.assign(ids, ids + n_ids);
     b->offs.assign(ids_offsets, ids_offsets + n_views + 1);
+    b->backward = false;
     cow_status rc = build_stage(b, 0, n_views);
     if (rc != COW_OK) return rc;
     if (out_pixels) *out_pixels = b->n_pixels;

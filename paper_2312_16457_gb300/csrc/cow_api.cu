@@ -77,17 +77,26 @@ void destroy(cow_ctx *c) {
     if (!c) return;
     DeviceGuard g(c->device);
     for (auto &b : c->blocks) {
-        cudaFree(b.grid);
-        for (auto *p : b.planes) cudaFree(p);
+        if (b.async_alloc) {  // pool memory: freed in stream order before the pool goes
+            if (b.grid) cudaFreeAsync(b.grid, nullptr);
+            for (auto *p : b.planes)
+                if (p) cudaFreeAsync(p, nullptr);
+        } else {
+            cudaFree(b.grid);
+            for (auto *p : b.planes) cudaFree(p);
+        }
         cudaFree(b.occ);
         cudaFree(b.occ2);
         cudaFree(b.scale);
         for (auto *h : b.host_feat)
             if (h) cudaFreeHost(h);
     }
-    cudaFree(c->d_blocks);
     cudaFree(c->d_err);
     cudaFree(c->d_mlp);
+    if (c->pool) {
+        cudaDeviceSynchronize();  // frees of pool memory queued in stream order have run
+        cudaMemPoolDestroy(c->pool);
+    }
     c->views.release();
     c->out_rgb.release();
     c->out_aux.release();
@@ -436,12 +445,12 @@ int64_t feature_bytes(const cow_ctx *c, const BlockHost &b) {
 
 void **tensor_slot(BlockHost &b, int t) { return t == 0 ? &b.grid : &b.planes[t - 1]; }
 
-// Write the host record of block i and its entry of the device record table.
-cow_status refresh_rec(cow_ctx *c, int32_t i, cudaStream_t st) {
+// Rewrite the host record of block i.  Kernels receive records by value (in
+// their parameter buffer or a per-call staging copy), so no device table
+// needs the change and the host does not wait for the stream.
+cow_status refresh_rec(cow_ctx *c, int32_t i, cudaStream_t) {
     c->recs[(size_t)i] = make_rec(c, c->blocks[(size_t)i]);
     c->rec_gen++;
-    COW_CUDA(cudaMemcpyAsync(c->d_blocks + i, &c->recs[(size_t)i], sizeof(cow::BlockRec), cudaMemcpyHostToDevice, st));
-    COW_CUDA(cudaStreamSynchronize(st));  // the host record is the copy's source
     return COW_OK;
 }
 
@@ -455,6 +464,10 @@ cow_status evict_block(cow_ctx *c, int32_t i, cudaStream_t st) {
         COW_CUDA(cudaStreamSynchronize(st));
         b.dirty = false;
     }
+    // memory from cudaMallocAsync returns to the pool in stream order, after
+    // the calls already queued that read it; the load-time allocations are
+    // freed once those calls have finished
+    if (!b.async_alloc) COW_CUDA(cudaStreamSynchronize(st));
     for (int t = 0; t < 4; t++) {
         void **slot = tensor_slot(b, t);
         if (b.async_alloc) COW_CUDA(cudaFreeAsync(*slot, st));
@@ -472,7 +485,7 @@ cow_status upload_block(cow_ctx *c, int32_t i, cudaStream_t st) {
     if (b.resident) return COW_OK;
     for (int t = 0; t < 4; t++) {
         void **slot = tensor_slot(b, t);
-        const cudaError_t e = cudaMallocAsync(slot, (size_t)tensor_bytes(c, b, t), st);
+        const cudaError_t e = cudaMallocFromPoolAsync(slot, (size_t)tensor_bytes(c, b, t), c->pool, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             for (int u = 0; u < t; u++) {
@@ -636,10 +649,7 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
     std::vector<cow::BlockRec> &recs = c->recs;
     recs.resize((size_t)n);
     for (int32_t i = 0; i < n; i++) recs[(size_t)i] = make_rec(c, c->blocks[(size_t)i]);
-    e = cudaMalloc((void **)&c->d_blocks, recs.size() * sizeof(cow::BlockRec));
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(c->d_blocks, recs.data(), recs.size() * sizeof(cow::BlockRec), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return cleanup(fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "cow_load_blocks: %s",
                             cudaGetErrorString(e)));
@@ -1098,6 +1108,19 @@ cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
     const int32_t nb = (int32_t)ctx->blocks.size();
     cow_status rc;
     if (budget_bytes > 0) {
+        if (!ctx->pool) {
+            // the context's own stream-ordered pool: memory of unloaded blocks
+            // stays mapped for the next loads instead of going back to the
+            // driver at every synchronisation
+            cudaMemPoolProps props;
+            std::memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = ctx->device;
+            COW_CUDA(cudaMemPoolCreate(&ctx->pool, &props));
+            uint64_t keep = ~(uint64_t)0;
+            COW_CUDA(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        }
         // pinned host copies of every block's packed features, taken once
         for (int32_t i = 0; i < nb; i++) {
             BlockHost &b = ctx->blocks[(size_t)i];
@@ -1143,6 +1166,7 @@ cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
     for (int32_t i = 0; i < nb; i++)
         if ((rc = upload_block(ctx, i, st)) != COW_OK) return rc;
     COW_CUDA(cudaStreamSynchronize(st));
+    COW_CUDA(cudaMemPoolTrimTo(ctx->pool, 0));  // return what unloaded blocks left in the pool
     for (auto &b : ctx->blocks) {
         for (int t = 0; t < 4; t++) {
             if (b.host_feat[t]) cudaFreeHost(b.host_feat[t]);

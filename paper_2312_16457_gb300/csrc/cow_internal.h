@@ -76,7 +76,7 @@ struct BlockHost {
     int32_t unb = 0;           // cow_set_block_unbounded flags
     bool resident = true;
     bool dirty = false;        // device copy newer than host_feat (cow_update_features)
-    bool async_alloc = false;  // device tensors from cudaMallocAsync
+    bool async_alloc = false;  // device tensors from the context's stream-ordered pool
     uint64_t last_use = 0;
     float *scale = nullptr;
     int32_t scale_exp[4][8];
@@ -113,8 +113,7 @@ struct cow_ctx {
     int schedule = COW_SCHED_THREAD_CONST;
     int tile_strip = 0;  // cow_set_tile_order
     std::vector<cowi::BlockHost> blocks;
-    cow::BlockRec *d_blocks = nullptr;
-    std::vector<cow::BlockRec> recs;  // host copy of d_blocks
+    std::vector<cow::BlockRec> recs;  // block records (kernels receive copies by value)
     unsigned *d_err = nullptr;
     float *d_mlp = nullptr;
     cowi::DevBuf views, out_rgb, out_aux, out_nsamp;
@@ -131,4 +130,5 @@ struct cow_ctx {
     int64_t n_uploads = 0, upload_bytes = 0, n_evictions = 0;
     int32_t n_batches = 0;  // live cow_batch objects on this context
     uint64_t rec_gen = 0;   // advances whenever a block record is rewritten
+    cudaMemPool_t pool = nullptr;  // loads under a budget allocate from it (created with the first budget)
 };
