@@ -84,6 +84,7 @@ def lib():
             "orc_block_mlp_nparam": (i32, [i32]),
             "orc_pe": (None, [P, i32, P]),
             "orc_render_view_block_mlp": (None, [P, i32, P, i32, P, P, i32, P, i64, P, P, P]),
+            "orc_render_rays_block_mlp": (None, [P, i32, P, i32, P, P, i64, P, i32, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -330,6 +331,22 @@ def render_view_block_mlp(osc: OracleScene, cam, order: Sequence[int], mlps, n_f
     ns = np.zeros(n, np.int32)
     lib().orc_render_view_block_mlp(osc.ptr(), len(osc), _ptr(ordr), len(ordr), C.byref(oc), _ptr(w), n_freq,
                                     _ptr(pix), 0 if pix is None else len(pix), _ptr(rgb), _ptr(aux), _ptr(ns))
+    return rgb, aux, ns
+
+
+def render_rays_block_mlp(osc: OracleScene, ids: Sequence[int], o, d, mlps, n_freq: int):
+    """Independent rays with per-block MLPs (Eq. 5); each ray sorts ids from
+    its own origin.  mlps: [n_blocks, nparam].  Returns (rgb, aux, nsamp)."""
+    of, df = _np(o).reshape(-1, 3), _np(d).reshape(-1, 3)
+    n = of.shape[0]
+    a = np.ascontiguousarray(ids, np.int32)
+    w = np.ascontiguousarray(_np(mlps, np.float64))
+    assert w.shape == (len(osc), block_mlp_nparam(n_freq)), w.shape
+    rgb = np.zeros((n, 3))
+    aux = np.zeros((n, 8))
+    ns = np.zeros(n, np.int32)
+    lib().orc_render_rays_block_mlp(osc.ptr(), len(osc), _ptr(a), len(a), _ptr(of), _ptr(df), n, _ptr(w), n_freq,
+                                    _ptr(rgb), _ptr(aux), _ptr(ns))
     return rgb, aux, ns
 
 

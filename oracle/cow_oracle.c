@@ -969,6 +969,51 @@ static void mlp_n(const double *w, int32_t n_in, const double *x, double out[MLP
     }
 }
 
+/* One ray with per-block MLPs (Sec. 4.1 Phi^{k,l}; Eq. 11 in-block weights,
+ * Eq. 3 per block, Eq. 5 blend near to far over `order`).  x: scratch of
+ * 7 + pe_dim(L) doubles.  Writes rgb (3), aux (C_d, F blended by Eq. 12 and
+ * the transmittance after the last block) and the occupied-sample count. */
+static void render_one_ray_block_mlp(const orc_block *blocks, const int32_t *order, int32_t n_order,
+                                     const float of[3], const float df[3], const double *mlps, int32_t L,
+                                     double *x, sample_vec *sv, double rgb[3], double aux[8], int32_t *nsamp) {
+    const int32_t n_in = 7 + orc_pe_dim(L), np = orc_block_mlp_nparam(L);
+    const double d[3] = {df[0], df[1], df[2]};
+    double C[3] = {0, 0, 0}, Cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0};
+    double Tb = 1.0; /* prod_{j<k} (1 - alpha^j) */
+    int32_t ns = 0;
+    for (int k = 0; k < n_order; k++) {
+        sv->n = 0;
+        const int64_t nk = block_samples(blocks, order[k], of, df, sv);
+        if (nk == 0) continue;
+        /* Eq. 11: C_d^k, F^k, alpha^k with in-block weights */
+        double ck[3] = {0, 0, 0}, fk[4] = {0, 0, 0, 0}, ak = 0.0, T = 1.0;
+        for (int64_t i = 0; i < nk; i++) {
+            const double w = T * sv->v[i].alpha;
+            for (int c = 0; c < 3; c++) ck[c] += w * sv->v[i].c[c];
+            for (int c = 0; c < 4; c++) fk[c] += w * sv->v[i].s[c];
+            ak += w;
+            T *= 1.0 - sv->v[i].alpha;
+        }
+        /* Eq. 3 with block k's MLP */
+        for (int c = 0; c < 3; c++) x[c] = ck[c];
+        for (int c = 0; c < 4; c++) x[3 + c] = fk[c];
+        orc_pe(d, L, x + 7);
+        double phi[MLP_OUT];
+        mlp_n(mlps + (int64_t)order[k] * np, n_in, x, phi);
+        /* Eq. 5 */
+        for (int c = 0; c < 3; c++) C[c] += Tb * (ck[c] + phi[c]);
+        for (int c = 0; c < 3; c++) Cd[c] += Tb * ck[c];
+        for (int c = 0; c < 4; c++) F[c] += Tb * fk[c];
+        Tb *= 1.0 - ak;
+        ns += (int32_t)nk;
+    }
+    for (int c = 0; c < 3; c++) rgb[c] = C[c];
+    for (int c = 0; c < 3; c++) aux[c] = Cd[c];
+    for (int c = 0; c < 4; c++) aux[3 + c] = F[c];
+    aux[7] = Tb;
+    *nsamp = ns;
+}
+
 /* Render pixels of one view with per-block MLPs.  mlps: nb blocks' weights,
  * block i's at mlps + i * orc_block_mlp_nparam(L).  Outputs: rgb = Eq. 5;
  * aux = the blended C_d, F (Eq. 12) and the transmittance after the last
@@ -979,7 +1024,7 @@ void orc_render_view_block_mlp(const orc_block *blocks, int32_t nb, const int32_
     (void)nb;
     const int64_t W = cam->width;
     const int64_t npx = pix ? n_pix : W * (int64_t)cam->height;
-    const int32_t n_in = 7 + orc_pe_dim(L), np = orc_block_mlp_nparam(L);
+    const int32_t n_in = 7 + orc_pe_dim(L);
 #pragma omp parallel
     {
         sample_vec sv = {0, 0, 0};
@@ -989,43 +1034,13 @@ void orc_render_view_block_mlp(const orc_block *blocks, int32_t nb, const int32_
             const int64_t lin = pix ? pix[r] : r;
             float of[3], df[3];
             orc_pixel_ray(cam, (int32_t)(lin % W), (int32_t)(lin / W), of, df);
-            const double d[3] = {df[0], df[1], df[2]};
-            double C[3] = {0, 0, 0}, Cd[3] = {0, 0, 0}, F[4] = {0, 0, 0, 0};
-            double Tb = 1.0; /* prod_{j<k} (1 - alpha^j) */
-            int32_t ns = 0;
-            for (int k = 0; k < n_order; k++) {
-                sv.n = 0;
-                const int64_t nk = block_samples(blocks, order[k], of, df, &sv);
-                if (nk == 0) continue;
-                /* Eq. 11: C_d^k, F^k, alpha^k with in-block weights */
-                double ck[3] = {0, 0, 0}, fk[4] = {0, 0, 0, 0}, ak = 0.0, T = 1.0;
-                for (int64_t i = 0; i < nk; i++) {
-                    const double w = T * sv.v[i].alpha;
-                    for (int c = 0; c < 3; c++) ck[c] += w * sv.v[i].c[c];
-                    for (int c = 0; c < 4; c++) fk[c] += w * sv.v[i].s[c];
-                    ak += w;
-                    T *= 1.0 - sv.v[i].alpha;
-                }
-                /* Eq. 3 with block k's MLP */
-                for (int c = 0; c < 3; c++) x[c] = ck[c];
-                for (int c = 0; c < 4; c++) x[3 + c] = fk[c];
-                orc_pe(d, L, x + 7);
-                double phi[MLP_OUT];
-                mlp_n(mlps + (int64_t)order[k] * np, n_in, x, phi);
-                /* Eq. 5 */
-                for (int c = 0; c < 3; c++) C[c] += Tb * (ck[c] + phi[c]);
-                for (int c = 0; c < 3; c++) Cd[c] += Tb * ck[c];
-                for (int c = 0; c < 4; c++) F[c] += Tb * fk[c];
-                Tb *= 1.0 - ak;
-                ns += (int32_t)nk;
-            }
+            double rgb[3], aux[8];
+            int32_t ns;
+            render_one_ray_block_mlp(blocks, order, n_order, of, df, mlps, L, x, &sv, rgb, aux, &ns);
             if (out_rgb)
-                for (int c = 0; c < 3; c++) out_rgb[r * 3 + c] = C[c];
-            if (out_aux) {
-                for (int c = 0; c < 3; c++) out_aux[r * 8 + c] = Cd[c];
-                for (int c = 0; c < 4; c++) out_aux[r * 8 + 3 + c] = F[c];
-                out_aux[r * 8 + 7] = Tb;
-            }
+                for (int c = 0; c < 3; c++) out_rgb[r * 3 + c] = rgb[c];
+            if (out_aux)
+                for (int c = 0; c < 8; c++) out_aux[r * 8 + c] = aux[c];
             if (out_nsamp) out_nsamp[r] = ns;
         }
         free(sv.v);
@@ -1093,6 +1108,37 @@ void orc_render_rays(const orc_block *blocks, int32_t nb, const int32_t *ids, in
         }
         free(sv.v);
         free(seg);
+        free(order);
+    }
+}
+
+/* Independent rays with per-block MLPs: each ray sorts the blocks ids from
+ * its own origin (as orc_render_rays) and composites them by Eq. 5 with
+ * block i's MLP at mlps + i * orc_block_mlp_nparam(L). */
+void orc_render_rays_block_mlp(const orc_block *blocks, int32_t nb, const int32_t *ids, int32_t n_ids,
+                               const float *o, const float *d, int64_t n_rays, const double *mlps, int32_t L,
+                               double *out_rgb, double *out_aux, int32_t *out_nsamp) {
+    (void)nb;
+    const int32_t n_in = 7 + orc_pe_dim(L);
+#pragma omp parallel
+    {
+        sample_vec sv = {0, 0, 0};
+        double *x = (double *)malloc((size_t)n_in * sizeof(double));
+        int32_t *order = (int32_t *)malloc((size_t)(n_ids ? n_ids : 1) * sizeof(int32_t));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < n_rays; r++) {
+            sort_ids_for_ray(blocks, ids, n_ids, o + 3 * r, order);
+            double rgb[3], aux[8];
+            int32_t ns;
+            render_one_ray_block_mlp(blocks, order, n_ids, o + 3 * r, d + 3 * r, mlps, L, x, &sv, rgb, aux, &ns);
+            if (out_rgb)
+                for (int c = 0; c < 3; c++) out_rgb[r * 3 + c] = rgb[c];
+            if (out_aux)
+                for (int c = 0; c < 8; c++) out_aux[r * 8 + c] = aux[c];
+            if (out_nsamp) out_nsamp[r] = ns;
+        }
+        free(sv.v);
+        free(x);
         free(order);
     }
 }

@@ -186,3 +186,31 @@ def test_identical_block_mlps_seam_only_where_blocks_meet(orc):
     np.testing.assert_allclose(r_b[one], r_g[one], rtol=0, atol=1e-13)
     seam = np.abs(r_b[many] - r_g[many]).max(axis=1)
     assert seam.max() > 1e-2 and np.median(seam) > 1e-4
+
+
+def test_ray_form_equals_view_form(orc):
+    """Independent rays through the pixel centres of a view, each sorting the
+    blocks from its own origin (the camera centre), composite exactly as the
+    view form does; a ray batch mixing two origins equals its two halves
+    rendered apart."""
+    sc = synth.city_scene(6, 2, 2.0, [(12, 32)])
+    n = len(sc.blocks)
+    L = 2
+    w = synth.block_mlp_weights(8, n, L, spread=0.5)
+    osc = orc.OracleScene(sc)
+    cam = synth.camera((-0.6, -4.0, 3.0), (0.2, 0.3, -0.5), 32, 24, 70.0)
+    order = orc.sort_view(osc, list(range(n)), cam)
+    pix = np.arange(0, 32 * 24, 3)
+    r_v, a_v, n_v = orc.render_view_block_mlp(osc, cam, order, w, L, pixels=pix)
+    o, d = orc.pixel_rays(cam, pix)
+    r_r, a_r, n_r = orc.render_rays_block_mlp(osc, list(range(n)), o, d, w, L)
+    assert np.array_equal(n_r, n_v) and (n_v > 0).mean() > 0.3
+    np.testing.assert_allclose(r_r, r_v, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(a_r, a_v, rtol=0, atol=1e-13)
+    o2, d2 = synth.random_rays(64, 5, sc.box_lo, sc.box_hi)
+    oo = np.concatenate([o, o2.numpy()])
+    dd = np.concatenate([d, d2.numpy()])
+    r_m, _, n_m = orc.render_rays_block_mlp(osc, list(range(n)), oo, dd, w, L)
+    r_2, _, n_2 = orc.render_rays_block_mlp(osc, list(range(n)), o2, d2, w, L)
+    assert np.array_equal(n_m, np.concatenate([n_r, n_2]))
+    np.testing.assert_allclose(r_m, np.concatenate([r_r, r_2]), rtol=0, atol=0)
