@@ -319,6 +319,10 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
  *   o, d        : device float32 n_rays x 3 origins and unit directions.
  *   ids, n_ids  : host array of the blocks to composite (1..64).
  *   other arguments as cow_render; outputs have n_rays rows.
+ *   flags       : as cow_render; with COW_FLAG_BLOCK_MLPS each ray blends
+ *                 its blocks by Eq. 5 with their own MLPs (cow_set_block_mlps)
+ *                 and mlp may be NULL.  The gradient calls take the global
+ *                 form only.
  * n_rays = 0 returns COW_OK at once (the arrays may then be NULL); the same
  * holds for cow_render_rays_block_t, cow_render_backward(_noalloc),
  * cow_opacity_loss and, with n_points = 0, cow_sparsity_loss. */

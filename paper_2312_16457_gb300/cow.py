@@ -262,7 +262,10 @@ class Context:
         self._block_mlp_src = m  # a device source stays alive until the stream has copied it
 
     def render_rays(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], mlp, ert_eps: float = 0.0,
-                    mlp_bf16: bool = False, aux: bool = True, nsamp: bool = False, stream=None):
+                    mlp_bf16: bool = False, aux: bool = True, nsamp: bool = False, stream=None,
+                    block_mlps: bool = False):
+        """Independent rays; block_mlps=True blends each ray's blocks by Eq. 5
+        with the per-block MLPs of set_block_mlps (`mlp` is then unused)."""
         n = o.shape[0]
         o = o.contiguous()
         d = d.contiguous()
@@ -270,10 +273,10 @@ class Context:
         rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
         ax = torch.empty((n, 8), dtype=torch.float32, device=o.device) if aux else None
         ns = torch.empty((n,), dtype=torch.int32, device=o.device) if nsamp else None
-        m = mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp)
+        m = None if mlp is None else (mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp))
+        flags = (FLAG_MLP_BF16 if mlp_bf16 else 0) | (FLAG_BLOCK_MLPS if block_mlps else 0)
         _check(lib().cow_render_rays(self._ctx, _ptr(o), _ptr(d), n, _ptr(a), len(a), _ptr(m), float(ert_eps),
-                                     FLAG_MLP_BF16 if mlp_bf16 else 0, _ptr(rgb), _ptr(ax), _ptr(ns),
-                                     _stream_ptr(stream)))
+                                     flags, _ptr(rgb), _ptr(ax), _ptr(ns), _stream_ptr(stream)))
         return rgb, ax, ns
 
     def render_backward(self, o, d, ids, mlp, aux, dL_drgb, grad_grids, grad_planes, grad_mlp,

@@ -816,11 +816,18 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
                                    float *out_aux, int32_t *out_nsamp, float *out_block_T, void *stream) {
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
-    if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !out_rgb)
+    const bool block_mlp = (flags & COW_FLAG_BLOCK_MLPS) != 0;
+    if (!ctx || !o || !d || n_rays < 0 || !ids || (!mlp && !block_mlp) || !out_rgb)
         return fail(COW_ERR_INVALID_ARG, "cow_render_rays: null argument");
     if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
     if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
-    if (flags & ~COW_FLAG_MLP_BF16) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    if (flags & ~(COW_FLAG_MLP_BF16 | COW_FLAG_BLOCK_MLPS)) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    if (block_mlp && (flags & COW_FLAG_MLP_BF16))
+        return fail(COW_ERR_INVALID_ARG, "COW_FLAG_BLOCK_MLPS runs the MLPs in FP32: drop COW_FLAG_MLP_BF16");
+    if (block_mlp && ctx->n_freq < 0)
+        return fail(COW_ERR_INVALID_ARG, "COW_FLAG_BLOCK_MLPS: no per-block MLPs set (cow_set_block_mlps)");
+    if (block_mlp && out_block_T)
+        return fail(COW_ERR_INVALID_ARG, "in-block transmittances are kept for the global-MLP form only");
     for (int32_t k = 0; k < n_ids; k++)
         if (ids[k] < 0 || ids[k] >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
     if (!is_device_ptr(o) || !is_device_ptr(d)) return fail(COW_ERR_INVALID_ARG, "ray origins and directions must be device memory");
@@ -830,7 +837,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     cow_status rc;
     if ((rc = ensure_resident(ctx, ids, n_ids, st)) != COW_OK) return rc;
     const float *d_mlp = nullptr;
-    if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
+    if (!block_mlp && (rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
     float *rgb, *aux;
     int32_t *ns;
     bool h_rgb, h_aux, h_ns;
@@ -851,6 +858,11 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     a.ray_d = d;
     a.n_rays = n_rays;
     a.out_block_T = out_block_T;
+    if (block_mlp) {
+        a.block_mlp_base = (const float *)ctx->block_mlps.p;
+        a.block_mlp_stride = ctx->block_mlp_nparam;
+        a.n_freq = ctx->n_freq;
+    }
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_march_rays(a, rr, st));

@@ -30,6 +30,8 @@ struct MarchArgs {
     const float *const *block_mlps;  // view mode, per-block MLPs: weights of record k, parallel to recs
     int32_t n_freq;                  // PE frequencies of the per-block MLPs
     float *out_block_T;              // ray mode, may be null: n_rays x n_ray_ids in-block transmittances
+    const float *block_mlp_base;     // ray mode, per-block MLPs: block id's weights at base + id * stride
+    int64_t block_mlp_stride;        // floats (null base: the global MLP)
 };
 
 // marching schedules of the view kernel

@@ -77,20 +77,20 @@ __device__ __forceinline__ int view_of_tile(const MarchArgs &a, int tile) {
 // / Eq. 11), a block with occupied samples adds T C^k with its own MLP, and
 // T carries the product of the blocks' 1 - alpha^k.  Early termination uses
 // the ray's total transmittance: inside block k it stops once
-// T_k < ert_eps / T.
-template <int DT>
-__device__ __forceinline__ void march_blocks_blend(const MarchArgs &a, const ViewRec &v, const BlockRec *recs,
-                                                   const float o[3], const float d[3], const float inv_d[3],
-                                                   float omax, int64_t row) {
+// T_k < ert_eps / T.  rec_at(k) / mlp_at(k): the k-th block's record and
+// MLP weights in near-to-far order.
+template <int DT, class RecAt, class MlpAt>
+__device__ __forceinline__ void blend_blocks(const MarchArgs &a, int n_blk, RecAt rec_at, MlpAt mlp_at,
+                                             const float o[3], const float d[3], const float inv_d[3], float omax,
+                                             int64_t row) {
     float C[3] = {0.f, 0.f, 0.f}, Cd[3] = {0.f, 0.f, 0.f}, F[4] = {0.f, 0.f, 0.f, 0.f}, T = 1.f;
     int nsamp = 0;
-    const int n_blk = v.ids_count;
     for (int k = 0; k < n_blk; k++) {
         RayState sb = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
-        march_block<DT>(recs[k], o, d, inv_d, omax, a.ert_eps > 0.f ? a.ert_eps / T : 0.f, sb, a.err);
+        march_block<DT>(rec_at(k), o, d, inv_d, omax, a.ert_eps > 0.f ? a.ert_eps / T : 0.f, sb, a.err);
         if (sb.nsamp == 0) continue;
         float phi[3];
-        block_mlp(a.block_mlps[v.ids_begin + k], a.n_freq, sb.Cd, sb.F, d, phi);
+        block_mlp(mlp_at(k), a.n_freq, sb.Cd, sb.F, d, phi);
 #pragma unroll
         for (int c = 0; c < 3; c++) {
             C[c] = fmaf(T, sb.Cd[c] + phi[c], C[c]);
@@ -112,6 +112,15 @@ __device__ __forceinline__ void march_blocks_blend(const MarchArgs &a, const Vie
         ap[1] = make_float4(F[1], F[2], F[3], T);
     }
     if (a.out_nsamp) a.out_nsamp[row] = nsamp;
+}
+
+template <int DT>
+__device__ __forceinline__ void march_blocks_blend(const MarchArgs &a, const ViewRec &v, const BlockRec *recs,
+                                                   const float o[3], const float d[3], const float inv_d[3],
+                                                   float omax, int64_t row) {
+    blend_blocks<DT>(
+        a, v.ids_count, [&](int k) -> const BlockRec & { return recs[k]; },
+        [&](int k) { return a.block_mlps[v.ids_begin + k]; }, o, d, inv_d, omax, row);
 }
 
 // One ray per thread of the tile: march the view's near-to-far block list
@@ -357,12 +366,14 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchAr
     write_outputs(a, v.pix_offset + (int64_t)py * v.W + px, s, md, s_mlp);
 }
 
-template <int DT>
+template <int DT, bool kBlockMlp>
 __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(MarchArgs a,
                                                                           const __grid_constant__ RayRecs rr) {
     __shared__ float s_mlp[kMlpParams + 1];
-    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
-    __syncthreads();
+    if (!kBlockMlp) {
+        load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+        __syncthreads();
+    }
     const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (r >= a.n_rays) return;
     float o[3], d[3];
@@ -376,6 +387,13 @@ __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(Ma
     const int n = sort_blocks_for_ray(rr, o, order);
     float inv_d[3], omax;
     ray_setup(d, o, inv_d, omax);
+    if (kBlockMlp) {  // Eq. 5 with block id's own MLP at block_mlp_base + id * block_mlp_stride
+        blend_blocks<DT>(
+            a, n, [&](int k) -> const BlockRec & { return rr.r[order[k]]; },
+            [&](int k) { return a.block_mlp_base + (int64_t)rr.id[order[k]] * a.block_mlp_stride; }, o, d, inv_d,
+            omax, r);
+        return;
+    }
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
     if (a.out_block_T) {
         // also every block's own transmittance, at its position in ids; -1
@@ -444,18 +462,27 @@ cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cu
                      : launch_thread_dt<false>(a, n_tiles, in_params, st, pr);
 }
 
-cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st) {
-    if (a.n_rays <= 0) return cudaSuccess;
+namespace {
+
+template <bool kBlockMlp>
+cudaError_t launch_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st) {
     const int64_t nb = (a.n_rays + kThreads - 1) / kThreads;
     switch (a.dtype) {
-    case kF32: k_march_rays<kF32><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
-    case kF16: k_march_rays<kF16><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
-    case kBF16: k_march_rays<kBF16><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
-    case kFP8: k_march_rays<kFP8><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
-    case kMixed: k_march_rays<kMixed><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kF32: k_march_rays<kF32, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kF16: k_march_rays<kF16, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_march_rays<kBF16, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_march_rays<kFP8, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_march_rays<kMixed, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st) {
+    if (a.n_rays <= 0) return cudaSuccess;
+    return a.block_mlp_base ? launch_rays<true>(a, rr, st) : launch_rays<false>(a, rr, st);
 }
 
 int march_tile_w() { return kTileW; }

@@ -150,3 +150,46 @@ def test_identical_block_mlps_seam_only_where_blocks_meet():
     assert one.mean() > 0.15 and many.mean() > 0.05
     assert np.abs(r_b[one] - r_g[one]).max() <= 1e-5
     assert np.abs(r_b[many] - r_g[many]).max() > 1e-2
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+def test_ray_form_matches_oracle(storage):
+    """Independent rays with per-block MLPs (Eq. 5, each ray sorting the
+    blocks from its own origin) against the oracle on the same values."""
+    sc = synth.city_scene(6, 2, 2.0, [(24, 64)])
+    n = len(sc.blocks)
+    L = 4
+    w = synth.block_mlp_weights(12, n, L, spread=0.3)
+    ctx = cow.Context(sc, storage)
+    ctx.set_block_mlps(w, L)
+    o, d = synth.random_rays(4096, 9, sc.box_lo, sc.box_hi, device="cuda")
+    ids = list(range(n))
+    rgb, aux, ns = ctx.render_rays(o, d, ids, None, nsamp=True, block_mlps=True)
+    rgb_e = ctx.render_rays(o, d, ids, None, ert_eps=1e-5, block_mlps=True)[0]
+    ctx.sync_check()
+    osc = oracle.OracleScene(sc, values="master" if storage == "fp32" else storage)
+    r_o, a_o, n_o = oracle.render_rays_block_mlp(osc, ids, o.cpu(), d.cpu(), w, L)
+    assert np.array_equal(ns.cpu().numpy(), n_o)
+    assert (n_o > 0).mean() > 0.5
+    assert np.abs(rgb.cpu().numpy() - r_o).max() <= TOL
+    assert np.abs(aux.cpu().numpy() - a_o).max() <= TOL
+    assert np.abs(rgb_e.cpu().numpy() - r_o).max() <= TOL
+    # the global form on the same rays differs (the blocks' MLPs are not the global one)
+    g = ctx.render_rays(o, d, ids, torch.from_numpy(synth.mlp_weights(1)).cuda())[0]
+    assert float((g - rgb).abs().max()) > 1e-2
+
+
+def test_ray_form_argument_errors():
+    sc = synth.city_scene(6, 2, 2.0, [(12, 32)])
+    ctx = cow.Context(sc, "fp32")
+    o, d = synth.random_rays(64, 9, sc.box_lo, sc.box_hi, device="cuda")
+    with pytest.raises(cow.CowError):  # no per-block MLPs set
+        ctx.render_rays(o, d, [0, 1], None, block_mlps=True)
+    ctx.set_block_mlps(synth.block_mlp_weights(1, len(sc.blocks), 0), 0)
+    with pytest.raises(cow.CowError):  # the per-block MLPs run in FP32
+        ctx.render_rays(o, d, [0, 1], None, block_mlps=True, mlp_bf16=True)
+    with pytest.raises(cow.CowError):  # the global form needs its MLP
+        ctx.render_rays(o, d, [0, 1], None)
+    rgb = ctx.render_rays(o, d, [0, 1], None, block_mlps=True)[0]
+    ctx.sync_check()
+    assert torch.isfinite(rgb).all()
