@@ -85,6 +85,7 @@ def lib():
             "orc_pe": (None, [P, i32, P]),
             "orc_render_view_block_mlp": (None, [P, i32, P, i32, P, P, i32, P, i64, P, P, P]),
             "orc_render_rays_block_mlp": (None, [P, i32, P, i32, P, P, i64, P, i32, P, P, P]),
+            "orc_render_rays_block_mlp_grad": (None, [P, i32, P, i32, P, P, i64, P, i32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -348,6 +349,25 @@ def render_rays_block_mlp(osc: OracleScene, ids: Sequence[int], o, d, mlps, n_fr
     lib().orc_render_rays_block_mlp(osc.ptr(), len(osc), _ptr(a), len(a), _ptr(of), _ptr(df), n, _ptr(w), n_freq,
                                     _ptr(rgb), _ptr(aux), _ptr(ns))
     return rgb, aux, ns
+
+
+def render_rays_block_mlp_grad(osc: OracleScene, ids: Sequence[int], o, d, mlps, n_freq: int, dL_drgb):
+    """Analytic FP64 gradient of sum(dL_drgb * rgb) of render_rays_block_mlp
+    w.r.t. every grid, plane and per-block MLP parameter; returns (grids,
+    planes, mlps) as float64 arrays shaped like the parameters."""
+    of, df = _np(o).reshape(-1, 3), _np(d).reshape(-1, 3)
+    n = of.shape[0]
+    a = np.ascontiguousarray(ids, np.int32)
+    w = np.ascontiguousarray(_np(mlps, np.float64))
+    assert w.shape == (len(osc), block_mlp_nparam(n_freq)), w.shape
+    g = np.ascontiguousarray(_np(dL_drgb, np.float64).reshape(n, 3))
+    gg, gp, gptr, pptr = _grad_arrays(osc)
+    gm = np.zeros(w.shape, np.float64)
+    lib().orc_render_rays_block_mlp_grad(osc.ptr(), len(osc), _ptr(a), len(a), _ptr(of), _ptr(df), n, _ptr(w),
+                                         n_freq, _ptr(g), C.cast(gptr, C.c_void_p), C.cast(pptr, C.c_void_p),
+                                         _ptr(gm))
+    planes = [gp[3 * i:3 * i + 3] for i in range(len(gg))]
+    return gg, planes, gm
 
 
 def render_rays(osc: OracleScene, ids: Sequence[int], o, d, mlp=None, mode: int = MODE_BLOCKWISE):

@@ -1322,6 +1322,190 @@ void orc_render_rays_grad(const orc_block *blocks, int32_t nb, const int32_t *id
 }
 
 /* ------------------------------------------------------------------------- */
+/* Gradient of the per-block form (Eq. 5 with Eq. 3 per block) for rays:
+ * C = sum_k B_k (C^k + Phi^k(C^k, F^k, PE(d))), B_{k+1} = B_k (1 - alpha^k),
+ * over the blocks with occupied samples.  Reverse mode: with u = B_k dL/dC,
+ * block k's MLP receives u (its weights' gradient, and dL/dC^k = u + J_C^T u,
+ * dL/dF^k = J_F^T u); dL/dB_k = dL/dC . (C^k + Phi^k) + dL/dB_{k+1} (1 -
+ * alpha^k) and dL/dalpha^k = -dL/dB_{k+1} B_k; inside the block the Eq. 11
+ * backward of the global form.  grad_mlps: nb x orc_block_mlp_nparam(L)
+ * doubles, accumulated (+=) like the feature gradients. */
+
+/* Phi of an n_in-input MLP and its reverse mode for the upstream u (3):
+ * adds u's gradient of every weight to gw and writes dPhi/dx^T u to gx. */
+static void mlp_n_backward(const double *w, int32_t n_in, const double *x, const double u[MLP_OUT],
+                           double phi[MLP_OUT], double *gx, double *gw) {
+    const double *W1 = w, *b1 = W1 + n_in * MLP_HID, *W2 = b1 + MLP_HID, *b2 = W2 + MLP_HID * MLP_HID;
+    const double *W3 = b2 + MLP_HID;
+    const double *b3 = W3 + MLP_HID * MLP_OUT;
+    double *gW1 = gw, *gb1 = gW1 + n_in * MLP_HID, *gW2 = gb1 + MLP_HID, *gb2 = gW2 + MLP_HID * MLP_HID;
+    double *gW3 = gb2 + MLP_HID, *gb3 = gW3 + MLP_HID * MLP_OUT;
+    double z1[MLP_HID], h1[MLP_HID], z2[MLP_HID], h2[MLP_HID];
+    for (int j = 0; j < MLP_HID; j++) {
+        double a = b1[j];
+        for (int i = 0; i < n_in; i++) a += x[i] * W1[i * MLP_HID + j];
+        z1[j] = a;
+        h1[j] = a > 0.0 ? a : 0.0;
+    }
+    for (int j = 0; j < MLP_HID; j++) {
+        double a = b2[j];
+        for (int i = 0; i < MLP_HID; i++) a += h1[i] * W2[i * MLP_HID + j];
+        z2[j] = a;
+        h2[j] = a > 0.0 ? a : 0.0;
+    }
+    double dz3[MLP_OUT], dh2[MLP_HID], dz2[MLP_HID], dh1[MLP_HID], dz1[MLP_HID];
+    for (int j = 0; j < MLP_OUT; j++) {
+        double a = b3[j];
+        for (int i = 0; i < MLP_HID; i++) a += h2[i] * W3[i * MLP_OUT + j];
+        phi[j] = sigmoid(a);
+        dz3[j] = u[j] * phi[j] * (1.0 - phi[j]);
+        gb3[j] += dz3[j];
+    }
+    for (int i = 0; i < MLP_HID; i++) {
+        dh2[i] = 0.0;
+        for (int j = 0; j < MLP_OUT; j++) {
+            gW3[i * MLP_OUT + j] += h2[i] * dz3[j];
+            dh2[i] += W3[i * MLP_OUT + j] * dz3[j];
+        }
+    }
+    for (int j = 0; j < MLP_HID; j++) {
+        dz2[j] = z2[j] > 0.0 ? dh2[j] : 0.0;
+        gb2[j] += dz2[j];
+    }
+    for (int i = 0; i < MLP_HID; i++) {
+        dh1[i] = 0.0;
+        for (int j = 0; j < MLP_HID; j++) {
+            gW2[i * MLP_HID + j] += h1[i] * dz2[j];
+            dh1[i] += W2[i * MLP_HID + j] * dz2[j];
+        }
+    }
+    for (int j = 0; j < MLP_HID; j++) {
+        dz1[j] = z1[j] > 0.0 ? dh1[j] : 0.0;
+        gb1[j] += dz1[j];
+    }
+    for (int i = 0; i < n_in; i++) {
+        double dx = 0.0;
+        for (int j = 0; j < MLP_HID; j++) {
+            gW1[i * MLP_HID + j] += x[i] * dz1[j];
+            dx += W1[i * MLP_HID + j] * dz1[j];
+        }
+        gx[i] = dx;
+    }
+}
+
+/* Scatter one sample's feature gradient gf (8 channels) through its taps. */
+static void scatter_feature_grad(const sample *s, const double gf[NCH], double *const *grad_grid,
+                                 double *const *grad_planes) {
+    const int32_t bi = s->block;
+    for (int q = 0; q < 8; q++)
+        for (int c = 0; c < NCH; c++) atomic_add(&grad_grid[bi][s->tp.gidx[q] + c], s->tp.gw[q] * gf[c]);
+    for (int pl = 0; pl < 3; pl++)
+        for (int q = 0; q < 4; q++)
+            for (int c = 0; c < NCH; c++)
+                atomic_add(&grad_planes[3 * bi + pl][s->tp.pidx[pl][q] + c], s->tp.pw[pl][q] * gf[c]);
+}
+
+void orc_render_rays_block_mlp_grad(const orc_block *blocks, int32_t nb, const int32_t *ids, int32_t n_ids,
+                                    const float *o, const float *d, int64_t n_rays, const double *mlps, int32_t L,
+                                    const double *dL_drgb, double *const *grad_grid, double *const *grad_planes,
+                                    double *grad_mlps) {
+    const int32_t n_in = 7 + orc_pe_dim(L), np = orc_block_mlp_nparam(L);
+#pragma omp parallel
+    {
+        sample_vec sv = {0, 0, 0};
+        int32_t *order = (int32_t *)malloc((size_t)(n_ids ? n_ids : 1) * sizeof(int32_t));
+        int64_t *seg = (int64_t *)malloc((size_t)(n_ids + 1) * sizeof(int64_t));
+        double *Ck = (double *)malloc((size_t)(n_ids ? n_ids : 1) * 8 * sizeof(double));
+        double *Bk = (double *)malloc((size_t)(n_ids + 1) * sizeof(double));
+        double *x = (double *)malloc((size_t)n_in * sizeof(double));
+        double *gx = (double *)malloc((size_t)n_in * sizeof(double));
+        double *gw = (double *)calloc((size_t)nb * (size_t)np, sizeof(double)); /* this thread's MLP gradients */
+        double *Tin = NULL; /* in-block transmittance before each sample */
+        int64_t tcap = 0;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t r = 0; r < n_rays; r++) {
+            const float *of = o + 3 * r, *df = d + 3 * r;
+            const double dd[3] = {df[0], df[1], df[2]};
+            sort_ids_for_ray(blocks, ids, n_ids, of, order);
+            sv.n = 0;
+            seg[0] = 0;
+            for (int k = 0; k < n_ids; k++) {
+                block_samples(blocks, order[k], of, df, &sv);
+                seg[k + 1] = sv.n;
+            }
+            if (sv.n > tcap) {
+                tcap = sv.n;
+                Tin = (double *)realloc(Tin, (size_t)tcap * sizeof(double));
+            }
+            /* forward: Eq. 11 per block; B_k over the blocks with samples */
+            Bk[0] = 1.0;
+            for (int k = 0; k < n_ids; k++) {
+                double *ck = Ck + 8 * k; /* C^k (3), F^k (4), alpha^k */
+                for (int c = 0; c < 8; c++) ck[c] = 0.0;
+                double T = 1.0;
+                for (int64_t i = seg[k]; i < seg[k + 1]; i++) {
+                    Tin[i] = T;
+                    const double w = T * sv.v[i].alpha;
+                    for (int c = 0; c < 3; c++) ck[c] += w * sv.v[i].c[c];
+                    for (int c = 0; c < 4; c++) ck[3 + c] += w * sv.v[i].s[c];
+                    ck[7] += w;
+                    T *= 1.0 - sv.v[i].alpha;
+                }
+                Bk[k + 1] = Bk[k] * (1.0 - ck[7]);
+            }
+            /* reverse over the blocks */
+            const double *g = dL_drgb + 3 * r;
+            double gBnext = 0.0;
+            for (int k = n_ids - 1; k >= 0; k--) {
+                const int64_t n = seg[k + 1] - seg[k];
+                if (n == 0) continue; /* a block without occupied samples takes no part */
+                const double *ck = Ck + 8 * k;
+                for (int c = 0; c < 7; c++) x[c] = ck[c];
+                orc_pe(dd, L, x + 7);
+                const double u[MLP_OUT] = {Bk[k] * g[0], Bk[k] * g[1], Bk[k] * g[2]};
+                double phi[MLP_OUT];
+                mlp_n_backward(mlps + (int64_t)order[k] * np, n_in, x, u, phi, gx, gw + (int64_t)order[k] * np);
+                const double gA = -gBnext * Bk[k];
+                double gB = gBnext * (1.0 - ck[7]);
+                for (int c = 0; c < 3; c++) gB += g[c] * (ck[c] + phi[c]);
+                gBnext = gB;
+                double gCk[3], gFk[4];
+                for (int c = 0; c < 3; c++) gCk[c] = u[c] + gx[c];
+                for (int c = 0; c < 4; c++) gFk[c] = gx[3 + c];
+                /* Eq. 11 backward, as in the global form */
+                double U = 0.0;
+                for (int64_t i = n - 1; i >= 0; i--) {
+                    const sample *s = &sv.v[seg[k] + i];
+                    const double T = Tin[seg[k] + i];
+                    const double w = T * s->alpha;
+                    double gw_i = gA;
+                    for (int c = 0; c < 3; c++) gw_i += gCk[c] * s->c[c];
+                    for (int c = 0; c < 4; c++) gw_i += gFk[c] * s->s[c];
+                    const double galpha = T * (gw_i - U);
+                    U = gw_i * s->alpha + (1.0 - s->alpha) * U;
+                    double gf[NCH];
+                    gf[0] = galpha * s->sigma * s->delta * (1.0 - s->alpha);
+                    for (int c = 0; c < 3; c++) gf[1 + c] = w * gCk[c] * s->c[c] * (1.0 - s->c[c]);
+                    for (int c = 0; c < 4; c++) gf[4 + c] = w * gFk[c] * s->s[c] * (1.0 - s->s[c]);
+                    scatter_feature_grad(s, gf, grad_grid, grad_planes);
+                }
+            }
+        }
+        for (int64_t i = 0; i < (int64_t)nb * np; i++)
+            if (gw[i] != 0.0) atomic_add(&grad_mlps[i], gw[i]);
+        free(sv.v);
+        free(order);
+        free(seg);
+        free(Ck);
+        free(Bk);
+        free(x);
+        free(gx);
+        free(gw);
+        free(Tin);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Training-stage regularisers of Sec. 4.3 on the baked representation, with
  * their gradients (accumulated into the same arrays as above).
  *

@@ -214,3 +214,66 @@ def test_ray_form_equals_view_form(orc):
     r_2, _, n_2 = orc.render_rays_block_mlp(osc, list(range(n)), o2, d2, w, L)
     assert np.array_equal(n_m, np.concatenate([n_r, n_2]))
     np.testing.assert_allclose(r_m, np.concatenate([r_r, r_2]), rtol=0, atol=0)
+
+
+def test_ray_form_gradient_matches_finite_differences(orc):
+    """The analytic FP64 adjoint of the per-block form (features and every
+    block's MLP) against central differences of the FP64 render."""
+    sc = synth.city_scene(17, 2, 2.0, [(6, 8)])
+    n = len(sc.blocks)
+    L = 2
+    osc = orc.OracleScene(sc, values="f64")
+    ids = list(range(n))
+    o, d = synth.random_rays(48, 3, sc.box_lo, sc.box_hi)
+    w = synth.block_mlp_weights(9, n, L, spread=0.3).astype(np.float64)
+    g = np.random.default_rng(4).normal(size=(48, 3))
+
+    def loss():
+        rgb, _, _ = orc.render_rays_block_mlp(osc, ids, o, d, w, L)
+        return float((rgb * g).sum())
+
+    gg, gp, gm = orc.render_rays_block_mlp_grad(osc, ids, o, d, w, L, g)
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    pools = [(osc.grids[b], gg[b]) for b in range(n)]
+    pools += [(osc.planes[b][p], gp[b][p]) for b in range(n) for p in range(3)]
+    pools += [(w[b], gm[b]) for b in range(n)]
+    cands = []
+    for arr, gr in pools:
+        nz = np.flatnonzero(np.abs(gr.reshape(-1)) > 1e-4)
+        for j in rng.choice(nz, size=min(6, len(nz)), replace=False):
+            cands.append((arr.reshape(-1), gr.reshape(-1), int(j)))
+    checked = 0
+    for arr, gr, j in cands:
+        x0 = arr[j]
+        arr[j] = x0 + h
+        lp = loss()
+        arr[j] = x0 - h
+        lm = loss()
+        arr[j] = x0
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gr[j]) <= 1e-4 * max(abs(fd), 1e-3), (fd, gr[j])
+        checked += 1
+    assert checked >= 80
+    # every block's MLP receives a gradient (each block has samples on some ray)
+    assert all(np.abs(gm[b]).max() > 0 for b in range(n))
+
+
+def test_ray_form_gradient_reduces_to_global_form(orc):
+    """One block with the global MLP (L = 0): the per-block form's gradient
+    equals the global form's on rays that have occupied samples."""
+    sc = synth.single_block_scene(1, 10, 16)
+    osc = orc.OracleScene(sc)
+    mlp = synth.mlp_weights(101).astype(np.float64)
+    o, d = synth.random_rays(64, 7, sc.box_lo, sc.box_hi)
+    _, _, ns = orc.render_rays(osc, [0], o, d, mlp)
+    hit = ns > 0
+    assert hit.mean() > 0.5
+    o, d = o[hit], d[hit]
+    g = np.random.default_rng(2).normal(size=(len(o), 3))
+    gg, gp, gm = orc.render_rays_grad(osc, [0], o, d, mlp, g)
+    bg, bp, bm = orc.render_rays_block_mlp_grad(osc, [0], o, d, mlp[None, :], 0, g)
+    np.testing.assert_allclose(bg[0], gg[0], rtol=0, atol=1e-12)
+    for k in range(3):
+        np.testing.assert_allclose(bp[0][k], gp[0][k], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(bm[0], gm, rtol=0, atol=1e-12)
