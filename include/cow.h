@@ -384,6 +384,29 @@ cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, const float
                                        const float *aux, const float *dL_drgb, float *const *grad_grid,
                                        float *const *grad_planes, float *grad_mlp, void *stream);
 
+/* Gradients of the ray-batch render with per-block MLPs (cow_render_rays
+ * with COW_FLAG_BLOCK_MLPS, no early termination): the adjoint of Eq. 5 with
+ * Eq. 3 per block (Sec. 4.1 Phi^{k,l}) and Eq. 11 inside each block, with
+ * respect to every grid and plane feature and every parameter of the MLPs
+ * of the blocks in ids, given dL/dC per ray.  Each ray is marched twice
+ * (once for every block's C^k, F^k and transmittance, once to scatter);
+ * between the two, one thread per (ray, block) back-propagates that block's
+ * MLP.  Occupancy is held fixed.
+ *   o, d, ids, n_ids : as the forward call (device o, d);
+ *   dL_drgb          : device float32 n_rays x 3;
+ *   grad_grid, grad_planes : as cow_render_backward (accumulated);
+ *   grad_block_mlps  : device float32 n_blocks x block_mlp_nparam(n_freq)
+ *                      (the layout cow_set_block_mlps takes), accumulated;
+ *                      rows of blocks not in ids are not touched.
+ * Scratch: 64 bytes per (ray, block of ids) of device memory, kept by the
+ * context.  Floating-point sums over rays are in no fixed order.
+ * Errors: INVALID_ARG (no per-block MLPs set, bad ids, host or misaligned
+ * arrays), OOM, CUDA; resident blocks as cow_render. */
+cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                          const int32_t *ids, int32_t n_ids, const float *dL_drgb,
+                                          float *const *grad_grid, float *const *grad_planes, float *grad_block_mlps,
+                                          void *stream);
+
 /* Re-pack block `block`'s features from new FP32 masters (same layouts as
  * cow_block_desc; host or device, 16-byte aligned) into the context's
  * storage format; occupancy and z_top stay as loaded (the differentiation

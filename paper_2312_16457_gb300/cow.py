@@ -37,6 +37,7 @@ EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "c
            "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_sparsity_loss", "cow_opacity_loss",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
+           "cow_render_backward_block_mlps",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
            "cow_batch_last_groups", "cow_last_error",
@@ -104,6 +105,7 @@ def lib():
             "cow_gather_peak": [i32, i64, i32, P, P],
             "cow_render_backward": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
             "cow_render_backward_noalloc": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
+            "cow_render_backward_block_mlps": [P, P, P, i64, P, i32, P, P, P, P, P],
             "cow_update_features": [P, i32, P, P, P, P, P],
             "cow_adam_step": [P, P, P, P, i64, flt, flt, flt, flt, i32, P],
             "cow_mse_grad": [P, P, i64, P, P, P],
@@ -296,6 +298,17 @@ class Context:
         fn = lib().cow_render_backward_noalloc if noalloc else lib().cow_render_backward
         _check(fn(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a), len(a), _ptr(mlp),
                   float(ert_eps), _ptr(aux), _ptr(dL_drgb.contiguous()), gg, gp, _ptr(grad_mlp), _stream_ptr(stream)))
+
+    def render_backward_block_mlps(self, o, d, ids, dL_drgb, grad_grids, grad_planes, grad_block_mlps,
+                                   stream=None):
+        """Accumulate dL/d(features, per-block MLPs) of a ray batch rendered
+        with block_mlps=True (no early termination) into FP32 device tensors;
+        grad_block_mlps: [n_blocks, block_mlp_nparam(n_freq)]."""
+        a = np.ascontiguousarray(ids, np.int32)
+        gg, gp = self._grad_tables((grad_grids, grad_planes))
+        _check(lib().cow_render_backward_block_mlps(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0],
+                                                    _ptr(a), len(a), _ptr(dL_drgb.contiguous()), gg, gp,
+                                                    _ptr(grad_block_mlps), _stream_ptr(stream)))
 
     def _grad_tables(self, grads):
         if grads is None:

@@ -464,6 +464,241 @@ __global__ void k_mse_grad(const float *__restrict__ rgb, const float *__restric
     }
 }
 
+// ---------------------------------------------------------------------------
+// Per-block MLP form (Eq. 5 with Eq. 3 per block):
+//   C = sum_k B_k X_k,  X_k = C^k + Phi^k(C^k, F^k, PE(d)),  B_{k+1} = B_k (1 - alpha^k)
+// over the blocks with occupied samples.  Three passes, ray by ray:
+//   P1  march every block once: C^k, F^k and B_k to scratch S;
+//   P2  per (ray, block): Phi^k backward with u = B_k dL/dC gives
+//       dL/dC^k = u + J_C^T u, dL/dF^k = J_F^T u and dL/dC . X_k (scratch G),
+//       and adds u's weight gradient to block k's MLP gradient;
+//   P3  march every block again and scatter the feature gradients: with
+//       Q_k = sum_{j>k} B_j dL/dC . X_j (the later blocks' dependence on
+//       1 - alpha^k), the Eq. 11 backward of the global form gives
+//         dL/df0 = sigma delta (T_i e_i (gC.c_i + gF.s_i) - (gC.S_C + gF.S_F) - Q_k)
+//       with in-block T_i and the block's own totals and upstreams.
+// No early termination (the ray form's training calls use none).
+
+// The per-block MLP input i: C^k (3), F^k (4), d (3), then sin / cos(2^l d).
+__device__ __forceinline__ float bm_input(int i, const float ck[7], const float d[3]) {
+    if (i < 7) return ck[i];
+    if (i < 10) return d[i - 7];
+    const int j = i - 10, l = j / 6, q = j % 6;
+    const float v = ldexpf(d[q % 3], l);
+    return q < 3 ? sinf(v) : cosf(v);
+}
+
+// P1
+template <int DT>
+__global__ void __launch_bounds__(kBwdThreads) k_bm_pass1(BmBwdArgs a, const __grid_constant__ RayRecs rr) {
+    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (r >= a.n_rays) return;
+    float o[3], d[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o[c] = __ldg(a.ray_o + 3 * r + c);
+        d[c] = __ldg(a.ray_d + 3 * r + c);
+    }
+    int order[kMaxRayIds];
+    const int n = sort_blocks_for_ray(rr, o, order);
+    float inv_d[3], omax;
+    ray_setup(d, o, inv_d, omax);
+    float B = 1.f;
+    for (int k = 0; k < n; k++) {
+        RayState sb = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+        march_block<DT>(rr.r[order[k]], o, d, inv_d, omax, 0.f, sb, a.err);
+        float4 *e = reinterpret_cast<float4 *>(a.S + 8 * (r * a.n_ids + order[k]));
+        if (sb.nsamp == 0) {
+            e[1] = make_float4(0.f, 0.f, 0.f, -1.f);
+            continue;
+        }
+        e[0] = make_float4(sb.Cd[0], sb.Cd[1], sb.Cd[2], sb.F[0]);
+        e[1] = make_float4(sb.F[1], sb.F[2], sb.F[3], B);
+        B *= sb.T;
+    }
+}
+
+// P2: one thread per (ray, block) pair
+__global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __grid_constant__ RayRecs rr) {
+    const int64_t t = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (t >= a.n_rays * a.n_ids) return;
+    const int64_t r = t / a.n_ids;
+    const int k = (int)(t % a.n_ids);
+    const float4 *e = reinterpret_cast<const float4 *>(a.S + 8 * t);
+    const float4 e0 = e[0], e1 = e[1];
+    float4 *go = reinterpret_cast<float4 *>(a.G + 8 * t);
+    if (e1.w < 0.f) {
+        go[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        go[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const float ck[7] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z};
+    const float B = e1.w;
+    float d[3], g[3], u[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        d[c] = __ldg(a.ray_d + 3 * r + c);
+        g[c] = __ldg(a.dL_drgb + 3 * r + c);
+        u[c] = B * g[c];
+    }
+    const int id = rr.id[k];
+    const int n_in = 10 + 6 * a.n_freq;
+    const float *W1 = a.mlps + (int64_t)id * a.mlp_stride;
+    const float *b1 = W1 + n_in * 16, *W2 = b1 + 16, *b2 = W2 + 256, *W3 = b2 + 16, *b3 = W3 + 48;
+    float *gW1 = a.grad_mlps + (int64_t)id * a.grad_stride;
+    float *gb1 = gW1 + n_in * 16, *gW2 = gb1 + 16, *gb2 = gW2 + 256, *gW3 = gb2 + 16, *gb3 = gW3 + 48;
+    float h1[16], h2[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) h1[j] = __ldg(b1 + j);
+    for (int i = 0; i < n_in; i++) {
+        const float xi = bm_input(i, ck, d);
+#pragma unroll
+        for (int j = 0; j < 16; j++) h1[j] = fmaf(xi, __ldg(W1 + i * 16 + j), h1[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) h1[j] = fmaxf(h1[j], 0.f);  // h1 > 0 iff z1 > 0
+#pragma unroll
+    for (int j = 0; j < 16; j++) {
+        float z = __ldg(b2 + j);
+#pragma unroll
+        for (int i = 0; i < 16; i++) z = fmaf(h1[i], __ldg(W2 + i * 16 + j), z);
+        h2[j] = fmaxf(z, 0.f);
+    }
+    float phi[3], dz3[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        float z = __ldg(b3 + j);
+#pragma unroll
+        for (int i = 0; i < 16; i++) z = fmaf(h2[i], __ldg(W3 + i * 3 + j), z);
+        phi[j] = 1.f / (1.f + expf(-z));
+        dz3[j] = u[j] * phi[j] * (1.f - phi[j]);
+        red_add1(gb3 + j, dz3[j]);
+    }
+    float dz2[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            s = fmaf(__ldg(W3 + i * 3 + j), dz3[j], s);
+            red_add1(gW3 + i * 3 + j, h2[i] * dz3[j]);
+        }
+        dz2[i] = h2[i] > 0.f ? s : 0.f;
+    }
+    float dz1[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) red_add1(gb2 + j, dz2[j]);
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            s = fmaf(__ldg(W2 + i * 16 + j), dz2[j], s);
+            red_add1(gW2 + i * 16 + j, h1[i] * dz2[j]);
+        }
+        dz1[i] = h1[i] > 0.f ? s : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; j++) red_add1(gb1 + j, dz1[j]);
+    float gx[7];
+    for (int i = 0; i < n_in; i++) {
+        const float xi = bm_input(i, ck, d);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            s = fmaf(__ldg(W1 + i * 16 + j), dz1[j], s);
+            red_add1(gW1 + i * 16 + j, xi * dz1[j]);
+        }
+        if (i < 7) gx[i] = s;
+    }
+    float xg = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) xg = fmaf(g[c], ck[c] + phi[c], xg);
+    go[0] = make_float4(u[0] + gx[0], u[1] + gx[1], u[2] + gx[2], gx[3]);
+    go[1] = make_float4(gx[4], gx[5], gx[6], xg);
+}
+
+// P3
+template <int DT>
+__global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_bm_remarch(BmBwdArgs a,
+                                                                          const __grid_constant__ RayRecs rr) {
+    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (r >= a.n_rays) return;
+    float o[3], d[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o[c] = __ldg(a.ray_o + 3 * r + c);
+        d[c] = __ldg(a.ray_d + 3 * r + c);
+    }
+    const float *S = a.S + 8 * r * a.n_ids, *G = a.G + 8 * r * a.n_ids;
+    float Qtot = 0.f;  // sum_k B_k dL/dC . X_k
+    for (int k = 0; k < a.n_ids; k++) {
+        const float B = __ldg(S + 8 * k + 7);
+        if (B >= 0.f) Qtot = fmaf(B, __ldg(G + 8 * k + 7), Qtot);
+    }
+    int order[kMaxRayIds];
+    const int n = sort_blocks_for_ray(rr, o, order);
+    float inv_d[3], omax;
+    ray_setup(d, o, inv_d, omax);
+    float P = 0.f;
+    for (int k = 0; k < n; k++) {
+        const int idx = order[k];
+        const float B = __ldg(S + 8 * idx + 7);
+        if (B < 0.f) continue;  // no occupied sample: no part in Eq. 5
+        float Cf[3], Ff[4], gC[3], gF[4];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            Cf[c] = __ldg(S + 8 * idx + c);
+            gC[c] = __ldg(G + 8 * idx + c);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            Ff[c] = __ldg(S + 8 * idx + 3 + c);
+            gF[c] = __ldg(G + 8 * idx + 3 + c);
+        }
+        P = fmaf(B, __ldg(G + 8 * idx + 7), P);
+        const float Q = Qtot - P;  // the blocks behind this one
+        const int id = rr.id[idx];
+        const BlockRec &b = rr.r[idx];
+        float *gg = a.grad_grid[id];
+        float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
+        float T = 1.f, PC[3] = {0.f, 0.f, 0.f}, PF[4] = {0.f, 0.f, 0.f, 0.f};
+        for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
+            float2 f2[4];
+            accumulate_sample<DT>(b, p, g, f2);
+            const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
+            const float sigma = __expf(f[0]);
+            const float e = __expf(-sigma * delta);
+            const float wt = T * (1.f - e);
+            float c[7];
+#pragma unroll
+            for (int q = 0; q < 7; q++) c[q] = sigmoidf_fast(f[1 + q]);
+            float gdot = 0.f, sdot = Q;
+#pragma unroll
+            for (int q = 0; q < 3; q++) {
+                PC[q] = fmaf(wt, c[q], PC[q]);
+                gdot = fmaf(gC[q], c[q], gdot);
+                sdot = fmaf(gC[q], Cf[q] - PC[q], sdot);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                PF[q] = fmaf(wt, c[3 + q], PF[q]);
+                gdot = fmaf(gF[q], c[3 + q], gdot);
+                sdot = fmaf(gF[q], Ff[q] - PF[q], sdot);
+            }
+            float gf[8];
+            gf[0] = sigma * delta * (T * e * gdot - sdot);
+#pragma unroll
+            for (int q = 0; q < 3; q++) gf[1 + q] = wt * gC[q] * c[q] * (1.f - c[q]);
+#pragma unroll
+            for (int q = 0; q < 4; q++) gf[4 + q] = wt * gF[q] * c[3 + q] * (1.f - c[3 + q]);
+            scatter_taps(b, gg, gp, p, g, gf);
+            T *= e;
+            return true;
+        });
+    }
+}
+
 }  // namespace
 
 int backward_rows(int64_t n_rays) { return (int)((n_rays + kBwdThreads - 1) / kBwdThreads); }
@@ -481,6 +716,33 @@ cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream
     case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kMixed: k_remarch_backward<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cudaStream_t st) {
+    if (a.n_rays <= 0) return cudaSuccess;
+    const int nb = backward_rows(a.n_rays);
+    const int64_t pairs = a.n_rays * a.n_ids;
+    switch (a.dtype) {
+    case kF32: k_bm_pass1<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kF16: k_bm_pass1<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_bm_pass1<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_bm_pass1<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_bm_pass1<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_bm_mlp<<<(unsigned)((pairs + kBwdThreads - 1) / kBwdThreads), kBwdThreads, 0, st>>>(a, rr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    switch (a.dtype) {
+    case kF32: k_bm_remarch<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kF16: k_bm_remarch<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kBF16: k_bm_remarch<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8: k_bm_remarch<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kMixed: k_bm_remarch<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -105,6 +105,7 @@ void destroy(cow_ctx *c) {
     c->partials.release();
     c->staging.release();
     c->block_mlps.release();
+    c->bm_scratch.release();
     delete c;
 }
 
@@ -943,6 +944,67 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_rays(a, rr, st));
+    return COW_OK;
+}
+
+cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                          const int32_t *ids, int32_t n_ids, const float *dL_drgb,
+                                          float *const *grad_grid, float *const *grad_planes, float *grad_block_mlps,
+                                          void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !dL_drgb || !grad_grid || !grad_planes || !grad_block_mlps)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_backward_block_mlps: null argument");
+    if (ctx->n_freq < 0) return fail(COW_ERR_INVALID_ARG, "no per-block MLPs set (cow_set_block_mlps)");
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    const int32_t nb = (int32_t)ctx->blocks.size();
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    for (const void *q : {(const void *)o, (const void *)d, (const void *)dL_drgb, (const void *)grad_block_mlps})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "backward arrays must be device memory");
+    if ((uintptr_t)grad_block_mlps & 3u) return fail(COW_ERR_INVALID_ARG, "grad_block_mlps must be 4-byte aligned");
+    if (n_rays > ((int64_t)1 << 40) / ((int64_t)n_ids * 64))
+        return fail(COW_ERR_INVALID_ARG, "too many rays x blocks for one call");
+    std::vector<float *> ptrs((size_t)nb * 4);
+    for (int32_t i = 0; i < nb; i++) {
+        ptrs[(size_t)i] = grad_grid[i];
+        for (int k = 0; k < 3; k++) ptrs[(size_t)nb + 3 * (size_t)i + k] = grad_planes[3 * i + k];
+        for (int k = 0; k < 4; k++) {
+            const float *q = k == 0 ? grad_grid[i] : grad_planes[3 * i + k - 1];
+            if (q && (((uintptr_t)q & 15u) || !is_device_ptr(q)))
+                return fail(COW_ERR_INVALID_ARG, "block %d: gradient arrays must be 16-byte aligned device memory", i);
+        }
+    }
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cow_status rc = ensure_resident(ctx, ids, n_ids, st);
+    if (rc != COW_OK) return rc;
+    COW_CUDA(ctx->gptrs.reserve(ptrs.size() * sizeof(float *)));
+    COW_CUDA(cudaMemcpyAsync(ctx->gptrs.p, ptrs.data(), ptrs.size() * sizeof(float *), cudaMemcpyHostToDevice, st));
+    const size_t half = (size_t)n_rays * (size_t)n_ids * 8 * sizeof(float);
+    COW_CUDA(ctx->bm_scratch.reserve(2 * half));
+    const int32_t n_in = 10 + 6 * ctx->n_freq;
+    cow::BmBwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.dtype = ctx->dtype;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.dL_drgb = dL_drgb;
+    a.grad_grid = (float *const *)ctx->gptrs.p;
+    a.grad_planes = (float *const *)ctx->gptrs.p + nb;
+    a.mlps = (const float *)ctx->block_mlps.p;
+    a.mlp_stride = ctx->block_mlp_nparam;
+    a.grad_mlps = grad_block_mlps;
+    a.grad_stride = 16 * n_in + 16 + 16 * 16 + 16 + 16 * 3 + 3;
+    a.n_freq = ctx->n_freq;
+    a.n_ids = n_ids;
+    a.S = (float *)ctx->bm_scratch.p;
+    a.G = (float *)((unsigned char *)ctx->bm_scratch.p + half);
+    a.err = ctx->d_err;
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_backward_block_mlps(a, rr, st));
     return COW_OK;
 }
 

@@ -62,6 +62,26 @@ struct BwdArgs {                  // the call's block records come by value (Ray
     unsigned *err;
 };
 
+// Gradients of the ray-batch form with per-block MLPs (Eq. 5), bwd.cu
+struct BmBwdArgs {                // the call's block records come by value (RayRecs)
+    int32_t dtype;
+    const float *ray_o, *ray_d;   // n_rays x 3
+    int64_t n_rays;
+    const float *dL_drgb;         // n_rays x 3
+    float *const *grad_grid;      // device array of per-block pointers (entries may be null)
+    float *const *grad_planes;    // device array of 3 per-block pointers
+    const float *mlps;            // block i's weights at mlps + i * mlp_stride (the context's copy)
+    int64_t mlp_stride;
+    float *grad_mlps;             // block i's weight gradient at grad_mlps + i * grad_stride (accumulated)
+    int64_t grad_stride;
+    int32_t n_freq;
+    int32_t n_ids;
+    float *S;                     // scratch n_rays x n_ids x 8: C^k (3), F^k (4), B_k (-1: no sample)
+    float *G;                     // scratch n_rays x n_ids x 8: dL/dC^k (3), dL/dF^k (4), dL/dC . X_k
+    unsigned *err;
+};
+cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cudaStream_t st);
+
 // Training-stage regularisers (bwd.cu): sparsity (Eq. 7) over points,
 // block opacity (Eq. 8) over rays
 struct RegArgs {                  // the blocks that take part come by value (RayRecs)
