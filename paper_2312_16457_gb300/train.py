@@ -54,11 +54,14 @@ class Fitter:
     batch: forward, MSE gradient, backward, Adam, re-pack -- all in libcow."""
 
     def __init__(self, scene, mlp, lr_feat=1e-2, lr_mlp=1e-3, device="cuda", lambda_sparsity=0.0,
-                 lambda_opacity=0.0, n_sparsity_points=1 << 14, seed=0):
+                 lambda_opacity=0.0, n_sparsity_points=1 << 14, seed=0, block_mlps=None, n_freq=0):
         """lambda_sparsity / lambda_opacity weight the regularisers of Eq. 7
         (mean alpha at n_sparsity_points uniform points of the scene box,
         redrawn every step) and Eq. 8 (entropy of block opacities of the
-        step's rays); the paper trains with 0.05 and 0.001."""
+        step's rays); the paper trains with 0.05 and 0.001.  block_mlps
+        ([n_blocks, block_mlp_nparam(n_freq)]) fits one MLP per block,
+        blended by Eq. 5, instead of the global `mlp` (which may be None);
+        that form has no early termination."""
         self.ctx = cow.Context(scene, "fp32")
         self.box_lo = torch.tensor(scene.box_lo, dtype=torch.float32, device=device)
         self.box_hi = torch.tensor(scene.box_hi, dtype=torch.float32, device=device)
@@ -71,9 +74,18 @@ class Fitter:
         self.params = []
         for b in scene.blocks:
             self.params += [b.grid.to(device).float().contiguous()] + [p.to(device).float().contiguous() for p in b.planes]
-        self.mlp = torch.as_tensor(mlp, dtype=torch.float32, device=device).contiguous()
-        self.m = [torch.zeros_like(p) for p in self.params] + [torch.zeros_like(self.mlp)]
-        self.v = [torch.zeros_like(p) for p in self.params] + [torch.zeros_like(self.mlp)]
+        self.n_freq = int(n_freq)
+        if block_mlps is not None:
+            self.block_mlps = torch.as_tensor(block_mlps, dtype=torch.float32, device=device).contiguous()
+            self.ctx.set_block_mlps(self.block_mlps, self.n_freq)
+            self.mlp = None
+            mw = self.block_mlps
+        else:
+            self.block_mlps = None
+            self.mlp = torch.as_tensor(mlp, dtype=torch.float32, device=device).contiguous()
+            mw = self.mlp
+        self.m = [torch.zeros_like(p) for p in self.params] + [torch.zeros_like(mw)]
+        self.v = [torch.zeros_like(p) for p in self.params] + [torch.zeros_like(mw)]
         self.lr_feat, self.lr_mlp = lr_feat, lr_mlp
         self.t = 0
 
@@ -82,16 +94,25 @@ class Fitter:
         before it (the weighted regularisers are in self.reg_loss)."""
         nb = len(self.ids)
         block_T = None
-        if self.lambda_opacity > 0.0 and ert_eps == 0.0:
+        per_block = self.block_mlps is not None
+        if per_block:
+            if ert_eps != 0.0:
+                raise ValueError("the per-block MLP form fits without early termination")
+            rgb = self.ctx.render_rays(o, d, self.ids, None, aux=False, block_mlps=True)[0]
+        elif self.lambda_opacity > 0.0 and ert_eps == 0.0:
             # the forward also keeps every block's transmittance for the opacity term
             rgb, aux, block_T = self.ctx.render_rays_block_t(o, d, self.ids, self.mlp)
         else:
             rgb, aux, _ = self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps)
         g, loss = cow.mse_grad(rgb, target)
         grads = [torch.zeros_like(p) for p in self.params]
-        gm = torch.zeros_like(self.mlp)
         gtab = ([grads[4 * i] for i in range(nb)], [grads[4 * i + 1:4 * i + 4] for i in range(nb)])
-        self.ctx.render_backward(o, d, self.ids, self.mlp, aux, g, gtab[0], gtab[1], gm, ert_eps=ert_eps)
+        if per_block:
+            gm = torch.zeros_like(self.block_mlps)
+            self.ctx.render_backward_block_mlps(o, d, self.ids, g, gtab[0], gtab[1], gm)
+        else:
+            gm = torch.zeros_like(self.mlp)
+            self.ctx.render_backward(o, d, self.ids, self.mlp, aux, g, gtab[0], gtab[1], gm, ert_eps=ert_eps)
         if self.lambda_sparsity > 0.0 or self.lambda_opacity > 0.0:
             self.reg_loss = torch.zeros(1, dtype=torch.float32, device=o.device)
             if self.lambda_sparsity > 0.0:
@@ -104,10 +125,16 @@ class Fitter:
         self.t += 1
         for k, p in enumerate(self.params):
             cow.adam_step(p, grads[k], self.m[k], self.v[k], self.lr_feat, self.t)
-        cow.adam_step(self.mlp, gm, self.m[-1], self.v[-1], self.lr_mlp, self.t)
+        if per_block:
+            cow.adam_step(self.block_mlps, gm, self.m[-1], self.v[-1], self.lr_mlp, self.t)
+            self.ctx.set_block_mlps(self.block_mlps, self.n_freq)
+        else:
+            cow.adam_step(self.mlp, gm, self.m[-1], self.v[-1], self.lr_mlp, self.t)
         for i in range(nb):
             self.ctx.update_features(i, self.params[4 * i], self.params[4 * i + 1:4 * i + 4])
         return loss
 
     def render(self, o, d, ert_eps: float = 0.0):
+        if self.block_mlps is not None:
+            return self.ctx.render_rays(o, d, self.ids, None, aux=False, block_mlps=True)[0]
         return self.ctx.render_rays(o, d, self.ids, self.mlp, ert_eps=ert_eps, aux=False)[0]

@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2312_16457_gb300 import cow, synth
+from paper_2312_16457_gb300 import cow, synth, train
 
 pytestmark = pytest.mark.gpu
 
@@ -232,3 +232,22 @@ def test_ray_form_backward_matches_oracle_gradient(storage):
     ctx.render_backward_block_mlps(o.cuda(), d.cuda(), ids, torch.from_numpy(g).cuda(), gg, gp, gm)
     ctx.sync_check()
     assert _rel(gm.cpu().numpy(), 2 * om) <= 1e-3
+
+
+def test_fit_with_block_mlps_reduces_loss():
+    """A short fit of one scene's features and per-block MLPs (Eq. 5 form)
+    to another seed's render."""
+    sc = synth.city_scene(4, 2, 2.0, [(24, 64)])
+    tgt_scene = synth.city_scene(40, 2, 2.0, [(24, 64)])
+    o, d = synth.random_rays(1 << 16, 4, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    tctx = cow.Context(tgt_scene, "fp32")
+    target = tctx.render_rays(o, d, [0, 1, 2, 3], synth.mlp_weights(140), aux=False)[0]
+    w = synth.block_mlp_weights(104, len(sc.blocks), 2)
+    fit = train.Fitter(sc, None, block_mlps=w, n_freq=2)
+    losses = [float(fit.step(o, d, target).item()) for _ in range(40)]
+    fit.ctx.sync_check()
+    assert all(np.isfinite(losses))
+    assert losses[-1] < 0.85 * losses[0], losses[::8]
+    # the fitted per-block MLPs are the context's
+    assert not np.allclose(fit.block_mlps.cpu().numpy(), w)
