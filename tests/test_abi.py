@@ -73,6 +73,9 @@ def test_calls_reject_null_context(L):
     assert L.cow_set_schedule(None, 0) == 1
     assert L.cow_set_tile_order(None, 0) == 1
     assert b"null context" in L.cow_last_error()
+    assert L.cow_render_backward_block_mlps(None, None, None, 1, None, 1, None, None, None, None, None) == 1
+    assert L.cow_batch_last_groups(None, C.byref(n)) == 1
+    assert L.cow_set_block_mlps(None, None, 0, 0, None) == 1
     assert L.cow_free(None) == 0
 
 
