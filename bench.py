@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--budget-frac", type=float, default=0.0,
                     help="batch_64: also serve the batch under a residency budget of this fraction of the "
                          "scene's packed bytes (views in planner order)")
+    ap.add_argument("--block-mlps", type=int, default=-1,
+                    help="fit_2x2: fit per-block MLPs (Eq. 5) with this many PE frequencies instead of the "
+                         "global MLP (-1)")
     ap.add_argument("--reg", action="store_true",
                     help="fit_2x2: add the sparsity (0.05) and opacity (0.001) regularisers to every step")
     return ap.parse_args()
@@ -429,7 +432,11 @@ def run_fit(args, ws, rank, local):
     tctx = cow.Context(tgt, "fp32")
     target = tctx.render_rays(o, d, [0, 1, 2, 3], mlp_t, aux=False)[0]
     tctx.close()
-    fit = train.Fitter(sc, mlp, lambda_sparsity=0.05 if args.reg else 0.0, lambda_opacity=0.001 if args.reg else 0.0)
+    per_block = args.block_mlps >= 0
+    bm = synth.block_mlp_weights(104, len(sc.blocks), args.block_mlps) if per_block else None
+    fit = train.Fitter(sc, None if per_block else mlp, lambda_sparsity=0.05 if args.reg else 0.0,
+                       lambda_opacity=0.001 if args.reg else 0.0, block_mlps=bm,
+                       n_freq=max(args.block_mlps, 0))
     stream = torch.cuda.current_stream()
 
     def psnr_now():
@@ -459,6 +466,9 @@ def run_fit(args, ws, rank, local):
             "config": {"workload": "fit_2x2", "scene": f"2x2 blocks, {R}^3 grid + {P}^2 planes, FP32 parameters",
                        "rays": n, "adam_steps": args.warmup + args.steps, "lr_features": fit.lr_feat,
                        "lr_mlp": fit.lr_mlp,
+                       "mlp": (f"per-block (Eq. 5), PE with {args.block_mlps} frequencies, "
+                               f"{synth.block_mlp_nparam(args.block_mlps)} parameters a block") if per_block
+                              else "one global deferred MLP (499 parameters)",
                        "regularisers": ({"sparsity": 0.05, "sparsity_points": fit.n_sparsity_points,
                                          "opacity": 0.001} if args.reg else None)},
             "fit_psnr_db": {"before": round(p0, 2), "after": round(p1, 2)}, "clocks": ck}

@@ -518,27 +518,42 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_pass1(BmBwdArgs a, const __g
     }
 }
 
-// P2: one thread per (ray, block) pair
+// A weight-gradient term summed over the warp's 32 rays, then one reduction.
+__device__ __forceinline__ void warp_red(float *dst, float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red_add1(dst, v);
+}
+
+// P2: one thread per (ray, block) pair.  The pairs are laid out block-major
+// with each block's rays padded to a multiple of 32, so a warp holds one
+// block for 32 rays and sums that block's weight gradients before reducing;
+// padding lanes and blocks a ray has no sample in take part with zeros.
 __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __grid_constant__ RayRecs rr) {
     const int64_t t = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    if (t >= a.n_rays * a.n_ids) return;
-    const int64_t r = t / a.n_ids;
-    const int k = (int)(t % a.n_ids);
-    const float4 *e = reinterpret_cast<const float4 *>(a.S + 8 * t);
-    const float4 e0 = e[0], e1 = e[1];
-    float4 *go = reinterpret_cast<float4 *>(a.G + 8 * t);
-    if (e1.w < 0.f) {
-        go[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        go[1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        return;
+    const int64_t rows = (a.n_rays + 31) & ~(int64_t)31;
+    const int k = (int)min(t / rows, (int64_t)a.n_ids - 1);  // warp-uniform
+    const int64_t r = t - (int64_t)k * rows;
+    const bool ray = t < rows * a.n_ids && r < a.n_rays;
+    const int64_t pe = r * a.n_ids + k;  // the pair's scratch entry
+    float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = make_float4(0.f, 0.f, 0.f, -1.f);
+    if (ray) {
+        const float4 *e = reinterpret_cast<const float4 *>(a.S + 8 * pe);
+        e0 = e[0];
+        e1 = e[1];
+    }
+    const bool act = ray && e1.w >= 0.f;
+    if (!act) {  // the scratch of a block without samples holds no C^k, F^k: zeros, not stale values
+        e0 = make_float4(0.f, 0.f, 0.f, 0.f);
+        e1 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     const float ck[7] = {e0.x, e0.y, e0.z, e0.w, e1.x, e1.y, e1.z};
-    const float B = e1.w;
+    const float B = act ? e1.w : 0.f;
     float d[3], g[3], u[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-        d[c] = __ldg(a.ray_d + 3 * r + c);
-        g[c] = __ldg(a.dL_drgb + 3 * r + c);
+        d[c] = ray ? __ldg(a.ray_d + 3 * r + c) : 0.f;
+        g[c] = ray ? __ldg(a.dL_drgb + 3 * r + c) : 0.f;
         u[c] = B * g[c];
     }
     const int id = rr.id[k];
@@ -572,7 +587,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __gri
         for (int i = 0; i < 16; i++) z = fmaf(h2[i], __ldg(W3 + i * 3 + j), z);
         phi[j] = 1.f / (1.f + expf(-z));
         dz3[j] = u[j] * phi[j] * (1.f - phi[j]);
-        red_add1(gb3 + j, dz3[j]);
+        warp_red(gb3 + j, dz3[j]);
     }
     float dz2[16];
 #pragma unroll
@@ -581,25 +596,25 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __gri
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             s = fmaf(__ldg(W3 + i * 3 + j), dz3[j], s);
-            red_add1(gW3 + i * 3 + j, h2[i] * dz3[j]);
+            warp_red(gW3 + i * 3 + j, h2[i] * dz3[j]);
         }
         dz2[i] = h2[i] > 0.f ? s : 0.f;
     }
     float dz1[16];
 #pragma unroll
-    for (int j = 0; j < 16; j++) red_add1(gb2 + j, dz2[j]);
+    for (int j = 0; j < 16; j++) warp_red(gb2 + j, dz2[j]);
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             s = fmaf(__ldg(W2 + i * 16 + j), dz2[j], s);
-            red_add1(gW2 + i * 16 + j, h1[i] * dz2[j]);
+            warp_red(gW2 + i * 16 + j, h1[i] * dz2[j]);
         }
         dz1[i] = h1[i] > 0.f ? s : 0.f;
     }
 #pragma unroll
-    for (int j = 0; j < 16; j++) red_add1(gb1 + j, dz1[j]);
+    for (int j = 0; j < 16; j++) warp_red(gb1 + j, dz1[j]);
     float gx[7];
     for (int i = 0; i < n_in; i++) {
         const float xi = bm_input(i, ck, d);
@@ -607,9 +622,16 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __gri
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             s = fmaf(__ldg(W1 + i * 16 + j), dz1[j], s);
-            red_add1(gW1 + i * 16 + j, xi * dz1[j]);
+            warp_red(gW1 + i * 16 + j, xi * dz1[j]);
         }
         if (i < 7) gx[i] = s;
+    }
+    if (!ray) return;
+    float4 *go = reinterpret_cast<float4 *>(a.G + 8 * pe);
+    if (!act) {
+        go[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        go[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
     }
     float xg = 0.f;
 #pragma unroll
@@ -724,7 +746,7 @@ cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream
 cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n_rays <= 0) return cudaSuccess;
     const int nb = backward_rows(a.n_rays);
-    const int64_t pairs = a.n_rays * a.n_ids;
+    const int64_t padded = ((a.n_rays + 31) & ~(int64_t)31) * a.n_ids;  // k_bm_mlp's threads
     switch (a.dtype) {
     case kF32: k_bm_pass1<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kF16: k_bm_pass1<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
@@ -735,7 +757,7 @@ cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cu
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_bm_mlp<<<(unsigned)((pairs + kBwdThreads - 1) / kBwdThreads), kBwdThreads, 0, st>>>(a, rr);
+    k_bm_mlp<<<(unsigned)((padded + kBwdThreads - 1) / kBwdThreads), kBwdThreads, 0, st>>>(a, rr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     switch (a.dtype) {
     case kF32: k_bm_remarch<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
