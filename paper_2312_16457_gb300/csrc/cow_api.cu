@@ -76,6 +76,9 @@ namespace {
 void destroy(cow_ctx *c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    // under a residency budget, calls return with loads from the pinned host
+    // copies still queued on the caller's stream: let them finish first
+    if (c->pool) cudaDeviceSynchronize();
     for (auto &b : c->blocks) {
         if (b.async_alloc) {  // pool memory: freed in stream order before the pool goes
             if (b.grid) cudaFreeAsync(b.grid, nullptr);
