@@ -277,3 +277,25 @@ def test_ray_form_gradient_reduces_to_global_form(orc):
     for k in range(3):
         np.testing.assert_allclose(bp[0][k], gp[0][k], rtol=0, atol=1e-12)
     np.testing.assert_allclose(bm[0], gm, rtol=0, atol=1e-12)
+
+
+def test_ray_form_gradient_of_a_block_without_samples_is_zero(orc):
+    """R20 in the adjoint: a block the rays cross only through empty cells
+    takes no part, so neither its features nor its MLP receive a gradient,
+    and dropping it from ids leaves every other gradient unchanged."""
+    sc = synth.city_scene(9, 2, 2.0, [(8, 16)])
+    sc.blocks[1].grid[..., 0] = -12.0  # below the occupancy threshold everywhere
+    n = len(sc.blocks)
+    L = 1
+    w = synth.block_mlp_weights(3, n, L)
+    osc = orc.OracleScene(sc)
+    o, d = synth.random_rays(128, 11, sc.box_lo, sc.box_hi)
+    g = np.random.default_rng(6).normal(size=(128, 3))
+    gg, gp, gm = orc.render_rays_block_mlp_grad(osc, list(range(n)), o, d, w, L, g)
+    assert np.all(gg[1] == 0.0) and all(np.all(x == 0.0) for x in gp[1]) and np.all(gm[1] == 0.0)
+    keep = [k for k in range(n) if k != 1]
+    gg2, gp2, gm2 = orc.render_rays_block_mlp_grad(osc, keep, o, d, w, L, g)
+    for b in keep:  # the oracle sums over rays on several threads: equal up to rounding order
+        np.testing.assert_allclose(gg2[b], gg[b], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(gm2[b], gm[b], rtol=0, atol=1e-12)
+    assert max(np.abs(gg[b]).max() for b in keep) > 0
