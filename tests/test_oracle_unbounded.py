@@ -177,3 +177,15 @@ def test_block_sequential_equals_single_pass_unbounded(orc):
     a1 = orc.render_view(osc, cams[0], order, None, orc.MODE_SINGLE_PASS)[1]
     np.testing.assert_allclose(a0, a1, rtol=0, atol=1e-12)
     assert (a0[:, 7] < 0.5).mean() > 0.5  # the horizon is mostly opaque
+
+
+def test_contraction_golden_points(orc):
+    """Eq. 16 at the hand-worked points of tests/golden/contraction_eq16.txt."""
+    import pathlib
+
+    rows = [ln.split() for ln in (pathlib.Path(__file__).parent / "golden" / "contraction_eq16.txt").read_text().splitlines()
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) >= 6
+    for row in rows:
+        v = [float(t) for t in row]
+        np.testing.assert_allclose(orc.contract(np.array(v[:3])), v[3:], rtol=0, atol=1e-15)
