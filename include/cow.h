@@ -262,6 +262,20 @@ cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, con
                                const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *out_order,
                                int64_t *out_upload_bytes, int64_t *out_upload_bytes_given);
 
+/* Improve a view order (host only): starting from io_order (a permutation
+ * of 0 .. n_views-1, for example cow_plan_view_order's), move one view at a
+ * time to another place and keep a move when the same simulation of the
+ * loading rule loads fewer bytes; rescan after each kept move and stop when
+ * no move helps or after max_evals simulated orders (deterministic).
+ * io_order receives the result, *out_upload_bytes (may be NULL) its bytes,
+ * never more than the input order's.  Each evaluation costs one simulation
+ * (about n_views x n_blocks steps).
+ * Errors: INVALID_ARG (as cow_plan_view_order, io_order not a permutation,
+ * max_evals < 1). */
+cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids,
+                                 const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *io_order,
+                                 int32_t max_evals, int64_t *out_upload_bytes);
+
 /* Batched form: many cameras of uneven size and LOD set served by one
  * persistent launch over a (view, tile, block) work queue.  Every CTA takes
  * the next (view, tile) item from a device counter, culls the view's block

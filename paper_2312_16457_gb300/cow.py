@@ -35,7 +35,7 @@ EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "c
            "cow_render", "cow_render_rays", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
-           "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_sparsity_loss", "cow_opacity_loss",
+           "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_refine_view_order", "cow_sparsity_loss", "cow_opacity_loss",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_render_backward_block_mlps",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
@@ -101,6 +101,7 @@ def lib():
             "cow_get_residency": [P, P],
             "cow_block_bytes": [P, i32, P],
             "cow_plan_view_order": [P, i32, P, P, i32, i64, P, P, P],
+            "cow_refine_view_order": [P, i32, P, P, i32, i64, P, i32, P],
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
             "cow_render_backward": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
@@ -436,16 +437,33 @@ class Context:
         return out, se
 
 
-def plan_view_order(block_bytes: Sequence[int], ids_per_view, budget_bytes: int):
-    """Residency-aware view order (host only): returns (order, bytes loaded in
-    that order, bytes loaded in the given order) under the LRU rule of
-    Context.set_residency, from a cold start, one view per render call."""
-    bb = np.ascontiguousarray(block_bytes, np.int64)
+def _views_csr(ids_per_view):
     offs = np.zeros(len(ids_per_view) + 1, np.int32)
     for v, ids in enumerate(ids_per_view):
         offs[v + 1] = offs[v] + len(ids)
     flat = np.ascontiguousarray(np.concatenate([np.asarray(i, np.int32) for i in ids_per_view])
                                 if offs[-1] > 0 else np.zeros(1, np.int32), np.int32)
+    return flat, offs
+
+
+def refine_view_order(block_bytes: Sequence[int], ids_per_view, budget_bytes: int, order, max_evals: int = 2000):
+    """Improve a view order by single-view moves under the same loading rule
+    (cow_refine_view_order); returns (order, bytes loaded in it)."""
+    bb = np.ascontiguousarray(block_bytes, np.int64)
+    flat, offs = _views_csr(ids_per_view)
+    out = np.ascontiguousarray(order, np.int32).copy()
+    n = C.c_int64()
+    _check(lib().cow_refine_view_order(_ptr(bb), len(bb), _ptr(flat), _ptr(offs), len(ids_per_view),
+                                       int(budget_bytes), _ptr(out), int(max_evals), C.byref(n)))
+    return out, n.value
+
+
+def plan_view_order(block_bytes: Sequence[int], ids_per_view, budget_bytes: int):
+    """Residency-aware view order (host only): returns (order, bytes loaded in
+    that order, bytes loaded in the given order) under the LRU rule of
+    Context.set_residency, from a cold start, one view per render call."""
+    bb = np.ascontiguousarray(block_bytes, np.int64)
+    flat, offs = _views_csr(ids_per_view)
     order = np.zeros(len(ids_per_view), np.int32)
     planned, given = C.c_int64(), C.c_int64()
     _check(lib().cow_plan_view_order(_ptr(bb), len(bb), _ptr(flat), _ptr(offs), len(ids_per_view), int(budget_bytes),

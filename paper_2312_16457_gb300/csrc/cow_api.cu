@@ -1274,12 +1274,12 @@ cow_status cow_block_bytes(const cow_ctx *ctx, int32_t block, int64_t *out_bytes
     return COW_OK;
 }
 
-cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids,
-                               const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *out_order,
-                               int64_t *out_upload_bytes, int64_t *out_upload_bytes_given) {
-    g_last_error.clear();
-    if (!block_bytes || n_blocks < 1 || !ids_offsets || n_views < 1 || budget_bytes < 1 || !out_order)
-        return fail(COW_ERR_INVALID_ARG, "cow_plan_view_order: bad argument");
+namespace {
+
+// Check a planning request: sizes, CSR offsets, ids, and every view's own
+// blocks within the budget.
+cow_status check_views(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids, const int32_t *ids_offsets,
+                       int32_t n_views, int64_t budget_bytes) {
     if (ids_offsets[0] != 0) return fail(COW_ERR_INVALID_ARG, "ids_offsets[0] must be 0");
     for (int32_t i = 0; i < n_blocks; i++)
         if (block_bytes[i] < 0) return fail(COW_ERR_INVALID_ARG, "block %d: negative size", i);
@@ -1296,57 +1296,91 @@ cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, con
         if (need > budget_bytes)
             return fail(COW_ERR_INVALID_ARG, "view %d needs %lld bytes, over the budget", v, (long long)need);
     }
-    // the runtime's LRU, from a cold start (cow_set_residency unloads every block)
-    struct Cache {
-        std::vector<char> res;
-        std::vector<uint64_t> last;
-        uint64_t clock = 0;
-        int64_t bytes = 0;
-    };
-    auto cost = [&](const Cache &c, int32_t v) {
-        std::vector<char> seen((size_t)n_blocks, 0);
+    return COW_OK;
+}
+
+// The runtime's loading rule (ensure_resident) on block sizes alone, from
+// the cold start cow_set_residency leaves: a view's call unloads the least
+// recently used blocks it does not use (ties: lowest index) until its missing
+// blocks fit, then loads them.
+struct LruSim {
+    const int64_t *bytes;
+    int32_t nb;
+    const int32_t *ids, *offs;
+    int64_t budget;
+    std::vector<char> res;
+    std::vector<uint64_t> last;
+    uint64_t clock = 0;
+    int64_t used = 0;
+
+    LruSim(const int64_t *b, int32_t n, const int32_t *i, const int32_t *o, int64_t bud)
+        : bytes(b), nb(n), ids(i), offs(o), budget(bud), res((size_t)n, 0), last((size_t)n, 0) {}
+
+    void reset() {
+        std::fill(res.begin(), res.end(), 0);
+        std::fill(last.begin(), last.end(), 0);
+        clock = 0;
+        used = 0;
+    }
+    // bytes view v would load now
+    int64_t cost(int32_t v) const {
+        std::vector<char> seen((size_t)nb, 0);
         int64_t m = 0;
-        for (int32_t k = ids_offsets[v]; k < ids_offsets[v + 1]; k++)
+        for (int32_t k = offs[v]; k < offs[v + 1]; k++)
             if (!seen[(size_t)ids[k]]) {
                 seen[(size_t)ids[k]] = 1;
-                if (!c.res[(size_t)ids[k]]) m += block_bytes[ids[k]];
+                if (!res[(size_t)ids[k]]) m += bytes[ids[k]];
             }
         return m;
-    };
-    auto apply = [&](Cache &c, int32_t v) {
-        std::vector<char> need((size_t)n_blocks, 0);
-        for (int32_t k = ids_offsets[v]; k < ids_offsets[v + 1]; k++) need[(size_t)ids[k]] = 1;
+    }
+    // serve view v; returns the bytes it loaded
+    int64_t apply(int32_t v) {
+        std::vector<char> need((size_t)nb, 0);
+        for (int32_t k = offs[v]; k < offs[v + 1]; k++) need[(size_t)ids[k]] = 1;
         int64_t missing = 0;
-        for (int32_t i = 0; i < n_blocks; i++)
-            if (need[(size_t)i] && !c.res[(size_t)i]) missing += block_bytes[i];
-        const uint64_t now = ++c.clock;
-        for (int32_t i = 0; i < n_blocks; i++)
-            if (need[(size_t)i]) c.last[(size_t)i] = now;
-        while (c.bytes + missing > budget_bytes) {
+        for (int32_t i = 0; i < nb; i++)
+            if (need[(size_t)i] && !res[(size_t)i]) missing += bytes[i];
+        const uint64_t now = ++clock;
+        for (int32_t i = 0; i < nb; i++)
+            if (need[(size_t)i]) last[(size_t)i] = now;
+        while (used + missing > budget) {
             int32_t victim = -1;
-            for (int32_t i = 0; i < n_blocks; i++) {
-                if (!c.res[(size_t)i] || need[(size_t)i]) continue;
-                if (victim < 0 || c.last[(size_t)i] < c.last[(size_t)victim]) victim = i;
+            for (int32_t i = 0; i < nb; i++) {
+                if (!res[(size_t)i] || need[(size_t)i]) continue;
+                if (victim < 0 || last[(size_t)i] < last[(size_t)victim]) victim = i;
             }
             if (victim < 0) break;
-            c.res[(size_t)victim] = 0;
-            c.bytes -= block_bytes[victim];
+            res[(size_t)victim] = 0;
+            used -= bytes[victim];
         }
-        for (int32_t i = 0; i < n_blocks; i++)
-            if (need[(size_t)i] && !c.res[(size_t)i]) {
-                c.res[(size_t)i] = 1;
-                c.bytes += block_bytes[i];
+        for (int32_t i = 0; i < nb; i++)
+            if (need[(size_t)i] && !res[(size_t)i]) {
+                res[(size_t)i] = 1;
+                used += bytes[i];
             }
         return missing;
-    };
-    auto fresh = [&]() {
-        Cache c;
-        c.res.assign((size_t)n_blocks, 0);
-        c.last.assign((size_t)n_blocks, 0);
-        return c;
-    };
+    }
+    // bytes loaded serving `order` from a cold start
+    int64_t total(const int32_t *order, int32_t n) {
+        reset();
+        int64_t s = 0;
+        for (int32_t k = 0; k < n; k++) s += apply(order[k]);
+        return s;
+    }
+};
+
+}  // namespace
+
+cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids,
+                               const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *out_order,
+                               int64_t *out_upload_bytes, int64_t *out_upload_bytes_given) {
+    g_last_error.clear();
+    if (!block_bytes || n_blocks < 1 || !ids_offsets || n_views < 1 || budget_bytes < 1 || !out_order)
+        return fail(COW_ERR_INVALID_ARG, "cow_plan_view_order: bad argument");
+    cow_status rc = check_views(block_bytes, n_blocks, ids, ids_offsets, n_views, budget_bytes);
+    if (rc != COW_OK) return rc;
     // greedy: next the view that loads the fewest bytes now (ties: lowest index)
-    Cache c = fresh();
+    LruSim c(block_bytes, n_blocks, ids, ids_offsets, budget_bytes);
     std::vector<char> done((size_t)n_views, 0);
     int64_t planned = 0;
     for (int32_t s = 0; s < n_views; s++) {
@@ -1354,7 +1388,7 @@ cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, con
         int64_t best_cost = 0;
         for (int32_t v = 0; v < n_views; v++) {
             if (done[(size_t)v]) continue;
-            const int64_t m = cost(c, v);
+            const int64_t m = c.cost(v);
             if (best < 0 || m < best_cost) {
                 best = v;
                 best_cost = m;
@@ -1362,15 +1396,57 @@ cow_status cow_plan_view_order(const int64_t *block_bytes, int32_t n_blocks, con
         }
         done[(size_t)best] = 1;
         out_order[s] = best;
-        planned += apply(c, best);
+        planned += c.apply(best);
     }
     if (out_upload_bytes) *out_upload_bytes = planned;
     if (out_upload_bytes_given) {
-        Cache g = fresh();
-        int64_t given = 0;
-        for (int32_t v = 0; v < n_views; v++) given += apply(g, v);
-        *out_upload_bytes_given = given;
+        std::vector<int32_t> given((size_t)n_views);
+        for (int32_t v = 0; v < n_views; v++) given[(size_t)v] = v;
+        *out_upload_bytes_given = c.total(given.data(), n_views);
     }
+    return COW_OK;
+}
+
+cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, const int32_t *ids,
+                                 const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *io_order,
+                                 int32_t max_evals, int64_t *out_upload_bytes) {
+    g_last_error.clear();
+    if (!block_bytes || n_blocks < 1 || !ids_offsets || n_views < 1 || budget_bytes < 1 || !io_order || max_evals < 1)
+        return fail(COW_ERR_INVALID_ARG, "cow_refine_view_order: bad argument");
+    cow_status rc = check_views(block_bytes, n_blocks, ids, ids_offsets, n_views, budget_bytes);
+    if (rc != COW_OK) return rc;
+    std::vector<char> seen((size_t)n_views, 0);
+    for (int32_t k = 0; k < n_views; k++) {
+        if (io_order[k] < 0 || io_order[k] >= n_views || seen[(size_t)io_order[k]])
+            return fail(COW_ERR_INVALID_ARG, "io_order must be a permutation of 0 .. n_views-1");
+        seen[(size_t)io_order[k]] = 1;
+    }
+    LruSim c(block_bytes, n_blocks, ids, ids_offsets, budget_bytes);
+    std::vector<int32_t> cur(io_order, io_order + n_views), cand((size_t)n_views);
+    int64_t best = c.total(cur.data(), n_views);
+    int32_t evals = 1;
+    // first improvement over single-view moves (view at i to place j), rescanned from the start after each
+    bool improved = true;
+    while (improved && evals < max_evals) {
+        improved = false;
+        for (int32_t i = 0; i < n_views && !improved && evals < max_evals; i++)
+            for (int32_t j = 0; j < n_views && !improved && evals < max_evals; j++) {
+                if (j == i) continue;
+                cand = cur;
+                const int32_t v = cand[(size_t)i];
+                cand.erase(cand.begin() + i);
+                cand.insert(cand.begin() + j, v);
+                const int64_t t = c.total(cand.data(), n_views);
+                evals++;
+                if (t < best) {
+                    best = t;
+                    cur.swap(cand);
+                    improved = true;
+                }
+            }
+    }
+    std::copy(cur.begin(), cur.end(), io_order);
+    if (out_upload_bytes) *out_upload_bytes = best;
     return COW_OK;
 }
 

@@ -153,3 +153,40 @@ def test_header_and_library_from_plain_c(L, tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
     assert out.stdout.strip() == "ok 2 40 60"
+
+
+def test_refine_view_order_matches_simulation(L):
+    """The refinement's order loads what the re-stated rule says, never more
+    than its input order, strictly less on some random cases, and leaves an
+    order no single move improves when it stops on its own."""
+    import numpy as np
+
+    rng = np.random.default_rng(7)
+    better = 0
+    for trial in range(20):
+        nb = int(rng.integers(4, 30))
+        bb = rng.integers(1, 100, nb).tolist()
+        views = [sorted(rng.choice(nb, size=int(rng.integers(1, min(nb, 8) + 1)), replace=False).tolist())
+                 for _ in range(int(rng.integers(2, 14)))]
+        budget = max(sum(bb[i] for i in v) for v in views) + int(rng.integers(0, 150))
+        order, planned, _ = cow.plan_view_order(bb, views, budget)
+        ref, loaded = cow.refine_view_order(bb, views, budget, order, max_evals=100000)
+        assert sorted(ref.tolist()) == list(range(len(views)))
+        assert loaded == _simulate(bb, views, ref.tolist(), budget)
+        assert loaded <= planned
+        better += loaded < planned
+        n = len(views)
+        for i in range(n):  # a local optimum for single-view moves
+            for j in range(n):
+                if i == j:
+                    continue
+                cand = ref.tolist()
+                v = cand.pop(i)
+                cand.insert(j, v)
+                assert _simulate(bb, views, cand, budget) >= loaded
+    assert better >= 1
+    # the hand case: greedy is already best
+    ref, loaded = cow.refine_view_order([10, 10, 10, 10], [[0, 1], [2, 3], [0, 1]], 20, [0, 2, 1])
+    assert ref.tolist() == [0, 2, 1] and loaded == 40
+    with pytest.raises(cow.CowError):  # not a permutation
+        cow.refine_view_order([10, 10], [[0], [1]], 20, [0, 0])
