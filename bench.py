@@ -34,15 +34,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
-# DRAM bytes (read + write) of one k_march_views launch from an ncu capture of
-# the default workload (profiles/march_views_city_lod_1080p_traffic.md); valid
-# for the marcher revision named here and null for any other configuration.
-MARCH_REVISION = "v8-unbounded"
-MEASURED_TRAFFIC = {("city_lod_1080p", "bf16", "thread_const", 1): 49487934976}
+# DRAM bytes (read + write) of one marcher launch on a workload, taken once
+# with ncu (dram__bytes_read.sum + dram__bytes_write.sum) and keyed to the
+# SHA-256 of the sources that build the marcher: after any change to them the
+# stored number no longer describes the kernel and the line reports null.
+MARCH_SOURCES = ["march.cu", "march_core.cuh", "cow_common.cuh", "cow_kernels.h"]
+MEASURED_TRAFFIC = {}  # (workload, storage, schedule, res_div) -> (bytes per launch, sources sha256)
+# The L1 data-pipe utilisation of the same kernel (ncu
+# l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed at half
+# resolution), keyed the same way.
+MEASURED_L1_WAVEFRONTS = {}  # (workload, storage, schedule) -> (fraction, sources sha256)
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}
 # per occupied sample: 20 texels x 8 channels (8 grid vertices + 12 plane texels)
 GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160, "bf16_fp8": 8 * 16 + 12 * 8}
+
+
+def march_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in MARCH_SOURCES:
+        with open(os.path.join(ROOT, "paper_2312_16457_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 
 
 def parse():
@@ -372,7 +387,11 @@ def run_cow(args, ws, rank, local):
     achieved = gb / (ms / 1000.0)
     # the HBM level: the launch's measured DRAM bytes (ncu, one capture of
     # this configuration) over the live step time, against the measured copy peak
-    traffic = MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div))
+    src_sha = march_sources_sha256()
+    tr = MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div))
+    traffic = tr[0] if tr and tr[1] == src_sha else None
+    l1w = MEASURED_L1_WAVEFRONTS.get((args.workload, storage, args.schedule))
+    l1_wavefront_frac = l1w[0] if l1w and l1w[1] == src_sha else None
     hbm_level = None
     if traffic and hbm:
         dram_gbs = traffic / 1e9 / (ms / 1000.0)
@@ -397,8 +416,9 @@ def run_cow(args, ws, rank, local):
         "roofline": {"bound": "gather", "kernel": KERNEL_OF_SCHEDULE[args.schedule], "achieved": round(achieved, 1),
                      "peak": round(peak_l1, 1), "unit": "GB/s", "frac": round(achieved / peak_l1, 3),
                      "traffic": traffic,
-                     "traffic_source": f"ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, marcher "
-                                       f"{MARCH_REVISION}",
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, valid for "
+                                       f"marcher sources sha256 {src_sha[:16]} (null when not measured on them)",
+                     "l1_data_pipe_frac": l1_wavefront_frac,
                      "peak_source": f"measured live: random {width}-byte gathers from a 64 KiB (L1-resident) "
                                     "buffer, cow_gather_peak",
                      "levels_gbs": {"l1_gather": round(peak_l1, 1), "l2_gather": round(peak_l2, 1),

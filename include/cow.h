@@ -381,18 +381,26 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
  * device memory once running -- a trainer or viewer inside a fixed
  * device-memory budget, or a steady-state loop that must not pay for
  * cudaMalloc / cudaFree and the device synchronisation cudaFree implies).
- * Same arguments, results and error behaviour as cow_render_backward, with:
+ * Same arguments and results as cow_render_backward, with these differences:
  *  - no device or host allocation: the scratch (per-CTA MLP-gradient rows,
- *    per-ray dL/dC_d and dL/dF, the gradient pointer table, the block ids)
- *    lives in one static device array of the library (3 MiB, held by every
- *    GPU that loads the library until the process exits);
+ *    per-ray dL/dC_d and dL/dF, the per-block gradient pointer table) lives
+ *    in one static device array of the library (3 MiB, held by every GPU
+ *    that loads the library until the process exits); the pointer table is
+ *    written by a small kernel that takes the call's gradient pointers as
+ *    launch parameters, so no enqueued work reads host memory after the
+ *    call returns;
  *  - at most 65536 rays and 1024 context blocks per call; larger requests
  *    return COW_ERR_INVALID_ARG with a message naming the limit;
+ *  - it loads no blocks: under a residency budget (cow_set_residency) a
+ *    block of `ids` that is not on the device returns COW_ERR_INVALID_ARG
+ *    (render the rays first), and the call does not refresh the blocks'
+ *    least-recently-used order;
  *  - the first call on a device looks the array's device address up
  *    (cudaGetSymbolAddress); make that first call before any stream capture;
  *  - every call on a device shares the array and rewrites what it reads, so
  *    calls that overlap on the GPU (other streams, other contexts on the same
- *    device) race on it: order them. */
+ *    device) race on it: order them.
+ * Errors: INVALID_ARG, UNSUPPORTED (device index >= 64), CUDA. */
 cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
                                        const int32_t *ids, int32_t n_ids, const float *mlp, float ert_eps,
                                        const float *aux, const float *dL_drgb, float *const *grad_grid,

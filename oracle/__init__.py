@@ -210,7 +210,7 @@ class OracleScene:
     run on the oracle's own dequantisation of the master, or "f64" to hold
     float64 copies (finite differences)."""
 
-    def __init__(self, scene, values: str = "master", occupancy_from=None):
+    def __init__(self, scene, values: str = "master"):
         self.scene = scene
         self.values = values
         self._keep = []
@@ -223,8 +223,7 @@ class OracleScene:
             f64 = values == "f64"
             g = _np(b.grid, np.float64 if f64 else np.float32)
             pls = [_np(p, np.float64 if f64 else np.float32) for p in b.planes]
-            occ_src = _np(b.grid) if occupancy_from is None else _np(occupancy_from[i])
-            bits = occupancy(occ_src, b.R, scene.occ_cell, scene.occ_thresh)
+            bits = occupancy(_np(b.grid), b.R, scene.occ_cell, scene.occ_thresh)
             if values in ("fp16", "bf16", "fp8", "bf16_fp8"):
                 gv, pv = (values, values) if values != "bf16_fp8" else ("bf16", "fp8")
                 g = quantize(g, gv, channel_scale_exps(g, gv))[1].reshape(g.shape)

@@ -42,7 +42,7 @@ namespace {
 #define COW_REG_MIN_BLOCKS 2
 #endif
 
-constexpr int kBwdThreads = 128;
+constexpr int kBwdThreads = kBwdCtaThreads;
 constexpr int kVec = 77;  // x (10), dz1 (16), h1 (16), dz2 (16), h2 (16), dz3 (3)
 
 // Vector reduction without a returned value (red, not atom: a float4

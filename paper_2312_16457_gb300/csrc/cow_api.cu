@@ -1539,9 +1539,12 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
 // pay for cudaMalloc / cudaFree (cudaFree also synchronises the device).
 // cow_render_backward_noalloc serves them: it computes exactly what
 // cow_render_backward computes, but its scratch -- the per-CTA rows of the
-// MLP weight gradient, the per-ray dL/dC_d, dL/dF, the per-block gradient
-// pointer table and the block ids -- lives in the file-scope array below
-// instead of context buffers, so the call itself allocates nothing.
+// MLP weight gradient, the per-ray dL/dC_d, dL/dF and the per-block gradient
+// pointer table -- lives in the file-scope array below instead of context
+// buffers, so the call itself allocates nothing.  The pointer table is
+// written on the device by a one-CTA kernel that receives the call's
+// gradient pointers as launch parameters, so no device work reads host
+// memory after the call returns.
 //
 // Limits: at most kNoAllocMaxRays rays and kNoAllocMaxBlocks blocks per call
 // (3 MiB of device memory, held by every GPU that loads the library until the
@@ -1554,16 +1557,36 @@ namespace {
 
 constexpr int64_t kNoAllocMaxRays = 65536;
 constexpr int32_t kNoAllocMaxBlocks = 1024;
-constexpr size_t kNaRowsBytes = (size_t)(kNoAllocMaxRays / 128) * cow::kMlpParams * sizeof(float);  // 1021952
-constexpr size_t kNaGcfBytes = (size_t)kNoAllocMaxRays * 8 * sizeof(float);                           // 2 MiB
-constexpr size_t kNaPtrBytes = (size_t)kNoAllocMaxBlocks * 4 * sizeof(float *);                        // 32 KiB
+// one MLP-gradient row per backward CTA: backward_rows(kNoAllocMaxRays) rows
+constexpr int64_t kNaRows = (kNoAllocMaxRays + cow::kBwdCtaThreads - 1) / cow::kBwdCtaThreads;
+constexpr size_t kNaRowsBytes = ((size_t)kNaRows * cow::kMlpParams * sizeof(float) + 255) / 256 * 256;
+constexpr size_t kNaGcfBytes = (size_t)kNoAllocMaxRays * 8 * sizeof(float);     // 2 MiB
+constexpr size_t kNaPtrBytes = (size_t)kNoAllocMaxBlocks * 4 * sizeof(float *);  // 32 KiB
 constexpr size_t kNaTotalBytes = kNaRowsBytes + kNaGcfBytes + kNaPtrBytes;
 static_assert(kNaRowsBytes % 256 == 0 && kNaGcfBytes % 256 == 0 && kNaPtrBytes % 256 == 0,
               "scratch sections must keep 256-byte alignment");
+static_assert(kNaRowsBytes >= (size_t)kNaRows * cow::kMlpParams * sizeof(float), "row section holds every row");
 
 // In host code this name is only a host-side handle, not a device address;
 // the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaTotalBytes];
+
+// The gradient pointers of one call's blocks, passed by value.
+struct NaPtrFill {
+    int32_t n;
+    int32_t id[cow::kMaxRayIds];
+    float *p[cow::kMaxRayIds][4];  // grid, planes xy, xz, yz (entries may be null)
+};
+
+// table[id] = grid gradient, table[nb + 3 id + k] = plane k gradient: the
+// layout the backward kernels index by block id.
+__global__ void k_noalloc_fill_ptrs(float **table, int32_t nb, const __grid_constant__ NaPtrFill f) {
+    const int k = threadIdx.x;
+    if (k >= f.n) return;
+    const int id = f.id[k];
+    table[id] = f.p[k][0];
+    for (int q = 0; q < 3; q++) table[nb + 3 * id + q] = f.p[k][1 + q];
+}
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
@@ -1597,7 +1620,7 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !aux || !dL_drgb || !grad_grid || !grad_planes || !grad_mlp)
         return fail(COW_ERR_INVALID_ARG, "cow_render_backward_noalloc: null argument");
-    if (n_rays > kNoAllocMaxRays)
+    if (n_rays > kNoAllocMaxRays || cow::backward_rows(n_rays) > kNaRows)
         return fail(COW_ERR_INVALID_ARG, "cow_render_backward_noalloc: %lld rays exceed its maximum of %lld per call",
                     (long long)n_rays, (long long)kNoAllocMaxRays);
     const int32_t nb = (int32_t)ctx->blocks.size();
@@ -1615,15 +1638,20 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     for (const void *q : {(const void *)o, (const void *)d, (const void *)aux, (const void *)dL_drgb, (const void *)grad_mlp, (const void *)mlp})
         if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "backward arrays and the MLP must be device memory");
     if (((uintptr_t)aux & 15u)) return fail(COW_ERR_INVALID_ARG, "aux must be 16-byte aligned");
-    float *table[kNoAllocMaxBlocks * 4];  // on the stack: the call allocates nothing, host or device
-    for (int32_t i = 0; i < nb; i++) {
-        table[i] = grad_grid[i];
-        for (int k = 0; k < 3; k++) table[nb + 3 * i + k] = grad_planes[3 * i + k];
+    for (int32_t i = 0; i < nb; i++)
         for (int k = 0; k < 4; k++) {
             const float *q = k == 0 ? grad_grid[i] : grad_planes[3 * i + k - 1];
             if (q && (((uintptr_t)q & 15u) || !is_device_ptr(q)))
                 return fail(COW_ERR_INVALID_ARG, "block %d: gradient arrays must be 16-byte aligned device memory", i);
         }
+    NaPtrFill fill;
+    std::memset(&fill, 0, sizeof(fill));
+    fill.n = n_ids;
+    for (int32_t k = 0; k < n_ids; k++) {
+        const int32_t id = ids[k];
+        fill.id[k] = id;
+        fill.p[k][0] = grad_grid[id];
+        for (int q = 0; q < 3; q++) fill.p[k][1 + q] = grad_planes[3 * id + q];
     }
     DeviceGuard dg(ctx->device);
     unsigned char *scratch = nullptr;
@@ -1633,7 +1661,8 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     float *gcf = (float *)(scratch + kNaRowsBytes);
     float **dptrs = (float **)(scratch + kNaRowsBytes + kNaGcfBytes);
     cudaStream_t st = (cudaStream_t)stream;
-    COW_CUDA(cudaMemcpyAsync(dptrs, table, (size_t)nb * 4 * sizeof(float *), cudaMemcpyHostToDevice, st));
+    k_noalloc_fill_ptrs<<<1, cow::kMaxRayIds, 0, st>>>(dptrs, nb, fill);
+    COW_CUDA(cudaGetLastError());
     cow::BwdArgs a;
     std::memset(&a, 0, sizeof(a));
     a.dtype = ctx->dtype;

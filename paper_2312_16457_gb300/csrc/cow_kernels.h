@@ -99,6 +99,9 @@ struct RegArgs {                  // the blocks that take part come by value (Ra
 };
 cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st);
 cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st);
+// threads per CTA of the backward kernels: one MLP-gradient scratch row per
+// CTA, backward_rows(n) = ceil(n / kBwdCtaThreads)
+constexpr int kBwdCtaThreads = 128;
 int backward_rows(int64_t n_rays);
 cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream_t st);
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,

@@ -13,6 +13,7 @@ import torch
 
 import oracle
 from paper_2312_16457_gb300 import cow, synth, train
+from gradcheck import assert_grad
 
 pytestmark = pytest.mark.gpu
 
@@ -195,12 +196,6 @@ def test_ray_form_argument_errors():
     assert torch.isfinite(rgb).all()
 
 
-def _rel(a, b):
-    a = np.asarray(a, np.float64).ravel()
-    b = np.asarray(b, np.float64).ravel()
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 @pytest.mark.parametrize("storage", ["fp32", "bf16"])
 def test_ray_form_backward_matches_oracle_gradient(storage):
     """cow_render_backward_block_mlps against the oracle's FP64 adjoint of the
@@ -223,15 +218,15 @@ def test_ray_form_backward_matches_oracle_gradient(storage):
     osc = oracle.OracleScene(sc, values="master" if storage == "fp32" else storage)
     og, op, om = oracle.render_rays_block_mlp_grad(osc, ids, o, d, w, L, g)
     for b in range(n):
-        assert _rel(gg[b].cpu().numpy(), og[b]) <= 1e-3, ("grid", b)
+        assert_grad(gg[b].cpu().numpy(), og[b], str(("grid", b)))
         for k in range(3):
-            assert _rel(gp[b][k].cpu().numpy(), op[b][k]) <= 1e-3, ("plane", b, k)
-        assert _rel(gm[b].cpu().numpy(), om[b]) <= 1e-3, ("mlp", b)
+            assert_grad(gp[b][k].cpu().numpy(), op[b][k], str(("plane", b, k)))
+        assert_grad(gm[b].cpu().numpy(), om[b], str(("mlp", b)))
     assert max(np.abs(x).max() for x in og) > 1e-4 and np.abs(om).max() > 1e-3
     # a second call accumulates
     ctx.render_backward_block_mlps(o.cuda(), d.cuda(), ids, torch.from_numpy(g).cuda(), gg, gp, gm)
     ctx.sync_check()
-    assert _rel(gm.cpu().numpy(), 2 * om) <= 1e-3
+    assert_grad(gm.cpu().numpy(), 2 * om, "mlp")
 
 
 def test_fit_with_block_mlps_reduces_loss():

@@ -26,6 +26,7 @@ import torch
 
 import oracle
 from paper_2312_16457_gb300 import cow, synth
+from gradcheck import assert_grad
 
 pytestmark = pytest.mark.gpu
 
@@ -166,12 +167,6 @@ def test_batch_64_views_sampled():
 # 2^20 random rays over 2x2 FP32 blocks (the differentiation benchmark)
 
 
-def _rel(a, b):
-    a = np.asarray(a, np.float64).ravel()
-    b = np.asarray(b, np.float64).ravel()
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def test_fit_2x2_full_launch_sampled_rays():
     sc, _, o, d, mlp, _ = synth.workload_grad(device="cuda")
     n = o.shape[0]
@@ -202,13 +197,13 @@ def test_fit_2x2_full_launch_sampled_rays():
     og, op, om = oracle.render_rays_grad(osc, ids, o_s, d_s, mlp, g[pick])
     for b in range(4):
         if np.abs(og[b]).max() > 0:
-            assert _rel(gg[b].cpu().numpy(), og[b]) <= 1e-3, ("grid", b)
+            assert_grad(gg[b].cpu().numpy(), og[b], str(("grid", b)))
         else:
             assert float(gg[b].abs().max()) == 0.0, ("grid", b)
         for k in range(3):
             if np.abs(op[b][k]).max() > 0:
-                assert _rel(gp[b][k].cpu().numpy(), op[b][k]) <= 1e-3, ("plane", b, k)
+                assert_grad(gp[b][k].cpu().numpy(), op[b][k], str(("plane", b, k)))
             else:
                 assert float(gp[b][k].abs().max()) == 0.0, ("plane", b, k)
-    assert _rel(gm.cpu().numpy(), om) <= 1e-3
+    assert_grad(gm.cpu().numpy(), om, "mlp")
     assert sum(np.count_nonzero(x) for x in og) > 1000

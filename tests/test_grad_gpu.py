@@ -8,6 +8,7 @@ import torch
 
 import oracle
 from paper_2312_16457_gb300 import cow, synth, train
+from gradcheck import assert_grad
 
 pytestmark = pytest.mark.gpu
 
@@ -56,10 +57,10 @@ def test_backward_matches_oracle_gradient(storage):
     assert np.array_equal(ns.cpu().numpy(), n_o)
     assert (n_o > 0).mean() > 0.5
     for b in range(4):
-        assert _rel(gg[b].cpu().numpy(), og[b]) <= 1e-3, ("grid", b)
+        assert_grad(gg[b].cpu().numpy(), og[b], str(("grid", b)))
         for k in range(3):
-            assert _rel(gp[b][k].cpu().numpy(), op[b][k]) <= 1e-3, ("plane", b, k)
-    assert _rel(gm.cpu().numpy(), om) <= 1e-3
+            assert_grad(gp[b][k].cpu().numpy(), op[b][k], str(("plane", b, k)))
+    assert_grad(gm.cpu().numpy(), om, "mlp")
     assert np.abs(om).max() > 1e-3 and max(np.abs(x).max() for x in og) > 1e-4
 
 

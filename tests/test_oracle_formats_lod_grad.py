@@ -6,6 +6,7 @@ import pytest
 import torch
 
 from paper_2312_16457_gb300 import synth
+from ztop_cases import ztop_case_scene, ztop_golden_cases
 
 
 # ---------------------------------------------------------------------------
@@ -222,3 +223,21 @@ def test_gradient_matches_finite_differences(orc):
         assert abs(fd - gr[j]) <= 1e-4 * max(abs(fd), 1e-3), (fd, gr[j])
         checked += 1
     assert checked >= 64
+
+
+# ---------------------------------------------------------------------------
+# z_top (Appendix D: the height of the highest part within the block)
+
+
+def test_block_ztop_hand_values(orc):
+    """orc_block_ztop against z_top worked out by hand: an empty block, one
+    dense vertex on and off cell boundaries, slabs ending on and inside a
+    cell, cell edges 3 and 4, and R - 1 not a multiple of the cell edge (the
+    clamp to the top vertex).  A reading of the top as the highest row's
+    bottom vertex (c C), or without the clamp, fails several rows."""
+    cases = ztop_golden_cases()
+    assert len(cases) >= 12
+    for R, C, zlo, zhi, kind, k, want in cases:
+        osc = orc.OracleScene(ztop_case_scene(R, C, zlo, zhi, kind, k))
+        got = osc.ztop(0)
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (R, C, zlo, zhi, kind, k, got, want)

@@ -59,6 +59,18 @@ def test_occupancy_bit_exact():
         assert ctx2.ztop(i) == oracle.OracleScene(city).ztop(i)
 
 
+def test_block_ztop_hand_values():
+    """The library's z_top (App. D) against the hand-worked values of
+    tests/golden/block_ztop.txt (the oracle is pinned to the same rows)."""
+    from ztop_cases import ztop_case_scene, ztop_golden_cases
+
+    for R, C, zlo, zhi, kind, k, want in ztop_golden_cases():
+        ctx = cow.Context(ztop_case_scene(R, C, zlo, zhi, kind, k), "fp32")
+        got = ctx.ztop(0)
+        ctx.close()
+        assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (R, C, zlo, zhi, kind, k, got, want)
+
+
 def _coarse_bits(words, nc):
     """Numpy OR over 4^3 groups of an occupancy bit array (z, y, x order)."""
     n = nc ** 3

@@ -8,6 +8,7 @@ import torch
 
 import oracle
 from paper_2312_16457_gb300 import cow, synth, train
+from gradcheck import assert_grad
 
 pytestmark = pytest.mark.gpu
 
@@ -23,12 +24,6 @@ def _gpu():
     torch.cuda.set_device(0)
 
 
-def _rel(a, b):
-    a = np.asarray(a, np.float64).ravel()
-    b = np.asarray(b, np.float64).ravel()
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
 def _zeros(sc):
     gg = [torch.zeros(b.grid.shape, device="cuda") for b in sc.blocks]
     gp = [[torch.zeros(p.shape, device="cuda") for p in b.planes] for b in sc.blocks]
@@ -37,9 +32,9 @@ def _zeros(sc):
 
 def _check_grads(gg, gp, og, op):
     for b in range(len(gg)):
-        assert _rel(gg[b].cpu().numpy(), og[b]) <= 1e-3, ("grid", b)
+        assert_grad(gg[b].cpu().numpy(), og[b], str(("grid", b)))
         for k in range(3):
-            assert _rel(gp[b][k].cpu().numpy(), op[b][k]) <= 1e-3, ("plane", b, k)
+            assert_grad(gp[b][k].cpu().numpy(), op[b][k], str(("plane", b, k)))
         assert torch.all(gg[b][..., 1:] == 0)
 
 

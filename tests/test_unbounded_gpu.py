@@ -10,6 +10,7 @@ import torch
 
 import oracle
 from paper_2312_16457_gb300 import cow, synth
+from gradcheck import assert_grad
 
 pytestmark = pytest.mark.gpu
 
@@ -25,12 +26,6 @@ def _gpu():
     build.build()
     oracle.build()
     torch.cuda.set_device(0)
-
-
-def _rel(a, b):
-    a = np.asarray(a, np.float64).ravel()
-    b = np.asarray(b, np.float64).ravel()
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
 @pytest.mark.parametrize("schedule", ["thread_const", "thread", "warp"])
@@ -72,10 +67,10 @@ def test_ray_form_and_gradient():
     ctx.sync_check()
     og, op, om = oracle.render_rays_grad(osc, ids, o, d, mlp, g)
     for b in range(4):
-        assert _rel(gg[b].cpu().numpy(), og[b]) <= 1e-3
+        assert_grad(gg[b].cpu().numpy(), og[b], f"grid {b}")
         for k in range(3):
-            assert _rel(gp[b][k].cpu().numpy(), op[b][k]) <= 1e-3
-    assert _rel(gm.cpu().numpy(), om) <= 1e-3
+            assert_grad(gp[b][k].cpu().numpy(), op[b][k], f"plane {b} {k}")
+    assert_grad(gm.cpu().numpy(), om, "mlp")
 
 
 def test_batched_and_block_mlp_forms():
@@ -125,6 +120,6 @@ def test_regularisers_through_unbounded_blocks():
     assert abs(float(ls.item()) - ols) <= 1e-4 * ols
     assert abs(float(lo.item()) - olo) <= 1e-4 * olo
     for b in range(4):
-        assert _rel(gg[b].cpu().numpy(), sg[b] + og[b]) <= 1e-3
+        assert_grad(gg[b].cpu().numpy(), sg[b] + og[b], f"grid {b}")
         for k in range(3):
-            assert _rel(gp[b][k].cpu().numpy(), sp[b][k] + op[b][k]) <= 1e-3
+            assert_grad(gp[b][k].cpu().numpy(), sp[b][k] + op[b][k], f"plane {b} {k}")
