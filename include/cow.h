@@ -62,8 +62,23 @@ typedef enum cow_status {
  * COW_BF16_FP8: the grid in BF16 and the three planes in FP8-E4M3 with
  * per-channel power-of-two scales, the planes in a quad layout (one 32-byte
  * element holds the 2x2 texels of a bilinear footprint), so a sample takes 7
- * gathers instead of 10. */
-typedef enum cow_dtype { COW_FP32 = 0, COW_FP16 = 1, COW_BF16 = 2, COW_FP8_E4M3 = 3, COW_BF16_FP8 = 4 } cow_dtype;
+ * gathers instead of 10.
+ * COW_FP8_BF16D: FP8-E4M3 features with per-channel power-of-two scales,
+ * except the grid's channel 0 (log-density), which is kept in BF16 (no
+ * scale): E4M3's 3-bit mantissa on a log-density near 3 moves sigma by up to
+ * 13 %, more than the precision form's 1e-2 colour bound allows, while the
+ * colour and specular channels and the planes' small values keep it.  The
+ * grid and planes are stored in the quad layout (2 x 2 FP8 vertices or texels
+ * in 32 bytes) and the density as the eight corners of each voxel (16
+ * bytes), so a sample takes 6 gathers (176 bytes). */
+typedef enum cow_dtype {
+    COW_FP32 = 0,
+    COW_FP16 = 1,
+    COW_BF16 = 2,
+    COW_FP8_E4M3 = 3,
+    COW_BF16_FP8 = 4,
+    COW_FP8_BF16D = 5
+} cow_dtype;
 
 /* One baked block at one level of detail (Sec. 4.1: f^{k,l}; LOD l merges 2x2
  * blocks of level l-1, Sec. 4.1 and Sec. 4.4). */
@@ -109,6 +124,27 @@ typedef struct cow_ctx cow_ctx;
  * OOM, CUDA. */
 cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
                            float occ_thresh, int32_t occ_cell, void *stream);
+
+/* Load flags of cow_load_blocks_ex. */
+#define COW_LOAD_BRICKS 1u /* brick-sparse grids (below) */
+
+/* cow_load_blocks with load flags (0 = cow_load_blocks).
+ * COW_LOAD_BRICKS stores every grid brick-sparse, the GPU form of the sparse
+ * voxel grid behind an indirection table that the paper's baked blocks use
+ * (Sec. 3 on MERF / SNeRG-style representations, Sec. 4.5 baking): the grid
+ * is cut into bricks of 16 voxels per edge (one coarse occupancy cell, 4 x 4 x
+ * 4 cells of occ_cell = 4 voxels); only bricks with an occupied cell are
+ * stored, each with the grid elements of its voxels (a halo of one vertex on
+ * the far faces), and a per-block table of ceil((R-1)/16)^3 int32 slots
+ * (-1 = empty brick) maps a voxel to its brick.  Lattice samples lie in
+ * occupied cells, whose bricks are stored, so renders, ray batches and
+ * gradients equal those of the dense grid bit for bit.  Device memory is the
+ * stored bricks (about 1.13x their voxels in the pair layout) plus the table.
+ * Errors as cow_load_blocks; UNSUPPORTED for occ_cell != 4.  On a
+ * brick-sparse context cow_sparsity_loss (it samples arbitrary points) and
+ * cow_export_packed of the grid return UNSUPPORTED. */
+cow_status cow_load_blocks_ex(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
+                              float occ_thresh, int32_t occ_cell, uint32_t load_flags, void *stream);
 
 /* Release a context and all its device memory (NULL is accepted). */
 cow_status cow_free(cow_ctx *ctx);
@@ -523,7 +559,11 @@ cow_status cow_export_occupancy_coarse(const cow_ctx *ctx, int32_t block, uint32
  * count x 8 x element size).  On the device FP16 / BF16 / FP8 are held in a
  * pair layout (each element also carries the next vertex of its row, so one
  * 32- or 16-byte load returns both corners of an interpolation pair): twice
- * the memory of the natural layout. */
+ * the memory of the natural layout.  For COW_FP8_BF16D, tensor 0 is the FP8
+ * grid (all 8 channels; the kernels read channel 0 from tensor 4) and tensor
+ * 4 the grid's BF16 channel 0, one value per vertex (scale exponents 0).
+ * Errors: INVALID_ARG (block or tensor out of range, nbytes too small),
+ * UNSUPPORTED (the grid of a brick-sparse context), CUDA. */
 cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, void *out, int64_t nbytes,
                              int32_t *out_scale_exp);
 

@@ -206,9 +206,10 @@ class OracleScene:
     computed by the oracle itself.
 
     values: "master" (FP32 arrays as given), or a storage format name
-    ("fp16", "bf16", "fp8", or "bf16_fp8" for a BF16 grid with FP8 planes) to
-    run on the oracle's own dequantisation of the master, or "f64" to hold
-    float64 copies (finite differences)."""
+    ("fp16", "bf16", "fp8", "bf16_fp8" for a BF16 grid with FP8 planes, or
+    "fp8_bf16d" for FP8 everywhere but the grid's log-density channel, which
+    is BF16) to run on the oracle's own dequantisation of the master, or "f64"
+    to hold float64 copies (finite differences)."""
 
     def __init__(self, scene, values: str = "master"):
         self.scene = scene
@@ -224,9 +225,12 @@ class OracleScene:
             g = _np(b.grid, np.float64 if f64 else np.float32)
             pls = [_np(p, np.float64 if f64 else np.float32) for p in b.planes]
             bits = occupancy(_np(b.grid), b.R, scene.occ_cell, scene.occ_thresh)
-            if values in ("fp16", "bf16", "fp8", "bf16_fp8"):
-                gv, pv = (values, values) if values != "bf16_fp8" else ("bf16", "fp8")
-                g = quantize(g, gv, channel_scale_exps(g, gv))[1].reshape(g.shape)
+            if values in ("fp16", "bf16", "fp8", "bf16_fp8", "fp8_bf16d"):
+                gv, pv = {"bf16_fp8": ("bf16", "fp8"), "fp8_bf16d": ("fp8", "fp8")}.get(values, (values, values))
+                gq = quantize(g, gv, channel_scale_exps(g, gv))[1].reshape(g.shape)
+                if values == "fp8_bf16d":  # the log-density channel of the grid in BF16, unscaled
+                    gq[..., 0] = quantize(g[..., 0], "bf16")[1].reshape(g.shape[:-1])
+                g = gq
                 pls = [quantize(p, pv, channel_scale_exps(p, pv))[1].reshape(p.shape) for p in pls]
             ob = self.blocks[i]
             ob.lo[:] = [float(v) for v in b.lo]

@@ -16,8 +16,10 @@ import torch
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcow.so")
 _lib = None
 
-# "bf16_fp8": BF16 grid, FP8-E4M3 planes (quad layout)
-DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3, "bf16_fp8": 4}
+# "bf16_fp8": BF16 grid, FP8-E4M3 planes (quad layout); "fp8_bf16d": FP8-E4M3
+# features with the grid's log-density channel in BF16
+DTYPES = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3, "bf16_fp8": 4, "fp8_bf16d": 5}
+LOAD_BRICKS = 1
 ELEM_BYTES = {"fp32": 4, "fp16": 2, "bf16": 2, "fp8": 1}
 
 
@@ -25,13 +27,15 @@ def tensor_storage(storage: str, tensor: int) -> str:
     """Storage of tensor 0 (grid) or 1-3 (planes) of a context."""
     if storage == "bf16_fp8":
         return "bf16" if tensor == 0 else "fp8"
+    if storage == "fp8_bf16d":
+        return "bf16" if tensor == 4 else "fp8"
     return storage
 FLAG_MLP_BF16 = 1
 FLAG_BLOCK_MLPS = 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE_ASSERT"}
 
 # every symbol include/cow.h declares
-EXPORTS = ["cow_load_blocks", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
+EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
@@ -80,6 +84,7 @@ def lib():
         P, i32, i64, dbl, flt, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float, C.c_uint32
         sig = {
             "cow_load_blocks": [P, P, i32, i32, flt, i32, P],
+            "cow_load_blocks_ex": [P, P, i32, i32, flt, i32, u32, P],
             "cow_free": [P],
             "cow_num_blocks": [P, P],
             "cow_block_ztop": [P, i32, P],
@@ -166,8 +171,11 @@ class Context:
     """A packed scene on one GPU (wraps cow_ctx)."""
 
     def __init__(self, scene, storage: str = "fp32", occ_thresh: Optional[float] = None,
-                 occ_cell: Optional[int] = None, stream=None):
+                 occ_cell: Optional[int] = None, stream=None, bricks: bool = False):
+        """bricks=True stores the grids brick-sparse (cow_load_blocks_ex with
+        COW_LOAD_BRICKS): only the 16^3-voxel bricks with occupied cells."""
         self.storage = storage
+        self.bricks = bricks
         self.scene = scene
         n = len(scene.blocks)
         descs = (BlockDesc * n)()
@@ -186,8 +194,8 @@ class Context:
         self._ctx = C.c_void_p()
         th = scene.occ_thresh if occ_thresh is None else occ_thresh
         cc = scene.occ_cell if occ_cell is None else occ_cell
-        _check(lib().cow_load_blocks(C.byref(self._ctx), descs, n, DTYPES[storage], float(th), int(cc),
-                                     _stream_ptr(stream)))
+        _check(lib().cow_load_blocks_ex(C.byref(self._ctx), descs, n, DTYPES[storage], float(th), int(cc),
+                                        LOAD_BRICKS if bricks else 0, _stream_ptr(stream)))
         self.n_blocks = n
         self.schedule = "thread_const"  # the library default
         for i, b in enumerate(scene.blocks):
@@ -428,7 +436,7 @@ class Context:
 
     def packed(self, i: int, tensor: int):
         b = self.scene.blocks[i]
-        n = (b.R ** 3 if tensor == 0 else b.P ** 2) * 8
+        n = b.R ** 3 if tensor == 4 else (b.R ** 3 if tensor == 0 else b.P ** 2) * 8
         dt = {"fp32": np.float32, "fp16": np.uint16, "bf16": np.uint16,
               "fp8": np.uint8}[tensor_storage(self.storage, tensor)]
         out = np.zeros(n, dt)

@@ -226,6 +226,7 @@ cudaError_t launch_march_batch(const BatchArgs &a, int tile_cfg, int grid, cudaS
     case kBF16: return launch_dt<kBF16>(a, tile_cfg, grid, st);
     case kFP8: return launch_dt<kFP8>(a, tile_cfg, grid, st);
     case kMixed: return launch_dt<kMixed>(a, tile_cfg, grid, st);
+    case kFP8D: return launch_dt<kFP8D>(a, tile_cfg, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -738,6 +738,7 @@ cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream
     case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kMixed: k_remarch_backward<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8D: k_remarch_backward<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -753,6 +754,7 @@ cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cu
     case kBF16: k_bm_pass1<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_bm_pass1<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kMixed: k_bm_pass1<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8D: k_bm_pass1<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();
@@ -765,6 +767,7 @@ cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cu
     case kBF16: k_bm_remarch<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_bm_remarch<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kMixed: k_bm_remarch<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8D: k_bm_remarch<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -779,6 +782,7 @@ cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st
     case kBF16: k_sparsity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_sparsity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kMixed: k_sparsity<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8D: k_sparsity<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -793,6 +797,7 @@ cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st)
     case kBF16: k_opacity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kFP8: k_opacity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     case kMixed: k_opacity<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
+    case kFP8D: k_opacity<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

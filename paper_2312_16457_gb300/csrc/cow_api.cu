@@ -44,20 +44,34 @@ using namespace cowi;
 namespace {
 
 // storage of tensor t (0 grid, 1-3 planes) of a context: the mixed format
-// keeps the grid in BF16 and the planes in FP8
+// keeps the grid in BF16 and the planes in FP8; the FP8 format with BF16
+// density stores every tensor in FP8 (the grid's channel 0 again in BF16)
 int tensor_dtype(int dtype, int t) {
     if (dtype == COW_BF16_FP8) return t == 0 ? COW_BF16 : COW_FP8_E4M3;
+    if (dtype == COW_FP8_BF16D) return COW_FP8_E4M3;
     return dtype;
 }
 
 int elem_bytes(int dtype) { return dtype == COW_FP32 ? 4 : dtype == COW_FP8_E4M3 ? 1 : 2; }
 
-// bytes of one packed element (a vertex, or a vertex pair in the pair layout)
 // bytes of one packed element: an FP32 vertex, a pair of 16- or 8-bit
-// vertices, or (mixed planes) a 2x2 quad of FP8 texels -- 32 bytes for the
-// mixed format's grid and planes alike
+// vertices, or a 2x2 quad of FP8 vertices / texels (the planes of the mixed
+// format, the grid and planes of the FP8 format with BF16 density) -- 32
+// bytes for every format but pure FP8 (16)
 int64_t packed_elem_bytes(int dtype) {
-    return dtype == COW_FP32 || dtype == COW_BF16_FP8 ? 32 : 2 * 8 * elem_bytes(dtype);
+    return dtype == COW_FP32 || dtype == COW_BF16_FP8 || dtype == COW_FP8_BF16D ? 32 : 2 * 8 * elem_bytes(dtype);
+}
+
+// element layout of the grid (k_pack_grid) and its element counts per brick
+// axis (the layout's halo: a paired axis needs no extra element)
+int grid_layout(int dtype) {
+    return dtype == COW_FP32 ? cow::kLayNat : dtype == COW_FP8_BF16D ? cow::kLayQuad8 : cow::kLayPair;
+}
+void brick_dims(int dtype, int *ex, int *ey, int *ez) {
+    const int lay = grid_layout(dtype);
+    *ex = cow::kBrick + (lay == cow::kLayNat ? 1 : 0);
+    *ey = cow::kBrick + (lay == cow::kLayQuad8 ? 0 : 1);
+    *ez = cow::kBrick + 1;
 }
 
 // smallest e with amax <= 448 * 2^e (e = 0 for an all-zero channel)
@@ -91,6 +105,8 @@ void destroy(cow_ctx *c) {
         cudaFree(b.occ);
         cudaFree(b.occ2);
         cudaFree(b.scale);
+        cudaFree(b.brick_tab);
+        cudaFree(b.brick_list);
         for (auto *h : b.host_feat)
             if (h) cudaFreeHost(h);
     }
@@ -127,96 +143,15 @@ double block_ztop(const BlockHost &b, const std::vector<uint32_t> &bits, int C) 
     return (double)b.lo[2];
 }
 
-// Re-pack the features of an existing block from new FP32 masters (occupancy
-// and z_top unchanged); FP8 scales are recomputed.
-cow_status repack_block(cow_ctx *c, BlockHost &b, const float *const src_in[4], void *staging, unsigned *d_amax,
-                        float *d_inv, cudaStream_t st) {
-    const int64_t nv[4] = {(int64_t)b.R * b.R * b.R, (int64_t)b.P * b.P, (int64_t)b.P * b.P, (int64_t)b.P * b.P};
-    void *dst[4] = {b.grid, b.planes[0], b.planes[1], b.planes[2]};
-    float scale_h[32];
-    for (int t = 0; t < 4; t++) {
-        const float *s = src_in[t];
-        if (!is_device_ptr(s)) {
-            COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
-            s = (const float *)staging;
-        }
-        int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (tensor_dtype(c->dtype, t) == COW_FP8_E4M3) {
-            COW_CUDA(cow::launch_amax8(s, nv[t], d_amax, st));
-            unsigned amax_bits[8];
-            COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
-            COW_CUDA(cudaStreamSynchronize(st));
-            for (int k = 0; k < 8; k++) {
-                float a;
-                std::memcpy(&a, &amax_bits[k], 4);
-                e[k] = fp8_exponent(a);
-            }
-        }
-        float inv[8];
-        for (int k = 0; k < 8; k++) {
-            b.scale_exp[t][k] = e[k];
-            inv[k] = std::ldexp(1.0f, -e[k]);
-            scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
-        }
-        COW_CUDA(cudaMemcpyAsync(d_inv + 8 * t, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
-        if (c->dtype == COW_BF16_FP8 && t > 0) COW_CUDA(cow::launch_pack_quad8(s, b.P, d_inv + 8 * t, dst[t], st));
-        else COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? b.R : b.P, tensor_dtype(c->dtype, t), d_inv + 8 * t, dst[t], st));
-    }
-    COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
-    return COW_OK;
-}
-
-cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *staging, unsigned *d_amax,
-                    float *d_inv, double log_thresh, cudaStream_t st) {
-    const int64_t nv[4] = {(int64_t)d.grid_res * d.grid_res * d.grid_res, (int64_t)d.plane_res * d.plane_res,
-                           (int64_t)d.plane_res * d.plane_res, (int64_t)d.plane_res * d.plane_res};
-    const float *src[4] = {d.grid, d.planes[0], d.planes[1], d.planes[2]};
-    void **dst[4] = {&b.grid, &b.planes[0], &b.planes[1], &b.planes[2]};
-    const int Nc = (d.grid_res - 1 + c->occ_cell - 1) / c->occ_cell;
-    b.occ_words = ((int64_t)Nc * Nc * Nc + 31) / 32;
-    COW_CUDA(cudaMalloc((void **)&b.occ, (size_t)b.occ_words * 4));
-    COW_CUDA(cudaMalloc((void **)&b.scale, 32 * sizeof(float)));
-    float scale_h[32];
-    for (int t = 0; t < 4; t++) {
-        COW_CUDA(cudaMalloc(dst[t], (size_t)(nv[t] * packed_elem_bytes(c->dtype))));
-        const float *s = src[t];
-        if (!is_device_ptr(s)) {
-            COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
-            s = (const float *)staging;
-        }
-        int e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (tensor_dtype(c->dtype, t) == COW_FP8_E4M3) {
-            COW_CUDA(cow::launch_amax8(s, nv[t], d_amax, st));
-            unsigned amax_bits[8];
-            COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
-            COW_CUDA(cudaStreamSynchronize(st));
-            for (int k = 0; k < 8; k++) {
-                float a;
-                std::memcpy(&a, &amax_bits[k], 4);
-                e[k] = fp8_exponent(a);
-            }
-        }
-        float inv[8];
-        for (int k = 0; k < 8; k++) {
-            b.scale_exp[t][k] = e[k];
-            inv[k] = std::ldexp(1.0f, -e[k]);
-            scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
-        }
-        COW_CUDA(cudaMemcpyAsync(d_inv, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
-        if (c->dtype == COW_BF16_FP8 && t > 0) COW_CUDA(cow::launch_pack_quad8(s, d.plane_res, d_inv, *dst[t], st));
-        else COW_CUDA(cow::launch_pack(s, nv[t], t == 0 ? d.grid_res : d.plane_res, tensor_dtype(c->dtype, t), d_inv,
-                                       *dst[t], st));
-        if (t == 0) COW_CUDA(cow::launch_occupancy(s, d.grid_res, c->occ_cell, log_thresh, b.occ, st));
-        // the staging buffer and d_inv are reused by the next tensor: the
-        // stream orders the next copies after these kernels
-    }
-    COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
+// After the occupancy kernel: z_top, the coarse occupancy level (the OR
+// over each group of kOccGroup^3 cells, clipped at the far faces) and, for a
+// brick-sparse context, the brick table (a brick is one coarse cell; it is
+// stored when its coarse bit is set).
+cow_status build_occupancy_levels(cow_ctx *c, BlockHost &b, int Nc, cudaStream_t st) {
     std::vector<uint32_t> bits((size_t)b.occ_words);
     COW_CUDA(cudaMemcpyAsync(bits.data(), b.occ, (size_t)b.occ_words * 4, cudaMemcpyDeviceToHost, st));
     COW_CUDA(cudaStreamSynchronize(st));
     b.ztop = block_ztop(b, bits, c->occ_cell);
-    // coarse level of the occupancy grid: the OR over each group of
-    // kOccGroup^3 cells (clipped at the far faces)
     const int Nc2 = (Nc + cow::kOccGroup - 1) / cow::kOccGroup;
     std::vector<uint32_t> coarse(((size_t)Nc2 * Nc2 * Nc2 + 31) / 32, 0u);
     for (int z = 0; z < Nc; z++)
@@ -231,6 +166,158 @@ cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *sta
     b.occ2_words = (int64_t)coarse.size();
     COW_CUDA(cudaMalloc((void **)&b.occ2, coarse.size() * 4));
     COW_CUDA(cudaMemcpy(b.occ2, coarse.data(), coarse.size() * 4, cudaMemcpyHostToDevice));
+    if (!c->bricks) return COW_OK;
+    // brick = coarse cell: kOccGroup cells of occ_cell (= 4) voxels = kBrick voxels
+    const int nb = Nc2;
+    std::vector<int32_t> tab((size_t)nb * nb * nb, -1), list;
+    for (int64_t k = 0; k < (int64_t)nb * nb * nb; k++)
+        if ((coarse[(size_t)(k >> 5)] >> (k & 31)) & 1u) {
+            tab[(size_t)k] = (int32_t)list.size();
+            list.push_back((int32_t)k);
+        }
+    b.Nb = nb;
+    b.n_bricks = (int32_t)list.size();
+    COW_CUDA(cudaMalloc((void **)&b.brick_tab, tab.size() * 4));
+    COW_CUDA(cudaMemcpy(b.brick_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice));
+    COW_CUDA(cudaMalloc((void **)&b.brick_list, std::max<size_t>(list.size(), 1) * 4));
+    if (!list.empty()) COW_CUDA(cudaMemcpy(b.brick_list, list.data(), list.size() * 4, cudaMemcpyHostToDevice));
+    return COW_OK;
+}
+
+// Elements of a block's packed grid: dense R^3, or its stored bricks; and
+// (FP8 with BF16 density) of the density octets that follow them.
+int64_t grid_elems(const cow_ctx *c, const BlockHost &b) {
+    if (b.Nb == 0) return (int64_t)b.R * b.R * b.R;
+    int ex, ey, ez;
+    brick_dims(c->dtype, &ex, &ey, &ez);
+    return (int64_t)b.n_bricks * ex * ey * ez;
+}
+int64_t dens_elems(const cow_ctx *c, const BlockHost &b) {
+    if (c->dtype != COW_FP8_BF16D) return 0;
+    return b.Nb == 0 ? (int64_t)b.R * b.R * b.R : (int64_t)b.n_bricks * cow::kDensBrickElems;
+}
+int64_t grid_main_bytes(const cow_ctx *c, const BlockHost &b) { return grid_elems(c, b) * packed_elem_bytes(c->dtype); }
+
+// Pack the grid master s (device, R^3 x 8) into b.grid (and its density
+// octets); d_inv: the grid's 8 inverse channel scales (device).
+cow_status pack_grid(cow_ctx *c, BlockHost &b, const float *s, const float *d_inv, cudaStream_t st) {
+    const int R = b.R;
+    if (b.Nb == 0 && c->dtype != COW_FP8_BF16D) {
+        COW_CUDA(cow::launch_pack(s, (int64_t)R * R * R, R, tensor_dtype(c->dtype, 0), d_inv, b.grid, st));
+        return COW_OK;
+    }
+    int ex, ey, ez;
+    brick_dims(c->dtype, &ex, &ey, &ez);
+    const bool sparse = b.Nb > 0;
+    const int sy = sparse ? ex : R, sz = sparse ? ex * ey : R * R, belem = sparse ? ex * ey * ez : 0;
+    COW_CUDA(cow::launch_pack_grid(s, R, grid_elems(c, b), sy, sz, belem, sparse ? b.brick_list : nullptr, b.Nb,
+                                   tensor_dtype(c->dtype, 0), grid_layout(c->dtype), d_inv, b.grid, st));
+    if (c->dtype == COW_FP8_BF16D) {
+        void *dens = (unsigned char *)b.grid + grid_main_bytes(c, b);
+        const int dsy = sparse ? cow::kBrick : R, dsz = sparse ? cow::kBrick * cow::kBrick : R * R;
+        COW_CUDA(cow::launch_pack_grid(s, R, dens_elems(c, b), dsy, dsz, sparse ? cow::kDensBrickElems : 0,
+                                       sparse ? b.brick_list : nullptr, b.Nb, COW_BF16, cow::kLayOct16, nullptr, dens,
+                                       st));
+    }
+    return COW_OK;
+}
+
+// FP8 scale exponents of one tensor (8 channels) from its device master:
+// e[k] = 0 unless the tensor is stored in FP8.
+cow_status fp8_exponents(const cow_ctx *c, int t, const float *s, int64_t nv, unsigned *d_amax, cudaStream_t st,
+                         int e[8]) {
+    for (int k = 0; k < 8; k++) e[k] = 0;
+    if (tensor_dtype(c->dtype, t) != COW_FP8_E4M3) return COW_OK;
+    COW_CUDA(cow::launch_amax8(s, nv, d_amax, st));
+    unsigned amax_bits[8];
+    COW_CUDA(cudaMemcpyAsync(amax_bits, d_amax, sizeof(amax_bits), cudaMemcpyDeviceToHost, st));
+    COW_CUDA(cudaStreamSynchronize(st));
+    for (int k = 0; k < 8; k++) {
+        float a;
+        std::memcpy(&a, &amax_bits[k], 4);
+        e[k] = fp8_exponent(a);
+    }
+    return COW_OK;
+}
+
+// Pack tensor t of block b from its device master s (grid or plane).
+cow_status pack_tensor(cow_ctx *c, BlockHost &b, int t, const float *s, const float *d_inv, cudaStream_t st) {
+    if (t == 0) return pack_grid(c, b, s, d_inv, st);
+    if (c->dtype == COW_BF16_FP8 || c->dtype == COW_FP8_BF16D)
+        COW_CUDA(cow::launch_pack_quad8(s, b.P, d_inv, b.planes[t - 1], st));
+    else
+        COW_CUDA(cow::launch_pack(s, (int64_t)b.P * b.P, b.P, tensor_dtype(c->dtype, t), d_inv, b.planes[t - 1], st));
+    return COW_OK;
+}
+
+// Re-pack the features of an existing block from new FP32 masters (occupancy,
+// z_top and the brick set unchanged); FP8 scales are recomputed.
+cow_status repack_block(cow_ctx *c, BlockHost &b, const float *const src_in[4], void *staging, unsigned *d_amax,
+                        float *d_inv, cudaStream_t st) {
+    const int64_t nv[4] = {(int64_t)b.R * b.R * b.R, (int64_t)b.P * b.P, (int64_t)b.P * b.P, (int64_t)b.P * b.P};
+    float scale_h[32];
+    for (int t = 0; t < 4; t++) {
+        const float *s = src_in[t];
+        if (!is_device_ptr(s)) {
+            COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
+            s = (const float *)staging;
+        }
+        int e[8];
+        cow_status rc = fp8_exponents(c, t, s, nv[t], d_amax, st, e);
+        if (rc != COW_OK) return rc;
+        float inv[8];
+        for (int k = 0; k < 8; k++) {
+            b.scale_exp[t][k] = e[k];
+            inv[k] = std::ldexp(1.0f, -e[k]);
+            scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
+        }
+        COW_CUDA(cudaMemcpyAsync(d_inv + 8 * t, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
+        if ((rc = pack_tensor(c, b, t, s, d_inv + 8 * t, st)) != COW_OK) return rc;
+    }
+    COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
+    return COW_OK;
+}
+
+cow_status load_one(cow_ctx *c, const cow_block_desc &d, BlockHost &b, void *staging, unsigned *d_amax,
+                    float *d_inv, double log_thresh, cudaStream_t st) {
+    const int64_t nv[4] = {(int64_t)d.grid_res * d.grid_res * d.grid_res, (int64_t)d.plane_res * d.plane_res,
+                           (int64_t)d.plane_res * d.plane_res, (int64_t)d.plane_res * d.plane_res};
+    const float *src[4] = {d.grid, d.planes[0], d.planes[1], d.planes[2]};
+    const int Nc = (d.grid_res - 1 + c->occ_cell - 1) / c->occ_cell;
+    b.occ_words = ((int64_t)Nc * Nc * Nc + 31) / 32;
+    COW_CUDA(cudaMalloc((void **)&b.occ, (size_t)b.occ_words * 4));
+    COW_CUDA(cudaMalloc((void **)&b.scale, 32 * sizeof(float)));
+    float scale_h[32];
+    // the grid first: its occupancy decides the coarse level and, for a
+    // brick-sparse grid, which bricks are stored
+    for (int t = 0; t < 4; t++) {
+        const float *s = src[t];
+        if (!is_device_ptr(s)) {
+            COW_CUDA(cudaMemcpyAsync(staging, s, (size_t)nv[t] * 32, cudaMemcpyHostToDevice, st));
+            s = (const float *)staging;
+        }
+        int e[8];
+        cow_status rc = fp8_exponents(c, t, s, nv[t], d_amax, st, e);
+        if (rc != COW_OK) return rc;
+        float inv[8];
+        for (int k = 0; k < 8; k++) {
+            b.scale_exp[t][k] = e[k];
+            inv[k] = std::ldexp(1.0f, -e[k]);
+            scale_h[8 * t + k] = std::ldexp(1.0f, e[k]);
+        }
+        COW_CUDA(cudaMemcpyAsync(d_inv, inv, sizeof(inv), cudaMemcpyHostToDevice, st));
+        if (t == 0) {
+            COW_CUDA(cow::launch_occupancy(s, d.grid_res, c->occ_cell, log_thresh, b.occ, st));
+            if ((rc = build_occupancy_levels(c, b, Nc, st)) != COW_OK) return rc;
+            COW_CUDA(cudaMalloc(&b.grid, (size_t)(grid_main_bytes(c, b) + dens_elems(c, b) * 16)));
+        } else {
+            COW_CUDA(cudaMalloc(&b.planes[t - 1], (size_t)(nv[t] * packed_elem_bytes(c->dtype))));
+        }
+        if ((rc = pack_tensor(c, b, t, s, d_inv, st)) != COW_OK) return rc;
+        // the staging buffer and d_inv are reused by the next tensor: the
+        // stream orders the next copies after these kernels
+    }
+    COW_CUDA(cudaMemcpyAsync(b.scale, scale_h, sizeof(scale_h), cudaMemcpyHostToDevice, st));
     return COW_OK;
 }
 
@@ -263,6 +350,22 @@ cow::BlockRec make_rec(const cow_ctx *c, const BlockHost &b) {
     r.cdiv = c->occ_cell > 1 ? (uint32_t)((0x100000000ull + (uint64_t)c->occ_cell - 1) / (uint64_t)c->occ_cell) : 0u;
     r.dtype = c->dtype;
     r.grid = b.grid;
+    r.dens = (b.grid && c->dtype == COW_FP8_BF16D) ? (const unsigned char *)b.grid + grid_main_bytes(c, b) : nullptr;
+    if (b.Nb > 0) {
+        int ex, ey, ez;
+        brick_dims(c->dtype, &ex, &ey, &ez);
+        r.brick = b.brick_tab;
+        r.Nb = b.Nb;
+        r.bsy = ex;
+        r.bsz = ex * ey;
+        r.belem = ex * ey * ez;
+    } else {
+        r.brick = nullptr;
+        r.Nb = 0;
+        r.bsy = b.R;
+        r.bsz = b.R * b.R;
+        r.belem = 0;
+    }
     for (int k = 0; k < 3; k++) r.planes[k] = b.planes[k];
     r.occ = b.occ;
     r.scale = b.scale;
@@ -437,8 +540,8 @@ void make_ray_recs(const cow_ctx *c, const int32_t *ids, int32_t n, cow::RayRecs
 // occupancy levels, scales and records stay resident (a few KB per block).
 
 int64_t tensor_bytes(const cow_ctx *c, const BlockHost &b, int t) {
-    const int64_t nv = t == 0 ? (int64_t)b.R * b.R * b.R : (int64_t)b.P * b.P;
-    return nv * packed_elem_bytes(c->dtype);
+    if (t == 0) return grid_main_bytes(c, b) + dens_elems(c, b) * 16;
+    return (int64_t)b.P * b.P * packed_elem_bytes(c->dtype);
 }
 
 int64_t feature_bytes(const cow_ctx *c, const BlockHost &b) {
@@ -571,11 +674,19 @@ const char *cow_last_error(void) { return g_last_error.c_str(); }
 
 cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
                            float occ_thresh, int32_t occ_cell, void *stream) {
+    return cow_load_blocks_ex(out, blocks, n, storage, occ_thresh, occ_cell, 0u, stream);
+}
+
+cow_status cow_load_blocks_ex(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
+                              float occ_thresh, int32_t occ_cell, uint32_t load_flags, void *stream) {
     g_last_error.clear();
     if (!out || !blocks || n < 1) return fail(COW_ERR_INVALID_ARG, "cow_load_blocks: null pointer or n < 1");
     *out = nullptr;
-    if ((int)storage < 0 || (int)storage > 4) return fail(COW_ERR_INVALID_ARG, "unknown storage dtype %d", (int)storage);
+    if ((int)storage < 0 || (int)storage > 5) return fail(COW_ERR_INVALID_ARG, "unknown storage dtype %d", (int)storage);
+    if (load_flags & ~(uint32_t)COW_LOAD_BRICKS) return fail(COW_ERR_INVALID_ARG, "unknown load flags 0x%x", load_flags);
     if (occ_cell < 1 || occ_cell > 4096) return fail(COW_ERR_INVALID_ARG, "occ_cell must be in [1, 4096]");
+    if ((load_flags & COW_LOAD_BRICKS) && occ_cell != 4)
+        return fail(COW_ERR_UNSUPPORTED, "brick-sparse grids need occ_cell = 4 (a brick is 4 x 4 cells of 4 voxels)");
     if (!(occ_thresh > 0.0f)) return fail(COW_ERR_INVALID_ARG, "occ_thresh must be > 0");
     size_t max_vec = 0;
     for (int32_t i = 0; i < n; i++) {
@@ -603,6 +714,7 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
         return fail(COW_ERR_CUDA, "no CUDA device");
     }
     c->dtype = (int)storage;
+    c->bricks = (load_flags & COW_LOAD_BRICKS) != 0;
     c->occ_cell = occ_cell;
     c->occ_thresh = occ_thresh;
     c->blocks.resize((size_t)n);
@@ -1058,6 +1170,9 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
     if (ctx && n_points == 0) return COW_OK;  // nothing to add (the arrays may be NULL)
     if (!ctx || !points || n_points < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_sparsity_loss: null argument");
     if (!is_device_ptr(points)) return fail(COW_ERR_INVALID_ARG, "points must be device memory");
+    if (ctx->bricks)
+        return fail(COW_ERR_UNSUPPORTED, "the sparsity regulariser samples arbitrary points, and a brick-sparse grid "
+                    "keeps only the bricks with occupied cells");
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     cow::RegArgs a;
@@ -1503,28 +1618,35 @@ cow_status cow_export_occupancy_coarse(const cow_ctx *ctx, int32_t block, uint32
 cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, void *out, int64_t nbytes,
                              int32_t *out_scale_exp) {
     if (!ctx || !out) return fail(COW_ERR_INVALID_ARG, "null argument");
-    if (block < 0 || block >= (int32_t)ctx->blocks.size() || tensor < 0 || tensor > 3)
+    const int max_tensor = ctx->dtype == COW_FP8_BF16D ? 4 : 3;
+    if (block < 0 || block >= (int32_t)ctx->blocks.size() || tensor < 0 || tensor > max_tensor)
         return fail(COW_ERR_INVALID_ARG, "block or tensor out of range");
     const BlockHost &b = ctx->blocks[(size_t)block];
-    const int64_t nv = tensor == 0 ? (int64_t)b.R * b.R * b.R : (int64_t)b.P * b.P;
-    const int tdt = tensor_dtype(ctx->dtype, tensor);
-    const int64_t need = nv * cow::kNch * elem_bytes(tdt);
+    if ((tensor == 0 || tensor == 4) && b.Nb > 0)
+        return fail(COW_ERR_UNSUPPORTED, "a brick-sparse grid holds no dense copy to export");
+    const int64_t nv = tensor == 0 || tensor == 4 ? (int64_t)b.R * b.R * b.R : (int64_t)b.P * b.P;
+    // tensor 4: the BF16 channel 0 of the FP8 format's grid (one value a vertex)
+    const int tdt = tensor == 4 ? COW_BF16 : tensor_dtype(ctx->dtype, tensor);
+    const int64_t nch = tensor == 4 ? 1 : cow::kNch;
+    const int64_t need = nv * nch * elem_bytes(tdt);
     if (nbytes < need) return fail(COW_ERR_INVALID_ARG, "need %lld bytes", (long long)need);
     DeviceGuard dg(ctx->device);
     // an unloaded block is read from its pinned host copy
-    const void *src = !b.resident ? b.host_feat[tensor] : tensor == 0 ? b.grid : b.planes[tensor - 1];
+    const void *src = !b.resident ? b.host_feat[tensor == 4 ? 0 : tensor]
+                                  : tensor == 0 || tensor == 4 ? b.grid : b.planes[tensor - 1];
+    if (tensor == 4) src = (const unsigned char *)src + grid_main_bytes(ctx, b);
     if (ctx->dtype == COW_FP32) {
         COW_CUDA(cudaMemcpy(out, src, (size_t)need, cudaMemcpyDefault));
     } else {
-        // pair layout on the device: keep the first vertex of every pair
-        // (the first texel of a mixed-format quad)
-        const int64_t pe = packed_elem_bytes(ctx->dtype), ve = cow::kNch * elem_bytes(tdt);
+        // pair layout on the device: keep the first vertex of every pair (the
+        // first texel of a quad, the first corner of a density octet)
+        const int64_t pe = tensor == 4 ? 16 : packed_elem_bytes(ctx->dtype), ve = nch * elem_bytes(tdt);
         std::vector<unsigned char> raw((size_t)(nv * pe));
         COW_CUDA(cudaMemcpy(raw.data(), src, raw.size(), cudaMemcpyDefault));
         for (int64_t i = 0; i < nv; i++) std::memcpy((unsigned char *)out + i * ve, raw.data() + i * pe, (size_t)ve);
     }
     if (out_scale_exp)
-        for (int k = 0; k < 8; k++) out_scale_exp[k] = b.scale_exp[tensor][k];
+        for (int k = 0; k < 8; k++) out_scale_exp[k] = tensor == 4 ? 0 : b.scale_exp[tensor][k];
     return COW_OK;
 }
 

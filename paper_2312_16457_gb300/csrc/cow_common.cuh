@@ -27,8 +27,22 @@ constexpr unsigned kErrTimeout = 2u;  // a bounded wait ran out
 constexpr unsigned kErrArg = 4u;      // a kernel met an argument it cannot handle
 
 // kMixed: BF16 grid (pair layout) with FP8-E4M3 planes (quad layout: element
-// (u, v) holds texels (u, v), (u+1, v), (u, v+1), (u+1, v+1), 8 bytes each)
-enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3, kMixed = 4 };
+// (u, v) holds texels (u, v), (u+1, v), (u, v+1), (u+1, v+1), 8 bytes each).
+// kFP8D: FP8-E4M3 features with the grid's log-density in BF16: the grid's
+// eight channels in FP8 in the quad layout over (x, y) (element (x, y, z)
+// holds vertices (x, y), (x+1, y), (x, y+1), (x+1, y+1) of slice z), channel
+// 0 of the grid again in BF16 in the octet layout (element (x, y, z) holds
+// the eight corners of voxel (x, y, z), corner k = dx + 2 dy + 4 dz, 16
+// bytes), and the planes in FP8 in the quad layout.
+enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3, kMixed = 4, kFP8D = 5 };
+
+// Brick-sparse grids: the grid is cut into bricks of kBrick voxels per edge
+// (one coarse occupancy cell, kOccGroup cells of 4 voxels); only bricks with
+// an occupied cell are stored, each holding the elements of its voxels' first
+// corners (with the layout's halo: 17 or 16 elements per axis).
+constexpr int kBrickLog2 = 4;
+constexpr int kBrick = 1 << kBrickLog2;
+constexpr int kDensBrickElems = kBrick * kBrick * kBrick;  // kFP8D density octets per brick
 
 // Unbounded boundary blocks (scene contraction, Eq. 16)
 constexpr int kUnbXLo = 1, kUnbXHi = 2, kUnbYLo = 4, kUnbYHi = 8, kUnbContracted = 16;
@@ -63,11 +77,17 @@ struct alignas(16) BlockRec {
     float cc[3];             // unbounded: (float)((lo + hi) / 2), computed in double
     float ih[3];             // unbounded: (float)(2 / (hi - lo)), computed in double
     float plo[3];            // origin of the lookup coordinates: lo, or -2 (contracted u) when unbounded
-    int32_t pad_[3];
+    int32_t Nb;              // brick-sparse grid: bricks per axis (0 for a dense grid)
+    const void *dens;        // kFP8D: BF16 log-density octets (dense: R^3 elements; bricks: 4096 a brick)
+    const int32_t *brick;    // brick-sparse grid: slot of brick (bz, by, bx), -1 when not stored; null: dense
+    int32_t bsy, bsz;        // element strides of the grid along y and z (dense: R, R^2; in a brick)
+    int32_t belem;           // brick-sparse grid: elements per brick
+    int32_t pad_;
     // when unbounded, kg and kp hold (R-1)/4 and (P-1)/4: lookups index u in [-2, 2]
 };
 static_assert(sizeof(BlockRec) % 16 == 0, "BlockRec must be a multiple of 16 bytes");
 static_assert(sizeof(BlockRec) * 96 + 512 <= 32764, "96 records fit the kernel parameter space");
+static_assert(sizeof(BlockRec) == 272, "BlockRec layout");
 
 // The blocks of a ray-batch call (at most kMaxRayIds), passed by value in the
 // launch's parameter buffer like ParamRecs: record k is block id[k].
@@ -313,6 +333,28 @@ __device__ __forceinline__ void ld256(const void *p, uint32_t r[8]) {
 #undef COW_LD256
 #undef COW_LD256_L2
 
+// 128-bit non-coherent global load with the same policies; p 16-byte aligned.
+#define COW_LD128(QUAL) \
+    asm("ld.global.nc" QUAL ".v4.b32 {%0,%1,%2,%3}, [%4];" : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]) : "l"(p))
+#define COW_LD128_L2(QUAL, FRAC)                                                                                 \
+    asm("{\n\t.reg .b64 pol;\n\tcreatepolicy.fractional." FRAC ".b64 pol, 1.0;\n\t"                              \
+        "ld.global.nc" QUAL ".L2::cache_hint.v4.b32 {%0,%1,%2,%3}, [%4], pol;\n\t}"                                \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])                                                         \
+        : "l"(p))
+
+template <int POL = kLdNormal>
+__device__ __forceinline__ void ld128(const void *p, uint32_t r[4]) {
+    if constexpr (POL == kLdEvictFirst) COW_LD128(".L1::evict_first");
+    else if constexpr (POL == kLdEvictLast) COW_LD128(".L1::evict_last");
+    else if constexpr (POL == kLdNoAllocate) COW_LD128(".L1::no_allocate");
+    else if constexpr (POL == kLdNoAllocateL2First) COW_LD128_L2(".L1::no_allocate", "L2::evict_first");
+    else if constexpr (POL == kLdL2Last) COW_LD128_L2("", "L2::evict_last");
+    else if constexpr (POL == kLdNoAllocateL2Last) COW_LD128_L2(".L1::no_allocate", "L2::evict_last");
+    else COW_LD128("");
+}
+#undef COW_LD128
+#undef COW_LD128_L2
+
 __device__ __forceinline__ float2 bf16x2_to_float2(uint32_t w) {
     // a bfloat16 is the upper half of the float with the same value
     return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
@@ -406,6 +448,16 @@ struct Store<kFP8> {
 // BF16 grid of the mixed format (its planes are read by accumulate_sample)
 template <>
 struct Store<kMixed> : Store<kBF16> {};
+
+// kFP8D: its quad-layout grid and planes are read by accumulate_sample
+template <>
+struct Store<kFP8D> {
+    static constexpr bool kPaired = false;
+    template <int POL = kLdNormal>
+    __device__ __forceinline__ static void load8(const void *, int64_t, float2[4]) {}
+    template <int POL = kLdNormal>
+    __device__ __forceinline__ static void load_pair(const void *, int64_t, float2[4], float2[4]) {}
+};
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
 

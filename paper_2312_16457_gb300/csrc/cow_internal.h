@@ -83,6 +83,12 @@ struct BlockHost {
     int64_t occ_words = 0;
     double ztop = 0.0;
     std::vector<int32_t> children;
+    // brick-sparse grid (cow_load_blocks_ex with COW_LOAD_BRICKS): the stored
+    // bricks, always resident like the occupancy levels
+    int32_t Nb = 0;                 // bricks per axis; 0 = dense grid
+    int32_t n_bricks = 0;           // stored bricks
+    int32_t *brick_tab = nullptr;   // device, Nb^3: slot of each brick, -1 = not stored
+    int32_t *brick_list = nullptr;  // device, n_bricks: brick id (bz Nb + by) Nb + bx of each slot
 };
 
 inline double focal_length(int32_t H, double fov_y_deg) {
@@ -108,6 +114,7 @@ cow_status make_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t
 struct cow_ctx {
     int device = 0;
     int dtype = 0;
+    bool bricks = false;  // brick-sparse grids
     int occ_cell = 4;
     float occ_thresh = 0.01f;
     int schedule = COW_SCHED_THREAD_CONST;

@@ -136,5 +136,15 @@ cudaError_t launch_pack(const float *x, int64_t n_vec, int row, int dtype, const
                         cudaStream_t st);
 cudaError_t launch_occupancy(const float *grid, int R, int C, double log_thresh, uint32_t *bits, cudaStream_t st);
 cudaError_t launch_pack_quad8(const float *x, int P, const float *inv_scale8, void *out, cudaStream_t st);
+// Grid element layouts (k_pack_grid): one FP32 vertex; a vertex pair along x
+// (FP16 / BF16 / FP8); a 2x2 quad of FP8 vertices over (x, y); the BF16
+// channel 0 of a voxel's eight corners.
+constexpr int kLayNat = 0, kLayPair = 1, kLayQuad8 = 2, kLayOct16 = 3;
+// Pack a grid (R^3 x 8 FP32 master) into n_elem elements of `layout`, dense
+// (blist null: element strides sy = R, sz = R^2) or brick-sparse (slot s of
+// belem elements holds brick blist[s], nb bricks per axis, strides sy, sz
+// inside a brick).  inv_scale8 may be null (scale 1).
+cudaError_t launch_pack_grid(const float *x, int R, int64_t n_elem, int sy, int sz, int belem, const int32_t *blist,
+                             int nb, int dtype, int layout, const float *inv_scale8, void *out, cudaStream_t st);
 
 }  // namespace cow

@@ -435,6 +435,7 @@ cudaError_t launch_thread_dt(const MarchArgs &a, int n_tiles, bool in_params, cu
     case kBF16: return launch_thread<kBF16, kBlockMlp>(a, n_tiles, in_params, st, pr);
     case kFP8: return launch_thread<kFP8, kBlockMlp>(a, n_tiles, in_params, st, pr);
     case kMixed: return launch_thread<kMixed, kBlockMlp>(a, n_tiles, in_params, st, pr);
+    case kFP8D: return launch_thread<kFP8D, kBlockMlp>(a, n_tiles, in_params, st, pr);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -452,6 +453,7 @@ cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cu
         case kBF16: k_march_views_w<kBF16><<<n_tiles, kThreads, 0, st>>>(a); break;
         case kFP8: k_march_views_w<kFP8><<<n_tiles, kThreads, 0, st>>>(a); break;
         case kMixed: k_march_views_w<kMixed><<<n_tiles, kThreads, 0, st>>>(a); break;
+        case kFP8D: k_march_views_w<kFP8D><<<n_tiles, kThreads, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
@@ -473,6 +475,7 @@ cudaError_t launch_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st) 
     case kBF16: k_march_rays<kBF16, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     case kFP8: k_march_rays<kFP8, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     case kMixed: k_march_rays<kMixed, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
+    case kFP8D: k_march_rays<kFP8D, kBlockMlp><<<(unsigned)nb, kThreads, 0, st>>>(a, rr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

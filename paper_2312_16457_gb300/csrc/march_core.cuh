@@ -27,6 +27,13 @@ constexpr int kPlaneLd = COW_PLANE_LD_POLICY;
 // g: the FP32 grid coordinate the cell decision computed.  The 8 channels are
 // accumulated as four float2 pairs with packed FP32 FMA (same rounding per
 // element as scalar FMA).
+//
+// The grid element of the voxel's first corner is found directly (dense) or
+// through the block's brick table (brick-sparse: the brick of the voxel, then
+// the voxel's place inside it); the other corners are at the layout's fixed
+// strides from it.  A voxel whose brick is not stored (only a lookup at an
+// arbitrary point can meet one: lattice samples lie in occupied cells, whose
+// bricks are stored) reads no grid element and takes the grid term as zero.
 template <int DT>
 __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], const float g[3],
                                                   float2 f[4]) {
@@ -38,34 +45,74 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
         c0[a] = v;
         fr[a] = fminf(fmaxf(g[a], 0.f), (float)(b.R - 1)) - (float)v;
     }
-    const int R = b.R;
-    const int64_t base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
+    int64_t base, dbase;
+    int slot = 0;
+    if (b.brick) {
+        const int nb = b.Nb;
+        slot = __ldg(b.brick + ((c0[2] >> kBrickLog2) * nb + (c0[1] >> kBrickLog2)) * nb + (c0[0] >> kBrickLog2));
+        const int loc = (c0[2] & (kBrick - 1)) * b.bsz + (c0[1] & (kBrick - 1)) * b.bsy + (c0[0] & (kBrick - 1));
+        base = (int64_t)slot * b.belem + loc;
+        dbase = (int64_t)slot * kDensBrickElems + loc;
+    } else {
+        const int R = b.R;
+        base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
+        dbase = base;
+    }
+    const int sy = b.bsy, sz = b.bsz;
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[c] = make_float2(0.f, 0.f);
     const float wx[2] = {1.f - fr[0], fr[0]}, wy[2] = {1.f - fr[1], fr[1]}, wz[2] = {1.f - fr[2], fr[2]};
-    if (Store<DT>::kPaired) {
-        // four loads, each the x-pair of one (y, z) edge of the voxel
+    float dens = 0.f;  // kFP8D: the BF16 log-density
+    if (slot >= 0) {
+        if constexpr (DT == kFP8D) {
+            // the eight FP8 channels of slices z and z+1: one 32-byte quad each
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const int dy = k & 1, dz = k >> 1;
-            const float wyz = wy[dy] * wz[dz];
-            const float2 w0 = make_float2(wyz * wx[0], wyz * wx[0]), w1 = make_float2(wyz * wx[1], wyz * wx[1]);
-            float2 lo[4], hi[4];
-            Store<DT>::template load_pair<kGridLd>(b.grid, base + ((int64_t)dz * R + dy) * R, lo, hi);
+            for (int dz = 0; dz < 2; dz++) {
+                uint32_t r[8];
+                ld256<kGridLd>(reinterpret_cast<const uint4 *>(b.grid) + 2 * (base + (int64_t)dz * sz), r);
 #pragma unroll
-            for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], acc[c]));
-        }
-    } else {
+                for (int q = 0; q < 4; q++) {
+                    const float w = (wy[q >> 1] * wz[dz]) * wx[q & 1];
+                    const float2 w2 = make_float2(w, w);
+                    acc[0] = __ffma2_rn(w2, fp8x2_to_float2(r[2 * q]), acc[0]);
+                    acc[1] = __ffma2_rn(w2, fp8x2_to_float2(r[2 * q] >> 16), acc[1]);
+                    acc[2] = __ffma2_rn(w2, fp8x2_to_float2(r[2 * q + 1]), acc[2]);
+                    acc[3] = __ffma2_rn(w2, fp8x2_to_float2(r[2 * q + 1] >> 16), acc[3]);
+                }
+            }
+            // channel 0 from the BF16 octet: corners 2j and 2j+1 in word j
+            uint32_t dv[4];
+            ld128<kGridLd>(reinterpret_cast<const uint4 *>(b.dens) + dbase, dv);
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-            const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
-            const float w = (wy[dy] * wz[dz]) * wx[dx];
-            const float2 w2 = make_float2(w, w);
-            float2 v[4];
-            Store<DT>::template load8<kGridLd>(b.grid, base + ((int64_t)dz * R + dy) * R + dx, v);
+            for (int j = 0; j < 4; j++) {
+                const float2 v = bf16x2_to_float2(dv[j]);
+                const float wyz = wy[j & 1] * wz[j >> 1];
+                dens = fmaf(wyz * wx[1], v.y, fmaf(wyz * wx[0], v.x, dens));
+            }
+        } else if (Store<DT>::kPaired) {
+            // four loads, each the x-pair of one (y, z) edge of the voxel
 #pragma unroll
-            for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
+            for (int k = 0; k < 4; k++) {
+                const int dy = k & 1, dz = k >> 1;
+                const float wyz = wy[dy] * wz[dz];
+                const float2 w0 = make_float2(wyz * wx[0], wyz * wx[0]), w1 = make_float2(wyz * wx[1], wyz * wx[1]);
+                float2 lo[4], hi[4];
+                Store<DT>::template load_pair<kGridLd>(b.grid, base + (int64_t)(dz * sz + dy * sy), lo, hi);
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], acc[c]));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+                const float w = (wy[dy] * wz[dz]) * wx[dx];
+                const float2 w2 = make_float2(w, w);
+                float2 v[4];
+                Store<DT>::template load8<kGridLd>(b.grid, base + (int64_t)(dz * sz + dy * sy + dx), v);
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
+            }
         }
     }
     // per-channel scales: 8 floats of one tensor as two 16-byte loads (the
@@ -73,9 +120,9 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
     // the non-coherent path measured 4 % slower in the batched kernel, whose
     // records sit in shared memory, and equal in the view kernel.
     const float4 *scale4 = reinterpret_cast<const float4 *>(b.scale);
-    if (DT == kFP8) {
+    if (DT == kFP8 || DT == kFP8D) {
         const float4 sa = scale4[0], sb = scale4[1];
-        f[0] = make_float2(acc[0].x * sa.x, acc[0].y * sa.y);
+        f[0] = make_float2(DT == kFP8D ? dens : acc[0].x * sa.x, acc[0].y * sa.y);
         f[1] = make_float2(acc[1].x * sa.z, acc[1].y * sa.w);
         f[2] = make_float2(acc[2].x * sb.x, acc[2].y * sb.y);
         f[3] = make_float2(acc[3].x * sb.z, acc[3].y * sb.w);
@@ -103,7 +150,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
         float2 pacc[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) pacc[c] = make_float2(0.f, 0.f);
-        if (DT == kMixed) {
+        if (DT == kMixed || DT == kFP8D) {
             // one 32-byte load: the 2x2 FP8 texels of the bilinear footprint
             // (hardware E4M3 conversions; an integer re-biasing of the bytes
             // measured 20 % slower)
@@ -140,7 +187,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
             }
         }
-        if (DT == kFP8 || DT == kMixed) {
+        if (DT == kFP8 || DT == kMixed || DT == kFP8D) {
             const float4 sa = scale4[2 * (pl + 1)], sb = scale4[2 * (pl + 1) + 1];
             f[0] = __ffma2_rn(pacc[0], make_float2(sa.x, sa.y), f[0]);
             f[1] = __ffma2_rn(pacc[1], make_float2(sa.z, sa.w), f[1]);

@@ -146,6 +146,95 @@ __global__ void k_pack_quad8(const float *__restrict__ x, int P, const float *__
     }
 }
 
+// Grid packing into any layout, dense or brick-sparse.  Output element e is
+// the element of the voxel corner (x, y, z):
+//   dense        e = (z R + y) R + x (sy = R, sz = R^2);
+//   brick-sparse e = s belem + lz sz + ly sy + lx: slot s holds brick
+//                blist[s] = (bz Nb + by) Nb + bx and (x, y, z) = kBrick (bx,
+//                by, bz) + (lx, ly, lz);
+// coordinates beyond R - 1 are clamped (elements never read by a lookup).
+// Layouts: kLayNat one vertex (FP32); kLayPair vertices x, x+1; kLayQuad8
+// the FP8 vertices (x..x+1, y..y+1) of slice z; kLayOct16 channel 0 of the
+// eight corners in BF16 (unscaled), corner k = dx + 2 dy + 4 dz.
+__global__ void __launch_bounds__(256) k_pack_grid(const float *__restrict__ x, int R, int64_t n_elem, int sy, int sz,
+                                                   int belem, const int32_t *__restrict__ blist, int nb, int dtype,
+                                                   int lay, const float *__restrict__ inv_scale, void *out) {
+    float s[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) s[c] = inv_scale ? inv_scale[c] : 1.0f;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_elem; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = e;
+        int ox = 0, oy = 0, oz = 0;
+        if (blist) {
+            const int64_t slot = e / belem;
+            r = e - slot * belem;
+            const int bid = blist[slot];
+            ox = (bid % nb) << kBrickLog2;
+            oy = ((bid / nb) % nb) << kBrickLog2;
+            oz = (bid / (nb * nb)) << kBrickLog2;
+        }
+        const int lz = (int)(r / sz), rem = (int)(r - (int64_t)lz * sz);
+        const int ly = rem / sy, lx = rem - ly * sy;
+        const int vx = min(ox + lx, R - 1), vy = min(oy + ly, R - 1), vz = min(oz + lz, R - 1);
+        const int vx1 = min(vx + 1, R - 1), vy1 = min(vy + 1, R - 1), vz1 = min(vz + 1, R - 1);
+        auto vid = [&](int xx, int yy, int zz) { return ((int64_t)zz * R + yy) * R + xx; };
+        if (lay == kLayOct16) {
+            uint32_t w[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int yy = (j & 1) ? vy1 : vy, zz = (j >> 1) ? vz1 : vz;
+                const float a = __ldg(x + 8 * vid(vx, yy, zz)), b2 = __ldg(x + 8 * vid(vx1, yy, zz));
+                __nv_bfloat162 h = __floats2bfloat162_rn(a, b2);
+                w[j] = *reinterpret_cast<uint32_t *>(&h);
+            }
+            reinterpret_cast<uint4 *>(out)[e] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else if (lay == kLayQuad8) {
+            const int64_t t[4] = {vid(vx, vy, vz), vid(vx1, vy, vz), vid(vx, vy1, vz), vid(vx1, vy1, vz)};
+            uint32_t w[8];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                float val[8];
+                load_scaled(x, t[q], s, val);
+                uint32_t enc[4];
+                encode8<kFP8>(val, enc);
+                w[2 * q] = enc[0];
+                w[2 * q + 1] = enc[1];
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out) + 2 * e;
+            o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+            o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        } else if (lay == kLayNat) {
+            float v[8];
+            load_scaled(x, vid(vx, vy, vz), s, v);
+            float4 *o = reinterpret_cast<float4 *>(out) + 2 * e;
+            o[0] = make_float4(v[0], v[1], v[2], v[3]);
+            o[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {  // kLayPair
+            float v[8], vn[8];
+            load_scaled(x, vid(vx, vy, vz), s, v);
+            load_scaled(x, vid(vx1, vy, vz), s, vn);
+            uint32_t a[4], b2[4];
+            if (dtype == kF16) {
+                encode8<kF16>(v, a);
+                encode8<kF16>(vn, b2);
+            } else if (dtype == kBF16) {
+                encode8<kBF16>(v, a);
+                encode8<kBF16>(vn, b2);
+            } else {
+                encode8<kFP8>(v, a);
+                encode8<kFP8>(vn, b2);
+            }
+            if (dtype == kFP8) {
+                reinterpret_cast<uint4 *>(out)[e] = make_uint4(a[0], a[1], b2[0], b2[1]);
+            } else {
+                uint4 *o = reinterpret_cast<uint4 *>(out) + 2 * e;
+                o[0] = make_uint4(a[0], a[1], a[2], a[3]);
+                o[1] = make_uint4(b2[0], b2[1], b2[2], b2[3]);
+            }
+        }
+    }
+}
+
 int grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     if (b > 152 * 64) b = 152 * 64;
@@ -176,6 +265,14 @@ cudaError_t launch_pack(const float *x, int64_t n_vec, int row, int dtype, const
 
 cudaError_t launch_pack_quad8(const float *x, int P, const float *inv_scale8, void *out, cudaStream_t st) {
     k_pack_quad8<<<grid_for((int64_t)P * P, 256), 256, 0, st>>>(x, P, inv_scale8, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_grid(const float *x, int R, int64_t n_elem, int sy, int sz, int belem, const int32_t *blist,
+                             int nb, int dtype, int layout, const float *inv_scale8, void *out, cudaStream_t st) {
+    if (n_elem <= 0) return cudaSuccess;
+    k_pack_grid<<<grid_for(n_elem, 256), 256, 0, st>>>(x, R, n_elem, sy, sz, belem, blist, nb, dtype, layout,
+                                                       inv_scale8, out);
     return cudaGetLastError();
 }
 

@@ -236,11 +236,13 @@ def single_block_scene(seed=1, R=64, P=256, device="cpu") -> Scene:
 
 
 def city_scene(seed: int, M: int, side: float, res: Sequence[tuple], height=2.0,
-               blobs_per_area=2.0, lod_thresh=None, device="cpu", levels=None, unbounded=False) -> Scene:
+               blobs_per_area=2.0, lod_thresh=None, device="cpu", levels=None, unbounded=False,
+               blob_top=0.5, blob_r=(0.1, 0.3)) -> Scene:
     """M x M ground blocks of the given side at LOD 1, merged 2x2 per level.
 
     res[l] = (R, P) of level l+1.  Blob centres are uniform over the ground
-    and the lower half of the height so that they cross block borders.
+    and the lowest blob_top of the height (half by default) so that they
+    cross block borders; blob radii are blob_r times half a block side.
     unbounded=True (one level only) makes the blocks on the scene's boundary
     unbounded: contracted, extending to infinity across their boundary sides
     (the ground slab then continues to the horizon)."""
@@ -251,8 +253,8 @@ def city_scene(seed: int, M: int, side: float, res: Sequence[tuple], height=2.0,
     box_hi = (half, half, 0.5 * height)
     area = (2 * half) ** 2
     fld = make_field(seed, box_lo, box_hi, int(round(blobs_per_area * area)),
-                     (0.1 * side / 2, 0.3 * side / 2), (-half, -half, box_lo[2]),
-                     (half, half, 0.0))
+                     (blob_r[0] * side / 2, blob_r[1] * side / 2), (-half, -half, box_lo[2]),
+                     (half, half, box_lo[2] + blob_top * height))
     blocks: List[Block] = []
     level_index = {}
     for lev in range(L, 0, -1):  # coarse first so parents have indices
@@ -387,13 +389,20 @@ def workload_city_4x4(R=256, P=1024, device="cpu", width=1280, height=720):
     return sc, [cam], mlp_weights(102)
 
 
+# A sparser city: blob centres in the lowest fifth of the height and radii of
+# 0.05-0.15 half block sides (the dense default: lower half, 0.1-0.3), so the
+# upper part of every block is empty air, as above a real city's ground.
+SPARSE_CITY = dict(blob_top=0.2, blob_r=(0.05, 0.15))
+
+
 def workload_city_lod(res=((256, 1024), (128, 512), (64, 256)), device="cpu", width=1920, height=1080,
-                      lod_thresh=(12.5, 16.5, 0.0)):
+                      lod_thresh=(12.5, 16.5, 0.0), sparse=False):
     """8x8 LOD-1 blocks of side 2 with 3 LOD levels (64 + 16 + 4 blocks),
     one 1920x1080 aerial camera (altitude 9, oblique) that sees every block;
     the thresholds keep the near blocks at level 1 and the far ones coarser.
-    Scene seed 3, MLP seed 103."""
-    sc = city_scene(3, 8, 2.0, list(res), lod_thresh=list(lod_thresh), device=device)
+    Scene seed 3, MLP seed 103; sparse=True: the SPARSE_CITY generator setting."""
+    sc = city_scene(3, 8, 2.0, list(res), lod_thresh=list(lod_thresh), device=device,
+                    **(SPARSE_CITY if sparse else {}))
     cam = camera((0.0, -13.0, 9.0), (0.0, -0.5, -1.0), width, height, 60.0)
     return sc, [cam], mlp_weights(103)
 

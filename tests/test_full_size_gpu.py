@@ -86,7 +86,7 @@ def city_lod():
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("storage", ["fp32", "bf16", "bf16_fp8", "fp8"])
+@pytest.mark.parametrize("storage", ["fp32", "bf16", "bf16_fp8", "fp8_bf16d", "fp8"])
 def test_city_lod_1080p_sampled(city_lod, storage):
     c = city_lod
     cam, ids, pix, mlp = c["cam"], c["ids"], c["pix"], c["mlp"]
@@ -118,10 +118,39 @@ def test_city_lod_1080p_sampled(city_lod, storage):
     assert np.abs(rgb0 - r_s).max() <= TOL
     assert np.abs(aux0[:, :7] - a_s[:, :7]).max() <= TOL
     assert np.abs(rgb - r_s).max() <= TOL
-    # the format against the FP32 master
+    # the format against the FP32 master (pure per-channel E4M3 is checked on
+    # its stored values and for PSNR only: it does not meet the 1e-2 bound)
     assert psnr(rgb, r_m) >= 45.0
-    if storage != "fp8":  # pure FP8 exceeds 1e-2 on the log-density channel (a format limit)
+    if storage != "fp8":
         assert np.abs(rgb - r_m).max() <= 1e-2
+
+
+def test_city_lod_1080p_bricks_whole_frame():
+    """The 1080p LOD city baked with the sparse generator setting, brick-sparse
+    BF16 grids against dense BF16 grids in the benchmark's launch: the whole
+    frame bit for bit, with fewer device bytes."""
+    sc, cams, mlp = synth.workload_city_lod(device="cuda", sparse=True)
+    cam = cams[0]
+    dense = cow.Context(sc, "bf16")
+    sparse = cow.Context(sc, "bf16", bricks=True)
+    ids = dense.select_lod(cam, sc.lod_thresh)
+    nb = len(sc.blocks)
+    del sc
+    mlp_d = torch.from_numpy(mlp).cuda()
+    for ert in (1e-5, 0.0):
+        a = dense.render([cam], [ids], mlp_d, ert_eps=ert, nsamp=True)
+        b = sparse.render([cam], [ids], mlp_d, ert_eps=ert, nsamp=True)
+        dense.sync_check()
+        sparse.sync_check()
+        for x, y in zip(a, b):
+            assert torch.equal(x, y), ert
+    assert float((a[2] > 0).float().mean()) > 0.3
+    bd = sum(dense.block_bytes(i) for i in range(nb))
+    bs = sum(sparse.block_bytes(i) for i in range(nb))
+    print(f"sparse city: dense {bd / 1e9:.2f} GB, brick-sparse {bs / 1e9:.2f} GB")
+    assert bs < 0.7 * bd
+    dense.close()
+    sparse.close()
 
 
 # ---------------------------------------------------------------------------

@@ -103,7 +103,7 @@ def test_coarse_occupancy_is_or_of_cells():
     assert max(n_on) > 0 and min(n_on) < 27  # both kinds of coarse cell occur
 
 
-@pytest.mark.parametrize("dtype", ["fp32", "fp16", "bf16", "fp8", "bf16_fp8"])
+@pytest.mark.parametrize("dtype", ["fp32", "fp16", "bf16", "fp8", "bf16_fp8", "fp8_bf16d"])
 def test_packed_bits_exact(dtype):
     sc = synth.city_scene(9, 2, 2.0, [(17, 24)])
     ctx = cow.Context(sc, dtype)
@@ -115,6 +115,10 @@ def test_packed_bits_exact(dtype):
             want, _ = oracle.quantize(src, tdt, want_se)
             assert np.array_equal(se, want_se)
             assert np.array_equal(got.view(want.dtype), want), (i, t)
+        if dtype == "fp8_bf16d":  # the grid's log-density channel, BF16 without a scale
+            got, se = ctx.packed(i, 4)
+            want, _ = oracle.quantize(b.grid[..., 0].contiguous(), "bf16")
+            assert np.array_equal(got.view(want.dtype), want) and not se.any(), i
 
 
 @pytest.mark.parametrize("schedule", ["warp", "thread", "thread_const"])
@@ -263,11 +267,15 @@ def test_select_lod_bit_exact():
         assert ctx.ztop(i) == osc.ztop(i)
 
 
-@pytest.mark.parametrize("dtype", ["bf16", "fp8", "bf16_fp8"])
+@pytest.mark.parametrize("dtype", ["bf16", "fp8", "bf16_fp8", "fp8_bf16d"])
 def test_precision_forms(dtype):
-    """LOD-mixed city at 1/4 resolution: BF16 / FP8 / BF16-grid-FP8-plane storage against the oracle
-    on the FP32 master (PSNR >= 45 dB, max <= 1e-2) and against the oracle on
-    the oracle's own dequantisation of the same storage (<= 1e-4)."""
+    """LOD-mixed city at 1/4 resolution: the storage formats against the
+    oracle on the FP32 master (PSNR >= 45 dB, max |dRGB| <= 1e-2) and against
+    the oracle on the oracle's own dequantisation of the same storage
+    (<= 1e-4).  Pure per-channel E4M3 ("fp8") does not meet the 1e-2 bound
+    (its 3-bit mantissa on the log-density gives 0.0144 in the oracle too):
+    it is checked on the same stored values and for PSNR only, and the FP8
+    form that meets the bound is "fp8_bf16d" (log-density in BF16)."""
     sc, cams, mlp = synth.workload_city_lod(res=((64, 256), (32, 128), (16, 64)), width=192, height=108)
     ctx = cow.Context(sc, dtype)
     ids = ctx.select_lod(cams[0], sc.lod_thresh)
@@ -282,13 +290,13 @@ def test_precision_forms(dtype):
     p, mx = psnr(rgb, r_m), float(np.abs(rgb - r_m).max())
     print(f"{dtype}: PSNR {p:.2f} dB, max |dRGB| {mx:.4g} vs the oracle on the FP32 master")
     assert p >= 45.0, p
-    # pure E4M3 log-density carries a 3-bit mantissa: its worst pixel is
-    # above 1e-2 in the oracle as well (the storage, not the kernel)
-    assert mx <= (2e-2 if dtype == "fp8" else 1e-2)
+    if dtype != "fp8":
+        assert mx <= 1e-2, mx
     # BF16 MLP operands with FP32 accumulation
     rgb_b, _, _ = _render(ctx, cams, [ids], mlp, mlp_bf16=True)
     assert psnr(rgb_b, r_m) >= 45.0
-    assert np.abs(rgb_b - r_m).max() <= (2e-2 if dtype == "fp8" else 1e-2)
+    if dtype != "fp8":
+        assert np.abs(rgb_b - r_m).max() <= 1e-2
 
 
 def _c2w_down(x, y, z):
