@@ -47,7 +47,8 @@ MEASURED_L1_WAVEFRONTS = {}  # (workload, storage, schedule) -> (fraction, sourc
 L2_FLUSH_BYTES = 512 << 20
 KERNEL_OF_SCHEDULE = {"thread": "k_march_views", "thread_const": "k_march_views_c", "warp": "k_march_views_w"}
 # per occupied sample: 20 texels x 8 channels (8 grid vertices + 12 plane texels)
-GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160, "bf16_fp8": 8 * 16 + 12 * 8}
+GATHER_BYTES = {"fp32": 640, "fp16": 320, "bf16": 320, "fp8": 160, "bf16_fp8": 8 * 16 + 12 * 8,
+                "fp8_bf16d": 8 * 8 + 8 * 2 + 12 * 8}
 
 
 def march_sources_sha256() -> str:
@@ -84,6 +85,10 @@ def parse():
                          "global MLP (-1)")
     ap.add_argument("--reg", action="store_true",
                     help="fit_2x2: add the sparsity (0.05) and opacity (0.001) regularisers to every step")
+    ap.add_argument("--bricks", action="store_true", help="brick-sparse grids for the timed context")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-view batched measurement")
+    ap.add_argument("--no-sparse-city", action="store_true", help="skip the sparse-city brick measurement")
+    ap.add_argument("--batch-storage", default="bf16", help="storage of the 64-view batched measurement")
     return ap.parse_args()
 
 
@@ -203,17 +208,17 @@ def sub_scene(sc, ids):
     return synth.Scene(blocks, sc.box_lo, sc.box_hi, [], sc.occ_cell, sc.occ_thresh)
 
 
-def oracle_sample(sc, cam, ids, mlp, n_pix, seed=0):
-    """Time the oracle (as it stands, all host cores) on n_pix random pixels."""
+def oracle_sample(host, cam, mlp, n_pix, seed=0):
+    """Time the oracle (as it stands, all host cores) on n_pix random pixels
+    of the frame; host: the frame's blocks on the host, in near-to-far order."""
     import oracle
 
     oracle.build()
-    host = sub_scene(sc, ids)
     osc = oracle.OracleScene(host)
     rng = np.random.default_rng(seed)
     pix = np.sort(rng.choice(cam.width * cam.height, size=n_pix, replace=False))
     t0 = time.perf_counter()
-    rgb, aux, ns = oracle.render_view(osc, cam, list(range(len(ids))), mlp, pixels=pix)
+    rgb, aux, ns = oracle.render_view(osc, cam, list(range(len(host.blocks))), mlp, pixels=pix)
     dt = time.perf_counter() - t0
     return pix, rgb, dt
 
@@ -240,8 +245,22 @@ def psnr(a, b):
 # ---------------------------------------------------------------------------
 
 
+def time_form(ctx, cam, ids, mlp_d, args, flush, stream, reps):
+    """Mean step time (ms) and the frame of one storage form on the frame."""
+    npix = cam.width * cam.height
+    out = (torch.empty((npix, 3), device=mlp_d.device), None, None)
+    t = time_steps(lambda: ctx.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=out), reps, 3, flush,
+                   stream)
+    ctx.sync_check()
+    return float(np.mean(t)), out[0].cpu().numpy()
+
+
+def scene_bytes(ctx, ids):
+    return int(sum(ctx.block_bytes(int(i)) for i in ids))
+
+
 def run_cow(args, ws, rank, local):
-    from paper_2312_16457_gb300 import build, cow
+    from paper_2312_16457_gb300 import build, cow, synth
 
     build.build()
     dev = torch.device("cuda", local)
@@ -249,20 +268,12 @@ def run_cow(args, ws, rank, local):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     sc, cam, mlp, storage, desc = make_workload(args.workload, dev, args.res_div)
     storage = args.storage or storage
-    ctx = cow.Context(sc, storage)
+    ctx = cow.Context(sc, storage, bricks=args.bricks)
     ctx.set_schedule(args.schedule)
     ctx.set_tile_order(args.strip)
     ids = block_ids(ctx, sc, cam)
-    ctx32 = cow.Context(sc, "fp32") if (not args.no_fp32 and storage != "fp32") else None
-    if ctx32 is not None:
-        ctx32.set_schedule(args.schedule)
-    # the mixed precision form (BF16 grid, FP8 planes) on the same frame
-    ctxm = cow.Context(sc, "bf16_fp8") if (not args.no_fp32 and storage == "bf16") else None
     need_master = rank == 0 and ws == 1 and not args.no_cpu
-    if not need_master:  # the contexts hold packed copies; drop the FP32 masters
-        for b in sc.blocks:
-            b.grid, b.planes = None, []
-        torch.cuda.empty_cache()
+    host = sub_scene(sc, ids) if need_master else None  # the oracle baseline's blocks, on the host
     mlp_d = torch.from_numpy(mlp).to(dev)
     stream = torch.cuda.current_stream()
     npix = cam.width * cam.height
@@ -274,6 +285,7 @@ def run_cow(args, ws, rank, local):
     ctx.sync_check()
     n_samples = int(ns0.to(torch.int64).sum().item())
     rgb_main = ctx.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False)[0].cpu().numpy()
+    del aux0, ns0
 
     def step():
         ctx.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=out)
@@ -308,57 +320,57 @@ def run_cow(args, ws, rank, local):
     e2e_ms = max_over_ranks(ws, 1000.0 * float(np.mean(e2e_t)))
     h2d = 80 + 4 * len(ids) + 4 * 499 + 4 * 2  # camera record, ids, MLP, offsets
     d2h = npix * 12
+    reps = max(5, args.steps // 2)
 
     # the same frame through the persistent batched path (one view, autotuned)
     batch = cow.Batch(ctx, 1, len(ids))
     batch.set_views([cam], [ids])
     tile, ctas, _ = batch.tune(mlp_d, out[0], ert_eps=args.ert)
-    tb = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), max(5, args.steps // 2), 3,
-                    flush, stream)
+    tb = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), reps, 3, flush, stream)
     batch_path = {"frames_per_s": round(1000.0 / float(np.mean(tb)), 3), "tile": cow.Batch.TILE_SHAPES[tile],
                   "ctas_per_sm": ctas}
     batch.close()
 
     # the same frame with per-block deferred MLPs blended by Eq. 5 (PE(d) at 4 octaves)
-    from paper_2312_16457_gb300 import synth
-
     ctx.set_block_mlps(synth.block_mlp_weights(104, len(sc.blocks), 4), 4)
     tbm = time_steps(lambda: ctx.render([cam], [ids], None, ert_eps=args.ert, aux=False, out=out, block_mlps=True),
-                     max(5, args.steps // 2), 3, flush, stream)
+                     reps, 3, flush, stream)
     ctx.sync_check()
     block_mlp_form = {"frames_per_s": round(1000.0 / float(np.mean(tbm)), 3), "n_freq": 4,
                       "mlp_params_per_block": synth.block_mlp_nparam(4)}
+    main_bytes = scene_bytes(ctx, ids)
 
-    mixed = {}
-    if ctxm is not None:
-        outm = (torch.empty((npix, 3), device=dev), None, None)
-        tm = time_steps(lambda: ctxm.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=outm),
-                        max(5, args.steps // 2), 3, flush, stream)
-        ctxm.sync_check()
-        mixed = {"frames_per_s": round(1000.0 / float(np.mean(tm)), 3), "rgb": outm[0].cpu().numpy()}
-        ctxm.close()
-
-    # plain FP32 storage, same frame
-    fp32 = {}
-    if ctx32 is not None:
-        out32 = (torch.empty((npix, 3), device=dev), None, None)
-        t32 = time_steps(lambda: ctx32.render([cam], [ids], mlp_d, ert_eps=args.ert, aux=False, out=out32),
-                         max(5, args.steps // 2), 3, flush, stream)
-        ctx32.sync_check()
-        rgb32 = out32[0].cpu().numpy()
-        fp32 = {"plain_fp32_frames_per_s": round(1000.0 / float(np.mean(t32)), 3),
-                "psnr_vs_plain_fp32_db": round(psnr(rgb_main, rgb32), 2)}
-        if mixed:
-            fp32["bf16_grid_fp8_planes_same_frame"] = {
-                "frames_per_s": mixed["frames_per_s"], "psnr_vs_plain_fp32_db": round(psnr(mixed["rgb"], rgb32), 2),
-                "storage": "BF16 grid, FP8-E4M3 planes (quad layout, per-channel scales)"}
-        ctx32.close()
+    # the other storage forms on the same frame, one context at a time: plain
+    # FP32 (the metric's comparison), BF16 grid + FP8 planes, FP8 with BF16
+    # log-density, brick-sparse BF16 grids
+    forms = {}
+    if not args.no_fp32 and storage == "bf16" and not args.bricks:
+        rgb32 = None
+        for key, st, br in (("plain_fp32", "fp32", False), ("bf16_grid_fp8_planes", "bf16_fp8", False),
+                            ("fp8_bf16_density", "fp8_bf16d", False), ("bf16_bricks", "bf16", True)):
+            cx = cow.Context(sc, st, bricks=br)
+            cx.set_schedule(args.schedule)
+            t_ms, rgb = time_form(cx, cam, ids, mlp_d, args, flush, stream, reps)
+            forms[key] = {"storage": st + (" brick-sparse" if br else ""), "frames_per_s": round(1000.0 / t_ms, 3),
+                          "device_gb_selected_blocks": round(scene_bytes(cx, ids) / 1e9, 3)}
+            if key == "plain_fp32":
+                rgb32 = rgb
+            else:
+                forms[key]["psnr_vs_plain_fp32_db"] = round(psnr(rgb, rgb32), 2)
+                forms[key]["max_abs_drgb_vs_plain_fp32"] = float(np.abs(rgb - rgb32).max())
+            if br:
+                forms[key]["frame_equal_to_dense"] = bool(np.array_equal(rgb, rgb_main))
+            cx.close()
+            torch.cuda.empty_cache()
+    for b in sc.blocks:  # the contexts hold packed copies: drop the FP32 masters
+        b.grid, b.planes = None, []
+    torch.cuda.empty_cache()
 
     # oracle on a bounded sample of this frame (rank 0, N = 1 only)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    if need_master:
         n_pix = min(args.cpu_pixels or npix, npix)  # the whole frame: ~10 s of oracle work on 16 cores
-        pix, rgb_o, dt = oracle_sample(sc, cam, ids, mlp, n_pix)
+        pix, rgb_o, dt = oracle_sample(host, cam, mlp, n_pix)
         cpu = {"value": round((n_pix / dt) / npix, 6), "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n_pix} pixels of the frame ({100.0 * n_pix / npix:.0f}%), FP64 oracle on the FP32 master, "
                          f"{dt:.2f} s",
@@ -370,15 +382,16 @@ def run_cow(args, ws, rank, local):
 
         oracle.set_threads(1)
         n1 = max(1, n_pix // 64)
-        _, _, dt1 = oracle_sample(sc, cam, ids, mlp, n1, seed=1)
+        _, _, dt1 = oracle_sample(host, cam, mlp, n1, seed=1)
         oracle.set_threads(os.cpu_count())
         cpu["one_core"] = {"value": round((n1 / dt1) / npix, 6), "unit": "frames/s", "cores": 1,
                            "sample": f"{n1} pixels, {dt1:.2f} s", "mrays_per_s": round(n1 / dt1 / 1e6, 6)}
+        del host
 
     # gather roofline: the marcher's algorithmic gather bytes against the
     # measured random-gather rate of the same load width from an L1-resident
     # buffer (L2- and HBM-resident levels reported beside it)
-    width = 32 if storage in ("fp32", "fp16", "bf16", "bf16_fp8") else 16
+    width = 16 if storage == "fp8" else 32
     peak_l1 = cow.gather_peak(width, 64 << 10)
     peak_l2 = cow.gather_peak(width, 32 << 20)
     peak_hbm = cow.gather_peak(width, 8 << 30, iters=64)
@@ -389,30 +402,44 @@ def run_cow(args, ws, rank, local):
     # this configuration) over the live step time, against the measured copy peak
     src_sha = march_sources_sha256()
     tr = MEASURED_TRAFFIC.get((args.workload, storage, args.schedule, args.res_div))
-    traffic = tr[0] if tr and tr[1] == src_sha else None
+    traffic = tr[0] if tr and tr[1] == src_sha and not args.bricks else None
     l1w = MEASURED_L1_WAVEFRONTS.get((args.workload, storage, args.schedule))
-    l1_wavefront_frac = l1w[0] if l1w and l1w[1] == src_sha else None
+    l1_wavefront_frac = l1w[0] if l1w and l1w[1] == src_sha and not args.bricks else None
     hbm_level = None
     if traffic and hbm:
         dram_gbs = traffic / 1e9 / (ms / 1000.0)
         hbm_level = {"achieved": round(dram_gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(dram_gbs / hbm, 3),
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
+    ctx.close()
+    torch.cuda.empty_cache()
+
+    # the batched form on its own workload (64 views, 16x16-block city):
+    # one persistent launch per batch against per-view launches
+    batch64 = None
+    if not args.no_batch and args.workload == "city_lod_1080p" and args.res_div == 1:
+        batch64 = measure_batch64(args, dev, flush, stream)
+    sparse_city = None
+    if not args.no_sparse_city and args.workload == "city_lod_1080p" and args.res_div == 1:
+        sparse_city = measure_sparse_city(args, dev, flush, stream)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 4), "ms_median": round(float(np.median(times)), 4),
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "scene": desc, "storage": storage, "n_blocks_selected": int(len(ids)),
-                   "schedule": args.schedule, "tile_strip": args.strip,
+        "config": {"workload": args.workload, "scene": desc, "storage": storage + (" brick-sparse" if args.bricks else ""),
+                   "n_blocks_selected": int(len(ids)), "schedule": args.schedule, "tile_strip": args.strip,
                    "width": cam.width, "height": cam.height, "ert_eps": args.ert,
                    "l2": "512 MiB write between timed steps, outside the per-step events",
                    "parallelism": f"replicas x{ws}"},
         "mrays_per_s": round(value * npix / 1e6, 3),
         "occupied_samples_per_frame": n_samples,
+        "samples_per_ray": round(n_samples / npix, 2),
+        "device_gb_selected_blocks": round(main_bytes / 1e9, 3),
         "batched_path_same_frame": batch_path,
         "block_mlp_form_same_frame": block_mlp_form,
-        "samples_per_ray": round(n_samples / npix, 2),
-        **fp32,
+        "storage_forms_same_frame": forms,
+        "batch_64": batch64,
+        "sparse_city_bricks": sparse_city,
         "roofline": {"bound": "gather", "kernel": KERNEL_OF_SCHEDULE[args.schedule], "achieved": round(achieved, 1),
                      "peak": round(peak_l1, 1), "unit": "GB/s", "frac": round(achieved / peak_l1, 3),
                      "traffic": traffic,
@@ -423,6 +450,7 @@ def run_cow(args, ws, rank, local):
                                     "buffer, cow_gather_peak",
                      "levels_gbs": {"l1_gather": round(peak_l1, 1), "l2_gather": round(peak_l2, 1),
                                     "hbm_gather": round(peak_hbm, 1), "hbm_copy_measured": hbm},
+                     "frac_of_l2_gather": round(achieved / peak_l2, 3),
                      "hbm_level": hbm_level,
                      "algorithmic_bytes_per_launch": int(GATHER_BYTES[storage] * n_samples),
                      "unit_note": f"{GATHER_BYTES[storage]} B per occupied sample (8 grid vertices + 12 plane "
@@ -436,7 +464,109 @@ def run_cow(args, ws, rank, local):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_batch64(args, dev, flush, stream, budget_frac=0.0):
+    """The batched form: a 16x16-block city (128^3 / 512^2 at LOD 1, 3 LOD
+    levels), 64 aerial views of 640x360 / 1280x720 / 1920x1080, LOD chosen per
+    view; BF16 storage served by one persistent (CUDA-graph replayed,
+    autotuned) launch per batch, against the same storage and plain FP32
+    rendered one view per launch."""
+    from paper_2312_16457_gb300 import cow, synth
+
+    div = args.res_div
+    res = tuple((r // div, p // div) for r, p in ((128, 512), (64, 256), (32, 128)))
+    sc, cams, mlp = synth.workload_batch(res=res, device=dev)
+    ctx = cow.Context(sc, args.batch_storage)
+    ctx32 = cow.Context(sc, "fp32")
+    for b in sc.blocks:
+        b.grid, b.planes = None, []
+    torch.cuda.empty_cache()
+    ids = [ctx.select_lod(c, sc.lod_thresh) for c in cams]
+    mlp_d = torch.from_numpy(mlp).to(dev)
+    batch = cow.Batch(ctx, len(cams), sum(len(i) for i in ids))
+    npix = batch.set_views(cams, ids)
+    out = torch.empty((npix, 3), device=dev)
+    tile, ctas, tune_ms = batch.tune(mlp_d, out, ert_eps=args.ert)
+    clocks = Clocks(torch.cuda.current_device())
+    steps = max(5, args.steps // 2)
+    times = time_steps(lambda: batch.render(mlp_d, out, ert_eps=args.ert, graph=True), steps, 3, flush, stream)
+    ck = clocks.stop()
+    ctx.sync_check()
+    ms = float(np.mean(times))
+    # plain FP32 storage, one launch per view
+    outs32 = [torch.empty((c.width * c.height, 3), device=dev) for c in cams]
+
+    def per_view():
+        for c, i, o32 in zip(cams, ids, outs32):
+            ctx32.render([c], [i], mlp_d, ert_eps=args.ert, aux=False, out=(o32, None, None))
+
+    t32 = time_steps(per_view, max(3, steps // 2), 2, flush, stream)
+    ctx32.sync_check()
+    ms32 = float(np.mean(t32))
+    # the same storage, one launch per view (what the persistent batch replaces)
+    outs16 = [torch.empty((c.width * c.height, 3), device=dev) for c in cams]
+
+    def per_view_same():
+        for c, i, o16 in zip(cams, ids, outs16):
+            ctx.render([c], [i], mlp_d, ert_eps=args.ert, aux=False, out=(o16, None, None))
+
+    t16 = time_steps(per_view_same, max(3, steps // 2), 2, flush, stream)
+    ctx.sync_check()
+    ms16 = float(np.mean(t16))
+    rgb32 = torch.cat(outs32).cpu().numpy()
+    p = psnr(out.cpu().numpy(), rgb32)
+    same = bool(torch.equal(out, torch.cat(outs16)))
+    ctx32.close()
+    px1080 = 1920 * 1080
+    res_d = {"views": len(cams), "pixels_per_batch": int(npix),
+             "scene": "16x16 blocks x 3 LOD (%s), %s" % (", ".join(f"{r}^3/{q}^2" for r, q in res), ctx.storage),
+             "blocks_per_view_mean": round(float(np.mean([len(i) for i in ids])), 1),
+             "tuned": {"tile": cow.Batch.TILE_SHAPES[tile], "ctas_per_sm": ctas, "ms": round(tune_ms, 3)},
+             "batched": {"ms_per_batch": round(ms, 3), "frames_per_s": round(npix / (ms / 1000.0) / px1080, 3),
+                         "mrays_per_s": round(npix / ms / 1e3, 3),
+                         "launch": "one persistent launch per batch, CUDA graph replay"},
+             "same_storage_per_view": {"ms_per_batch": round(ms16, 3),
+                                       "frames_per_s": round(npix / (ms16 / 1000.0) / px1080, 3)},
+             "plain_fp32_per_view": {"ms_per_batch": round(ms32, 3),
+                                     "frames_per_s": round(npix / (ms32 / 1000.0) / px1080, 3)},
+             "pixels_equal_per_view": same,
+             "psnr_vs_plain_fp32_db": round(p, 2), "clocks": ck,
+             "frames_per_s_note": "1080p-equivalent frames/s = pixels of the batch per second / (1920 x 1080)"}
+    if budget_frac > 0:
+        res_d["under_residency_budget"] = run_batch_budget(args, ctx, cams, ids, mlp_d, out, tile, ctas, flush,
+                                                           stream, px1080)
+    batch.close()
     ctx.close()
+    torch.cuda.empty_cache()
+    return res_d
+
+
+def measure_sparse_city(args, dev, flush, stream):
+    """The 1080p LOD city baked with the sparse generator setting (content in
+    the lower fifth of the height): dense against brick-sparse BF16 grids,
+    frames/s and device bytes of the frame's blocks."""
+    from paper_2312_16457_gb300 import cow, synth
+
+    sc, cams, mlp = synth.workload_city_lod(device=dev, sparse=True)
+    cam = cams[0]
+    mlp_d = torch.from_numpy(mlp).to(dev)
+    out = {}
+    rgb_dense = None
+    for key, br in (("dense_bf16", False), ("bricks_bf16", True)):
+        cx = cow.Context(sc, "bf16", bricks=br)
+        ids = cx.select_lod(cam, sc.lod_thresh)
+        t_ms, rgb = time_form(cx, cam, ids, mlp_d, args, flush, stream, max(5, args.steps // 2))
+        out[key] = {"frames_per_s": round(1000.0 / t_ms, 3), "device_gb_selected_blocks": round(scene_bytes(cx, ids) / 1e9, 3),
+                    "device_gb_all_blocks": round(scene_bytes(cx, range(len(sc.blocks))) / 1e9, 3)}
+        if br:
+            out[key]["frame_equal_to_dense"] = bool(np.array_equal(rgb, rgb_dense))
+        rgb_dense = rgb
+        cx.close()
+        torch.cuda.empty_cache()
+    del sc
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_fit(args, ws, rank, local):
@@ -497,81 +627,24 @@ def run_fit(args, ws, rank, local):
 
 
 def run_batch(args, ws, rank, local):
-    """Batched form: a 16x16-block city (128^3 / 512^2 at LOD 1, 3 LOD levels),
-    64 aerial views of 640x360 / 1280x720 / 1920x1080, LOD chosen per view.
-    BF16 storage served by one persistent (CUDA-graph replayed, autotuned)
-    launch per batch vs the plain FP32 storage rendered one view per launch."""
-    from paper_2312_16457_gb300 import build, cow, synth
+    """The batched workload as the benchmark line (see measure_batch64)."""
+    from paper_2312_16457_gb300 import build
 
     build.build()
     dev = torch.device("cuda", local)
-    div = args.res_div
-    res = tuple((r // div, p // div) for r, p in ((128, 512), (64, 256), (32, 128)))
-    sc, cams, mlp = synth.workload_batch(res=res, device=dev)
-    ctx = cow.Context(sc, args.storage or "bf16")
-    ctx32 = cow.Context(sc, "fp32")
-    for b in sc.blocks:
-        b.grid, b.planes = None, []
-    torch.cuda.empty_cache()
-    ids = [ctx.select_lod(c, sc.lod_thresh) for c in cams]
-    mlp_d = torch.from_numpy(mlp).to(dev)
-    batch = cow.Batch(ctx, len(cams), sum(len(i) for i in ids))
-    npix = batch.set_views(cams, ids)
-    out = torch.empty((npix, 3), device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    tile, ctas, tune_ms = batch.tune(mlp_d, out, ert_eps=args.ert)
-    clocks = Clocks(torch.cuda.current_device())
-    times = time_steps(lambda: batch.render(mlp_d, out, ert_eps=args.ert, graph=True), args.steps, args.warmup,
-                       flush, stream)
-    ck = clocks.stop()
-    ctx.sync_check()
-    ms = max_over_ranks(ws, float(np.mean(times)))
-    # plain FP32 storage, one launch per view
-    outs32 = [torch.empty((c.width * c.height, 3), device=dev) for c in cams]
-
-    def per_view():
-        for c, i, o32 in zip(cams, ids, outs32):
-            ctx32.render([c], [i], mlp_d, ert_eps=args.ert, aux=False, out=(o32, None, None))
-
-    t32 = time_steps(per_view, max(3, args.steps // 4), 2, flush, stream)
-    ctx32.sync_check()
-    ms32 = float(np.mean(t32))
-    # the same storage, one launch per view (what the persistent batch replaces)
-    outs16 = [torch.empty((c.width * c.height, 3), device=dev) for c in cams]
-
-    def per_view_same():
-        for c, i, o16 in zip(cams, ids, outs16):
-            ctx.render([c], [i], mlp_d, ert_eps=args.ert, aux=False, out=(o16, None, None))
-
-    t16 = time_steps(per_view_same, max(3, args.steps // 4), 2, flush, stream)
-    ctx.sync_check()
-    ms16 = float(np.mean(t16))
-    rgb32 = torch.cat(outs32).cpu().numpy()
-    p = psnr(out.cpu().numpy(), rgb32)
-    px1080 = 1920 * 1080
-    budgeted = None
-    if args.budget_frac > 0:
-        budgeted = run_batch_budget(args, ctx, cams, ids, mlp_d, out, tile, ctas, flush, stream, px1080)
-    line = {"metric": METRIC, "value": round(npix / (ms / 1000.0) / px1080 * ws, 3), "unit": "frames/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+    r = measure_batch64(args, dev, flush, stream, budget_frac=args.budget_frac)
+    ms = max_over_ranks(ws, r["batched"]["ms_per_batch"])
+    npix = r["pixels_per_batch"]
+    line = {"metric": METRIC, "value": round(npix / (ms / 1000.0) / (1920 * 1080) * ws, 3), "unit": "frames/s",
+            "n_gpus": ws, "steps": max(5, args.steps // 2), "warmup": 3, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch_64", "views": len(cams), "pixels_per_batch": int(npix),
-                       "scene": "16x16 blocks x 3 LOD (%s), %s" % (", ".join(f"{r}^3/{q}^2" for r, q in res),
-                                                                   ctx.storage),
-                       "blocks_per_view_mean": round(float(np.mean([len(i) for i in ids])), 1),
-                       "tuned": {"tile": cow.Batch.TILE_SHAPES[tile], "ctas_per_sm": ctas, "ms": round(tune_ms, 3)},
-                       "launch": "one persistent launch per batch, CUDA graph replay",
-                       "l2": "512 MiB write between timed steps, outside the per-step events"},
-            "frames_per_s_note": "1080p-equivalent frames/s = pixels of the batch per second / (1920 x 1080)",
+            "config": {"workload": "batch_64", "l2": "512 MiB write between timed steps, outside the per-step events",
+                       **{k: r[k] for k in ("views", "pixels_per_batch", "scene", "blocks_per_view_mean", "tuned")}},
             "mrays_per_s": round(npix / ms / 1e3 * ws, 3),
-            "plain_fp32_per_view": {"ms_per_batch": round(ms32, 3),
-                                    "frames_per_s": round(npix / (ms32 / 1000.0) / px1080, 3)},
-            "same_storage_per_view": {"ms_per_batch": round(ms16, 3),
-                                      "frames_per_s": round(npix / (ms16 / 1000.0) / px1080, 3)},
-            "psnr_vs_plain_fp32_db": round(p, 2), "clocks": ck}
-    if budgeted is not None:
-        line["under_residency_budget"] = budgeted
+            **{k: v for k, v in r.items() if k not in ("views", "pixels_per_batch", "scene", "blocks_per_view_mean",
+                                                      "tuned")}}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

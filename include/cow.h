@@ -540,6 +540,20 @@ cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles);
  * this context (COW_ERR_DEVICE_ASSERT or COW_ERR_TIMEOUT); clears it. */
 cow_status cow_sync_check(cow_ctx *ctx, void *stream);
 
+/* Test hook (no counterpart in the paper): lets a test drive the bounded
+ * device-side waits to their time-out without faulting anything.  The
+ * kernels that stage a view's block records into shared memory with a TMA
+ * bulk copy (the COW_SCHED_THREAD and COW_SCHED_WARP view schedules and the
+ * batched form) wait for it on an mbarrier with an iteration limit.  With
+ * COW_TEST_SKIP_RECORD_COPY the copy is not issued, so the barrier's phase
+ * never completes and nothing is in flight; each wait gives up after
+ * wait_polls polls (0 = the default 2^24), the kernel records the time-out
+ * (cow_sync_check then returns COW_ERR_TIMEOUT), its CTAs leave without
+ * writing their pixels, and the context stays usable.  Production callers
+ * never call this (flags 0, wait_polls 0).  Errors: INVALID_ARG. */
+#define COW_TEST_SKIP_RECORD_COPY 1u
+cow_status cow_set_test_hooks(cow_ctx *ctx, uint32_t flags, uint32_t wait_polls);
+
 /* Copy out a block's occupancy bits (ceil(ncell/32) words, cell index
  * (cz*Nc + cy)*Nc + cx, bit c&31 of word c>>5) into host memory. */
 cow_status cow_export_occupancy(const cow_ctx *ctx, int32_t block, uint32_t *out_bits, int64_t n_words);

@@ -37,7 +37,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
-           "cow_sync_check", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
+           "cow_sync_check", "cow_set_test_hooks", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_refine_view_order", "cow_sparsity_loss", "cow_opacity_loss",
            "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
@@ -93,6 +93,7 @@ def lib():
             "cow_render": [P, P, i32, P, P, P, flt, u32, P, P, P, P],
             "cow_render_rays": [P, P, P, i64, P, i32, P, flt, u32, P, P, P, P],
             "cow_sync_check": [P, P],
+            "cow_set_test_hooks": [P, u32, u32],
             "cow_set_schedule": [P, i32],
             "cow_set_tile_order": [P, i32],
             "cow_set_block_mlps": [P, P, i32, i32, P],
@@ -390,6 +391,10 @@ class Context:
     def set_tile_order(self, strip_tiles: int):
         """0: raster tile order; k > 0: vertical strips of k tile columns."""
         _check(lib().cow_set_tile_order(self._ctx, int(strip_tiles)))
+
+    def set_test_hooks(self, skip_record_copy: bool = False, wait_polls: int = 0):
+        """Tests of the bounded device waits (cow_set_test_hooks)."""
+        _check(lib().cow_set_test_hooks(self._ctx, 1 if skip_record_copy else 0, int(wait_polls)))
 
     def sync_check(self, stream=None):
         _check(lib().cow_sync_check(self._ctx, _stream_ptr(stream)))

@@ -109,19 +109,24 @@ __global__ void __launch_bounds__(TW * TH, kBatchThreadsPerSm / (TW * TH)) k_mar
             if (staged) {
                 // thread 0 copies and waits (bounded); the CTA then proceeds or
                 // leaves as one, so no thread is left at a later barrier
+                // (a second wait that also runs out leaves the copy possibly
+                // still writing this CTA's shared memory: two waits of 2^24
+                // polls, never seen short of a stalled copy engine)
+                const unsigned polls = a.wait_polls ? a.wait_polls : kBatchWaitPolls;
                 if (threadIdx.x == 0) {
                     fence_proxy_async();
-                    bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
+                    if (!(a.test_flags & kTestSkipRecordCopy))
+                        bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
                     int ok = 1;
-                    if (!mbar_wait(&s_bar, phase, kBatchWaitPolls)) {
+                    if (!mbar_wait(&s_bar, phase, polls)) {
                         atomicOr(a.err, kErrTimeout);
-                        ok = mbar_wait(&s_bar, phase, kBatchWaitPolls) ? 1 : 0;
+                        ok = mbar_wait(&s_bar, phase, polls) ? 1 : 0;
                     }
                     s_n = ok;
                 }
                 __syncthreads();
                 if (!s_n) return;  // the copy never completed: every thread leaves
-                mbar_wait(&s_bar, phase, kBatchWaitPolls);  // completed phase: returns at once, orders the reads
+                mbar_wait(&s_bar, phase, polls);  // completed phase: returns at once, orders the reads
                 phase ^= 1u;
             }
         }

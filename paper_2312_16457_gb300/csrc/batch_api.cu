@@ -119,6 +119,8 @@ cow::BatchArgs make_args(cow_batch *b, const float *mlp, float ert_eps, uint32_t
     a.out_nsamp = ns;
     a.err = b->ctx->d_err;
     a.counter = b->d_counter;
+    a.test_flags = b->ctx->test_flags;
+    a.wait_polls = b->ctx->wait_polls;
     return a;
 }
 

@@ -900,6 +900,8 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     a.out_aux = aux;
     a.out_nsamp = ns;
     a.err = ctx->d_err;
+    a.test_flags = ctx->test_flags;
+    a.wait_polls = ctx->wait_polls;
     if (block_mlp) {
         a.block_mlps = (const float *const *)((unsigned char *)ctx->views.p + vbytes + rbytes);
         a.n_freq = ctx->n_freq;
@@ -970,6 +972,8 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     a.out_aux = aux;
     a.out_nsamp = ns;
     a.err = ctx->d_err;
+    a.test_flags = ctx->test_flags;
+    a.wait_polls = ctx->wait_polls;
     a.ray_o = o;
     a.ray_d = d;
     a.n_rays = n_rays;
@@ -1577,6 +1581,17 @@ cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule) {
     if (schedule != COW_SCHED_WARP && schedule != COW_SCHED_THREAD && schedule != COW_SCHED_THREAD_CONST)
         return fail(COW_ERR_INVALID_ARG, "unknown schedule %d", schedule);
     ctx->schedule = schedule;
+    return COW_OK;
+}
+
+static_assert(COW_TEST_SKIP_RECORD_COPY == cow::kTestSkipRecordCopy, "test flag values");
+
+cow_status cow_set_test_hooks(cow_ctx *ctx, uint32_t flags, uint32_t wait_polls) {
+    g_last_error.clear();
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    if (flags & ~(uint32_t)COW_TEST_SKIP_RECORD_COPY) return fail(COW_ERR_INVALID_ARG, "unknown test flags 0x%x", flags);
+    ctx->test_flags = flags;
+    ctx->wait_polls = wait_polls;
     return COW_OK;
 }
 

@@ -119,6 +119,7 @@ struct cow_ctx {
     float occ_thresh = 0.01f;
     int schedule = COW_SCHED_THREAD_CONST;
     int tile_strip = 0;  // cow_set_tile_order
+    uint32_t test_flags = 0, wait_polls = 0;  // cow_set_test_hooks
     std::vector<cowi::BlockHost> blocks;
     std::vector<cow::BlockRec> recs;  // block records (kernels receive copies by value)
     unsigned *d_err = nullptr;

@@ -32,7 +32,14 @@ struct MarchArgs {
     float *out_block_T;              // ray mode, may be null: n_rays x n_ray_ids in-block transmittances
     const float *block_mlp_base;     // ray mode, per-block MLPs: block id's weights at base + id * stride
     int64_t block_mlp_stride;        // floats (null base: the global MLP)
+    uint32_t test_flags;             // kTestSkipRecordCopy (tests of the bounded waits); 0 in production
+    uint32_t wait_polls;             // bound on each mbarrier wait (0: the kernel's default)
 };
+
+// Test hook of the kernels that stage block records with a TMA bulk copy:
+// the copy is not issued, so the barrier's phase never completes and the
+// bounded wait runs out with nothing in flight.
+constexpr uint32_t kTestSkipRecordCopy = 1u;
 
 // marching schedules of the view kernel
 constexpr int kSchedWarp = 0;         // one ray per warp, lanes on consecutive lattice samples
@@ -123,6 +130,8 @@ struct BatchArgs {
     int32_t *out_nsamp;      // may be null
     unsigned *err;
     unsigned *counter;       // work-queue head, zero at launch
+    uint32_t test_flags;     // kTestSkipRecordCopy (tests of the bounded waits); 0 in production
+    uint32_t wait_polls;     // bound on each mbarrier wait (0: the kernel's default)
 };
 // tile_cfg: 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8 pixels per CTA
 void batch_tile_shape(int tile_cfg, int *tw, int *th);

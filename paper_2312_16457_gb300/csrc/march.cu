@@ -164,13 +164,19 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_march_views(MarchArgs 
     if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
     if (!kBlockMlp) load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
-    // the view's block records (near to far) go to shared memory by one TMA bulk copy
+    // the view's block records (near to far) go to shared memory by one TMA
+    // bulk copy.  A wait that runs out records kErrTimeout and waits once more
+    // (bounded) for the copy; if that also runs out the CTA leaves without
+    // touching the records (the copy would then still be writing this CTA's
+    // shared memory: two waits of 2^24 polls each, seconds, never seen short
+    // of a stalled copy engine).
     if (staged) {
-        if (threadIdx.x == 0)
+        const unsigned polls = a.wait_polls ? a.wait_polls : kWaitPolls;
+        if (threadIdx.x == 0 && !(a.test_flags & kTestSkipRecordCopy))
             bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
-        if (!mbar_wait(&s_bar, 0, kWaitPolls)) {
+        if (!mbar_wait(&s_bar, 0, polls)) {
             atomicOr(a.err, kErrTimeout);
-            if (!mbar_wait(&s_bar, 0, kWaitPolls)) return;  // copy still in flight: leave without touching it
+            if (!mbar_wait(&s_bar, 0, polls)) return;  // copy still in flight: leave without touching it
         }
     }
     march_tile_rays<DT, kBlockMlp>(a, v, staged ? s_rec : a.recs + v.ids_begin, tile, s_mlp);
@@ -312,12 +318,13 @@ __global__ void __launch_bounds__(kThreads, kMinBlocksW) k_march_views_w(MarchAr
     if (threadIdx.x == 0 && staged) mbar_init(&s_bar, 1);
     load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
     __syncthreads();
-    if (staged) {
-        if (threadIdx.x == 0)
+    if (staged) {  // as in k_march_views
+        const unsigned polls = a.wait_polls ? a.wait_polls : kWaitPolls;
+        if (threadIdx.x == 0 && !(a.test_flags & kTestSkipRecordCopy))
             bulk_copy_g2s(s_rec, a.recs + v.ids_begin, (unsigned)(n_blk * sizeof(BlockRec)), &s_bar);
-        if (!mbar_wait(&s_bar, 0, kWaitPolls)) {
+        if (!mbar_wait(&s_bar, 0, polls)) {
             atomicOr(a.err, kErrTimeout);
-            if (!mbar_wait(&s_bar, 0, kWaitPolls)) return;
+            if (!mbar_wait(&s_bar, 0, polls)) return;
         }
     }
     const BlockRec *recs = staged ? s_rec : a.recs + v.ids_begin;
