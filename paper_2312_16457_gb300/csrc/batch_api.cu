@@ -38,6 +38,23 @@ struct cow_batch {
     cudaGraphExec_t exec = nullptr;
     cow::BatchArgs gargs;
     int g_tile = -1, g_grid = -1;
+    uint64_t g_gen = 0;
+    // runs of views whose distinct blocks fit the launch parameter buffer:
+    // one persistent launch a run, records by value (used when every view
+    // has at most kParamRecs blocks and no residency budget is set)
+    struct Run {
+        size_t off = 0;           // the run's [hdr | views | index lists] in stage2
+        int32_t n_views = 0, n_items = 0;
+        cow::ParamRecs pr;        // its distinct blocks' records
+    };
+    std::vector<Run> runs;
+    bool param_mode = false;
+    size_t stage2_cap = 0, stage2_bytes = 0;
+    unsigned char *h_stage2 = nullptr;  // pinned
+    unsigned char *d_stage2 = nullptr;
+    unsigned *d_counters = nullptr;     // one work-queue head per run
+    int32_t counters_cap = 0;
+    uint64_t stage_gen = 0;             // advances whenever a staging is rebuilt
 };
 
 namespace {
@@ -51,6 +68,9 @@ void batch_destroy(cow_batch *b) {
     cudaFreeHost(b->h_stage);
     cudaFree(b->d_stage);
     cudaFree(b->d_counter);
+    cudaFreeHost(b->h_stage2);
+    cudaFree(b->d_stage2);
+    cudaFree(b->d_counters);
     delete b;
 }
 
@@ -99,7 +119,177 @@ cow_status build_stage(cow_batch *b, int32_t first, int32_t last) {
     for (int32_t v = 0; v < nv; v++) b->n_pixels += (int64_t)b->cams[(size_t)v].width * b->cams[(size_t)v].height;
     b->rec_gen = b->ctx->rec_gen;
     b->dirty = first != 0 || last != nv;  // a group's staging: the whole batch must be rebuilt later
+    b->param_mode = false;
+    b->stage_gen++;
     return COW_OK;
+}
+
+// Views in runs whose distinct blocks fit a launch's parameter buffer
+// (kParamRecs records): a run grows by the view that adds the fewest new
+// blocks (in view order for very large batches) while the union still fits.
+// Every run gets its records by value and its views' lists as byte indices
+// into them; the staging of all runs is one pinned buffer copied at once.
+cow_status build_runs(cow_batch *b) {
+    cudaError_t e = cudaEventSynchronize(b->copied);  // the previous copy has read the stagings
+    if (e != cudaSuccess) return fail(COW_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+    int tw, th;
+    cow::batch_tile_shape(b->tile_cfg, &tw, &th);
+    const int32_t nv = (int32_t)b->cams.size();
+    const int32_t nb = (int32_t)b->ctx->blocks.size();
+    // distinct blocks of every view
+    std::vector<std::vector<int32_t>> own((size_t)nv);
+    for (int32_t v = 0; v < nv; v++) {
+        for (int32_t k = b->offs[(size_t)v]; k < b->offs[(size_t)v + 1]; k++) {
+            const int32_t id = b->ids[(size_t)k];
+            if (std::find(own[(size_t)v].begin(), own[(size_t)v].end(), id) == own[(size_t)v].end())
+                own[(size_t)v].push_back(id);
+        }
+    }
+    std::vector<std::vector<int32_t>> run_views;
+    {
+        std::vector<char> done((size_t)nv, 0), in((size_t)nb, 0);
+        const bool pick_best = nv <= 1024;
+        int32_t left = nv, next = 0;
+        while (left > 0) {
+            std::vector<int32_t> views, blocks;
+            for (;;) {
+                int32_t best = -1, best_add = 1 << 30;
+                if (views.empty() || !pick_best) {
+                    while (next < nv && done[(size_t)next]) next++;
+                    if (next < nv) {
+                        int32_t add = 0;
+                        for (int32_t id : own[(size_t)next]) add += in[(size_t)id] ? 0 : 1;
+                        best = next;
+                        best_add = add;
+                    }
+                } else {
+                    for (int32_t v = 0; v < nv; v++) {
+                        if (done[(size_t)v]) continue;
+                        int32_t add = 0;
+                        for (int32_t id : own[(size_t)v]) add += in[(size_t)id] ? 0 : 1;
+                        if (add < best_add) {
+                            best_add = add;
+                            best = v;
+                        }
+                    }
+                }
+                if (best < 0 || (int32_t)blocks.size() + best_add > cow::kParamRecs) break;
+                done[(size_t)best] = 1;
+                left--;
+                views.push_back(best);
+                for (int32_t id : own[(size_t)best])
+                    if (!in[(size_t)id]) {
+                        in[(size_t)id] = 1;
+                        blocks.push_back(id);
+                    }
+            }
+            for (int32_t id : blocks) in[(size_t)id] = 0;
+            run_views.push_back(std::move(views));
+        }
+    }
+    // staging: per run [hdr 256 B | views | index bytes], 256-byte aligned
+    size_t need = 0;
+    for (const auto &rv : run_views) {
+        size_t ni = 0;
+        for (int32_t v : rv) ni += (size_t)(b->offs[(size_t)v + 1] - b->offs[(size_t)v]);
+        need += 256 + ((rv.size() * sizeof(cow::ViewRec) + 255) & ~(size_t)255) + ((ni + 255) & ~(size_t)255);
+    }
+    if (need > b->stage2_cap) {
+        cudaFreeHost(b->h_stage2);
+        cudaFree(b->d_stage2);
+        b->h_stage2 = nullptr;
+        b->d_stage2 = nullptr;
+        b->stage2_cap = 0;
+        e = cudaHostAlloc((void **)&b->h_stage2, need, cudaHostAllocDefault);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_stage2, need);
+        if (e != cudaSuccess)
+            return fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "batch staging: %s",
+                        cudaGetErrorString(e));
+        b->stage2_cap = need;
+    }
+    if ((int32_t)run_views.size() > b->counters_cap) {
+        cudaFree(b->d_counters);
+        b->d_counters = nullptr;
+        b->counters_cap = 0;
+        e = cudaMalloc((void **)&b->d_counters, run_views.size() * sizeof(unsigned));
+        if (e != cudaSuccess)
+            return fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "batch counters: %s",
+                        cudaGetErrorString(e));
+        b->counters_cap = (int32_t)run_views.size();
+    }
+    std::vector<int64_t> pix_of((size_t)nv + 1, 0);
+    for (int32_t v = 0; v < nv; v++)
+        pix_of[(size_t)v + 1] = pix_of[(size_t)v] + (int64_t)b->cams[(size_t)v].width * b->cams[(size_t)v].height;
+    b->runs.assign(run_views.size(), cow_batch::Run());
+    std::vector<int32_t> slot((size_t)nb, -1);
+    size_t off = 0;
+    int64_t total_items = 0;
+    b->max_blk = 0;
+    for (size_t r = 0; r < run_views.size(); r++) {
+        cow_batch::Run &run = b->runs[r];
+        const auto &rv = run_views[r];
+        run.off = off;
+        run.n_views = (int32_t)rv.size();
+        std::memset(&run.pr, 0, sizeof(run.pr));
+        int32_t n_rec = 0;
+        std::vector<int32_t> used;
+        cow::ViewRec *vr = (cow::ViewRec *)(b->h_stage2 + off + 256);
+        unsigned char *idx = b->h_stage2 + off + 256 + ((rv.size() * sizeof(cow::ViewRec) + 255) & ~(size_t)255);
+        int64_t tiles = 0;
+        int32_t n_idx = 0;
+        for (size_t k = 0; k < rv.size(); k++) {
+            const int32_t v = rv[k];
+            const cow_camera &cam = b->cams[(size_t)v];
+            cow::ViewRec &w = vr[k];
+            std::memset(&w, 0, sizeof(w));
+            for (int rr = 0; rr < 3; rr++) {
+                for (int q = 0; q < 3; q++) w.Rm[3 * rr + q] = (float)cam.c2w[4 * rr + q];
+                w.o[rr] = (float)cam.c2w[4 * rr + 3];
+            }
+            w.f = (float)focal_length(cam.height, cam.fov_y_deg);
+            w.W = cam.width;
+            w.H = cam.height;
+            w.tiles_x = (cam.width + tw - 1) / tw;
+            w.tile_begin = (int32_t)tiles;
+            w.ids_begin = n_idx;
+            w.ids_count = b->offs[(size_t)v + 1] - b->offs[(size_t)v];
+            w.pix_offset = pix_of[(size_t)v];
+            b->max_blk = std::max(b->max_blk, w.ids_count);
+            tiles += (int64_t)w.tiles_x * ((cam.height + th - 1) / th);
+            for (int32_t q = b->offs[(size_t)v]; q < b->offs[(size_t)v + 1]; q++) {
+                const int32_t id = b->ids[(size_t)q];
+                if (slot[(size_t)id] < 0) {
+                    slot[(size_t)id] = n_rec;
+                    run.pr.r[n_rec++] = b->ctx->recs[(size_t)id];
+                    used.push_back(id);
+                }
+                idx[n_idx++] = (unsigned char)slot[(size_t)id];
+            }
+        }
+        for (int32_t id : used) slot[(size_t)id] = -1;
+        if (tiles > 0x7fffffff) return fail(COW_ERR_INVALID_ARG, "too many tiles in one batch run");
+        int32_t *hdr = (int32_t *)(b->h_stage2 + off);
+        hdr[0] = run.n_views;
+        hdr[1] = (int32_t)tiles;
+        run.n_items = (int32_t)tiles;
+        total_items += tiles;
+        off += 256 + ((rv.size() * sizeof(cow::ViewRec) + 255) & ~(size_t)255) + (((size_t)n_idx + 255) & ~(size_t)255);
+    }
+    b->stage2_bytes = off;
+    b->n_pixels = pix_of[(size_t)nv];
+    b->n_items = (int32_t)std::min<int64_t>(total_items, 0x7fffffff);
+    b->rec_gen = b->ctx->rec_gen;
+    b->dirty = false;
+    b->param_mode = true;
+    b->stage_gen++;
+    return COW_OK;
+}
+
+// Every view's list fits a launch's parameter buffer.
+bool runs_fit(const cow_batch *b) {
+    for (size_t v = 0; v + 1 < b->offs.size(); v++)
+        if (b->offs[v + 1] - b->offs[v] > cow::kParamRecs) return false;
+    return true;
 }
 
 cow::BatchArgs make_args(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *rgb, float *aux,
@@ -112,7 +302,7 @@ cow::BatchArgs make_args(cow_batch *b, const float *mlp, float ert_eps, uint32_t
     a.mlp = mlp;
     a.ert_eps = ert_eps;
     a.flags = flags;
-    a.dtype = b->ctx->dtype;
+    a.dtype = kernel_dtype(b->ctx);
     a.smem_recs = b->max_blk <= 96 ? b->max_blk : 0;  // longer lists are read from global memory
     a.out_rgb = rgb;
     a.out_aux = aux;
@@ -129,6 +319,24 @@ cow::BatchArgs make_args(cow_batch *b, const float *mlp, float ert_eps, uint32_t
 // captured event cannot be waited on from outside; graph launches record it
 // after the whole graph instead).
 cudaError_t enqueue(cow_batch *b, const cow::BatchArgs &a, int tile_cfg, int grid, cudaStream_t st, bool mark) {
+    if (b->param_mode) {  // all runs: one staging copy, the queue heads, one launch a run
+        cudaError_t e = cudaMemcpyAsync(b->d_stage2, b->h_stage2, b->stage2_bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && mark) e = cudaEventRecord(b->copied, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, b->runs.size() * sizeof(unsigned), st);
+        for (size_t r = 0; r < b->runs.size() && e == cudaSuccess; r++) {
+            const cow_batch::Run &run = b->runs[r];
+            if (run.n_items == 0) continue;
+            cow::BatchArgs ar = a;
+            ar.hdr = (const int32_t *)(b->d_stage2 + run.off);
+            ar.views = (const cow::ViewRec *)(b->d_stage2 + run.off + 256);
+            ar.vidx = b->d_stage2 + run.off + 256 + (((size_t)run.n_views * sizeof(cow::ViewRec) + 255) & ~(size_t)255);
+            ar.recs = nullptr;
+            ar.smem_recs = 0;
+            ar.counter = b->d_counters + r;
+            e = cow::launch_march_batch(ar, tile_cfg, grid, st, &run.pr);
+        }
+        return e;
+    }
     cudaError_t e = cudaMemcpyAsync(b->d_stage, b->h_stage, b->stage_bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && mark) e = cudaEventRecord(b->copied, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st);
@@ -286,8 +494,10 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     DeviceGuard dg(b->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (b->ctx->budget > 0) return render_groups(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
-    if (b->dirty || b->rec_gen != b->ctx->rec_gen) {  // new views, tile shape, or block records
-        cow_status rc = build_stage(b, 0, (int32_t)b->cams.size());
+    const bool want_runs = runs_fit(b);
+    if (b->dirty || b->rec_gen != b->ctx->rec_gen || b->param_mode != want_runs) {
+        // new views, tile shape, or block records
+        cow_status rc = want_runs ? build_runs(b) : build_stage(b, 0, (int32_t)b->cams.size());
         if (rc != COW_OK) return rc;
     }
     b->last_groups = 1;
@@ -297,7 +507,7 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
         COW_CUDA(enqueue(b, a, b->tile_cfg, grid, st, true));
         return COW_OK;
     }
-    const bool same = b->exec && b->g_tile == b->tile_cfg && b->g_grid == grid &&
+    const bool same = b->exec && b->g_tile == b->tile_cfg && b->g_grid == grid && b->g_gen == b->stage_gen &&
                       std::memcmp(&b->gargs, &a, sizeof(a)) == 0;
     if (!same) {
         if (b->exec) {
@@ -319,6 +529,7 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
         b->gargs = a;
         b->g_tile = b->tile_cfg;
         b->g_grid = grid;
+        b->g_gen = b->stage_gen;
     }
     COW_CUDA(cudaGraphLaunch(b->exec, st));
     COW_CUDA(cudaEventRecord(b->copied, st));

@@ -732,14 +732,12 @@ cudaError_t launch_backward_rays(const BwdArgs &a, const RayRecs &rr, cudaStream
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_reduce_rows<<<(kMlpParams + 127) / 128, 128, 0, st>>>(a.partials, nb, a.grad_mlp);
-    switch (a.dtype) {
-    case kF32: k_remarch_backward<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kF16: k_remarch_backward<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kBF16: k_remarch_backward<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8: k_remarch_backward<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kMixed: k_remarch_backward<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8D: k_remarch_backward<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    default: return cudaErrorInvalidValue;
+    {
+        const cudaError_t e_ = dispatch_dt(a.dtype, [&](auto D) {
+            k_remarch_backward<decltype(D)::value><<<nb, kBwdThreads, 0, st>>>(a, rr);
+            return cudaSuccess;
+        });
+        if (e_ != cudaSuccess) return e_;
     }
     return cudaGetLastError();
 }
@@ -748,27 +746,23 @@ cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cu
     if (a.n_rays <= 0) return cudaSuccess;
     const int nb = backward_rows(a.n_rays);
     const int64_t padded = ((a.n_rays + 31) & ~(int64_t)31) * a.n_ids;  // k_bm_mlp's threads
-    switch (a.dtype) {
-    case kF32: k_bm_pass1<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kF16: k_bm_pass1<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kBF16: k_bm_pass1<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8: k_bm_pass1<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kMixed: k_bm_pass1<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8D: k_bm_pass1<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    default: return cudaErrorInvalidValue;
+    {
+        const cudaError_t e_ = dispatch_dt(a.dtype, [&](auto D) {
+            k_bm_pass1<decltype(D)::value><<<nb, kBwdThreads, 0, st>>>(a, rr);
+            return cudaSuccess;
+        });
+        if (e_ != cudaSuccess) return e_;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_bm_mlp<<<(unsigned)((padded + kBwdThreads - 1) / kBwdThreads), kBwdThreads, 0, st>>>(a, rr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    switch (a.dtype) {
-    case kF32: k_bm_remarch<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kF16: k_bm_remarch<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kBF16: k_bm_remarch<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8: k_bm_remarch<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kMixed: k_bm_remarch<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8D: k_bm_remarch<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    default: return cudaErrorInvalidValue;
+    {
+        const cudaError_t e_ = dispatch_dt(a.dtype, [&](auto D) {
+            k_bm_remarch<decltype(D)::value><<<nb, kBwdThreads, 0, st>>>(a, rr);
+            return cudaSuccess;
+        });
+        if (e_ != cudaSuccess) return e_;
     }
     return cudaGetLastError();
 }
@@ -776,14 +770,12 @@ cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cu
 cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const int nb = (int)((a.n + kBwdThreads - 1) / kBwdThreads);
-    switch (a.dtype) {
-    case kF32: k_sparsity<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kF16: k_sparsity<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kBF16: k_sparsity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8: k_sparsity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kMixed: k_sparsity<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8D: k_sparsity<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    default: return cudaErrorInvalidValue;
+    {
+        const cudaError_t e_ = dispatch_dt(a.dtype, [&](auto D) {
+            k_sparsity<decltype(D)::value><<<nb, kBwdThreads, 0, st>>>(a, rr);
+            return cudaSuccess;
+        });
+        if (e_ != cudaSuccess) return e_;
     }
     return cudaGetLastError();
 }
@@ -791,14 +783,12 @@ cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st
 cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const int nb = (int)((a.n + kBwdThreads - 1) / kBwdThreads);
-    switch (a.dtype) {
-    case kF32: k_opacity<kF32><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kF16: k_opacity<kF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kBF16: k_opacity<kBF16><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8: k_opacity<kFP8><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kMixed: k_opacity<kMixed><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    case kFP8D: k_opacity<kFP8D><<<nb, kBwdThreads, 0, st>>>(a, rr); break;
-    default: return cudaErrorInvalidValue;
+    {
+        const cudaError_t e_ = dispatch_dt(a.dtype, [&](auto D) {
+            k_opacity<decltype(D)::value><<<nb, kBwdThreads, 0, st>>>(a, rr);
+            return cudaSuccess;
+        });
+        if (e_ != cudaSuccess) return e_;
     }
     return cudaGetLastError();
 }

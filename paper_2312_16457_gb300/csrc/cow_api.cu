@@ -892,7 +892,7 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
     a.recs = (const cow::BlockRec *)((unsigned char *)ctx->views.p + vbytes);
     a.views = (const cow::ViewRec *)ctx->views.p;
     a.n_views = n_views;
-    a.dtype = ctx->dtype;
+    a.dtype = kernel_dtype(ctx);
     a.mlp = d_mlp;
     a.ert_eps = ert_eps;
     a.flags = flags;
@@ -964,7 +964,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     if ((rc = resolve_out(out_nsamp, (size_t)n_rays * 4, ctx->out_nsamp, &ns, &h_ns)) != COW_OK) return rc;
     cow::MarchArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.dtype = ctx->dtype;
+    a.dtype = kernel_dtype(ctx);
     a.mlp = d_mlp;
     a.ert_eps = ert_eps;
     a.flags = flags;
@@ -1046,7 +1046,7 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     COW_CUDA(ctx->partials.reserve(part_bytes + (size_t)std::max<int64_t>(n_rays, 1) * 8 * sizeof(float)));
     cow::BwdArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.dtype = ctx->dtype;
+    a.dtype = kernel_dtype(ctx);
     a.mlp = mlp;
     a.ert_eps = ert_eps;
     a.ray_o = o;
@@ -1105,7 +1105,7 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
     const int32_t n_in = 10 + 6 * ctx->n_freq;
     cow::BmBwdArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.dtype = ctx->dtype;
+    a.dtype = kernel_dtype(ctx);
     a.ray_o = o;
     a.ray_d = d;
     a.n_rays = n_rays;
@@ -1159,7 +1159,7 @@ cow_status reg_prepare(cow_ctx *ctx, const int32_t *ids, int32_t n_ids, float *l
         a.grad_grid = (float *const *)ctx->gptrs.p;
         a.grad_planes = (float *const *)ctx->gptrs.p + nb;
     }
-    a.dtype = ctx->dtype;
+    a.dtype = kernel_dtype(ctx);
     a.loss = loss;
     a.err = ctx->d_err;
     return COW_OK;
@@ -1802,7 +1802,7 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     COW_CUDA(cudaGetLastError());
     cow::BwdArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.dtype = ctx->dtype;
+    a.dtype = kernel_dtype(ctx);
     a.mlp = mlp;
     a.ert_eps = ert_eps;
     a.ray_o = o;

@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace cow {
 
 constexpr int kNch = 8;
@@ -35,6 +37,12 @@ constexpr unsigned kErrArg = 4u;      // a kernel met an argument it cannot hand
 // the eight corners of voxel (x, y, z), corner k = dx + 2 dy + 4 dz, 16
 // bytes), and the planes in FP8 in the quad layout.
 enum Dtype { kF32 = 0, kF16 = 1, kBF16 = 2, kFP8 = 3, kMixed = 4, kFP8D = 5 };
+
+// A kernel's DT template argument is the storage dtype, plus kBrickBit for a
+// brick-sparse grid (its lookups go through the brick table; the dense
+// variants keep the plain vertex indexing and register budget).
+constexpr int kBrickBit = 8;
+constexpr int kStoreMask = 7;
 
 // Brick-sparse grids: the grid is cut into bricks of kBrick voxels per edge
 // (one coarse occupancy cell, kOccGroup cells of 4 voxels); only bricks with
@@ -460,5 +468,30 @@ struct Store<kFP8D> {
 };
 
 __device__ __forceinline__ float sigmoidf_fast(float x) { return __fdividef(1.0f, 1.0f + __expf(-x)); }
+
+// Host: calls f(std::integral_constant<int, DT>{}) with the kernel variant of
+// a kernel dtype (storage, | kBrickBit for brick-sparse grids); returns its
+// result, or cudaErrorInvalidValue for an unknown dtype.
+template <class F>
+inline cudaError_t dispatch_dt(int dt, F &&f) {
+#define COW_DT_CASE(V) \
+    case (V): return f(std::integral_constant<int, (V)>{});
+    switch (dt) {
+        COW_DT_CASE(kF32)
+        COW_DT_CASE(kF16)
+        COW_DT_CASE(kBF16)
+        COW_DT_CASE(kFP8)
+        COW_DT_CASE(kMixed)
+        COW_DT_CASE(kFP8D)
+        COW_DT_CASE(kF32 | kBrickBit)
+        COW_DT_CASE(kF16 | kBrickBit)
+        COW_DT_CASE(kBF16 | kBrickBit)
+        COW_DT_CASE(kFP8 | kBrickBit)
+        COW_DT_CASE(kMixed | kBrickBit)
+        COW_DT_CASE(kFP8D | kBrickBit)
+    default: return cudaErrorInvalidValue;
+    }
+#undef COW_DT_CASE
+}
 
 }  // namespace cow

@@ -141,3 +141,11 @@ struct cow_ctx {
     uint64_t rec_gen = 0;   // advances whenever a block record is rewritten
     cudaMemPool_t pool = nullptr;  // loads under a budget allocate from it (created with the first budget)
 };
+
+namespace cowi {
+
+// The DT a context's kernels are instantiated for: the storage dtype, with
+// cow::kBrickBit for brick-sparse grids.
+inline int kernel_dtype(const cow_ctx *c) { return c->dtype | (c->bricks ? cow::kBrickBit : 0); }
+
+}  // namespace cowi

@@ -132,10 +132,14 @@ struct BatchArgs {
     unsigned *counter;       // work-queue head, zero at launch
     uint32_t test_flags;     // kTestSkipRecordCopy (tests of the bounded waits); 0 in production
     uint32_t wait_polls;     // bound on each mbarrier wait (0: the kernel's default)
+    const unsigned char *vidx;  // records by value (pr): each view's list as indices into them, by ids_begin
 };
-// tile_cfg: 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8 pixels per CTA
+// tile_cfg: 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8 pixels per CTA.  pr: the
+// run's distinct block records by value (at most kParamRecs; the views'
+// lists in a.vidx), or null for records in a.recs (staged into shared memory).
 void batch_tile_shape(int tile_cfg, int *tw, int *th);
-cudaError_t launch_march_batch(const BatchArgs &a, int tile_cfg, int grid, cudaStream_t st);
+cudaError_t launch_march_batch(const BatchArgs &a, int tile_cfg, int grid, cudaStream_t st,
+                               const ParamRecs *pr = nullptr);
 
 // K4 / K5: packing and occupancy (pack.cu)
 cudaError_t launch_amax8(const float *x, int64_t n_vec, unsigned *amax_bits, cudaStream_t st);

@@ -37,6 +37,8 @@ constexpr int kPlaneLd = COW_PLANE_LD_POLICY;
 template <int DT>
 __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], const float g[3],
                                                   float2 f[4]) {
+    constexpr int ST = DT & kStoreMask;                 // storage format
+    constexpr bool kBricks = (DT & kBrickBit) != 0;     // brick-sparse grid
     float fr[3];
     int c0[3];
 #pragma unroll
@@ -45,27 +47,33 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
         c0[a] = v;
         fr[a] = fminf(fmaxf(g[a], 0.f), (float)(b.R - 1)) - (float)v;
     }
-    int64_t base, dbase;
-    int slot = 0;
-    if (b.brick) {
+    const int R = b.R;
+    int64_t base, dbase = 0;
+    int sy, sz;
+    bool stored = true;
+    if constexpr (kBricks) {
         const int nb = b.Nb;
-        slot = __ldg(b.brick + ((c0[2] >> kBrickLog2) * nb + (c0[1] >> kBrickLog2)) * nb + (c0[0] >> kBrickLog2));
-        const int loc = (c0[2] & (kBrick - 1)) * b.bsz + (c0[1] & (kBrick - 1)) * b.bsy + (c0[0] & (kBrick - 1));
+        const int slot =
+            __ldg(b.brick + ((c0[2] >> kBrickLog2) * nb + (c0[1] >> kBrickLog2)) * nb + (c0[0] >> kBrickLog2));
+        sy = b.bsy;
+        sz = b.bsz;
+        const int loc = (c0[2] & (kBrick - 1)) * sz + (c0[1] & (kBrick - 1)) * sy + (c0[0] & (kBrick - 1));
         base = (int64_t)slot * b.belem + loc;
         dbase = (int64_t)slot * kDensBrickElems + loc;
+        stored = slot >= 0;
     } else {
-        const int R = b.R;
         base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
         dbase = base;
+        sy = R;
+        sz = R * R;
     }
-    const int sy = b.bsy, sz = b.bsz;
     float2 acc[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) acc[c] = make_float2(0.f, 0.f);
     const float wx[2] = {1.f - fr[0], fr[0]}, wy[2] = {1.f - fr[1], fr[1]}, wz[2] = {1.f - fr[2], fr[2]};
     float dens = 0.f;  // kFP8D: the BF16 log-density
-    if (slot >= 0) {
-        if constexpr (DT == kFP8D) {
+    if (stored) {
+        if constexpr (ST == kFP8D) {
             // the eight FP8 channels of slices z and z+1: one 32-byte quad each
 #pragma unroll
             for (int dz = 0; dz < 2; dz++) {
@@ -90,7 +98,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 const float wyz = wy[j & 1] * wz[j >> 1];
                 dens = fmaf(wyz * wx[1], v.y, fmaf(wyz * wx[0], v.x, dens));
             }
-        } else if (Store<DT>::kPaired) {
+        } else if (Store<ST>::kPaired) {
             // four loads, each the x-pair of one (y, z) edge of the voxel
 #pragma unroll
             for (int k = 0; k < 4; k++) {
@@ -98,7 +106,8 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 const float wyz = wy[dy] * wz[dz];
                 const float2 w0 = make_float2(wyz * wx[0], wyz * wx[0]), w1 = make_float2(wyz * wx[1], wyz * wx[1]);
                 float2 lo[4], hi[4];
-                Store<DT>::template load_pair<kGridLd>(b.grid, base + (int64_t)(dz * sz + dy * sy), lo, hi);
+                const int64_t e = kBricks ? base + (int64_t)(dz * sz + dy * sy) : base + ((int64_t)dz * R + dy) * R;
+                Store<ST>::template load_pair<kGridLd>(b.grid, e, lo, hi);
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], acc[c]));
             }
@@ -109,7 +118,9 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 const float w = (wy[dy] * wz[dz]) * wx[dx];
                 const float2 w2 = make_float2(w, w);
                 float2 v[4];
-                Store<DT>::template load8<kGridLd>(b.grid, base + (int64_t)(dz * sz + dy * sy + dx), v);
+                const int64_t e =
+                    kBricks ? base + (int64_t)(dz * sz + dy * sy + dx) : base + ((int64_t)dz * R + dy) * R + dx;
+                Store<ST>::template load8<kGridLd>(b.grid, e, v);
 #pragma unroll
                 for (int c = 0; c < 4; c++) acc[c] = __ffma2_rn(w2, v[c], acc[c]);
             }
@@ -120,9 +131,9 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
     // the non-coherent path measured 4 % slower in the batched kernel, whose
     // records sit in shared memory, and equal in the view kernel.
     const float4 *scale4 = reinterpret_cast<const float4 *>(b.scale);
-    if (DT == kFP8 || DT == kFP8D) {
+    if (ST == kFP8 || ST == kFP8D) {
         const float4 sa = scale4[0], sb = scale4[1];
-        f[0] = make_float2(DT == kFP8D ? dens : acc[0].x * sa.x, acc[0].y * sa.y);
+        f[0] = make_float2(ST == kFP8D ? dens : acc[0].x * sa.x, acc[0].y * sa.y);
         f[1] = make_float2(acc[1].x * sa.z, acc[1].y * sa.w);
         f[2] = make_float2(acc[2].x * sb.x, acc[2].y * sb.y);
         f[3] = make_float2(acc[3].x * sb.z, acc[3].y * sb.w);
@@ -150,7 +161,7 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
         float2 pacc[4];
 #pragma unroll
         for (int c = 0; c < 4; c++) pacc[c] = make_float2(0.f, 0.f);
-        if (DT == kMixed || DT == kFP8D) {
+        if (ST == kMixed || ST == kFP8D) {
             // one 32-byte load: the 2x2 FP8 texels of the bilinear footprint
             // (hardware E4M3 conversions; an integer re-biasing of the bytes
             // measured 20 % slower)
@@ -165,13 +176,13 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 pacc[2] = __ffma2_rn(w2, fp8x2_to_float2(r[2 * q + 1]), pacc[2]);
                 pacc[3] = __ffma2_rn(w2, fp8x2_to_float2(r[2 * q + 1] >> 16), pacc[3]);
             }
-        } else if (Store<DT>::kPaired) {
+        } else if (Store<ST>::kPaired) {
 #pragma unroll
             for (int dv = 0; dv < 2; dv++) {
                 const float2 w0 = make_float2(wv[dv] * wu[0], wv[dv] * wu[0]);
                 const float2 w1 = make_float2(wv[dv] * wu[1], wv[dv] * wu[1]);
                 float2 lo[4], hi[4];
-                Store<DT>::template load_pair<kPlaneLd>(b.planes[pl], tb + (int64_t)dv * P, lo, hi);
+                Store<ST>::template load_pair<kPlaneLd>(b.planes[pl], tb + (int64_t)dv * P, lo, hi);
 #pragma unroll
                 for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w1, hi[c], __ffma2_rn(w0, lo[c], pacc[c]));
             }
@@ -182,12 +193,12 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
                 const float w = wv[dv] * wu[du];
                 const float2 w2 = make_float2(w, w);
                 float2 v[4];
-                Store<DT>::template load8<kPlaneLd>(b.planes[pl], tb + (int64_t)dv * P + du, v);
+                Store<ST>::template load8<kPlaneLd>(b.planes[pl], tb + (int64_t)dv * P + du, v);
 #pragma unroll
                 for (int c = 0; c < 4; c++) pacc[c] = __ffma2_rn(w2, v[c], pacc[c]);
             }
         }
-        if (DT == kFP8 || DT == kMixed || DT == kFP8D) {
+        if (ST == kFP8 || ST == kMixed || ST == kFP8D) {
             const float4 sa = scale4[2 * (pl + 1)], sb = scale4[2 * (pl + 1) + 1];
             f[0] = __ffma2_rn(pacc[0], make_float2(sa.x, sa.y), f[0]);
             f[1] = __ffma2_rn(pacc[1], make_float2(sa.z, sa.w), f[1]);

@@ -91,3 +91,46 @@ def test_batch_rejects_bad_arguments():
         b.set_views(cams[:1], [list(range(9))])  # more ids than the batch holds
     with pytest.raises(cow.CowError):
         b.set_config(7, 2)
+
+
+def test_batch_runs_and_long_lists():
+    """Views whose blocks together exceed one launch's parameter buffer (96
+    records) are served in several runs, and a view with more than 96
+    blocks falls back to records read from memory; both equal the per-view
+    kernel (sample counts bit for bit)."""
+    sc = synth.city_scene(33, 12, 1.0, [(10, 16)])
+    nb = len(sc.blocks)
+    ctx = cow.Context(sc, "bf16")
+    mlp_d = torch.from_numpy(synth.mlp_weights(5)).cuda()
+    cams = [synth.camera((x, y, 2.5), (x + 0.5, y + 0.8, -0.8), 48, 36, 70.0)
+            for x, y in ((-4.5, -4.5), (3.0, -4.0), (-4.0, 3.5), (3.5, 3.0))]
+    ids = []
+    for c in cams:  # each view: the 60 blocks nearest to its camera, near to far
+        order = ctx.sort_blocks(c, list(range(nb)))
+        ids.append(ctx.sort_blocks(c, sorted(order[:60].tolist())))
+    assert len(set(np.concatenate(ids).tolist())) > 96
+    cams.append(synth.camera((0.0, -7.0, 4.0), (0.0, 0.0, -0.5), 64, 40, 70.0))
+    ids.append(ctx.sort_blocks(cams[-1], list(range(nb))))  # 144 blocks: over 96
+    ref = ctx.render(cams, ids, mlp_d, nsamp=True)
+    ctx.sync_check()
+    b = cow.Batch(ctx, 8, 1024)
+    n = b.set_views(cams, ids)
+    for graph in (False, True):
+        out = (torch.full((n, 3), -1.0, device="cuda"), torch.zeros((n, 8), device="cuda"),
+               torch.zeros(n, dtype=torch.int32, device="cuda"))
+        b.render(mlp_d, *out, graph=graph)
+        ctx.sync_check()
+        assert torch.equal(out[2], ref[2]), graph
+        assert float((out[0] - ref[0]).abs().max()) <= 2e-6
+    # without the long view: every list fits, the views go in runs
+    b2 = cow.Batch(ctx, 8, 1024)
+    n2 = b2.set_views(cams[:4], ids[:4])
+    ref2 = ctx.render(cams[:4], ids[:4], mlp_d, nsamp=True)
+    out = (torch.empty((n2, 3), device="cuda"), torch.zeros((n2, 8), device="cuda"),
+           torch.zeros(n2, dtype=torch.int32, device="cuda"))
+    b2.render(mlp_d, *out, graph=True)
+    ctx.sync_check()
+    assert torch.equal(out[2], ref2[2])
+    assert float((out[0] - ref2[0]).abs().max()) <= 2e-6
+    b.close()
+    b2.close()
