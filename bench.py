@@ -610,6 +610,36 @@ def run_fit(args, ws, rank, local):
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     p1 = psnr_now()
     n = o.shape[0]
+    # the backward alone (K7 + the K6 re-march), against the measured rate of
+    # random non-returning float4 reductions into an L2-resident buffer: K6
+    # scatters 2 float4 reductions to each of the 20 taps of every occupied
+    # sample
+    bwd = None
+    if not per_block and not args.reg:
+        rgb, aux, ns = fit.ctx.render_rays(o, d, fit.ids, fit.mlp, nsamp=True)
+        g, _ = cow.mse_grad(rgb, target)
+        grads = [torch.zeros_like(p) for p in fit.params]
+        nb = len(fit.ids)
+        gm = torch.zeros_like(fit.mlp)
+        call = lambda: fit.ctx.render_backward(o, d, fit.ids, fit.mlp, aux, g, [grads[4 * i] for i in range(nb)],
+                                               [grads[4 * i + 1:4 * i + 4] for i in range(nb)], gm)
+        tb = time_steps(call, max(3, args.steps // 2), 2, torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev),
+                        stream)
+        fit.ctx.sync_check()
+        samples = int(ns.to(torch.int64).sum().item())
+        reds = 40 * samples
+        ms_b = float(np.mean(tb))
+        peak_red = cow.reduce_peak(32 << 20)
+        peak_red_hbm = cow.reduce_peak(8 << 30, iters=64)
+        rate = reds / (ms_b / 1000.0) / 1e9
+        bwd = {"ms": round(ms_b, 3), "occupied_samples": samples, "float4_reductions": reds,
+               "achieved_gred_per_s": round(rate, 2),
+               "peak_gred_per_s_l2": round(peak_red, 2), "frac_of_l2_reduce_peak": round(rate / peak_red, 3),
+               "peak_gred_per_s_hbm": round(peak_red_hbm, 2),
+               "peak_source": "measured live: random red.global.add.v4.f32 into a 32 MiB (L2-resident) buffer, "
+                              "cow_reduce_peak",
+               "note": "time of the whole backward call (MLP backward + re-march); reductions counted as 40 per "
+                       "occupied sample"}
     line = {"metric": "differentiation form: training rays/s (forward + backward + Adam)", "value": round(n / ms / 1e3, 3),
             "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
@@ -621,7 +651,7 @@ def run_fit(args, ws, rank, local):
                               else "one global deferred MLP (499 parameters)",
                        "regularisers": ({"sparsity": 0.05, "sparsity_points": fit.n_sparsity_points,
                                          "opacity": 0.001} if args.reg else None)},
-            "fit_psnr_db": {"before": round(p0, 2), "after": round(p1, 2)}, "clocks": ck}
+            "fit_psnr_db": {"before": round(p0, 2), "after": round(p1, 2)}, "backward_roofline": bwd, "clocks": ck}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

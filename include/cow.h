@@ -592,6 +592,15 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
 cow_status cow_gather_peak(int32_t bytes_per_load, int64_t buffer_bytes, int32_t iters, double *out_gbs,
                            void *stream);
 
+/* Measurement aid (no counterpart in the paper): the rate of random,
+ * 16-byte-aligned non-returning 4-float reductions (red.global.add.v4.f32,
+ * the backward's scatter) by every thread of a full-GPU launch into a device
+ * buffer of buffer_bytes (a power of two, 1 KiB to 64 GiB), in 10^9
+ * reductions per second.  A buffer that fits L2 gives the L2 reduction rate.
+ * Allocates and frees its buffer; synchronises `stream`.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+cow_status cow_reduce_peak(int64_t buffer_bytes, int32_t iters, double *out_gred_per_s, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *cow_last_error(void);
 

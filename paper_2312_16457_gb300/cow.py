@@ -40,7 +40,7 @@ EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks"
            "cow_sync_check", "cow_set_test_hooks", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_refine_view_order", "cow_sparsity_loss", "cow_opacity_loss",
-           "cow_export_packed", "cow_gather_peak", "cow_render_backward", "cow_render_backward_noalloc",
+           "cow_export_packed", "cow_gather_peak", "cow_reduce_peak", "cow_render_backward", "cow_render_backward_noalloc",
            "cow_render_backward_block_mlps",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
@@ -110,6 +110,7 @@ def lib():
             "cow_refine_view_order": [P, i32, P, P, i32, i64, P, i32, P],
             "cow_export_packed": [P, i32, i32, P, i64, P],
             "cow_gather_peak": [i32, i64, i32, P, P],
+            "cow_reduce_peak": [i64, i32, P, P],
             "cow_render_backward": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
             "cow_render_backward_noalloc": [P, P, P, i64, P, i32, P, flt, P, P, P, P, P, P],
             "cow_render_backward_block_mlps": [P, P, P, i64, P, i32, P, P, P, P, P],
@@ -490,6 +491,14 @@ def gather_peak(bytes_per_load: int, buffer_bytes: int, iters: int = 256, stream
     v = C.c_double()
     _check(lib().cow_gather_peak(int(bytes_per_load), int(buffer_bytes), int(iters), C.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def reduce_peak(buffer_bytes: int, iters: int = 256, stream=None) -> float:
+    """Random non-returning float4 reductions per second (10^9) into a
+    device buffer (cow_reduce_peak)."""
+    out = C.c_double()
+    _check(lib().cow_reduce_peak(int(buffer_bytes), int(iters), C.byref(out), _stream_ptr(stream)))
+    return out.value
 
 
 def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, lr: float, step: int,

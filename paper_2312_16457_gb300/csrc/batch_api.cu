@@ -14,6 +14,7 @@ using namespace cowi;
 
 struct cow_batch {
     cow_ctx *ctx = nullptr;
+    int device = 0;
     int32_t max_views = 0, max_ids = 0;
     // staging: [hdr 256 B | views max_views x ViewRec | recs max_ids x BlockRec]
     size_t stage_bytes = 0, views_off = 256, recs_off = 0;
@@ -61,7 +62,7 @@ namespace {
 
 void batch_destroy(cow_batch *b) {
     if (!b) return;
-    DeviceGuard dg(b->ctx ? b->ctx->device : 0);
+    DeviceGuard dg(b->device);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->copied) cudaEventDestroy(b->copied);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -370,6 +371,7 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
         if ((rc = build_stage(b, lo, hi)) != COW_OK) return rc;
         const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, rgb, aux, ns);
         COW_CUDA(enqueue(b, a, b->tile_cfg, std::max(1, b->sms * b->ctas_per_sm), st, true));
+        if ((rc = note_use(c, run_ids.data(), (int64_t)run_ids.size(), st)) != COW_OK) return rc;
         groups++;
         return COW_OK;
     };
@@ -414,6 +416,14 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
 
 }  // namespace
 
+namespace cowi {
+
+void batch_detach(cow_batch *b) {
+    if (b) b->ctx = nullptr;
+}
+
+}  // namespace cowi
+
 extern "C" {
 
 cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, cow_batch **out) {
@@ -424,6 +434,7 @@ cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, co
     DeviceGuard dg(ctx->device);
     cow_batch *b = new cow_batch();
     b->ctx = ctx;
+    b->device = ctx->device;
     b->max_views = max_views;
     b->max_ids = max_ids;
     b->recs_off = (b->views_off + (size_t)max_views * sizeof(cow::ViewRec) + 255) & ~(size_t)255;
@@ -440,13 +451,16 @@ cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, co
                     cudaGetErrorString(e));
     }
     std::memset(b->h_stage, 0, b->stage_bytes);
-    ctx->n_batches++;
+    ctx->batches.push_back(b);
     *out = b;
     return COW_OK;
 }
 
 cow_status cow_batch_free(cow_batch *b) {
-    if (b && b->ctx) b->ctx->n_batches--;
+    if (b && b->ctx) {
+        auto &v = b->ctx->batches;
+        v.erase(std::remove(v.begin(), v.end(), b), v.end());
+    }
     batch_destroy(b);
     return COW_OK;
 }
@@ -454,6 +468,7 @@ cow_status cow_batch_free(cow_batch *b) {
 cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_views, const int32_t *ids,
                                const int32_t *ids_offsets, int64_t *out_pixels) {
     g_last_error.clear();
+    if (b && !b->ctx) return fail(COW_ERR_INVALID_ARG, "the batch's context has been freed");
     if (!b || !cams || n_views < 1 || !ids_offsets) return fail(COW_ERR_INVALID_ARG, "cow_batch_set_views: null argument");
     if (n_views > b->max_views) return fail(COW_ERR_INVALID_ARG, "%d views exceed the batch's %d", n_views, b->max_views);
     const int32_t n_ids = ids_offsets[n_views];
@@ -483,6 +498,7 @@ cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_v
 cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                             float *out_aux, int32_t *out_nsamp, int32_t use_graph, void *stream) {
     g_last_error.clear();
+    if (b && !b->ctx) return fail(COW_ERR_INVALID_ARG, "the batch's context has been freed");
     if (!b || !mlp || !out_rgb) return fail(COW_ERR_INVALID_ARG, "cow_batch_render: null argument");
     if (b->cams.empty()) return fail(COW_ERR_INVALID_ARG, "cow_batch_render: no views set");
     if (!(ert_eps >= 0.0f && ert_eps < 1.0f)) return fail(COW_ERR_INVALID_ARG, "ert_eps must be in [0, 1)");
@@ -555,6 +571,7 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
                           void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms) {
     g_last_error.clear();
     if (!b || !mlp || !out_rgb || reps < 1) return fail(COW_ERR_INVALID_ARG, "cow_batch_tune: bad argument");
+    if (!b->ctx) return fail(COW_ERR_INVALID_ARG, "the batch's context has been freed");
     if (b->cams.empty()) return fail(COW_ERR_INVALID_ARG, "cow_batch_tune: no views set");
     DeviceGuard dg(b->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;

@@ -90,26 +90,27 @@ namespace {
 void destroy(cow_ctx *c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    for (cow_batch *b : c->batches) batch_detach(b);  // batches freed later no longer reach the context
     // under a residency budget, calls return with loads from the pinned host
-    // copies still queued on the caller's stream: let them finish first
+    // copies still queued: let them finish first
     if (c->pool) cudaDeviceSynchronize();
     for (auto &b : c->blocks) {
-        if (b.async_alloc) {  // pool memory: freed in stream order before the pool goes
-            if (b.grid) cudaFreeAsync(b.grid, nullptr);
-            for (auto *p : b.planes)
-                if (p) cudaFreeAsync(p, nullptr);
+        if (b.chunk) {  // pool memory: freed in stream order before the pool goes
+            cudaFreeAsync(b.chunk, nullptr);
         } else {
             cudaFree(b.grid);
             for (auto *p : b.planes) cudaFree(p);
         }
+        b.use_ev.reset();
         cudaFree(b.occ);
         cudaFree(b.occ2);
         cudaFree(b.scale);
         cudaFree(b.brick_tab);
         cudaFree(b.brick_list);
-        for (auto *h : b.host_feat)
-            if (h) cudaFreeHost(h);
+        if (b.host_feat) cudaFreeHost(b.host_feat);
     }
+    if (c->loaded) cudaEventDestroy(c->loaded);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaFree(c->d_err);
     cudaFree(c->d_mlp);
     if (c->pool) {
@@ -552,6 +553,15 @@ int64_t feature_bytes(const cow_ctx *c, const BlockHost &b) {
 
 void **tensor_slot(BlockHost &b, int t) { return t == 0 ? &b.grid : &b.planes[t - 1]; }
 
+// Offset of tensor t in a block's host copy and pooled chunk (256-byte
+// aligned), and the chunk's size.
+int64_t feature_offset(const cow_ctx *c, const BlockHost &b, int t) {
+    int64_t off = 0;
+    for (int u = 0; u < t; u++) off = (off + tensor_bytes(c, b, u) + 255) & ~(int64_t)255;
+    return off;
+}
+int64_t chunk_bytes(const cow_ctx *c, const BlockHost &b) { return feature_offset(c, b, 3) + tensor_bytes(c, b, 3); }
+
 // Rewrite the host record of block i.  Kernels receive records by value (in
 // their parameter buffer or a per-call staging copy), so no device table
 // needs the change and the host does not wait for the stream.
@@ -561,62 +571,64 @@ cow_status refresh_rec(cow_ctx *c, int32_t i, cudaStream_t) {
     return COW_OK;
 }
 
-cow_status evict_block(cow_ctx *c, int32_t i, cudaStream_t st) {
+// Unload block i on the copy stream, after the kernels that read it: write a
+// changed device copy back to the host copy, then free the device memory.
+cow_status evict_block(cow_ctx *c, int32_t i) {
     BlockHost &b = c->blocks[(size_t)i];
     if (!b.resident) return COW_OK;
+    cudaStream_t cs = c->copy_stream;
+    if (b.use_ev) COW_CUDA(cudaStreamWaitEvent(cs, b.use_ev->e, 0));
     if (b.dirty) {  // features changed on the device since the host copy was taken
         for (int t = 0; t < 4; t++)
-            COW_CUDA(cudaMemcpyAsync(b.host_feat[t], *tensor_slot(b, t), (size_t)tensor_bytes(c, b, t),
-                                     cudaMemcpyDeviceToHost, st));
-        COW_CUDA(cudaStreamSynchronize(st));
+            COW_CUDA(cudaMemcpyAsync((unsigned char *)b.host_feat + feature_offset(c, b, t), *tensor_slot(b, t),
+                                     (size_t)tensor_bytes(c, b, t), cudaMemcpyDeviceToHost, cs));
         b.dirty = false;
     }
-    // memory from cudaMallocAsync returns to the pool in stream order, after
-    // the calls already queued that read it; the load-time allocations are
-    // freed once those calls have finished
-    if (!b.async_alloc) COW_CUDA(cudaStreamSynchronize(st));
-    for (int t = 0; t < 4; t++) {
-        void **slot = tensor_slot(b, t);
-        if (b.async_alloc) COW_CUDA(cudaFreeAsync(*slot, st));
-        else COW_CUDA(cudaFree(*slot));
-        *slot = nullptr;
+    if (b.chunk) {
+        // back to the pool in the copy stream's order: the next loads reuse it
+        COW_CUDA(cudaFreeAsync(b.chunk, cs));
+    } else {
+        // the load-time allocations: freed once the copy stream has passed
+        // the kernels that read them (and the write-back)
+        COW_CUDA(cudaStreamSynchronize(cs));
+        for (int t = 0; t < 4; t++) COW_CUDA(cudaFree(*tensor_slot(b, t)));
     }
+    b.chunk = nullptr;
+    for (int t = 0; t < 4; t++) *tensor_slot(b, t) = nullptr;
+    b.use_ev.reset();
     b.resident = false;
     c->resident_bytes -= feature_bytes(c, b);
     c->n_evictions++;
-    return refresh_rec(c, i, st);
+    return refresh_rec(c, i, cs);
 }
 
-cow_status upload_block(cow_ctx *c, int32_t i, cudaStream_t st) {
+// Load block i on the copy stream: one chunk from the pool, one copy.
+cow_status upload_block(cow_ctx *c, int32_t i) {
     BlockHost &b = c->blocks[(size_t)i];
     if (b.resident) return COW_OK;
-    for (int t = 0; t < 4; t++) {
-        void **slot = tensor_slot(b, t);
-        const cudaError_t e = cudaMallocFromPoolAsync(slot, (size_t)tensor_bytes(c, b, t), c->pool, st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            for (int u = 0; u < t; u++) {
-                cudaFreeAsync(*tensor_slot(b, u), st);
-                *tensor_slot(b, u) = nullptr;
-            }
-            *slot = nullptr;
-            return fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "loading block %d: %s", i,
-                        cudaGetErrorString(e));
-        }
-        COW_CUDA(cudaMemcpyAsync(*slot, b.host_feat[t], (size_t)tensor_bytes(c, b, t), cudaMemcpyHostToDevice, st));
+    cudaStream_t cs = c->copy_stream;
+    void *chunk = nullptr;
+    const cudaError_t e = cudaMallocFromPoolAsync(&chunk, (size_t)chunk_bytes(c, b), c->pool, cs);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? COW_ERR_OOM : COW_ERR_CUDA, "loading block %d: %s", i,
+                    cudaGetErrorString(e));
     }
-    b.async_alloc = true;
+    COW_CUDA(cudaMemcpyAsync(chunk, b.host_feat, (size_t)chunk_bytes(c, b), cudaMemcpyHostToDevice, cs));
+    b.chunk = chunk;
+    for (int t = 0; t < 4; t++) *tensor_slot(b, t) = (unsigned char *)chunk + feature_offset(c, b, t);
     b.resident = true;
     const int64_t bytes = feature_bytes(c, b);
     c->resident_bytes += bytes;
     c->n_uploads++;
     c->upload_bytes += bytes;
-    return refresh_rec(c, i, st);
+    return refresh_rec(c, i, cs);
 }
 
 // Make the blocks of one call resident: unload the least recently used
 // blocks the call does not need until the missing ones fit the budget, then
-// load those (in id order).
+// load those (in id order).  Loads and unloads go to the copy stream; st
+// waits for the loads.
 cow_status ensure_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) {
     if (c->budget <= 0) return COW_OK;
     const int32_t nb = (int32_t)c->blocks.size();
@@ -643,14 +655,29 @@ cow_status ensure_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream
             if (victim < 0 || b.last_use < c->blocks[(size_t)victim].last_use) victim = i;
         }
         if (victim < 0) break;  // cannot happen: the needed blocks alone fit
-        cow_status rc = evict_block(c, victim, st);
+        cow_status rc = evict_block(c, victim);
         if (rc != COW_OK) return rc;
     }
+    bool loaded = false;
     for (int32_t i = 0; i < nb; i++)
         if (need[(size_t)i] && !c->blocks[(size_t)i].resident) {
-            cow_status rc = upload_block(c, i, st);
+            cow_status rc = upload_block(c, i);
             if (rc != COW_OK) return rc;
+            loaded = true;
         }
+    if (loaded) {
+        COW_CUDA(cudaEventRecord(c->loaded, c->copy_stream));
+        COW_CUDA(cudaStreamWaitEvent(st, c->loaded, 0));
+    }
+    return COW_OK;
+}
+
+cow_status note_use_impl(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) {
+    if (c->budget <= 0 || n <= 0) return COW_OK;
+    auto ev = std::make_shared<SharedEvent>();
+    if (!ev->e) return fail(COW_ERR_CUDA, "cudaEventCreate failed");
+    COW_CUDA(cudaEventRecord(ev->e, st));
+    for (int64_t k = 0; k < n; k++) c->blocks[(size_t)ids[k]].use_ev = ev;
     return COW_OK;
 }
 
@@ -662,6 +689,10 @@ int64_t block_feature_bytes(const cow_ctx *c, int32_t i) { return feature_bytes(
 
 cow_status make_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) {
     return ensure_resident(c, ids, n, st);
+}
+
+cow_status note_use(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) {
+    return note_use_impl(c, ids, n, st);
 }
 
 }  // namespace cowi
@@ -923,6 +954,7 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
                                          ctx->schedule == COW_SCHED_WARP && !any_unbounded ? cow::kSchedWarp
                                                                                            : cow::kSchedThread, st));
     }
+    if ((rc = note_use_impl(ctx, ids, n_ids, st)) != COW_OK) return rc;
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)plan.n_pix * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)plan.n_pix * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)plan.n_pix * 4, cudaMemcpyDeviceToHost, st));
@@ -986,6 +1018,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_march_rays(a, rr, st));
+    if ((rc = note_use_impl(ctx, ids, n_ids, st)) != COW_OK) return rc;
     if (h_rgb) COW_CUDA(cudaMemcpyAsync(out_rgb, rgb, (size_t)n_rays * 12, cudaMemcpyDeviceToHost, st));
     if (h_aux) COW_CUDA(cudaMemcpyAsync(out_aux, aux, (size_t)n_rays * 32, cudaMemcpyDeviceToHost, st));
     if (h_ns) COW_CUDA(cudaMemcpyAsync(out_nsamp, ns, (size_t)n_rays * 4, cudaMemcpyDeviceToHost, st));
@@ -1063,7 +1096,7 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_rays(a, rr, st));
-    return COW_OK;
+    return note_use_impl(ctx, ids, n_ids, st);
 }
 
 cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
@@ -1124,7 +1157,7 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_block_mlps(a, rr, st));
-    return COW_OK;
+    return note_use_impl(ctx, ids, n_ids, st);
 }
 
 namespace {
@@ -1188,7 +1221,7 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_sparsity(a, rr, st));
-    return COW_OK;
+    return note_use_impl(ctx, ids, n_ids, st);
 }
 
 cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
@@ -1212,7 +1245,7 @@ cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_opacity(a, rr, st));
-    return COW_OK;
+    return note_use_impl(ctx, ids, n_ids, st);
 }
 
 cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, const float *plane_xy,
@@ -1234,7 +1267,10 @@ cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, c
     cow_status rc = ensure_resident(ctx, &block, 1, st);
     if (rc != COW_OK) return rc;
     rc = repack_block(ctx, b, src, ctx->staging.p, d_amax, d_inv, st);
-    if (rc == COW_OK && ctx->budget > 0) b.dirty = true;
+    if (rc == COW_OK && ctx->budget > 0) {
+        b.dirty = true;
+        rc = note_use_impl(ctx, &block, 1, st);  // an unload waits for the re-pack (and writes it back)
+    }
     return rc;
 }
 
@@ -1301,6 +1337,7 @@ cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
     DeviceGuard dg(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     COW_CUDA(cudaStreamSynchronize(st));
+    if (ctx->copy_stream) COW_CUDA(cudaStreamSynchronize(ctx->copy_stream));
     const int32_t nb = (int32_t)ctx->blocks.size();
     cow_status rc;
     if (budget_bytes > 0) {
@@ -1317,24 +1354,22 @@ cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
             uint64_t keep = ~(uint64_t)0;
             COW_CUDA(cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep));
         }
-        // pinned host copies of every block's packed features, taken once
+        if (!ctx->copy_stream) COW_CUDA(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        if (!ctx->loaded) COW_CUDA(cudaEventCreateWithFlags(&ctx->loaded, cudaEventDisableTiming));
+        // pinned host copies of every block's packed features (one buffer a
+        // block, the tensors at the chunk offsets), taken once
         for (int32_t i = 0; i < nb; i++) {
             BlockHost &b = ctx->blocks[(size_t)i];
-            if (b.host_feat[0]) continue;
-            for (int t = 0; t < 4; t++) {
-                const cudaError_t e = cudaMallocHost(&b.host_feat[t], (size_t)tensor_bytes(ctx, b, t));
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    for (int u = 0; u < t; u++) {
-                        cudaFreeHost(b.host_feat[u]);
-                        b.host_feat[u] = nullptr;
-                    }
-                    b.host_feat[t] = nullptr;
-                    return fail(COW_ERR_OOM, "pinned host copy of block %d: %s", i, cudaGetErrorString(e));
-                }
-                COW_CUDA(cudaMemcpy(b.host_feat[t], *tensor_slot(b, t), (size_t)tensor_bytes(ctx, b, t),
-                                    cudaMemcpyDeviceToHost));
+            if (b.host_feat) continue;
+            const cudaError_t e = cudaMallocHost(&b.host_feat, (size_t)chunk_bytes(ctx, b));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                b.host_feat = nullptr;
+                return fail(COW_ERR_OOM, "pinned host copy of block %d: %s", i, cudaGetErrorString(e));
             }
+            for (int t = 0; t < 4; t++)
+                COW_CUDA(cudaMemcpy((unsigned char *)b.host_feat + feature_offset(ctx, b, t), *tensor_slot(b, t),
+                                    (size_t)tensor_bytes(ctx, b, t), cudaMemcpyDeviceToHost));
             b.dirty = false;
         }
         if (ctx->budget == 0) {
@@ -1343,7 +1378,7 @@ cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
             for (const auto &b : ctx->blocks)
                 if (b.resident) ctx->resident_bytes += feature_bytes(ctx, b);
             for (int32_t i = 0; i < nb; i++)
-                if ((rc = evict_block(ctx, i, st)) != COW_OK) return rc;
+                if ((rc = evict_block(ctx, i)) != COW_OK) return rc;
         }
         ctx->budget = budget_bytes;
         while (ctx->resident_bytes > ctx->budget) {  // a smaller budget: unload least recently used first
@@ -1352,23 +1387,23 @@ cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
                 const BlockHost &b = ctx->blocks[(size_t)i];
                 if (b.resident && (victim < 0 || b.last_use < ctx->blocks[(size_t)victim].last_use)) victim = i;
             }
-            if ((rc = evict_block(ctx, victim, st)) != COW_OK) return rc;
+            if ((rc = evict_block(ctx, victim)) != COW_OK) return rc;
         }
-        COW_CUDA(cudaStreamSynchronize(st));
+        COW_CUDA(cudaStreamSynchronize(ctx->copy_stream));
         return COW_OK;
     }
+    if (ctx->budget == 0) return COW_OK;
     // leaving: load every block back, drop the host copies
     ctx->budget = 0;
     for (int32_t i = 0; i < nb; i++)
-        if ((rc = upload_block(ctx, i, st)) != COW_OK) return rc;
-    COW_CUDA(cudaStreamSynchronize(st));
+        if ((rc = upload_block(ctx, i)) != COW_OK) return rc;
+    COW_CUDA(cudaStreamSynchronize(ctx->copy_stream));
     COW_CUDA(cudaMemPoolTrimTo(ctx->pool, 0));  // return what unloaded blocks left in the pool
     for (auto &b : ctx->blocks) {
-        for (int t = 0; t < 4; t++) {
-            if (b.host_feat[t]) cudaFreeHost(b.host_feat[t]);
-            b.host_feat[t] = nullptr;
-        }
+        if (b.host_feat) cudaFreeHost(b.host_feat);
+        b.host_feat = nullptr;
         b.dirty = false;
+        b.use_ev.reset();
     }
     return COW_OK;
 }
@@ -1646,8 +1681,11 @@ cow_status cow_export_packed(const cow_ctx *ctx, int32_t block, int32_t tensor, 
     const int64_t need = nv * nch * elem_bytes(tdt);
     if (nbytes < need) return fail(COW_ERR_INVALID_ARG, "need %lld bytes", (long long)need);
     DeviceGuard dg(ctx->device);
-    // an unloaded block is read from its pinned host copy
-    const void *src = !b.resident ? b.host_feat[tensor == 4 ? 0 : tensor]
+    // an unloaded block is read from its pinned host copy (after any
+    // write-back still queued on the copy stream)
+    if (!b.resident && ctx->copy_stream) COW_CUDA(cudaStreamSynchronize(ctx->copy_stream));
+    const int tslot = tensor == 4 ? 0 : tensor;
+    const void *src = !b.resident ? (const void *)((const unsigned char *)b.host_feat + feature_offset(ctx, b, tslot))
                                   : tensor == 0 || tensor == 4 ? b.grid : b.planes[tensor - 1];
     if (tensor == 4) src = (const unsigned char *)src + grid_main_bytes(ctx, b);
     if (ctx->dtype == COW_FP32) {
@@ -1819,5 +1857,5 @@ extern "C" cow_status cow_render_backward_noalloc(cow_ctx *ctx, const float *o, 
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_rays(a, rr, st));
-    return COW_OK;
+    return note_use_impl(ctx, ids, n_ids, st);
 }

@@ -4,6 +4,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -62,6 +63,19 @@ struct DevBuf {
     }
 };
 
+// A CUDA event owned by reference count: the calls that read a block record
+// one after their kernels, and the block keeps the latest until it is
+// unloaded (the unload waits for it).
+struct SharedEvent {
+    cudaEvent_t e = nullptr;
+    SharedEvent() { cudaEventCreateWithFlags(&e, cudaEventDisableTiming); }
+    ~SharedEvent() {
+        if (e) cudaEventDestroy(e);
+    }
+    SharedEvent(const SharedEvent &) = delete;
+    SharedEvent &operator=(const SharedEvent &) = delete;
+};
+
 struct BlockHost {
     float lo[3], hi[3];
     int32_t lod, parent, R, P;
@@ -71,12 +85,15 @@ struct BlockHost {
     uint32_t *occ2 = nullptr;  // coarse occupancy level (OR over kOccGroup^3 cells)
     int64_t occ2_words = 0;
     // dynamic loading (cow_set_residency): the packed grid and planes may live
-    // only in pinned host memory while the block is unloaded
-    void *host_feat[4] = {nullptr, nullptr, nullptr, nullptr};
+    // only in pinned host memory while the block is unloaded, as one buffer
+    // (tensor t at feature_offset(t)); a loaded block's tensors are one chunk
+    // of the context's stream-ordered pool at the same offsets
+    void *host_feat = nullptr;
+    void *chunk = nullptr;     // null while the tensors are the load-time allocations
+    std::shared_ptr<SharedEvent> use_ev;  // after the last enqueued kernel that reads the block
     int32_t unb = 0;           // cow_set_block_unbounded flags
     bool resident = true;
     bool dirty = false;        // device copy newer than host_feat (cow_update_features)
-    bool async_alloc = false;  // device tensors from the context's stream-ordered pool
     uint64_t last_use = 0;
     float *scale = nullptr;
     int32_t scale_exp[4][8];
@@ -98,6 +115,7 @@ inline double focal_length(int32_t H, double fov_y_deg) {
 }  // namespace cowi
 
 struct cow_ctx;
+struct cow_batch;
 
 namespace cowi {
 
@@ -106,8 +124,17 @@ int64_t block_feature_bytes(const cow_ctx *c, int32_t i);
 
 // Make the blocks ids[0 .. n) resident under the context's budget (LRU
 // unloading of the others); a no-op without a budget.  Block records of
-// loaded or unloaded blocks are rewritten (cow_ctx::rec_gen advances).
+// loaded or unloaded blocks are rewritten (cow_ctx::rec_gen advances); work
+// enqueued on st afterwards waits for the loads.
 cow_status make_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st);
+
+// cow_free of a context with live batches: the batch drops its context
+// pointer (its later calls fail with INVALID_ARG; cow_batch_free still works).
+void batch_detach(struct cow_batch *b);
+
+// After a call's kernels on st: under a budget, the blocks ids[0 .. n)
+// remember that their next unload waits for this point of st.
+cow_status note_use(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st);
 
 }  // namespace cowi
 
@@ -137,9 +164,14 @@ struct cow_ctx {
     uint64_t use_clock = 0;
     int64_t resident_bytes = 0;
     int64_t n_uploads = 0, upload_bytes = 0, n_evictions = 0;
-    int32_t n_batches = 0;  // live cow_batch objects on this context
+    std::vector<struct cow_batch *> batches;  // live cow_batch objects on this context (cow_free detaches them)
     uint64_t rec_gen = 0;   // advances whenever a block record is rewritten
     cudaMemPool_t pool = nullptr;  // loads under a budget allocate from it (created with the first budget)
+    // loads and unloads run on their own stream, ordered by events: an unload
+    // waits for the kernels that read the block, a call's kernels wait for
+    // the loads it needs, so a call's loads can overlap earlier calls' kernels
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t loaded = nullptr;  // recorded on copy_stream after a call's loads
 };
 
 namespace cowi {

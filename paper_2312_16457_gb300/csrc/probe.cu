@@ -1,5 +1,6 @@
-// probe.cu -- random-gather throughput probe: the denominator of the marcher's
-// gather roofline.
+// probe.cu -- throughput probes: random gathers (the denominator of the
+// marcher's gather roofline) and random non-returning vector reductions (the
+// backward's scatter).
 //
 // Every thread issues `iters` loads of `bytes` (16 or 32) bytes at
 // pseudo-random, aligned offsets of a device buffer of `buffer_bytes`, the
@@ -45,6 +46,21 @@ __global__ void __launch_bounds__(256) k_gather_probe(const uint4 *__restrict__ 
         }
     }
     if (acc == 0x12345678u) sink[0] = acc;  // keeps the loads alive
+}
+
+// Every thread issues `iters` non-returning 4-float reductions
+// (red.global.add.v4.f32, the backward's scatter instruction) at
+// pseudo-random 16-byte-aligned offsets of a buffer of n_vec4 float4s.
+__global__ void __launch_bounds__(256) k_reduce_probe(float *__restrict__ buf, uint32_t n_vec4_mask, int iters) {
+    uint32_t h = mix32((uint32_t)(blockIdx.x * blockDim.x + threadIdx.x) * 0x9e3779b9u + 7u);
+#pragma unroll 4
+    for (int it = 0; it < iters; it++) {
+        h = mix32(h + (uint32_t)it);
+        float *dst = buf + 4 * (size_t)(h & n_vec4_mask);
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(1.0f), "f"(2.0f), "f"(3.0f),
+                     "f"(4.0f)
+                     : "memory");
+    }
 }
 
 }  // namespace
@@ -94,5 +110,37 @@ extern "C" cow_status cow_gather_peak(int32_t bytes_per_load, int64_t buffer_byt
     if (e != cudaSuccess || ms <= 0.f) return COW_ERR_CUDA;
     const double bytes = (double)reps * blocks * 256.0 * iters * bytes_per_load;
     *out_gbs = bytes / (ms * 1e-3) / 1e9;
+    return COW_OK;
+}
+
+extern "C" cow_status cow_reduce_peak(int64_t buffer_bytes, int32_t iters, double *out_gred_per_s, void *stream) {
+    if (!out_gred_per_s || iters < 1 || buffer_bytes < 1024 || (buffer_bytes & (buffer_bytes - 1)) ||
+        buffer_bytes > ((int64_t)1 << 36))
+        return COW_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *buf = nullptr;
+    if (cudaMalloc((void **)&buf, (size_t)buffer_bytes) != cudaSuccess) return COW_ERR_OOM;
+    cudaMemsetAsync(buf, 0, (size_t)buffer_bytes, st);
+    const int64_t n_vec4 = buffer_bytes / 16;
+    const uint32_t mask = (uint32_t)(n_vec4 - 1 > 0xffffffffLL ? 0xffffffffu : (uint32_t)(n_vec4 - 1));
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    const int blocks = sms * 8;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cow::k_reduce_probe<<<blocks, 256, 0, st>>>(buf, mask, iters);  // warm-up
+    cudaEventRecord(a, st);
+    const int reps = 5;
+    for (int r = 0; r < reps; r++) cow::k_reduce_probe<<<blocks, 256, 0, st>>>(buf, mask, iters);
+    cudaEventRecord(b, st);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(buf);
+    if (e != cudaSuccess || ms <= 0.f) return COW_ERR_CUDA;
+    *out_gred_per_s = (double)reps * blocks * 256.0 * iters / (ms * 1e-3) / 1e9;
     return COW_OK;
 }

@@ -63,8 +63,10 @@ def test_view_record_wait_times_out(schedule):
     ctx.close()
 
 
-@pytest.mark.parametrize("graph", [False, True])
-def test_batch_record_wait_times_out(graph):
+def test_batch_record_wait_times_out():
+    """The batched form stages records with a bulk copy when it serves its
+    views in runs under a residency budget (without one, runs take their
+    records in the parameter buffer and nothing waits)."""
     sc, cam, mlp = _small()
     ctx = cow.Context(sc, "bf16")
     cams = [cam, synth.camera((2.0, 2.5, 1.5), (-0.2, -0.1, -0.9), 32, 32, 60.0)]
@@ -73,19 +75,38 @@ def test_batch_record_wait_times_out(graph):
     batch = cow.Batch(ctx, 2, 8)
     npix = batch.set_views(cams, ids)
     ref = torch.empty((npix, 3), device="cuda")
-    batch.render(mlp_d, ref, graph=graph)
+    batch.render(mlp_d, ref)
     ctx.sync_check()
+    ctx.set_residency(sum(ctx.block_bytes(i) for i in range(4)))
     out = torch.full((npix, 3), -1.0, device="cuda")
     ctx.set_test_hooks(skip_record_copy=True, wait_polls=1024)
-    batch.render(mlp_d, out, graph=graph)
+    batch.render(mlp_d, out)
     assert _status(ctx.sync_check) == TIMEOUT
     assert bool((out == -1.0).all())  # the CTAs left without writing pixels
     ctx.set_test_hooks()
-    batch.render(mlp_d, out, graph=graph)
+    batch.render(mlp_d, out)
     ctx.sync_check()
     assert torch.equal(out, ref)
+    ctx.set_residency(0)
     batch.close()
     ctx.close()
+
+
+def test_context_freed_before_its_batch():
+    """A batch outliving its context (garbage collection can free them in
+    either order) is detached: its calls fail cleanly and freeing it works."""
+    sc, cam, mlp = _small()
+    ctx = cow.Context(sc, "bf16")
+    batch = cow.Batch(ctx, 1, 8)
+    npix = batch.set_views([cam], [ctx.sort_blocks(cam, list(range(4)))])
+    ctx.close()
+    with pytest.raises(cow.CowError, match="freed"):
+        batch.render(torch.from_numpy(mlp).cuda(), torch.empty((npix, 3), device="cuda"))
+    batch.close()
+    # the runtime's error state is clean: a new context loads
+    ctx2 = cow.Context(sc, "bf16")
+    ctx2.sync_check()
+    ctx2.close()
 
 
 def test_default_schedule_has_no_wait():
