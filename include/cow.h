@@ -380,6 +380,30 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);
 
+/* Block-parallel form of the ray-batch render (Sec. 4.2, Eq. 11-13; the
+ * paper renders every block in its own shader and alpha-blends the images,
+ * Sec. 4.2 and App. A).  Two calls:
+ *   cow_render_partials: every block of ids marched alone, from an in-block
+ *     transmittance of 1, for every ray: out_partials[(r * n_ids + k) * 8 ..]
+ *     = (C_d^k (3), F^k (4), T^k) of block ids[k] (Eq. 11; T^k = 1 - alpha^k,
+ *     = 1 with C_d^k = F^k = 0 for a ray that takes no sample in it).  No
+ *     early termination.  The blocks may be split between calls or devices;
+ *     each partial depends on its block alone.
+ *   cow_composite_over (K2): per ray, the partials of ids folded near to far
+ *     (App. D order from the ray's origin, as cow_render_rays) with the
+ *     associative "over" of Eq. 12-13, (C, F, T) <- (C + T C^k, F + T F^k,
+ *     T T^k), then the deferred MLP (Eq. 3): out_rgb (n x 3), out_aux (n x 8:
+ *     C_d, F, T; may be NULL).  flags: 0 or COW_FLAG_MLP_BF16.
+ * Composited partials equal cow_render_rays without early termination up to
+ * FP32 rounding (the fused marcher carries T through the samples instead).
+ * Arrays are device memory; partials 16-byte aligned.  Errors: INVALID_ARG,
+ * OOM (residency budget), CUDA. */
+cow_status cow_render_partials(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                               int32_t n_ids, float *out_partials, void *stream);
+cow_status cow_composite_over(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                              int32_t n_ids, const float *partials, const float *mlp, uint32_t flags, float *out_rgb,
+                              float *out_aux, void *stream);
+
 /* cow_render_rays without early termination that also writes every block's
  * own transmittance prod (1 - alpha_i) over its occupied samples (Eq. 11),
  * -1 for a block without one: out_block_T is device float32 n_rays x n_ids,

@@ -36,7 +36,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
-           "cow_render", "cow_render_rays", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
+           "cow_render", "cow_render_rays", "cow_render_partials", "cow_composite_over", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_set_test_hooks", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_refine_view_order", "cow_sparsity_loss", "cow_opacity_loss",
@@ -92,6 +92,8 @@ def lib():
             "cow_sort_blocks": [P, P, P, i32, P],
             "cow_render": [P, P, i32, P, P, P, flt, u32, P, P, P, P],
             "cow_render_rays": [P, P, P, i64, P, i32, P, flt, u32, P, P, P, P],
+            "cow_render_partials": [P, P, P, i64, P, i32, P, P],
+            "cow_composite_over": [P, P, P, i64, P, i32, P, P, u32, P, P, P],
             "cow_sync_check": [P, P],
             "cow_set_test_hooks": [P, u32, u32],
             "cow_set_schedule": [P, i32],
@@ -291,6 +293,27 @@ class Context:
         _check(lib().cow_render_rays(self._ctx, _ptr(o), _ptr(d), n, _ptr(a), len(a), _ptr(m), float(ert_eps),
                                      flags, _ptr(rgb), _ptr(ax), _ptr(ns), _stream_ptr(stream)))
         return rgb, ax, ns
+
+    def render_partials(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], stream=None) -> torch.Tensor:
+        """Per-block partials (C_d^k, F^k, T^k) of a ray batch: [n, len(ids), 8]."""
+        a = np.ascontiguousarray(ids, np.int32)
+        out = torch.empty((o.shape[0], len(a), 8), dtype=torch.float32, device=o.device)
+        _check(lib().cow_render_partials(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a),
+                                         len(a), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def composite_over(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], partials: torch.Tensor, mlp,
+                       mlp_bf16: bool = False, aux: bool = True, stream=None):
+        """K2: the partials folded near to far (Eq. 12-13) and shaded (Eq. 3)."""
+        a = np.ascontiguousarray(ids, np.int32)
+        n = o.shape[0]
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
+        ax = torch.empty((n, 8), dtype=torch.float32, device=o.device) if aux else None
+        m = mlp if isinstance(mlp, torch.Tensor) else torch.from_numpy(_as_f32(mlp)).to(o.device)
+        _check(lib().cow_composite_over(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), n, _ptr(a), len(a),
+                                        _ptr(partials.contiguous()), _ptr(m), FLAG_MLP_BF16 if mlp_bf16 else 0,
+                                        _ptr(rgb), _ptr(ax), _stream_ptr(stream)))
+        return rgb, ax
 
     def render_backward(self, o, d, ids, mlp, aux, dL_drgb, grad_grids, grad_planes, grad_mlp,
                         ert_eps: float = 0.0, stream=None, noalloc: bool = False):

@@ -1025,6 +1025,74 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     return COW_OK;
 }
 
+cow_status cow_render_partials(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                               int32_t n_ids, float *out_partials, void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !out_partials)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_partials: null argument");
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    for (const void *q : {(const void *)o, (const void *)d, (const void *)out_partials})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "rays and partials must be device memory");
+    if ((uintptr_t)out_partials & 15u) return fail(COW_ERR_INVALID_ARG, "partials must be 16-byte aligned");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cow_status rc;
+    if ((rc = ensure_resident(ctx, ids, n_ids, st)) != COW_OK) return rc;
+    cow::MarchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.dtype = kernel_dtype(ctx);
+    a.err = ctx->d_err;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.out_partials = out_partials;
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_march_partials(a, rr, st));
+    return note_use_impl(ctx, ids, n_ids, st);
+}
+
+cow_status cow_composite_over(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                              int32_t n_ids, const float *partials, const float *mlp, uint32_t flags, float *out_rgb,
+                              float *out_aux, void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !partials || !mlp || !out_rgb)
+        return fail(COW_ERR_INVALID_ARG, "cow_composite_over: null argument");
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    if (flags & ~COW_FLAG_MLP_BF16) return fail(COW_ERR_INVALID_ARG, "unknown flags");
+    for (int32_t k = 0; k < n_ids; k++)
+        if (ids[k] < 0 || ids[k] >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+    for (const void *q : {(const void *)o, (const void *)d, (const void *)partials, (const void *)out_rgb})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "rays, partials and outputs must be device memory");
+    if (out_aux && (!is_device_ptr(out_aux) || ((uintptr_t)out_aux & 15u)))
+        return fail(COW_ERR_INVALID_ARG, "aux must be 16-byte aligned device memory");
+    if (((uintptr_t)partials & 15u) || ((uintptr_t)out_rgb & 3u)) return fail(COW_ERR_INVALID_ARG, "misaligned array");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const float *d_mlp = nullptr;
+    cow_status rc;
+    if ((rc = resolve_mlp(ctx, mlp, st, &d_mlp)) != COW_OK) return rc;
+    cow::MarchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.mlp = d_mlp;
+    a.flags = flags;
+    a.out_rgb = out_rgb;
+    a.out_aux = out_aux;
+    a.err = ctx->d_err;
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.in_partials = partials;
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);  // only the blocks' centres are read (the per-ray order)
+    COW_CUDA(cow::launch_composite_over(a, rr, st));
+    return COW_OK;
+}
+
 cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream) {

@@ -34,6 +34,8 @@ struct MarchArgs {
     int64_t block_mlp_stride;        // floats (null base: the global MLP)
     uint32_t test_flags;             // kTestSkipRecordCopy (tests of the bounded waits); 0 in production
     uint32_t wait_polls;             // bound on each mbarrier wait (0: the kernel's default)
+    float *out_partials;             // block-parallel form: n_rays x n_ids x 8 per-block partials (written)
+    const float *in_partials;        // block-parallel form: the same, read by the compositor
 };
 
 // Test hook of the kernels that stage block records with a TMA bulk copy:
@@ -49,6 +51,11 @@ struct ParamRecs;
 cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st,
                                const ParamRecs *pr = nullptr);
 cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
+// Block-parallel form: per-block partials of a ray batch (8 floats per ray
+// and block, in the order of rr), and K2, their near-to-far "over" with the
+// deferred MLP (Eq. 12-13, Eq. 3).
+cudaError_t launch_march_partials(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
+cudaError_t launch_composite_over(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
 int march_tile_w();
 int march_tile_h();
 

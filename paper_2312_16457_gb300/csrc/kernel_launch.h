@@ -13,6 +13,8 @@ cudaError_t launch_views_dt(const MarchArgs &a, int n_tiles, int schedule, cudaS
 template <int DT>
 cudaError_t launch_rays_dt(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
 template <int DT>
+cudaError_t launch_partials_dt(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
+template <int DT>
 cudaError_t launch_batch_smem_dt(const BatchArgs &a, int tile_cfg, int grid, cudaStream_t st);
 template <int DT>
 cudaError_t launch_batch_param_dt(const BatchArgs &a, int tile_cfg, int grid, cudaStream_t st, const ParamRecs *pr);

@@ -423,6 +423,33 @@ __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(Ma
     write_outputs(a, r, s, d, s_mlp);
 }
 
+// Block-parallel form, first half: every block of the call marched on its
+// own from an in-block transmittance of 1 (Eq. 11: C_d^k, F^k and T^k =
+// 1 - alpha^k of block k alone), written as 8 floats per (ray, block) in
+// the order of the call's ids.  No early termination (a partial must not
+// depend on the blocks in front of it).
+template <int DT>
+__global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_partials(MarchArgs a,
+                                                                              const __grid_constant__ RayRecs rr) {
+    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (r >= a.n_rays) return;
+    float o[3], d[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o[c] = __ldg(a.ray_o + 3 * r + c);
+        d[c] = __ldg(a.ray_d + 3 * r + c);
+    }
+    float inv_d[3], omax;
+    ray_setup(d, o, inv_d, omax);
+    for (int k = 0; k < rr.n; k++) {
+        RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+        march_block<DT>(rr.r[k], o, d, inv_d, omax, 0.f, s, a.err);
+        float4 *pp = reinterpret_cast<float4 *>(a.out_partials + 8 * (r * rr.n + k));
+        pp[0] = make_float4(s.Cd[0], s.Cd[1], s.Cd[2], s.F[0]);
+        pp[1] = make_float4(s.F[1], s.F[2], s.F[3], s.T);
+    }
+}
+
 template <int DT, bool kBlockMlp>
 cudaError_t launch_thread(const MarchArgs &a, int n_tiles, bool in_params, cudaStream_t st, const ParamRecs *pr) {
     if (in_params) {
@@ -462,8 +489,16 @@ cudaError_t launch_rays_dt(const MarchArgs &a, const RayRecs &rr, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <int DT>
+cudaError_t launch_partials_dt(const MarchArgs &a, const RayRecs &rr, cudaStream_t st) {
+    const int64_t nb = (a.n_rays + kThreads - 1) / kThreads;
+    k_march_partials<DT><<<(unsigned)nb, kThreads, 0, st>>>(a, rr);
+    return cudaGetLastError();
+}
+
 #define COW_INST_MARCH(D)                                                                                           \
     template cudaError_t launch_views_dt<(D)>(const MarchArgs &, int, int, cudaStream_t, const ParamRecs *);       \
-    template cudaError_t launch_rays_dt<(D)>(const MarchArgs &, const RayRecs &, cudaStream_t);
+    template cudaError_t launch_rays_dt<(D)>(const MarchArgs &, const RayRecs &, cudaStream_t);                    \
+    template cudaError_t launch_partials_dt<(D)>(const MarchArgs &, const RayRecs &, cudaStream_t);
 
 }  // namespace cow
