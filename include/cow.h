@@ -312,14 +312,18 @@ cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, c
                                  const int32_t *ids_offsets, int32_t n_views, int64_t budget_bytes, int32_t *io_order,
                                  int32_t max_evals, int64_t *out_upload_bytes);
 
-/* Batched form: many cameras of uneven size and LOD set served by one
- * persistent launch over a (view, tile, block) work queue.  Every CTA takes
+/* Batched form: many cameras of uneven size and LOD set served by
+ * persistent launches over a (view, tile, block) work queue.  Every CTA takes
  * the next (view, tile) item from a device counter, culls the view's block
  * list against the tile's pyramid (blocks that no ray of the tile can sample)
  * and marches the tile's rays; each pixel equals cow_render's bit for bit.
- * The launch can be replayed from a CUDA graph, and its tile shape and
- * resident CTAs per SM can be picked by cow_batch_tune, which times the
- * candidates on the batch that is set.
+ * When every view has at most 96 blocks the views are grouped into runs
+ * whose distinct blocks fit one launch's parameter buffer (96 records, read
+ * through the constant cache), one persistent launch a run; otherwise one
+ * launch stages each view's records into shared memory.  The launches can
+ * be replayed from one CUDA graph, and their tile shape and resident CTAs
+ * per SM can be picked by cow_batch_tune, which times the candidates on the
+ * batch that is set.
  *
  * cow_batch_create : pinned + device staging for up to max_views cameras and
  *                    max_ids block ids (sum over views); owned by the caller
@@ -334,7 +338,10 @@ cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, c
  *                    Under a residency budget (cow_set_residency) the views
  *                    are cut, in the order set, into runs: a view joins the
  *                    current run while the run's distinct blocks plus its own
- *                    fit the budget, else it starts the next run.  Successive
+ *                    fit the run fraction of the budget (1/2 by default, so
+ *                    a run's loads overlap the previous run's marching; a
+ *                    view above it forms its own run), else it starts the
+ *                    next run.  Successive
  *                    renders walk the views first to last, then last to
  *                    first, and so on (cow_batch_set_views restarts at first
  *                    to last), so each render begins with the blocks the
@@ -360,6 +367,9 @@ cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_v
 cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                             float *out_aux, int32_t *out_nsamp, int32_t use_graph, void *stream);
 cow_status cow_batch_last_groups(const cow_batch *b, int32_t *out_groups);
+/* The fraction of the residency budget one run of cow_batch_render may fill
+ * (0 < frac <= 1; default 0.5).  Errors: INVALID_ARG. */
+cow_status cow_batch_set_run_fraction(cow_batch *b, float frac);
 cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm);
 cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb, int32_t reps,
                           void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms);

@@ -44,7 +44,7 @@ EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks"
            "cow_render_backward_block_mlps",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
-           "cow_batch_last_groups", "cow_last_error",
+           "cow_batch_last_groups", "cow_batch_set_run_fraction", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
@@ -125,6 +125,7 @@ def lib():
             "cow_batch_render": [P, P, flt, u32, P, P, P, i32, P],
             "cow_batch_set_config": [P, i32, i32],
             "cow_batch_last_groups": [P, P],
+            "cow_batch_set_run_fraction": [P, flt],
             "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
         }
         for name, args in sig.items():
@@ -588,6 +589,10 @@ class Batch:
         n = C.c_int32()
         _check(lib().cow_batch_last_groups(self._b, C.byref(n)))
         return n.value
+
+    def set_run_fraction(self, frac: float):
+        """Under a residency budget: the fraction of it one run may fill."""
+        _check(lib().cow_batch_set_run_fraction(self._b, float(frac)))
 
     def set_config(self, tile_cfg: int, ctas_per_sm: int):
         _check(lib().cow_batch_set_config(self._b, int(tile_cfg), int(ctas_per_sm)))

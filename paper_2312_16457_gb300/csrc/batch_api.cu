@@ -34,6 +34,7 @@ struct cow_batch {
     int32_t last_groups = 0;           // launches of the last render (groups under a budget)
     bool backward = false;             // under a budget: the next render serves the views last to first
     int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
+    float run_frac = 0.5f;             // under a budget: a run's blocks fill at most this fraction of it
     int sms = 0;
     // captured graph and the arguments it was captured with
     cudaGraphExec_t exec = nullptr;
@@ -346,13 +347,16 @@ cudaError_t enqueue(cow_batch *b, const cow::BatchArgs &a, int tile_cfg, int gri
 }
 
 // Under a residency budget: cut the views, in the batch's order, into runs
-// whose blocks fit the budget together (a view joins the current run while
-// the run's distinct blocks plus its own still fit), make each run's blocks
+// whose blocks fit a fraction of the budget together (a view joins the
+// current run while the run's distinct blocks plus its own still fit; a view
+// alone above that fraction forms its own run), make each run's blocks
 // resident (LRU unloading of the others) and launch the persistent kernel on
-// that run.  Successive renders walk the views in alternating directions, so
-// a render starts with the blocks the previous one left resident.  Runs are
-// launched eagerly on the caller's stream, never from the graph: each one
-// rewrites the staging and the block records.
+// that run.  With runs of at most half the budget a run's loads unload only
+// blocks of earlier runs, so they proceed on the copy stream while the
+// previous run marches.  Successive renders walk the views in alternating
+// directions, so a render starts with the blocks the previous one left
+// resident.  Runs are launched eagerly on the caller's stream, never from the
+// graph: each one rewrites the staging and the block records.
 cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *rgb, float *aux,
                          int32_t *ns, cudaStream_t st) {
     cow_ctx *c = b->ctx;
@@ -391,7 +395,8 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
         if (own_bytes > c->budget)
             return fail(COW_ERR_OOM, "batch view %d needs %lld bytes, over the residency budget of %lld", v,
                         (long long)own_bytes, (long long)c->budget);
-        if (k > first && run_bytes + add > c->budget) {
+        const int64_t cap = std::max<int64_t>(1, (int64_t)((double)c->budget * (double)b->run_frac));
+        if (k > first && run_bytes + add > cap) {
             cow_status rc = launch(k);
             if (rc != COW_OK) return rc;
             for (int32_t id : run_ids) in[(size_t)id] = 0;
@@ -467,6 +472,7 @@ cow_status cow_batch_free(cow_batch *b) {
 
 cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_views, const int32_t *ids,
                                const int32_t *ids_offsets, int64_t *out_pixels) {
+    COW_NVTX("cow_batch_set_views");
     g_last_error.clear();
     if (b && !b->ctx) return fail(COW_ERR_INVALID_ARG, "the batch's context has been freed");
     if (!b || !cams || n_views < 1 || !ids_offsets) return fail(COW_ERR_INVALID_ARG, "cow_batch_set_views: null argument");
@@ -497,6 +503,7 @@ cow_status cow_batch_set_views(cow_batch *b, const cow_camera *cams, int32_t n_v
 
 cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                             float *out_aux, int32_t *out_nsamp, int32_t use_graph, void *stream) {
+    COW_NVTX("cow_batch_render");
     g_last_error.clear();
     if (b && !b->ctx) return fail(COW_ERR_INVALID_ARG, "the batch's context has been freed");
     if (!b || !mlp || !out_rgb) return fail(COW_ERR_INVALID_ARG, "cow_batch_render: null argument");
@@ -552,6 +559,13 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     return COW_OK;
 }
 
+cow_status cow_batch_set_run_fraction(cow_batch *b, float frac) {
+    g_last_error.clear();
+    if (!b || !(frac > 0.0f && frac <= 1.0f)) return fail(COW_ERR_INVALID_ARG, "run fraction must be in (0, 1]");
+    b->run_frac = frac;
+    return COW_OK;
+}
+
 cow_status cow_batch_last_groups(const cow_batch *b, int32_t *out_groups) {
     if (!b || !out_groups) return fail(COW_ERR_INVALID_ARG, "cow_batch_last_groups: null argument");
     *out_groups = b->last_groups;
@@ -569,6 +583,7 @@ cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per
 
 cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb, int32_t reps,
                           void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms) {
+    COW_NVTX("cow_batch_tune");
     g_last_error.clear();
     if (!b || !mlp || !out_rgb || reps < 1) return fail(COW_ERR_INVALID_ARG, "cow_batch_tune: bad argument");
     if (!b->ctx) return fail(COW_ERR_INVALID_ARG, "the batch's context has been freed");

@@ -710,6 +710,7 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
 
 cow_status cow_load_blocks_ex(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
                               float occ_thresh, int32_t occ_cell, uint32_t load_flags, void *stream) {
+    COW_NVTX("cow_load_blocks_ex");
     g_last_error.clear();
     if (!out || !blocks || n < 1) return fail(COW_ERR_INVALID_ARG, "cow_load_blocks: null pointer or n < 1");
     *out = nullptr;
@@ -825,6 +826,7 @@ cow_status cow_block_ztop(const cow_ctx *ctx, int32_t block, double *out_ztop) {
 
 cow_status cow_select_lod(const cow_ctx *ctx, const cow_camera *cam, const double *lod_thresh, int32_t n_lod,
                           int32_t *out_ids, int32_t cap, int32_t *out_n) {
+    COW_NVTX("cow_select_lod");
     if (!ctx || !cam || !out_n || (n_lod > 0 && !lod_thresh) || (cap > 0 && !out_ids))
         return fail(COW_ERR_INVALID_ARG, "cow_select_lod: null argument");
     const ViewGeom g = view_geom(*cam);
@@ -875,6 +877,7 @@ cow_status cow_sort_blocks(const cow_ctx *ctx, const cow_camera *cam, const int3
 cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, const int32_t *ids,
                       const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                       float *out_aux, int32_t *out_nsamp, void *stream) {
+    COW_NVTX("cow_render");
     g_last_error.clear();
     const bool block_mlp = (flags & COW_FLAG_BLOCK_MLPS) != 0;
     if (!ctx || !cams || n_views < 1 || !ids_offsets || (!mlp && !block_mlp) || !out_rgb)
@@ -964,6 +967,7 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
 static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                                    int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                                    float *out_aux, int32_t *out_nsamp, float *out_block_T, void *stream) {
+    COW_NVTX("cow_render_rays");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     const bool block_mlp = (flags & COW_FLAG_BLOCK_MLPS) != 0;
@@ -1027,6 +1031,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
 
 cow_status cow_render_partials(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                                int32_t n_ids, float *out_partials, void *stream) {
+    COW_NVTX("cow_render_partials");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !out_partials)
@@ -1058,6 +1063,7 @@ cow_status cow_render_partials(cow_ctx *ctx, const float *o, const float *d, int
 cow_status cow_composite_over(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                               int32_t n_ids, const float *partials, const float *mlp, uint32_t flags, float *out_rgb,
                               float *out_aux, void *stream) {
+    COW_NVTX("cow_composite_over");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !partials || !mlp || !out_rgb)
@@ -1114,6 +1120,7 @@ cow_status cow_render_rays_block_t(cow_ctx *ctx, const float *o, const float *d,
 cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                                int32_t n_ids, const float *mlp, float ert_eps, const float *aux, const float *dL_drgb,
                                float *const *grad_grid, float *const *grad_planes, float *grad_mlp, void *stream) {
+    COW_NVTX("cow_render_backward");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !aux || !dL_drgb || !grad_grid || !grad_planes || !grad_mlp)
@@ -1171,6 +1178,7 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
                                           const int32_t *ids, int32_t n_ids, const float *dL_drgb,
                                           float *const *grad_grid, float *const *grad_planes, float *grad_block_mlps,
                                           void *stream) {
+    COW_NVTX("cow_render_backward_block_mlps");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !dL_drgb || !grad_grid || !grad_planes || !grad_block_mlps)
@@ -1271,6 +1279,7 @@ cow_status reg_prepare(cow_ctx *ctx, const int32_t *ids, int32_t n_ids, float *l
 cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points, const int32_t *ids, int32_t n_ids,
                              float weight, float *loss, float *const *grad_grid, float *const *grad_planes,
                              void *stream) {
+    COW_NVTX("cow_sparsity_loss");
     g_last_error.clear();
     if (ctx && n_points == 0) return COW_OK;  // nothing to add (the arrays may be NULL)
     if (!ctx || !points || n_points < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_sparsity_loss: null argument");
@@ -1295,6 +1304,7 @@ cow_status cow_sparsity_loss(cow_ctx *ctx, const float *points, int64_t n_points
 cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                             int32_t n_ids, const float *block_T, float weight, float *loss, float *const *grad_grid,
                             float *const *grad_planes, void *stream) {
+    COW_NVTX("cow_opacity_loss");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // nothing to add (the arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids) return fail(COW_ERR_INVALID_ARG, "cow_opacity_loss: null argument");
@@ -1318,6 +1328,7 @@ cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_
 
 cow_status cow_update_features(cow_ctx *ctx, int32_t block, const float *grid, const float *plane_xy,
                                const float *plane_xz, const float *plane_yz, void *stream) {
+    COW_NVTX("cow_update_features");
     g_last_error.clear();
     if (!ctx || !grid || !plane_xy || !plane_xz || !plane_yz) return fail(COW_ERR_INVALID_ARG, "null argument");
     if (block < 0 || block >= (int32_t)ctx->blocks.size()) return fail(COW_ERR_INVALID_ARG, "block out of range");
@@ -1400,6 +1411,7 @@ cow_status cow_set_block_unbounded(cow_ctx *ctx, int32_t block, int32_t flags, v
 }
 
 cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream) {
+    COW_NVTX("cow_set_residency");
     g_last_error.clear();
     if (!ctx || budget_bytes < 0) return fail(COW_ERR_INVALID_ARG, "cow_set_residency: null context or budget < 0");
     DeviceGuard dg(ctx->device);

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cow.h"
 #include "cow_common.cuh"
 #include "cow_kernels.h"
@@ -29,6 +31,17 @@ bool is_device_ptr(const void *p);
                               "%s failed: %s", #call, cudaGetErrorString(e_));              \
         }                                                                                   \
     } while (0)
+
+// An NVTX range around one C-ABI call (header-only NVTX v3: a no-op unless a
+// profiler that collects NVTX, such as Nsight Systems or ncu with
+// --nvtx, is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define COW_NVTX(name) cowi::NvtxRange cow_nvtx_range_(name)
 
 // Restores the caller's current device when it leaves scope.
 struct DeviceGuard {

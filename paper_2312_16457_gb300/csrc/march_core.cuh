@@ -34,9 +34,17 @@ constexpr int kPlaneLd = COW_PLANE_LD_POLICY;
 // strides from it.  A voxel whose brick is not stored (only a lookup at an
 // arbitrary point can meet one: lattice samples lie in occupied cells, whose
 // bricks are stored) reads no grid element and takes the grid term as zero.
+// The brick slot of the last lookup of one ray in one block (brick-sparse
+// grids): successive samples mostly stay in one 16^3-voxel brick, so the
+// table read leaves the gathers' address path.
+struct BrickCache {
+    int key = -1;
+    int slot = 0;
+};
+
 template <int DT>
-__device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], const float g[3],
-                                                  float2 f[4]) {
+__device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float p[3], const float g[3], float2 f[4],
+                                                  BrickCache *bc = nullptr) {
     constexpr int ST = DT & kStoreMask;                 // storage format
     constexpr bool kBricks = (DT & kBrickBit) != 0;     // brick-sparse grid
     float fr[3];
@@ -53,8 +61,17 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
     bool stored = true;
     if constexpr (kBricks) {
         const int nb = b.Nb;
-        const int slot =
-            __ldg(b.brick + ((c0[2] >> kBrickLog2) * nb + (c0[1] >> kBrickLog2)) * nb + (c0[0] >> kBrickLog2));
+        const int key = ((c0[2] >> kBrickLog2) * nb + (c0[1] >> kBrickLog2)) * nb + (c0[0] >> kBrickLog2);
+        int slot;
+        if (bc) {
+            if (key != bc->key) {
+                bc->key = key;
+                bc->slot = __ldg(b.brick + key);
+            }
+            slot = bc->slot;
+        } else {
+            slot = __ldg(b.brick + key);
+        }
         sy = b.bsy;
         sz = b.bsz;
         const int loc = (c0[2] & (kBrick - 1)) * sz + (c0[1] & (kBrick - 1)) * sy + (c0[0] & (kBrick - 1));
@@ -423,9 +440,10 @@ template <int DT>
 __device__ __forceinline__ void march_block(const BlockRec &b, const float o[3], const float d[3],
                                             const float inv_d[3], float omax, float ert_eps, RayState &s,
                                             unsigned *err, float *tb = nullptr) {
+    BrickCache bc;
     const bool more = for_each_sample(b, o, d, inv_d, omax, err, [&](const float p[3], const float g[3], float dt) {
         float2 f2[4];
-        accumulate_sample<DT>(b, p, g, f2);
+        accumulate_sample<DT>(b, p, g, f2, &bc);
         const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
         const float sigma = __expf(f[0]);
         const float e = __expf(-sigma * dt);

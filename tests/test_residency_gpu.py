@@ -154,11 +154,13 @@ def _lru_uploads(bb, runs, budget, resident=()):
     return up, res
 
 
-def test_batch_under_budget_equals_all_resident():
+@pytest.mark.parametrize("run_frac", [1.0, 0.5])
+def test_batch_under_budget_equals_all_resident(run_frac):
     """The batched form under a residency budget: the views run in groups
-    whose blocks fit together, the pixels equal the all-resident batch's bit
-    for bit, the loads equal a re-statement of the rule, the budget holds,
-    and leaving the budget serves the whole batch in one launch again."""
+    whose blocks fit together in the run fraction of the budget, the pixels
+    equal the all-resident batch's bit for bit, the loads equal a
+    re-statement of the rule, the budget holds, and leaving the budget serves
+    the whole batch in one launch again."""
     sc, cams, mlp = _scene()
     ref = cow.Context(sc, "bf16")
     ctx = cow.Context(sc, "bf16")
@@ -179,14 +181,16 @@ def test_batch_under_budget_equals_all_resident():
     need = [sum(bb[i] for i in set(v.tolist())) for v in ids]
     budget = int(1.25 * max(need))
     batch = cow.Batch(ctx, len(cams), n_ids)  # created before the budget is set
+    batch.set_run_fraction(run_frac)
     assert batch.set_views(cams, ids) == npix
     got = outs(npix)
     batch.render(mlp_d, *got, graph=True)
     assert batch.last_groups() == 1
     ctx.set_residency(budget)
     r0 = ctx.residency()
-    runs = _runs(bb, ids, budget)
-    runs_back = _runs(bb, ids[::-1], budget)  # the second render walks the views last to first
+    cap = int(budget * run_frac)
+    runs = _runs(bb, ids, cap)
+    runs_back = _runs(bb, ids[::-1], cap)  # the second render walks the views last to first
     assert len(runs) > 2
     for step in range(2):  # the second render starts from what the first left resident
         for t in got:
