@@ -146,6 +146,20 @@ cow_status cow_load_blocks(cow_ctx **out, const cow_block_desc *blocks, int32_t 
 cow_status cow_load_blocks_ex(cow_ctx **out, const cow_block_desc *blocks, int32_t n, cow_dtype storage,
                               float occ_thresh, int32_t occ_cell, uint32_t load_flags, void *stream);
 
+/* Packed scene files (the paper bakes its blocks to texture assets, Sec.
+ * 4.5; this is the GPU equivalent, no counterpart of the format in the
+ * paper): cow_save_scene writes what a context holds -- every block's packed
+ * features in the storage format (dense or brick-sparse), occupancy levels,
+ * FP8 scales, z_top and LOD links -- as a binary header and block table, a
+ * JSON manifest of the same facts, then the raw arrays (unloaded blocks are
+ * written from their host copies).  cow_load_scene creates a context from
+ * such a file on the current device with every block resident, without the
+ * FP32 masters or a re-pack; its renders equal the saved context's bit for
+ * bit.  Errors: INVALID_ARG (unreadable, truncated or foreign file, write
+ * failure), OOM, CUDA. */
+cow_status cow_save_scene(const cow_ctx *ctx, const char *path);
+cow_status cow_load_scene(cow_ctx **out, const char *path, void *stream);
+
 /* Release a context and all its device memory (NULL is accepted). */
 cow_status cow_free(cow_ctx *ctx);
 
@@ -356,8 +370,11 @@ cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, c
  * cow_batch_set_config : tile_cfg 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8
  *                    pixels per CTA; ctas_per_sm resident CTAs per SM (1..32).
  * cow_batch_tune   : times every (tile_cfg, ctas_per_sm in {2,3,4,6,8}) on the
- *                    set views (reps renders each, into out_rgb) and keeps the
- *                    fastest; reports it and its time per batch in ms.
+ *                    set views (reps renders each, into out_rgb) with the
+ *                    records in the parameter buffer, then the best of them
+ *                    with the records staged in shared memory, and keeps the
+ *                    fastest; reports its tile and CTAs and its time per
+ *                    batch in ms (cow_batch_get_config: the record mode).
  * Errors: INVALID_ARG, OOM, CUDA. */
 typedef struct cow_batch cow_batch;
 cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, cow_batch **out);
@@ -370,6 +387,18 @@ cow_status cow_batch_last_groups(const cow_batch *b, int32_t *out_groups);
 /* The fraction of the residency budget one run of cow_batch_render may fill
  * (0 < frac <= 1; default 0.5).  Errors: INVALID_ARG. */
 cow_status cow_batch_set_run_fraction(cow_batch *b, float frac);
+/* Where the batched kernels read block records (the batch's marching
+ * schedule): COW_BATCH_RECORDS_PARAM (default) groups the views into runs
+ * whose records travel in the launch's parameter buffer (when every view has
+ * at most 96 blocks, else as SHARED); COW_BATCH_RECORDS_SHARED has one launch
+ * stage each view's records into shared memory.  cow_batch_tune picks it
+ * (after tile shape and CTAs per SM); cow_batch_get_config reports the
+ * configuration in use.  Errors: INVALID_ARG. */
+#define COW_BATCH_RECORDS_PARAM 0
+#define COW_BATCH_RECORDS_SHARED 1
+cow_status cow_batch_set_records(cow_batch *b, int32_t mode);
+cow_status cow_batch_get_config(const cow_batch *b, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm,
+                                int32_t *out_records);
 cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm);
 cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb, int32_t reps,
                           void *stream, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm, float *out_ms);
@@ -569,6 +598,18 @@ cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule);
  * each walked row by row, so the tiles in flight cover a compact screen
  * region (their rays share more texels in L2).  Errors: INVALID_ARG. */
 cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles);
+
+/* Autotuner of cow_render's marching schedule: renders the given views
+ * (arguments as cow_render, device outputs only: out_rgb is overwritten)
+ * with every schedule (COW_SCHED_THREAD_CONST, COW_SCHED_THREAD,
+ * COW_SCHED_WARP) and tile order (raster, strips of 2 and 4 tile columns),
+ * reps timed renders each after one warm-up, keeps the fastest on the
+ * context and reports it (any out pointer may be NULL).
+ * Errors: as cow_render. */
+cow_status cow_tune_schedule(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                             const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags,
+                             float *out_rgb, int32_t reps, void *stream, int32_t *out_schedule,
+                             int32_t *out_strip, float *out_ms);
 
 /* Wait for the stream and report a device-side error word set by a kernel of
  * this context (COW_ERR_DEVICE_ASSERT or COW_ERR_TIMEOUT); clears it. */

@@ -35,7 +35,7 @@ FLAG_BLOCK_MLPS = 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "TIMEOUT", 6: "DEVICE_ASSERT"}
 
 # every symbol include/cow.h declares
-EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
+EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_save_scene", "cow_load_scene", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
            "cow_render", "cow_render_rays", "cow_render_partials", "cow_composite_over", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_set_test_hooks", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
@@ -44,7 +44,8 @@ EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_free", "cow_num_blocks"
            "cow_render_backward_block_mlps",
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
-           "cow_batch_last_groups", "cow_batch_set_run_fraction", "cow_last_error",
+           "cow_batch_last_groups", "cow_batch_set_run_fraction", "cow_batch_set_records", "cow_batch_get_config",
+           "cow_tune_schedule", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
@@ -85,6 +86,8 @@ def lib():
         sig = {
             "cow_load_blocks": [P, P, i32, i32, flt, i32, P],
             "cow_load_blocks_ex": [P, P, i32, i32, flt, i32, u32, P],
+            "cow_save_scene": [P, C.c_char_p],
+            "cow_load_scene": [P, C.c_char_p, P],
             "cow_free": [P],
             "cow_num_blocks": [P, P],
             "cow_block_ztop": [P, i32, P],
@@ -126,6 +129,9 @@ def lib():
             "cow_batch_set_config": [P, i32, i32],
             "cow_batch_last_groups": [P, P],
             "cow_batch_set_run_fraction": [P, flt],
+            "cow_batch_set_records": [P, i32],
+            "cow_batch_get_config": [P, P, P, P],
+            "cow_tune_schedule": [P, P, i32, P, P, P, flt, u32, P, i32, P, P, P, P],
             "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
         }
         for name, args in sig.items():
@@ -212,6 +218,26 @@ class Context:
         if self._ctx:
             lib().cow_free(self._ctx)
             self._ctx = C.c_void_p()
+
+    def save(self, path: str):
+        """Write the packed scene to a file (cow_save_scene)."""
+        _check(lib().cow_save_scene(self._ctx, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str, scene=None, stream=None) -> "Context":
+        """A context from a packed scene file (cow_load_scene); `scene` (the
+        synthetic description, optional) is kept for inspection helpers."""
+        self = cls.__new__(cls)
+        self._ctx = C.c_void_p()
+        _check(lib().cow_load_scene(C.byref(self._ctx), os.fsencode(path), _stream_ptr(stream)))
+        n = C.c_int32()
+        _check(lib().cow_num_blocks(self._ctx, C.byref(n)))
+        self.n_blocks = n.value
+        self.scene = scene
+        self.storage = None
+        self.bricks = None
+        self.schedule = "thread_const"
+        return self
 
     def __del__(self):
         try:
@@ -406,6 +432,20 @@ class Context:
         _check(lib().cow_update_features(self._ctx, int(i), _ptr(g), _ptr(pls[0]), _ptr(pls[1]), _ptr(pls[2]),
                                          _stream_ptr(stream)))
 
+    def tune_schedule(self, cams, ids_per_view, mlp, out_rgb, ert_eps: float = 0.0, reps: int = 2, stream=None):
+        """Times every marching schedule and tile order on these views and
+        keeps the fastest (cow_tune_schedule); returns (schedule, strip, ms)."""
+        cams = list(cams)
+        cc = (Camera * len(cams))(*[_camera(c) for c in cams])
+        flat, offs = _views_csr(ids_per_view)
+        m = mlp if isinstance(mlp, torch.Tensor) else _as_f32(mlp)
+        s, t, ms = C.c_int32(), C.c_int32(), C.c_float()
+        _check(lib().cow_tune_schedule(self._ctx, cc, len(cams), _ptr(flat), _ptr(offs), _ptr(m), float(ert_eps), 0,
+                                       _ptr(out_rgb), int(reps), _stream_ptr(stream), C.byref(s), C.byref(t),
+                                       C.byref(ms)))
+        self.schedule = {v: k for k, v in SCHEDULES.items()}[s.value]
+        return self.schedule, t.value, ms.value
+
     def set_schedule(self, name: str):
         """"thread_const" (default: one ray per thread, block records in the
         kernel parameter buffer), "thread" (records in shared memory) or
@@ -589,6 +629,19 @@ class Batch:
         n = C.c_int32()
         _check(lib().cow_batch_last_groups(self._b, C.byref(n)))
         return n.value
+
+    RECORDS = {"param": 0, "shared": 1}
+
+    def set_records(self, mode: str):
+        """Record placement of the batched kernels: "param" (runs, records in
+        the parameter buffer) or "shared" (staged in shared memory)."""
+        _check(lib().cow_batch_set_records(self._b, self.RECORDS[mode]))
+
+    def config(self):
+        """(tile shape, CTAs per SM, record placement) in use."""
+        t, c, r = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().cow_batch_get_config(self._b, C.byref(t), C.byref(c), C.byref(r)))
+        return self.TILE_SHAPES[t.value], c.value, {v: k for k, v in self.RECORDS.items()}[r.value]
 
     def set_run_fraction(self, frac: float):
         """Under a residency budget: the fraction of it one run may fill."""

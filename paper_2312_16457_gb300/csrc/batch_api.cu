@@ -35,6 +35,7 @@ struct cow_batch {
     bool backward = false;             // under a budget: the next render serves the views last to first
     int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
     float run_frac = 0.5f;             // under a budget: a run's blocks fill at most this fraction of it
+    int records = COW_BATCH_RECORDS_PARAM;  // record placement (cow_batch_set_records)
     int sms = 0;
     // captured graph and the arguments it was captured with
     cudaGraphExec_t exec = nullptr;
@@ -517,7 +518,7 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     DeviceGuard dg(b->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (b->ctx->budget > 0) return render_groups(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
-    const bool want_runs = runs_fit(b);
+    const bool want_runs = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b);
     if (b->dirty || b->rec_gen != b->ctx->rec_gen || b->param_mode != want_runs) {
         // new views, tile shape, or block records
         cow_status rc = want_runs ? build_runs(b) : build_stage(b, 0, (int32_t)b->cams.size());
@@ -563,6 +564,23 @@ cow_status cow_batch_set_run_fraction(cow_batch *b, float frac) {
     g_last_error.clear();
     if (!b || !(frac > 0.0f && frac <= 1.0f)) return fail(COW_ERR_INVALID_ARG, "run fraction must be in (0, 1]");
     b->run_frac = frac;
+    return COW_OK;
+}
+
+cow_status cow_batch_set_records(cow_batch *b, int32_t mode) {
+    g_last_error.clear();
+    if (!b || (mode != COW_BATCH_RECORDS_PARAM && mode != COW_BATCH_RECORDS_SHARED))
+        return fail(COW_ERR_INVALID_ARG, "cow_batch_set_records: bad argument");
+    b->records = mode;
+    return COW_OK;
+}
+
+cow_status cow_batch_get_config(const cow_batch *b, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm,
+                                int32_t *out_records) {
+    if (!b) return fail(COW_ERR_INVALID_ARG, "cow_batch_get_config: null batch");
+    if (out_tile_cfg) *out_tile_cfg = b->tile_cfg;
+    if (out_ctas_per_sm) *out_ctas_per_sm = b->ctas_per_sm;
+    if (out_records) *out_records = b->records;
     return COW_OK;
 }
 
@@ -620,6 +638,32 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
                 best_c = c;
             }
         }
+    }
+    // the record placement at the best tile and CTAs
+    const int rec0 = b->records;
+    int best_r = rec0;
+    if (rc == COW_OK) {
+        const int other = rec0 == COW_BATCH_RECORDS_PARAM ? COW_BATCH_RECORDS_SHARED : COW_BATCH_RECORDS_PARAM;
+        rc = cow_batch_set_config(b, best_t, best_c);
+        if (rc == COW_OK) rc = cow_batch_set_records(b, other);
+        if (rc == COW_OK) rc = cow_batch_render(b, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, 0, stream);
+        if (rc == COW_OK) {
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && rc == COW_OK; r++)
+                rc = cow_batch_render(b, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, 0, stream);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(COW_ERR_CUDA, "cow_batch_tune: synchronisation failed");
+        }
+        if (rc == COW_OK) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < best) {
+                best = ms;
+                best_r = other;
+            }
+        }
+        b->records = best_r;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

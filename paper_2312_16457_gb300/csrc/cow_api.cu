@@ -695,6 +695,11 @@ cow_status note_use(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st) 
     return note_use_impl(c, ids, n, st);
 }
 
+int64_t block_tensor_bytes(const cow_ctx *c, const BlockHost &b, int t) { return tensor_bytes(c, b, t); }
+int64_t block_feature_offset(const cow_ctx *c, const BlockHost &b, int t) { return feature_offset(c, b, t); }
+cow::BlockRec block_record(const cow_ctx *c, const BlockHost &b) { return make_rec(c, b); }
+void destroy_context(cow_ctx *c) { destroy(c); }
+
 }  // namespace cowi
 
 extern "C" {
@@ -1688,6 +1693,62 @@ cow_status cow_set_tile_order(cow_ctx *ctx, int32_t strip_tiles) {
     if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
     if (strip_tiles < 0 || strip_tiles > 4096) return fail(COW_ERR_INVALID_ARG, "strip_tiles must be in [0, 4096]");
     ctx->tile_strip = strip_tiles;
+    return COW_OK;
+}
+
+cow_status cow_tune_schedule(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, const int32_t *ids,
+                             const int32_t *ids_offsets, const float *mlp, float ert_eps, uint32_t flags,
+                             float *out_rgb, int32_t reps, void *stream, int32_t *out_schedule,
+                             int32_t *out_strip, float *out_ms) {
+    g_last_error.clear();
+    if (!ctx || !out_rgb || reps < 1) return fail(COW_ERR_INVALID_ARG, "cow_tune_schedule: bad argument");
+    if (!is_device_ptr(out_rgb)) return fail(COW_ERR_INVALID_ARG, "cow_tune_schedule: out_rgb must be device memory");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    static const int kScheds[] = {COW_SCHED_THREAD_CONST, COW_SCHED_THREAD, COW_SCHED_WARP};
+    static const int kStrips[] = {0, 2, 4};
+    const int s0 = ctx->schedule, t0 = ctx->tile_strip;
+    cudaEvent_t e0, e1;
+    COW_CUDA(cudaEventCreate(&e0));
+    COW_CUDA(cudaEventCreate(&e1));
+    float best = 3.0e38f;
+    int best_s = s0, best_t = t0;
+    cow_status rc = COW_OK;
+    for (int sc : kScheds) {
+        for (int tr : kStrips) {
+            ctx->schedule = sc;
+            ctx->tile_strip = tr;
+            rc = cow_render(ctx, cams, n_views, ids, ids_offsets, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, stream);
+            if (rc != COW_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && rc == COW_OK; r++)
+                rc = cow_render(ctx, cams, n_views, ids, ids_offsets, mlp, ert_eps, flags, out_rgb, nullptr, nullptr,
+                                stream);
+            cudaEventRecord(e1, st);
+            if (rc != COW_OK) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(COW_ERR_CUDA, "cow_tune_schedule: synchronisation failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < best) {
+                best = ms;
+                best_s = sc;
+                best_t = tr;
+            }
+        }
+        if (rc != COW_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->schedule = rc == COW_OK ? best_s : s0;
+    ctx->tile_strip = rc == COW_OK ? best_t : t0;
+    if (rc != COW_OK) return rc;
+    if (out_schedule) *out_schedule = best_s;
+    if (out_strip) *out_strip = best_t;
+    if (out_ms) *out_ms = best;
     return COW_OK;
 }
 

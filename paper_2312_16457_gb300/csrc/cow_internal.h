@@ -141,6 +141,14 @@ int64_t block_feature_bytes(const cow_ctx *c, int32_t i);
 // enqueued on st afterwards waits for the loads.
 cow_status make_resident(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t st);
 
+// Context internals for the scene files (scene_io.cu): packed bytes of
+// tensor t of a block (0 grid with its density octets, 1-3 planes), its
+// offset in a block's host copy, a block's kernel record, and teardown.
+int64_t block_tensor_bytes(const cow_ctx *c, const BlockHost &b, int t);
+int64_t block_feature_offset(const cow_ctx *c, const BlockHost &b, int t);
+cow::BlockRec block_record(const cow_ctx *c, const BlockHost &b);
+void destroy_context(cow_ctx *c);
+
 // cow_free of a context with live batches: the batch drops its context
 // pointer (its later calls fail with INVALID_ARG; cow_batch_free still works).
 void batch_detach(struct cow_batch *b);

@@ -134,6 +134,42 @@ class Fitter:
             self.ctx.update_features(i, self.params[4 * i], self.params[4 * i + 1:4 * i + 4])
         return loss
 
+    def state_dict(self) -> dict:
+        """Everything a resumed fit needs: the FP32 parameters, the MLP (or
+        per-block MLPs), Adam's moments and step count, the learning rates."""
+        return {"params": [p.detach().cpu() for p in self.params],
+                "mlp": None if self.mlp is None else self.mlp.detach().cpu(),
+                "block_mlps": None if self.block_mlps is None else self.block_mlps.detach().cpu(),
+                "n_freq": self.n_freq, "m": [x.detach().cpu() for x in self.m], "v": [x.detach().cpu() for x in self.v],
+                "t": self.t, "lr_feat": self.lr_feat, "lr_mlp": self.lr_mlp, "rng": self.gen.get_state().cpu()}
+
+    def save(self, path: str):
+        """Checkpoint of the fit (torch.save of state_dict())."""
+        torch.save(self.state_dict(), path)
+
+    def load(self, path_or_state):
+        """Resume from save(): parameters and Adam state are restored and the
+        context's packed features re-packed from the parameters."""
+        st = torch.load(path_or_state, map_location="cpu") if isinstance(path_or_state, str) else path_or_state
+        if len(st["params"]) != len(self.params) or (st["block_mlps"] is None) != (self.block_mlps is None):
+            raise ValueError("checkpoint of a different fit")
+        for p, q in zip(self.params, st["params"]):
+            p.copy_(q.to(p.device))
+        for x, q in zip(self.m, st["m"]):
+            x.copy_(q.to(x.device))
+        for x, q in zip(self.v, st["v"]):
+            x.copy_(q.to(x.device))
+        if self.block_mlps is not None:
+            self.block_mlps.copy_(st["block_mlps"].to(self.block_mlps.device))
+            self.ctx.set_block_mlps(self.block_mlps, self.n_freq)
+        else:
+            self.mlp.copy_(st["mlp"].to(self.mlp.device))
+        self.t = int(st["t"])
+        self.lr_feat, self.lr_mlp = st["lr_feat"], st["lr_mlp"]
+        self.gen.set_state(st["rng"].to(self.gen.get_state().device))
+        for i in range(len(self.ids)):
+            self.ctx.update_features(i, self.params[4 * i], self.params[4 * i + 1:4 * i + 4])
+
     def render(self, o, d, ert_eps: float = 0.0):
         if self.block_mlps is not None:
             return self.ctx.render_rays(o, d, self.ids, None, aux=False, block_mlps=True)[0]

@@ -76,7 +76,44 @@ def test_calls_reject_null_context(L):
     assert L.cow_render_backward_block_mlps(None, None, None, 1, None, 1, None, None, None, None, None) == 1
     assert L.cow_batch_last_groups(None, C.byref(n)) == 1
     assert L.cow_set_block_mlps(None, None, 0, 0, None) == 1
+    assert L.cow_set_test_hooks(None, 0, 0) == 1
+    assert L.cow_render_partials(None, None, None, 1, None, 1, None, None) == 1
+    assert L.cow_composite_over(None, None, None, 1, None, 1, None, None, 0, None, None, None) == 1
+    assert L.cow_tune_schedule(None, None, 1, None, None, None, 0.0, 0, None, 1, None, None, None, None) == 1
+    assert L.cow_batch_set_run_fraction(None, 0.5) == 1
+    assert L.cow_batch_set_records(None, 0) == 1
+    assert L.cow_save_scene(None, b"x") == 1
     assert L.cow_free(None) == 0
+
+
+def test_scene_file_checks_on_the_host(L, tmp_path):
+    """cow_load_scene refuses a missing or foreign file before any device work."""
+    ctx = C.c_void_p()
+    assert L.cow_load_scene(C.byref(ctx), str(tmp_path / "missing.cow").encode(), None) == 1
+    p = tmp_path / "junk.cow"
+    p.write_bytes(b"\0" * 4096)
+    assert L.cow_load_scene(C.byref(ctx), str(p).encode(), None) == 1
+    assert b"packed scene" in L.cow_last_error()
+    assert not ctx.value
+
+
+def test_load_flags_checked_on_the_host(L):
+    """Unknown load flags and brick-sparse grids with a cell edge other
+    than 4 are refused before any device work."""
+    g = (C.c_float * (2 * 2 * 2 * 8))()
+    pl = (C.c_float * (2 * 2 * 8))()
+    d = cow.BlockDesc()
+    d.lo[:] = [0.0, 0.0, 0.0]
+    d.hi[:] = [1.0, 1.0, 1.0]
+    d.lod, d.parent, d.grid_res, d.plane_res = 1, -1, 2, 2
+    d.grid = C.cast(g, C.c_void_p)
+    for k in range(3):
+        d.planes[k] = C.cast(pl, C.c_void_p)
+    ctx = C.c_void_p()
+    assert L.cow_load_blocks_ex(C.byref(ctx), C.byref(d), 1, 2, 0.01, 4, 2, None) == 1
+    assert L.cow_load_blocks_ex(C.byref(ctx), C.byref(d), 1, 2, 0.01, 3, 1, None) == 4  # UNSUPPORTED
+    assert b"occ_cell" in L.cow_last_error()
+    assert L.cow_load_blocks_ex(C.byref(ctx), C.byref(d), 1, 9, 0.01, 4, 0, None) == 1  # unknown dtype
 
 
 # --- residency-aware view order (host only) --------------------------------

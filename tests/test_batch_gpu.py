@@ -134,3 +134,35 @@ def test_batch_runs_and_long_lists():
     assert float((out[0] - ref2[0]).abs().max()) <= 2e-6
     b.close()
     b2.close()
+
+
+def test_tuners_pick_valid_schedules():
+    """cow_tune_schedule (per-view schedule and tile order) and the record
+    placement cow_batch_tune adds: the kept configuration is one of the
+    candidates and renders the same image."""
+    sc, cams, mlp = _scene()
+    ctx = cow.Context(sc, "bf16")
+    ids = [ctx.select_lod(c, sc.lod_thresh) for c in cams]
+    mlp_d = torch.from_numpy(mlp).cuda()
+    ref = ctx.render(cams, ids, mlp_d, nsamp=True)
+    n = ref[0].shape[0]
+    sched, strip, ms = ctx.tune_schedule(cams, ids, mlp_d, torch.empty((n, 3), device="cuda"))
+    assert sched in ("thread_const", "thread", "warp") and strip in (0, 2, 4) and ms > 0
+    got = ctx.render(cams, ids, mlp_d, nsamp=True)
+    ctx.sync_check()
+    assert torch.equal(got[2], ref[2])
+    assert float((got[0] - ref[0]).abs().max()) <= 2e-6
+    b = cow.Batch(ctx, 16, 4096)
+    b.set_views(cams, ids)
+    for mode in ("shared", "param"):
+        b.set_records(mode)
+        out = torch.empty((n, 3), device="cuda")
+        ns = torch.zeros(n, dtype=torch.int32, device="cuda")
+        b.render(mlp_d, out, None, ns, graph=True)
+        ctx.sync_check()
+        assert torch.equal(ns, ref[2]), mode
+    b.tune(mlp_d, torch.empty((n, 3), device="cuda"))
+    tile, ctas, rec = b.config()
+    assert tile in cow.Batch.TILE_SHAPES.values() and ctas in (2, 3, 4, 6, 8) and rec in ("param", "shared")
+    b.close()
+    ctx.close()

@@ -158,3 +158,28 @@ def test_backward_matches_gpu_finite_differences():
         assert abs(fd - float(gm[j])) <= 0.03 * abs(float(gm[j])) + 2e-3, ("mlp", j, fd, float(gm[j]))
         checked += 1
     assert checked >= 8
+
+
+def test_fit_checkpoint_resumes_exactly(tmp_path):
+    """A fit saved after some Adam steps and resumed in a new Fitter takes
+    the same next steps as the uninterrupted one (parameters, Adam moments,
+    step count and the sampler's state are all in the checkpoint)."""
+    sc = synth.city_scene(4, 2, 2.0, [(12, 24)])
+    tgt = synth.city_scene(40, 2, 2.0, [(12, 24)])
+    o, d = synth.random_rays(1 << 13, 4, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    tctx = cow.Context(tgt, "fp32")
+    target = tctx.render_rays(o, d, [0, 1, 2, 3], synth.mlp_weights(140), aux=False)[0]
+    a = train.Fitter(sc, synth.mlp_weights(104), lambda_sparsity=0.05)
+    for _ in range(3):
+        a.step(o, d, target)
+    path = str(tmp_path / "fit.pt")
+    a.save(path)
+    la = [float(a.step(o, d, target).item()) for _ in range(3)]
+    b = train.Fitter(sc, synth.mlp_weights(7), lambda_sparsity=0.05)
+    b.load(path)
+    lb = [float(b.step(o, d, target).item()) for _ in range(3)]
+    np.testing.assert_allclose(lb, la, rtol=1e-5)
+    for p, q in zip(a.params, b.params):
+        assert float((p - q).abs().max()) <= 1e-5 * max(1.0, float(p.abs().max()))
+    assert b.t == a.t
