@@ -89,6 +89,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-view batched measurement")
     ap.add_argument("--no-sparse-city", action="store_true", help="skip the sparse-city brick measurement")
     ap.add_argument("--batch-storage", default="bf16", help="storage of the 64-view batched measurement")
+    ap.add_argument("--minimal", action="store_true",
+                    help="the headline frame only: no batched path, per-block MLP form, storage forms, 64-view batch "
+                         "or sparse city (profiling runs)")
     return ap.parse_args()
 
 
@@ -259,6 +262,29 @@ def scene_bytes(ctx, ids):
     return int(sum(ctx.block_bytes(int(i)) for i in ids))
 
 
+def measure_frame_forms(ctx, sc, cam, ids, mlp_d, out, args, flush, stream, reps):
+    """The headline frame through the persistent batched path (one view,
+    autotuned) and with per-block deferred MLPs blended by Eq. 5 (PE(d) at 4
+    octaves)."""
+    from paper_2312_16457_gb300 import cow, synth
+
+    batch = cow.Batch(ctx, 1, len(ids))
+    batch.set_views([cam], [ids])
+    tile, ctas, _ = batch.tune(mlp_d, out[0], ert_eps=args.ert)
+    rec = batch.config()[2]
+    tb = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), reps, 3, flush, stream)
+    batch_path = {"frames_per_s": round(1000.0 / float(np.mean(tb)), 3), "tile": cow.Batch.TILE_SHAPES[tile],
+                  "ctas_per_sm": ctas, "records": rec}
+    batch.close()
+    ctx.set_block_mlps(synth.block_mlp_weights(104, len(sc.blocks), 4), 4)
+    tbm = time_steps(lambda: ctx.render([cam], [ids], None, ert_eps=args.ert, aux=False, out=out, block_mlps=True),
+                     reps, 3, flush, stream)
+    ctx.sync_check()
+    block_mlp_form = {"frames_per_s": round(1000.0 / float(np.mean(tbm)), 3), "n_freq": 4,
+                      "mlp_params_per_block": synth.block_mlp_nparam(4)}
+    return batch_path, block_mlp_form
+
+
 def run_cow(args, ws, rank, local):
     from paper_2312_16457_gb300 import build, cow, synth
 
@@ -322,28 +348,18 @@ def run_cow(args, ws, rank, local):
     d2h = npix * 12
     reps = max(5, args.steps // 2)
 
+    if args.minimal:
+        args.no_batch = args.no_sparse_city = args.no_fp32 = True
     # the same frame through the persistent batched path (one view, autotuned)
-    batch = cow.Batch(ctx, 1, len(ids))
-    batch.set_views([cam], [ids])
-    tile, ctas, _ = batch.tune(mlp_d, out[0], ert_eps=args.ert)
-    tb = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), reps, 3, flush, stream)
-    batch_path = {"frames_per_s": round(1000.0 / float(np.mean(tb)), 3), "tile": cow.Batch.TILE_SHAPES[tile],
-                  "ctas_per_sm": ctas}
-    batch.close()
-
-    # the same frame with per-block deferred MLPs blended by Eq. 5 (PE(d) at 4 octaves)
-    ctx.set_block_mlps(synth.block_mlp_weights(104, len(sc.blocks), 4), 4)
-    tbm = time_steps(lambda: ctx.render([cam], [ids], None, ert_eps=args.ert, aux=False, out=out, block_mlps=True),
-                     reps, 3, flush, stream)
-    ctx.sync_check()
-    block_mlp_form = {"frames_per_s": round(1000.0 / float(np.mean(tbm)), 3), "n_freq": 4,
-                      "mlp_params_per_block": synth.block_mlp_nparam(4)}
+    batch_path = block_mlp_form = None
     main_bytes = scene_bytes(ctx, ids)
+    if not args.minimal:
+        batch_path, block_mlp_form = measure_frame_forms(ctx, sc, cam, ids, mlp_d, out, args, flush, stream, reps)
+    forms = {}
 
     # the other storage forms on the same frame, one context at a time: plain
     # FP32 (the metric's comparison), BF16 grid + FP8 planes, FP8 with BF16
     # log-density, brick-sparse BF16 grids
-    forms = {}
     if not args.no_fp32 and storage == "bf16" and not args.bricks:
         rgb32 = None
         for key, st, br in (("plain_fp32", "fp32", False), ("bf16_grid_fp8_planes", "bf16_fp8", False),
@@ -722,6 +738,8 @@ def run_batch_budget(args, ctx, cams, ids, mlp_d, out_all, tile, ctas, flush, st
             "runs_per_batch": groups,
             "upload_bytes_per_batch": int((r1["upload_bytes"] - r0["upload_bytes"]) / n_renders),
             "evictions_per_batch": round((r1["evictions"] - r0["evictions"]) / n_renders, 1),
+            "evictions_waiting_previous_run_per_batch": round(
+                (r1["evictions_waiting_last_call"] - r0["evictions_waiting_last_call"]) / n_renders, 1),
             "pixels_equal_all_resident": bool(same)}
     return out
 

@@ -293,6 +293,8 @@ typedef struct {
     int64_t uploads;       /* blocks loaded */
     int64_t upload_bytes;  /* bytes copied host -> device by loads */
     int64_t evictions;     /* blocks unloaded */
+    int64_t evictions_waiting_last_call; /* unloads that had to wait for the kernels of the call just
+                                            before (a load behind them cannot overlap that call) */
 } cow_residency;
 cow_status cow_set_residency(cow_ctx *ctx, int64_t budget_bytes, void *stream);
 cow_status cow_get_residency(const cow_ctx *ctx, cow_residency *out);

@@ -52,7 +52,8 @@ SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
 class Residency(C.Structure):
     _fields_ = [("budget_bytes", C.c_int64), ("resident_bytes", C.c_int64), ("resident_blocks", C.c_int32),
-                ("uploads", C.c_int64), ("upload_bytes", C.c_int64), ("evictions", C.c_int64)]
+                ("uploads", C.c_int64), ("upload_bytes", C.c_int64), ("evictions", C.c_int64),
+                ("evictions_waiting_last_call", C.c_int64)]
 
 
 class CowError(RuntimeError):

@@ -132,7 +132,7 @@ cow_status build_stage(cow_batch *b, int32_t first, int32_t last) {
 // blocks (in view order for very large batches) while the union still fits.
 // Every run gets its records by value and its views' lists as byte indices
 // into them; the staging of all runs is one pinned buffer copied at once.
-cow_status build_runs(cow_batch *b) {
+cow_status build_runs(cow_batch *b, int32_t first, int32_t last) {
     cudaError_t e = cudaEventSynchronize(b->copied);  // the previous copy has read the stagings
     if (e != cudaSuccess) return fail(COW_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
     int tw, th;
@@ -150,9 +150,11 @@ cow_status build_runs(cow_batch *b) {
     }
     std::vector<std::vector<int32_t>> run_views;
     {
-        std::vector<char> done((size_t)nv, 0), in((size_t)nb, 0);
-        const bool pick_best = nv <= 1024;
-        int32_t left = nv, next = 0;
+        // views outside [first, last) count as done
+        std::vector<char> done((size_t)nv, 1), in((size_t)nb, 0);
+        for (int32_t v = first; v < last; v++) done[(size_t)v] = 0;
+        const bool pick_best = last - first <= 1024;
+        int32_t left = last - first, next = first;
         while (left > 0) {
             std::vector<int32_t> views, blocks;
             for (;;) {
@@ -282,16 +284,18 @@ cow_status build_runs(cow_batch *b) {
     b->n_pixels = pix_of[(size_t)nv];
     b->n_items = (int32_t)std::min<int64_t>(total_items, 0x7fffffff);
     b->rec_gen = b->ctx->rec_gen;
-    b->dirty = false;
+    b->dirty = first != 0 || last != nv;  // a budget run's staging: the whole batch must be rebuilt later
     b->param_mode = true;
     b->stage_gen++;
     return COW_OK;
 }
 
-// Every view's list fits a launch's parameter buffer.
-bool runs_fit(const cow_batch *b) {
-    for (size_t v = 0; v + 1 < b->offs.size(); v++)
-        if (b->offs[v + 1] - b->offs[v] > cow::kParamRecs) return false;
+// Every view's list (of views first .. last-1, or all) fits a launch's
+// parameter buffer.
+bool runs_fit(const cow_batch *b, int32_t first = 0, int32_t last = -1) {
+    if (last < 0) last = (int32_t)b->offs.size() - 1;
+    for (int32_t v = first; v < last; v++)
+        if (b->offs[(size_t)v + 1] - b->offs[(size_t)v] > cow::kParamRecs) return false;
     return true;
 }
 
@@ -373,7 +377,10 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
         cow_status rc = make_resident(c, run_ids.data(), (int64_t)run_ids.size(), st);
         if (rc != COW_OK) return rc;
         const int32_t lo = back ? nv - last : first, hi = back ? nv - first : last;
-        if ((rc = build_stage(b, lo, hi)) != COW_OK) return rc;
+        // the run's views in sub-runs with records in the parameter buffer
+        // when their lists fit, else one launch staging records in shared memory
+        const bool param = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b, lo, hi);
+        if ((rc = param ? build_runs(b, lo, hi) : build_stage(b, lo, hi)) != COW_OK) return rc;
         const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, rgb, aux, ns);
         COW_CUDA(enqueue(b, a, b->tile_cfg, std::max(1, b->sms * b->ctas_per_sm), st, true));
         if ((rc = note_use(c, run_ids.data(), (int64_t)run_ids.size(), st)) != COW_OK) return rc;
@@ -521,7 +528,7 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     const bool want_runs = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b);
     if (b->dirty || b->rec_gen != b->ctx->rec_gen || b->param_mode != want_runs) {
         // new views, tile shape, or block records
-        cow_status rc = want_runs ? build_runs(b) : build_stage(b, 0, (int32_t)b->cams.size());
+        cow_status rc = want_runs ? build_runs(b, 0, (int32_t)b->cams.size()) : build_stage(b, 0, (int32_t)b->cams.size());
         if (rc != COW_OK) return rc;
     }
     b->last_groups = 1;

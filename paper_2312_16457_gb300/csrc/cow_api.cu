@@ -109,6 +109,7 @@ void destroy(cow_ctx *c) {
         cudaFree(b.brick_list);
         if (b.host_feat) cudaFreeHost(b.host_feat);
     }
+    c->last_call_ev.reset();
     if (c->loaded) cudaEventDestroy(c->loaded);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     cudaFree(c->d_err);
@@ -577,7 +578,10 @@ cow_status evict_block(cow_ctx *c, int32_t i) {
     BlockHost &b = c->blocks[(size_t)i];
     if (!b.resident) return COW_OK;
     cudaStream_t cs = c->copy_stream;
-    if (b.use_ev) COW_CUDA(cudaStreamWaitEvent(cs, b.use_ev->e, 0));
+    if (b.use_ev) {
+        COW_CUDA(cudaStreamWaitEvent(cs, b.use_ev->e, 0));
+        if (b.use_ev == c->last_call_ev) c->n_evict_wait_last++;
+    }
     if (b.dirty) {  // features changed on the device since the host copy was taken
         for (int t = 0; t < 4; t++)
             COW_CUDA(cudaMemcpyAsync((unsigned char *)b.host_feat + feature_offset(c, b, t), *tensor_slot(b, t),
@@ -678,6 +682,7 @@ cow_status note_use_impl(cow_ctx *c, const int32_t *ids, int64_t n, cudaStream_t
     if (!ev->e) return fail(COW_ERR_CUDA, "cudaEventCreate failed");
     COW_CUDA(cudaEventRecord(ev->e, st));
     for (int64_t k = 0; k < n; k++) c->blocks[(size_t)ids[k]].use_ev = ev;
+    c->last_call_ev = ev;
     return COW_OK;
 }
 
@@ -1503,6 +1508,7 @@ cow_status cow_get_residency(const cow_ctx *ctx, cow_residency *out) {
     out->uploads = ctx->n_uploads;
     out->upload_bytes = ctx->upload_bytes;
     out->evictions = ctx->n_evictions;
+    out->evictions_waiting_last_call = ctx->n_evict_wait_last;
     return COW_OK;
 }
 

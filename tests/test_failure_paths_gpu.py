@@ -64,15 +64,16 @@ def test_view_record_wait_times_out(schedule):
 
 
 def test_batch_record_wait_times_out():
-    """The batched form stages records with a bulk copy when it serves its
-    views in runs under a residency budget (without one, runs take their
-    records in the parameter buffer and nothing waits)."""
+    """The batched form stages records with a bulk copy when its record mode
+    is "shared" (otherwise runs take their records in the parameter buffer
+    and nothing waits), here under a residency budget as well."""
     sc, cam, mlp = _small()
     ctx = cow.Context(sc, "bf16")
     cams = [cam, synth.camera((2.0, 2.5, 1.5), (-0.2, -0.1, -0.9), 32, 32, 60.0)]
     ids = [ctx.sort_blocks(c, list(range(4))) for c in cams]
     mlp_d = torch.from_numpy(mlp).cuda()
     batch = cow.Batch(ctx, 2, 8)
+    batch.set_records("shared")
     npix = batch.set_views(cams, ids)
     ref = torch.empty((npix, 3), device="cuda")
     batch.render(mlp_d, ref)
