@@ -186,7 +186,7 @@ struct cow_ctx {
     int64_t resident_bytes = 0;
     int64_t n_uploads = 0, upload_bytes = 0, n_evictions = 0;
     int64_t n_evict_wait_last = 0;              // unloads behind the kernels of the call just before
-    std::shared_ptr<SharedEvent> last_call_ev;  // the use event of the most recent call
+    std::shared_ptr<cowi::SharedEvent> last_call_ev;  // the use event of the most recent call
     std::vector<struct cow_batch *> batches;  // live cow_batch objects on this context (cow_free detaches them)
     uint64_t rec_gen = 0;   // advances whenever a block record is rewritten
     cudaMemPool_t pool = nullptr;  // loads under a budget allocate from it (created with the first budget)
