@@ -421,6 +421,22 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);
 
+/* Check aid for the differentiation form (the benchmark spec: FP64 on the GPU only
+ * in the finite-difference gradient check): the ray-batch render of
+ * cow_render_rays without early termination, taking the same lattice samples
+ * (decided by the FP32 sequence of the marcher) but computing every lookup
+ * (Sec. 4.1 f^{k,l}), activation, weight (Eq. 1-2), composite (Eq. 12) and
+ * the deferred MLP (Eq. 3) in FP64 from FP64 copies of the features:
+ * grids[i] (R^3 x 8) and planes[3 i + k] (P^2 x 8) of block i, host arrays
+ * of n_blocks / 3 n_blocks device pointers (only the blocks of ids are read;
+ * the occupancy is the context's).  mlp: 499 FP64; out_rgb n x 3, out_aux n x
+ * 8 (C_d, F, T; may be NULL), FP64 device memory.  A central difference of
+ * it checks cow_render_backward at 1e-3 entry by entry.  Synchronises
+ * stream.  Errors: INVALID_ARG, CUDA. */
+cow_status cow_render_rays_f64(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                               int32_t n_ids, const double *mlp, const double *const *grids,
+                               const double *const *planes, double *out_rgb, double *out_aux, void *stream);
+
 /* Block-parallel form of the ray-batch render (Sec. 4.2, Eq. 11-13; the
  * paper renders every block in its own shader and alpha-blends the images,
  * Sec. 4.2 and App. A).  Two calls:

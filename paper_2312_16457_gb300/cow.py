@@ -36,7 +36,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "UNSUPPORTED", 5: "
 
 # every symbol include/cow.h declares
 EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_save_scene", "cow_load_scene", "cow_free", "cow_num_blocks", "cow_block_ztop", "cow_select_lod", "cow_sort_blocks",
-           "cow_render", "cow_render_rays", "cow_render_partials", "cow_composite_over", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
+           "cow_render", "cow_render_rays", "cow_render_partials", "cow_composite_over", "cow_render_rays_f64", "cow_render_rays_block_t", "cow_set_schedule", "cow_set_tile_order", "cow_set_block_mlps",
            "cow_sync_check", "cow_set_test_hooks", "cow_export_occupancy", "cow_export_occupancy_coarse", "cow_set_residency",
            "cow_set_block_unbounded",
            "cow_get_residency", "cow_block_bytes", "cow_plan_view_order", "cow_refine_view_order", "cow_sparsity_loss", "cow_opacity_loss",
@@ -97,6 +97,7 @@ def lib():
             "cow_render": [P, P, i32, P, P, P, flt, u32, P, P, P, P],
             "cow_render_rays": [P, P, P, i64, P, i32, P, flt, u32, P, P, P, P],
             "cow_render_partials": [P, P, P, i64, P, i32, P, P],
+            "cow_render_rays_f64": [P, P, P, i64, P, i32, P, P, P, P, P, P],
             "cow_composite_over": [P, P, P, i64, P, i32, P, P, u32, P, P, P],
             "cow_sync_check": [P, P],
             "cow_set_test_hooks": [P, u32, u32],
@@ -321,6 +322,26 @@ class Context:
         _check(lib().cow_render_rays(self._ctx, _ptr(o), _ptr(d), n, _ptr(a), len(a), _ptr(m), float(ert_eps),
                                      flags, _ptr(rgb), _ptr(ax), _ptr(ns), _stream_ptr(stream)))
         return rgb, ax, ns
+
+    def render_rays_f64(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], mlp64: torch.Tensor, grids64,
+                        planes64, stream=None):
+        """FP64 render for finite-difference checks (cow_render_rays_f64):
+        grids64[i] / planes64[i][k] FP64 device tensors of every block (None
+        for blocks outside ids); returns (rgb, aux) FP64."""
+        a = np.ascontiguousarray(ids, np.int32)
+        nb = self.n_blocks
+        gg = (C.c_void_p * nb)(*[_ptr(g) if g is not None else None for g in grids64])
+        flat = []
+        for i in range(nb):
+            pl = planes64[i] if planes64[i] is not None else [None, None, None]
+            flat += [_ptr(t) if t is not None else None for t in pl]
+        gp = (C.c_void_p * (3 * nb))(*flat)
+        n = o.shape[0]
+        rgb = torch.empty((n, 3), dtype=torch.float64, device=o.device)
+        ax = torch.empty((n, 8), dtype=torch.float64, device=o.device)
+        _check(lib().cow_render_rays_f64(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), n, _ptr(a), len(a),
+                                         _ptr(mlp64.contiguous()), gg, gp, _ptr(rgb), _ptr(ax), _stream_ptr(stream)))
+        return rgb, ax
 
     def render_partials(self, o: torch.Tensor, d: torch.Tensor, ids: Sequence[int], stream=None) -> torch.Tensor:
         """Per-block partials (C_d^k, F^k, T^k) of a ray batch: [n, len(ids), 8]."""

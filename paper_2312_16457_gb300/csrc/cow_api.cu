@@ -123,6 +123,7 @@ void destroy(cow_ctx *c) {
     c->out_aux.release();
     c->out_nsamp.release();
     c->gptrs.release();
+    c->f64ptrs.release();
     c->partials.release();
     c->staging.release();
     c->block_mlps.release();
@@ -1107,6 +1108,55 @@ cow_status cow_composite_over(cow_ctx *ctx, const float *o, const float *d, int6
     make_ray_recs(ctx, ids, n_ids, rr);  // only the blocks' centres are read (the per-ray order)
     COW_CUDA(cow::launch_composite_over(a, rr, st));
     return COW_OK;
+}
+
+cow_status cow_render_rays_f64(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
+                               int32_t n_ids, const double *mlp, const double *const *grids,
+                               const double *const *planes, double *out_rgb, double *out_aux, void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;
+    if (!ctx || !o || !d || n_rays < 0 || !ids || !mlp || !grids || !planes || !out_rgb)
+        return fail(COW_ERR_INVALID_ARG, "cow_render_rays_f64: null argument");
+    if (n_ids < 1 || n_ids > cow::kMaxRayIds) return fail(COW_ERR_INVALID_ARG, "n_ids must be in [1, %d]", cow::kMaxRayIds);
+    const int32_t nb = (int32_t)ctx->blocks.size();
+    for (int32_t k = 0; k < n_ids; k++) {
+        if (ids[k] < 0 || ids[k] >= nb) return fail(COW_ERR_INVALID_ARG, "block id %d out of range", ids[k]);
+        const int32_t id = ids[k];
+        for (int q = 0; q < 4; q++) {
+            const void *p = q == 0 ? (const void *)grids[id] : (const void *)planes[3 * id + q - 1];
+            if (!p || !is_device_ptr(p)) return fail(COW_ERR_INVALID_ARG, "block %d: FP64 features must be device memory", id);
+        }
+    }
+    for (const void *q : {(const void *)o, (const void *)d, (const void *)mlp, (const void *)out_rgb})
+        if (!is_device_ptr(q)) return fail(COW_ERR_INVALID_ARG, "rays, MLP and outputs must be device memory");
+    if (out_aux && !is_device_ptr(out_aux)) return fail(COW_ERR_INVALID_ARG, "aux must be device memory");
+    DeviceGuard dg(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cow_status rc;
+    if ((rc = ensure_resident(ctx, ids, n_ids, st)) != COW_OK) return rc;  // the records' occupancy and tables
+    std::vector<const double *> tab((size_t)nb * 4, nullptr);
+    for (int32_t i = 0; i < nb; i++) {
+        tab[(size_t)i] = grids[i];
+        for (int q = 0; q < 3; q++) tab[(size_t)nb + 3 * (size_t)i + q] = planes[3 * i + q];
+    }
+    COW_CUDA(ctx->f64ptrs.reserve(tab.size() * sizeof(double *)));
+    COW_CUDA(cudaMemcpyAsync(ctx->f64ptrs.p, tab.data(), tab.size() * sizeof(double *), cudaMemcpyHostToDevice, st));
+    cow::F64Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.ray_o = o;
+    a.ray_d = d;
+    a.n_rays = n_rays;
+    a.grids = (const double *const *)ctx->f64ptrs.p;
+    a.planes = (const double *const *)ctx->f64ptrs.p + nb;
+    a.mlp = mlp;
+    a.out_rgb = out_rgb;
+    a.out_aux = out_aux;
+    a.err = ctx->d_err;
+    cow::RayRecs rr;
+    make_ray_recs(ctx, ids, n_ids, rr);
+    COW_CUDA(cow::launch_march_rays_f64(a, rr, st));
+    COW_CUDA(cudaStreamSynchronize(st));  // the host pointer table is reused by the next call
+    return note_use_impl(ctx, ids, n_ids, st);
 }
 
 cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,

@@ -174,6 +174,7 @@ struct cow_ctx {
     float *d_mlp = nullptr;
     cowi::DevBuf views, out_rgb, out_aux, out_nsamp;
     cowi::DevBuf gptrs, partials;  // backward: per-block gradient pointers, per-CTA MLP-gradient rows
+    cowi::DevBuf f64ptrs;          // cow_render_rays_f64: per-block FP64 feature pointers
     cowi::DevBuf staging;          // host masters of cow_update_features
     cowi::DevBuf block_mlps;       // cow_set_block_mlps: n_blocks x block_mlp_nparam FP32
     cowi::DevBuf bm_scratch;       // backward of the per-block MLP form: 2 x n_rays x n_ids x 8 FP32

@@ -122,6 +122,21 @@ cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n,
                         float eps, int step, cudaStream_t st);
 cudaError_t launch_mse_grad(const float *rgb, const float *tgt, int64_t n, float *grad, float *loss, cudaStream_t st);
 
+// FP64 render of ray batches for finite-difference checks (check_f64.cu):
+// the FP32 marcher's samples, every value after them in FP64 from FP64
+// copies of the features (device tables of per-block pointers by block id).
+struct F64Args {
+    const float *ray_o, *ray_d;   // n_rays x 3 (device)
+    int64_t n_rays;
+    const double *const *grids;   // [block id] -> R^3 x 8 FP64
+    const double *const *planes;  // [3 id + k] -> P^2 x 8 FP64
+    const double *mlp;            // 499 FP64
+    double *out_rgb;              // n_rays x 3
+    double *out_aux;              // n_rays x 8 (may be null): C_d, F, T
+    unsigned *err;
+};
+cudaError_t launch_march_rays_f64(const F64Args &a, const RayRecs &rr, cudaStream_t st);
+
 // K8: persistent batched renderer (batch.cu)
 struct BatchArgs {
     const int32_t *hdr;      // device: n_views, n_items (tiles of all views)

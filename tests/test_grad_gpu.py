@@ -183,3 +183,60 @@ def test_fit_checkpoint_resumes_exactly(tmp_path):
     for p, q in zip(a.params, b.params):
         assert float((p - q).abs().max()) <= 1e-5 * max(1.0, float(p.abs().max()))
     assert b.t == a.t
+
+
+def test_backward_matches_fp64_gpu_central_differences():
+    """Central differences of the FP64 GPU render (cow_render_rays_f64: the
+    same samples, every value after them in FP64) against the FP32 backward,
+    entry by entry at the differentiation form's 1e-3: the largest entries
+    and random ones of every grid, plane and the deferred MLP (~80 entries)."""
+    sc = synth.city_scene(21, 2, 2.0, [(12, 32)])
+    o, d = synth.random_rays(4096, 13, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    mlp = torch.from_numpy(synth.mlp_weights(5)).cuda()
+    w = torch.randn(4096, 3, device="cuda", generator=torch.Generator(device="cuda").manual_seed(2))
+    ctx = cow.Context(sc, "fp32")
+    ids = list(range(4))
+    _, _, gg, gp, gm = _gpu_grads(ctx, sc, o, d, ids, mlp, w)
+    g64 = [b.grid.double().cuda().contiguous() for b in sc.blocks]
+    p64 = [[p.double().cuda().contiguous() for p in b.planes] for b in sc.blocks]
+    m64 = mlp.double().clone()
+    w64 = w.double()
+
+    def loss():
+        rgb, _ = ctx.render_rays_f64(o, d, ids, m64, g64, p64)
+        return float((rgb * w64).sum())
+
+    # the FP64 render and the FP32 render agree (same samples)
+    rgb32 = ctx.render_rays(o, d, ids, mlp, aux=False)[0]
+    rgb64, _ = ctx.render_rays_f64(o, d, ids, m64, g64, p64)
+    assert float((rgb64 - rgb32.double()).abs().max()) <= 1e-5
+    rng = np.random.default_rng(9)
+    targets = []
+    for b in range(4):
+        targets.append((g64[b], gg[b]))
+        targets += [(p64[b][k], gp[b][k]) for k in range(3)]
+    targets.append((m64, gm))
+    checked = 0
+    for x64, g in targets:
+        flat_g = g.reshape(-1)
+        scale = float(flat_g.abs().max())
+        big = torch.nonzero(flat_g.abs() >= 0.05 * scale).reshape(-1).cpu().numpy()
+        picks = list(flat_g.abs().argsort(descending=True)[:2].tolist())
+        if len(big):
+            picks += list(rng.choice(big, size=min(3, len(big)), replace=False))
+        xf = x64.view(-1)
+        for j in dict.fromkeys(int(v) for v in picks):
+            x0 = float(xf[j])
+            h = 1e-4 * max(1.0, abs(x0))
+            xf[j] = x0 + h
+            lp = loss()
+            xf[j] = x0 - h
+            lm = loss()
+            xf[j] = x0
+            fd = (lp - lm) / (2 * h)
+            gv = float(flat_g[j])
+            bound = 1e-3 * abs(fd) if abs(fd) >= 1e-2 * scale else 1e-3 * scale
+            assert abs(fd - gv) <= bound, (j, fd, gv, scale)
+            checked += 1
+    assert checked >= 60
