@@ -22,7 +22,7 @@ def L():
 def _declared():
     hdr = open(os.path.join(ROOT, "include", "cow.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"\b(cow_[a-z_]+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"\b(cow_[a-z0-9_]+)\s*\(", hdr)))
 
 
 def test_exports_every_declared_symbol(L):
