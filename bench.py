@@ -38,7 +38,7 @@ METRIC = "1080p frames/s & Mrays/s: BF16/batched vs plain FP32 at >=45 dB PSNR"
 # with ncu (dram__bytes_read.sum + dram__bytes_write.sum) and keyed to the
 # SHA-256 of the sources that build the marcher: after any change to them the
 # stored number no longer describes the kernel and the line reports null.
-MARCH_SOURCES = ["march.cu", "march_core.cuh", "cow_common.cuh", "cow_kernels.h"]
+MARCH_SOURCES = ["march.cu", "march_kernels.cuh", "march_core.cuh", "cow_common.cuh", "cow_kernels.h", "kernel_launch.h"]
 MEASURED_TRAFFIC = {}  # (workload, storage, schedule, res_div) -> (bytes per launch, sources sha256)
 # The L1 data-pipe utilisation of the same kernel (ncu
 # l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed at half
