@@ -392,8 +392,8 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
         // the view's distinct blocks, and the bytes it adds to the current run
         std::vector<int32_t> own;
         int64_t own_bytes = 0, add = 0;
-        for (int32_t k = b->offs[(size_t)v]; k < b->offs[(size_t)v + 1]; k++) {
-            const int32_t id = b->ids[(size_t)k];
+        for (int32_t q = b->offs[(size_t)v]; q < b->offs[(size_t)v + 1]; q++) {
+            const int32_t id = b->ids[(size_t)q];
             if (std::find(own.begin(), own.end(), id) != own.end()) continue;
             own.push_back(id);
             const int64_t by = block_feature_bytes(c, id);
