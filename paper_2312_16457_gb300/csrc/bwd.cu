@@ -227,10 +227,11 @@ __global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_remarch_bac
         const BlockRec &b = rr.r[order[k]];
         float *gg = a.grad_grid[id];
         float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
+        BrickCache bc;
         const bool more = for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3],
                                                                            float delta) {
             float2 f2[4];
-            accumulate_sample<DT>(b, p, g, f2);
+            accumulate_sample<DT>(b, p, g, f2, &bc);
             const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
             const float sigma = __expf(f[0]);
             const float e = __expf(-sigma * delta);
@@ -396,9 +397,10 @@ __global__ void __launch_bounds__(kBwdThreads, COW_REG_MIN_BLOCKS) k_opacity(Reg
                 if (T < 0.f) continue;  // no occupied sample
             } else {
                 int nk = 0;
+                BrickCache bc;
                 for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
                     float2 f2[4];
-                    accumulate_sample<DT>(b, p, g, f2);
+                    accumulate_sample<DT>(b, p, g, f2, &bc);
                     T *= expf(-expf(f2[0].x) * delta);
                     nk++;
                     return true;
@@ -412,9 +414,10 @@ __global__ void __launch_bounds__(kBwdThreads, COW_REG_MIN_BLOCKS) k_opacity(Reg
             const float ga = -scale * (logf(al) - log1pf(-al));  // d loss / d alpha^k
             float *gg = a.grad_grid[id];
             float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
+            BrickCache bc;
             for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
                 float2 f2[4];
-                accumulate_sample<DT>(b, p, g, f2);
+                accumulate_sample<DT>(b, p, g, f2, &bc);
                 scatter_ch0(b, gg, gp, p, g, ga * expf(f2[0].x) * delta * T);
                 return true;
             });
@@ -685,9 +688,10 @@ __global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_bm_remarch(
         float *gg = a.grad_grid[id];
         float *const gp[3] = {a.grad_planes[3 * id], a.grad_planes[3 * id + 1], a.grad_planes[3 * id + 2]};
         float T = 1.f, PC[3] = {0.f, 0.f, 0.f}, PF[4] = {0.f, 0.f, 0.f, 0.f};
+        BrickCache bc;
         for_each_sample(b, o, d, inv_d, omax, a.err, [&](const float p[3], const float g[3], float delta) {
             float2 f2[4];
-            accumulate_sample<DT>(b, p, g, f2);
+            accumulate_sample<DT>(b, p, g, f2, &bc);
             const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
             const float sigma = __expf(f[0]);
             const float e = __expf(-sigma * delta);

@@ -33,7 +33,8 @@ constexpr int kPlaneLd = COW_PLANE_LD_POLICY;
 // the voxel's place inside it); the other corners are at the layout's fixed
 // strides from it.  A voxel whose brick is not stored (only a lookup at an
 // arbitrary point can meet one: lattice samples lie in occupied cells, whose
-// bricks are stored) reads no grid element and takes the grid term as zero.
+// bricks are stored) reads no grid element and takes the grid term as zero;
+// callers that pass a BrickCache march lattice samples and skip that test.
 // The brick slot of the last lookup of one ray in one block (brick-sparse
 // grids): successive samples mostly stay in one 16^3-voxel brick, so the
 // table read leaves the gathers' address path.
@@ -77,7 +78,10 @@ __device__ __forceinline__ void accumulate_sample(const BlockRec &b, const float
         const int loc = (c0[2] & (kBrick - 1)) * sz + (c0[1] & (kBrick - 1)) * sy + (c0[0] & (kBrick - 1));
         base = (int64_t)slot * b.belem + loc;
         dbase = (int64_t)slot * kDensBrickElems + loc;
-        stored = slot >= 0;
+        // a lattice sample (the callers that pass a cache) lies in an
+        // occupied cell, whose brick is stored; only a lookup at an
+        // arbitrary point can meet an empty brick
+        stored = bc != nullptr || slot >= 0;
     } else {
         base = ((int64_t)c0[2] * R + c0[1]) * R + c0[0];
         dbase = base;

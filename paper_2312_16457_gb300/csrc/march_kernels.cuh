@@ -266,7 +266,8 @@ __device__ __forceinline__ void march_block_warp(const BlockRec &b, const float 
         float e = 1.f, c[7];
         if (occ) {
             float2 f2[4];
-            accumulate_sample<DT>(b, p, g, f2);
+            BrickCache bc;  // one lattice sample of this lane: the brick is stored
+            accumulate_sample<DT>(b, p, g, f2, &bc);
             const float f[8] = {f2[0].x, f2[0].y, f2[1].x, f2[1].y, f2[2].x, f2[2].y, f2[3].x, f2[3].y};
             e = __expf(-__expf(f[0]) * delta);
 #pragma unroll
