@@ -217,7 +217,8 @@ def test_backward_matches_fp64_gpu_central_differences():
         targets.append((g64[b], gg[b]))
         targets += [(p64[b][k], gp[b][k]) for k in range(3)]
     targets.append((m64, gm))
-    checked = 0
+    checked = skipped = 0
+    l0 = loss()
     for x64, g in targets:
         flat_g = g.reshape(-1)
         scale = float(flat_g.abs().max())
@@ -226,17 +227,28 @@ def test_backward_matches_fp64_gpu_central_differences():
         if len(big):
             picks += list(rng.choice(big, size=min(3, len(big)), replace=False))
         xf = x64.view(-1)
-        for j in dict.fromkeys(int(v) for v in picks):
+
+        def central(j, h):
             x0 = float(xf[j])
-            h = 1e-4 * max(1.0, abs(x0))
             xf[j] = x0 + h
             lp = loss()
             xf[j] = x0 - h
             lm = loss()
             xf[j] = x0
-            fd = (lp - lm) / (2 * h)
+            return (lp - lm) / (2 * h)
+
+        for j in dict.fromkeys(int(v) for v in picks):
+            # small steps (the FP64 loss rounds at ~1e-14 of its size), taken
+            # twice: where the two disagree a ReLU of the deferred MLP changes
+            # sign inside the step for some ray, so the difference quotient is
+            # not the derivative there and the entry is skipped
+            h = 1e-6 * max(1.0, abs(float(xf[j])))
+            fd, fd2 = central(j, h), central(j, 2 * h)
+            if abs(fd - fd2) > 1e-5 * max(abs(fd), 1e-2 * scale) + 1e-13 * abs(l0) / h:
+                skipped += 1
+                continue
             gv = float(flat_g[j])
             bound = 1e-3 * abs(fd) if abs(fd) >= 1e-2 * scale else 1e-3 * scale
             assert abs(fd - gv) <= bound, (j, fd, gv, scale)
             checked += 1
-    assert checked >= 60
+    assert checked >= 60 and skipped <= 4, (checked, skipped)
