@@ -4,6 +4,7 @@
 // assets without the FP32 masters or a re-pack.  The file is a fixed binary
 // header and block table, a JSON manifest of the same facts for other tools,
 // then the raw arrays.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -36,6 +37,8 @@ struct FileBlock {
     uint64_t off[kSections], bytes[kSections];
 };
 
+static_assert(sizeof(FileHeader) == 40 && sizeof(FileBlock) == 320, "the packed scene file layout is fixed");
+
 struct FileCloser {
     FILE *f;
     ~FileCloser() {
@@ -65,6 +68,37 @@ const void *section_src(const cow_ctx *c, const BlockHost &b, int k, int64_t *by
     }
     *bytes = b.Nb > 0 ? (int64_t)b.n_bricks * 4 : 0;
     return b.brick_list;
+}
+
+// The coarse level is the OR of the fine cells of each group; with bricks, the
+// table and the list are inverse of each other, and every coarse cell with a
+// set bit has a stored brick.  sec: the block's occ, occ2, brick table and
+// brick list as read from the file.
+bool occupancy_consistent(const BlockHost &b, int Nc, int Nc2, const std::vector<unsigned char> sec[4]) {
+    const uint32_t *occ = (const uint32_t *)sec[0].data();
+    const uint32_t *occ2 = (const uint32_t *)sec[1].data();
+    std::vector<uint32_t> coarse(((size_t)Nc2 * Nc2 * Nc2 + 31) / 32, 0u);
+    for (int z = 0; z < Nc; z++)
+        for (int y = 0; y < Nc; y++)
+            for (int x = 0; x < Nc; x++) {
+                const int64_t ci = ((int64_t)z * Nc + y) * Nc + x;
+                if (!((occ[ci >> 5] >> (ci & 31)) & 1u)) continue;
+                const int64_t c2 = ((int64_t)(z >> cow::kOccGroupLog2) * Nc2 + (y >> cow::kOccGroupLog2)) * Nc2 +
+                                   (x >> cow::kOccGroupLog2);
+                coarse[(size_t)(c2 >> 5)] |= 1u << (c2 & 31);
+            }
+    if (sec[1].size() != coarse.size() * 4 || std::memcmp(occ2, coarse.data(), sec[1].size()) != 0) return false;
+    if (b.Nb == 0) return true;
+    const int64_t n3 = (int64_t)b.Nb * b.Nb * b.Nb;
+    const int32_t *tab = (const int32_t *)sec[2].data();
+    const int32_t *list = (const int32_t *)sec[3].data();
+    for (int32_t s = 0; s < b.n_bricks; s++)
+        if (list[s] < 0 || list[s] >= n3 || tab[list[s]] != s) return false;
+    for (int64_t k = 0; k < n3; k++) {
+        const bool set = (coarse[(size_t)(k >> 5)] >> (k & 31)) & 1u;
+        if (tab[k] < -1 || tab[k] >= b.n_bricks || (set && tab[k] < 0)) return false;
+    }
+    return true;
 }
 
 }  // namespace
@@ -197,11 +231,15 @@ cow_status cow_load_scene(cow_ctx **out, const char *path, void *stream) {
     if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(unsigned));
     if (e != cudaSuccess) return bail(fail(COW_ERR_OOM, "cow_load_scene: %s", cudaGetErrorString(e)));
     std::vector<unsigned char> host;
+    std::vector<unsigned char> sec[4];  // host copies of sections 4-7: occ, occ2, brick table, brick list
     for (size_t i = 0; i < table.size(); i++) {
+        for (auto &v : sec) v.clear();
         const FileBlock &fb = table[i];
         BlockHost &b = c->blocks[i];
+        bool box_ok = fb.lod >= 1;
+        for (int a = 0; a < 3; a++) box_ok = box_ok && std::isfinite(fb.lo[a]) && std::isfinite(fb.hi[a]) && fb.lo[a] < fb.hi[a];
         if (fb.R < 2 || fb.P < 2 || fb.R > 1024 || fb.P > 16384 || fb.parent < -1 || fb.parent >= h.n_blocks ||
-            fb.Nb < 0 || fb.n_bricks < 0 || (fb.Nb > 0) != c->bricks)
+            fb.parent == (int32_t)i || fb.Nb < 0 || fb.n_bricks < 0 || (fb.Nb > 0) != c->bricks || !box_ok)
             return bail(fail(COW_ERR_INVALID_ARG, "cow_load_scene: bad block %zu in %s", i, path));
         for (int a = 0; a < 3; a++) {
             b.lo[a] = fb.lo[a];
@@ -218,6 +256,8 @@ cow_status cow_load_scene(cow_ctx **out, const char *path, void *stream) {
         std::memcpy(b.scale_exp, fb.scale_exp, sizeof(fb.scale_exp));
         const int Nc = (b.R - 1 + c->occ_cell - 1) / c->occ_cell;
         const int Nc2 = (Nc + cow::kOccGroup - 1) / cow::kOccGroup;
+        if (c->bricks && (c->occ_cell != 4 || b.Nb != Nc2 || (int64_t)b.n_bricks > (int64_t)Nc2 * Nc2 * Nc2))
+            return bail(fail(COW_ERR_INVALID_ARG, "cow_load_scene: bad brick counts for block %zu in %s", i, path));
         b.occ_words = ((int64_t)Nc * Nc * Nc + 31) / 32;
         b.occ2_words = ((int64_t)Nc2 * Nc2 * Nc2 + 31) / 32;
         const int64_t want[kSections] = {block_tensor_bytes(c, b, 0), block_tensor_bytes(c, b, 1),
@@ -241,7 +281,15 @@ cow_status cow_load_scene(cow_ctx **out, const char *path, void *stream) {
                 return bail(fail(COW_ERR_INVALID_ARG, "cow_load_scene: truncated data in %s", path));
             e = cudaMemcpy(*dst[k], host.data(), (size_t)want[k], cudaMemcpyHostToDevice);
             if (e != cudaSuccess) return bail(fail(COW_ERR_CUDA, "cow_load_scene: %s", cudaGetErrorString(e)));
+            if (k >= 4) sec[k - 4].assign(host.begin(), host.end());
         }
+        // the occupancy levels and the brick table must describe one another:
+        // the kernels skip a coarse cell whose bit is clear without reading its
+        // fine cells, and read the brick of every occupied cell without testing
+        // its slot, so a file that breaks this is refused rather than rendered
+        if (!occupancy_consistent(b, Nc, Nc2, sec))
+            return bail(fail(COW_ERR_INVALID_ARG, "cow_load_scene: block %zu in %s has inconsistent occupancy or bricks",
+                             i, path));
         e = cudaMalloc((void **)&b.scale, 32 * sizeof(float));
         if (e != cudaSuccess) return bail(fail(COW_ERR_OOM, "cow_load_scene: %s", cudaGetErrorString(e)));
         float scale_h[32];

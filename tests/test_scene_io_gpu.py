@@ -87,3 +87,57 @@ def test_load_rejects_foreign_files(tmp_path):
     with pytest.raises(cow.CowError, match="truncated"):
         cow.Context.load(str(tmp_path / "cut.cow"))
     ctx.close()
+
+
+def _sections(data):
+    """(data start, per block (offsets, bytes) of its 8 sections) of a packed
+    scene file: header 40 bytes, 320-byte block records, the JSON manifest,
+    then the arrays from the next 256-byte boundary."""
+    import struct
+
+    n_blocks = struct.unpack_from("<i", data, 12)[0]
+    json_bytes = struct.unpack_from("<Q", data, 32)[0]
+    data0 = (40 + 320 * n_blocks + json_bytes + 255) & ~255
+    blocks = []
+    for i in range(n_blocks):
+        base = 40 + 320 * i
+        blocks.append((struct.unpack_from("<8Q", data, base + 192), struct.unpack_from("<8Q", data, base + 256)))
+    return data0, blocks
+
+
+def test_load_rejects_inconsistent_occupancy_and_bricks(tmp_path):
+    """A file whose coarse occupancy is not the OR of its fine cells, or whose
+    brick table leaves an occupied brick unstored, is refused: the kernels
+    trust both (they skip coarse cells without reading fine ones, and read an
+    occupied cell's brick without testing its slot)."""
+    import struct
+
+    sc = synth.city_scene(43, 2, 2.0, [(20, 24)], **synth.SPARSE_CITY)
+    ctx = cow.Context(sc, "bf16", bricks=True)
+    path = tmp_path / "s.cow"
+    ctx.save(str(path))
+    ctx.close()
+    data = bytearray(path.read_bytes())
+    data0, blocks = _sections(bytes(data))
+    ok = cow.Context.load(str(path))  # the file as saved loads
+    ok.close()
+    # a block with a stored brick: clear that brick's coarse bit
+    for off, nbytes in blocks:
+        tab = np.frombuffer(bytes(data[data0 + off[6]: data0 + off[6] + nbytes[6]]), dtype=np.int32)
+        stored = np.nonzero(tab >= 0)[0]
+        if len(stored):
+            k = int(stored[0])
+            bad = bytearray(data)
+            w = data0 + off[5] + 4 * (k >> 5)
+            struct.pack_into("<I", bad, w, struct.unpack_from("<I", bad, w)[0] & ~(1 << (k & 31)))
+            (tmp_path / "occ2.cow").write_bytes(bytes(bad))
+            with pytest.raises(cow.CowError, match="inconsistent"):
+                cow.Context.load(str(tmp_path / "occ2.cow"))
+            bad = bytearray(data)
+            struct.pack_into("<i", bad, data0 + off[6] + 4 * k, -1)
+            (tmp_path / "tab.cow").write_bytes(bytes(bad))
+            with pytest.raises(cow.CowError, match="inconsistent"):
+                cow.Context.load(str(tmp_path / "tab.cow"))
+            break
+    else:
+        pytest.fail("no stored brick in the scene")
