@@ -280,10 +280,16 @@ def measure_frame_forms(ctx, sc, cam, ids, mlp_d, out, args, flush, stream, reps
     batch = cow.Batch(ctx, 1, len(ids))
     batch.set_views([cam], [ids])
     tile, ctas, _ = batch.tune(mlp_d, out[0], ert_eps=args.ert)
-    rec = batch.config()[2]
+    rec, sched = batch.config()[2], batch.schedule()
     tb = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), reps, 3, flush, stream)
-    batch_path = {"frames_per_s": round(1000.0 / float(np.mean(tb)), 3), "tile": cow.Batch.TILE_SHAPES[tile],
-                  "ctas_per_sm": ctas, "records": rec}
+    batch_path = {"frames_per_s": round(1000.0 / float(np.mean(tb)), 3), "schedule": sched,
+                  "tile": cow.Batch.TILE_SHAPES[tile], "ctas_per_sm": ctas, "records": rec}
+    # both schedules, whichever the tuner kept: the persistent work queue and
+    # the view marcher's grid
+    for other in ("queue", "grid"):
+        batch.set_schedule(other)
+        to = time_steps(lambda: batch.render(mlp_d, out[0], ert_eps=args.ert, graph=True), reps, 3, flush, stream)
+        batch_path[other + "_frames_per_s"] = round(1000.0 / float(np.mean(to)), 3)
     batch.close()
     ctx.set_block_mlps(synth.block_mlp_weights(104, len(sc.blocks), 4), 4)
     tbm = time_steps(lambda: ctx.render([cam], [ids], None, ert_eps=args.ert, aux=False, out=out, block_mlps=True),
@@ -550,7 +556,8 @@ def measure_batch64(args, dev, flush, stream, budget_frac=0.0):
     res_d = {"views": len(cams), "pixels_per_batch": int(npix),
              "scene": "16x16 blocks x 3 LOD (%s), %s" % (", ".join(f"{r}^3/{q}^2" for r, q in res), ctx.storage),
              "blocks_per_view_mean": round(float(np.mean([len(i) for i in ids])), 1),
-             "tuned": {"tile": cow.Batch.TILE_SHAPES[tile], "ctas_per_sm": ctas, "ms": round(tune_ms, 3)},
+             "tuned": {"tile": cow.Batch.TILE_SHAPES[tile], "ctas_per_sm": ctas, "records": batch.config()[2],
+                       "schedule": batch.schedule(), "ms": round(tune_ms, 3)},
              "batched": {"ms_per_batch": round(ms, 3), "frames_per_s": round(npix / (ms / 1000.0) / px1080, 3),
                          "mrays_per_s": round(npix / ms / 1e3, 3),
                          "launch": "one persistent launch per batch, CUDA graph replay"},

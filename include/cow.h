@@ -374,9 +374,11 @@ cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, c
  * cow_batch_tune   : times every (tile_cfg, ctas_per_sm in {2,3,4,6,8}) on the
  *                    set views (reps renders each, into out_rgb) with the
  *                    records in the parameter buffer, then the best of them
- *                    with the records staged in shared memory, and keeps the
- *                    fastest; reports its tile and CTAs and its time per
- *                    batch in ms (cow_batch_get_config: the record mode).
+ *                    with the records staged in shared memory, then (without
+ *                    a residency budget) the grid schedule, and keeps the
+ *                    fastest; reports the queue's best tile and CTAs and the
+ *                    kept time per batch in ms (cow_batch_get_config: the
+ *                    record mode; cow_batch_get_schedule: the schedule).
  * Errors: INVALID_ARG, OOM, CUDA. */
 typedef struct cow_batch cow_batch;
 cow_status cow_batch_create(cow_ctx *ctx, int32_t max_views, int32_t max_ids, cow_batch **out);
@@ -399,6 +401,20 @@ cow_status cow_batch_set_run_fraction(cow_batch *b, float frac);
 #define COW_BATCH_RECORDS_PARAM 0
 #define COW_BATCH_RECORDS_SHARED 1
 cow_status cow_batch_set_records(cow_batch *b, int32_t mode);
+/* How cow_batch_render schedules the views' tiles without a residency
+ * budget: COW_BATCH_SCHED_QUEUE (default), the persistent launches over the
+ * (view, tile) work queue described above; COW_BATCH_SCHED_GRID, the view
+ * marcher of cow_render -- one CTA per 16x8 tile, scheduled by the
+ * hardware -- on groups of consecutive views whose block lists, concatenated,
+ * fit one launch's parameter buffer (96 records; a longer list forms its own
+ * group), one launch per group, use_graph ignored.  The queue pays per tile
+ * for its work counter and cull and gains on many small views; the grid
+ * pays per launch.  Pixels are the same either way.  cow_batch_tune times
+ * both.  Under a budget the queue is used.  Errors: INVALID_ARG. */
+#define COW_BATCH_SCHED_QUEUE 0
+#define COW_BATCH_SCHED_GRID 1
+cow_status cow_batch_set_schedule(cow_batch *b, int32_t sched);
+cow_status cow_batch_get_schedule(const cow_batch *b, int32_t *out_sched);
 cow_status cow_batch_get_config(const cow_batch *b, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm,
                                 int32_t *out_records);
 cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm);

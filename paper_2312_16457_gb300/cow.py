@@ -45,7 +45,7 @@ EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_save_scene", "cow_load_
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
            "cow_batch_last_groups", "cow_batch_set_run_fraction", "cow_batch_set_records", "cow_batch_get_config",
-           "cow_tune_schedule", "cow_last_error",
+           "cow_batch_set_schedule", "cow_batch_get_schedule", "cow_tune_schedule", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
@@ -133,6 +133,8 @@ def lib():
             "cow_batch_set_run_fraction": [P, flt],
             "cow_batch_set_records": [P, i32],
             "cow_batch_get_config": [P, P, P, P],
+            "cow_batch_set_schedule": [P, i32],
+            "cow_batch_get_schedule": [P, P],
             "cow_tune_schedule": [P, P, i32, P, P, P, flt, u32, P, i32, P, P, P, P],
             "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
         }
@@ -664,6 +666,18 @@ class Batch:
         t, c, r = C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().cow_batch_get_config(self._b, C.byref(t), C.byref(c), C.byref(r)))
         return self.TILE_SHAPES[t.value], c.value, {v: k for k, v in self.RECORDS.items()}[r.value]
+
+    SCHEDULES = {"queue": 0, "grid": 1}
+
+    def set_schedule(self, sched: str):
+        """"queue" (persistent launches over the (view, tile) work queue) or
+        "grid" (the view marcher, one launch per group of views)."""
+        _check(lib().cow_batch_set_schedule(self._b, self.SCHEDULES[sched]))
+
+    def schedule(self) -> str:
+        k = C.c_int32()
+        _check(lib().cow_batch_get_schedule(self._b, C.byref(k)))
+        return {v: n for n, v in self.SCHEDULES.items()}[k.value]
 
     def set_run_fraction(self, frac: float):
         """Under a residency budget: the fraction of it one run may fill."""

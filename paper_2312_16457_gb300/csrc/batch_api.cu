@@ -36,6 +36,7 @@ struct cow_batch {
     int tile_cfg = 0, ctas_per_sm = 4; // launch configuration (autotuned)
     float run_frac = 0.5f;             // under a budget: a run's blocks fill at most this fraction of it
     int records = COW_BATCH_RECORDS_PARAM;  // record placement (cow_batch_set_records)
+    int sched = COW_BATCH_SCHED_QUEUE;      // persistent queue, or the view marcher's grid (cow_batch_set_schedule)
     int sms = 0;
     // captured graph and the arguments it was captured with
     cudaGraphExec_t exec = nullptr;
@@ -427,6 +428,38 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
     return COW_OK;
 }
 
+// The grid schedule: the views in groups whose block lists, concatenated,
+// fit one launch's parameter buffer, each group one launch of the view
+// marcher (cow_render: one CTA per 16x8 tile, scheduled by the hardware);
+// a view with a longer list forms its own group.  Outputs keep each view's
+// place in the batch.
+cow_status render_grid(cow_batch *b, const float *mlp, float ert_eps, uint32_t flags, float *rgb, float *aux,
+                       int32_t *ns, cudaStream_t st) {
+    const int32_t nv = (int32_t)b->cams.size();
+    int64_t pix = 0;
+    int32_t groups = 0;
+    std::vector<int32_t> offs;
+    for (int32_t v0 = 0; v0 < nv;) {
+        int32_t v1 = v0 + 1;
+        while (v1 < nv && b->offs[(size_t)v1 + 1] - b->offs[(size_t)v0] <= cow::kParamRecs) v1++;
+        offs.assign((size_t)(v1 - v0) + 1, 0);
+        int64_t gpix = 0;
+        for (int32_t v = v0; v < v1; v++) {
+            offs[(size_t)(v - v0) + 1] = b->offs[(size_t)v + 1] - b->offs[(size_t)v0];
+            gpix += (int64_t)b->cams[(size_t)v].width * b->cams[(size_t)v].height;
+        }
+        cow_status rc = cow_render(b->ctx, b->cams.data() + v0, v1 - v0, b->ids.data() + b->offs[(size_t)v0], offs.data(),
+                                   mlp, ert_eps, flags, rgb + 3 * pix, aux ? aux + 8 * pix : nullptr,
+                                   ns ? ns + pix : nullptr, st);
+        if (rc != COW_OK) return rc;
+        pix += gpix;
+        groups++;
+        v0 = v1;
+    }
+    b->last_groups = groups;
+    return COW_OK;
+}
+
 }  // namespace
 
 namespace cowi {
@@ -525,6 +558,7 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     DeviceGuard dg(b->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (b->ctx->budget > 0) return render_groups(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
+    if (b->sched == COW_BATCH_SCHED_GRID) return render_grid(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
     const bool want_runs = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b);
     if (b->dirty || b->rec_gen != b->ctx->rec_gen || b->param_mode != want_runs) {
         // new views, tile shape, or block records
@@ -582,6 +616,20 @@ cow_status cow_batch_set_records(cow_batch *b, int32_t mode) {
     return COW_OK;
 }
 
+cow_status cow_batch_set_schedule(cow_batch *b, int32_t sched) {
+    g_last_error.clear();
+    if (!b || (sched != COW_BATCH_SCHED_QUEUE && sched != COW_BATCH_SCHED_GRID))
+        return fail(COW_ERR_INVALID_ARG, "cow_batch_set_schedule: bad argument");
+    b->sched = sched;
+    return COW_OK;
+}
+
+cow_status cow_batch_get_schedule(const cow_batch *b, int32_t *out_sched) {
+    if (!b || !out_sched) return fail(COW_ERR_INVALID_ARG, "cow_batch_get_schedule: null argument");
+    *out_sched = b->sched;
+    return COW_OK;
+}
+
 cow_status cow_batch_get_config(const cow_batch *b, int32_t *out_tile_cfg, int32_t *out_ctas_per_sm,
                                 int32_t *out_records) {
     if (!b) return fail(COW_ERR_INVALID_ARG, "cow_batch_get_config: null batch");
@@ -619,6 +667,8 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
     COW_CUDA(cudaEventCreate(&e0));
     COW_CUDA(cudaEventCreate(&e1));
     static const int kCtas[] = {2, 3, 4, 6, 8};
+    const int sched0 = b->sched;
+    b->sched = COW_BATCH_SCHED_QUEUE;  // the queue's configurations first
     float best = 3.0e38f;
     int best_t = b->tile_cfg, best_c = b->ctas_per_sm;
     cow_status rc = COW_OK;
@@ -672,6 +722,30 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
         }
         b->records = best_r;
     }
+    // the grid schedule (the view marcher, one launch per group of views);
+    // not under a budget, where runs are cut by residency
+    int best_s = COW_BATCH_SCHED_QUEUE;
+    if (rc == COW_OK && b->ctx->budget == 0) {
+        b->sched = COW_BATCH_SCHED_GRID;
+        rc = cow_batch_render(b, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, 0, stream);
+        if (rc == COW_OK) {
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && rc == COW_OK; r++)
+                rc = cow_batch_render(b, mlp, ert_eps, flags, out_rgb, nullptr, nullptr, 0, stream);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(COW_ERR_CUDA, "cow_batch_tune: synchronisation failed");
+        }
+        if (rc == COW_OK) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= (float)reps;
+            if (ms < best) {
+                best = ms;
+                best_s = COW_BATCH_SCHED_GRID;
+            }
+        }
+    }
+    b->sched = rc == COW_OK ? best_s : sched0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != COW_OK) return rc;

@@ -82,6 +82,8 @@ def test_calls_reject_null_context(L):
     assert L.cow_tune_schedule(None, None, 1, None, None, None, 0.0, 0, None, 1, None, None, None, None) == 1
     assert L.cow_batch_set_run_fraction(None, 0.5) == 1
     assert L.cow_batch_set_records(None, 0) == 1
+    assert L.cow_batch_set_schedule(None, 0) == 1
+    assert L.cow_batch_get_schedule(None, C.byref(n)) == 1
     assert L.cow_save_scene(None, b"x") == 1
     assert L.cow_free(None) == 0
 

@@ -166,3 +166,48 @@ def test_tuners_pick_valid_schedules():
     assert tile in cow.Batch.TILE_SHAPES.values() and ctas in (2, 3, 4, 6, 8) and rec in ("param", "shared")
     b.close()
     ctx.close()
+
+
+def test_grid_schedule_equals_per_view():
+    """The grid schedule (the view marcher on groups of views whose lists
+    fit one parameter buffer; a view over 96 blocks alone) writes the
+    per-view render's pixels at each view's place in the batch (sample counts
+    bit for bit, colours to FP32 rounding), and the tuner keeps one of the
+    two schedules."""
+    sc = synth.city_scene(33, 12, 1.0, [(10, 16)])
+    nb = len(sc.blocks)
+    ctx = cow.Context(sc, "bf16")
+    mlp_d = torch.from_numpy(synth.mlp_weights(5)).cuda()
+    cams = [synth.camera((x, y, 2.5), (x + 0.5, y + 0.8, -0.8), 48, 36, 70.0)
+            for x, y in ((-4.5, -4.5), (3.0, -4.0), (-4.0, 3.5), (3.5, 3.0))]
+    ids = []
+    for c in cams:
+        order = ctx.sort_blocks(c, list(range(nb)))
+        ids.append(ctx.sort_blocks(c, sorted(order[:30].tolist())))
+    cams.append(synth.camera((0.0, -7.0, 4.0), (0.0, 0.0, -0.5), 64, 40, 70.0))
+    ids.append(ctx.sort_blocks(cams[-1], list(range(nb))))  # 144 blocks: a group of its own
+    ref = ctx.render(cams, ids, mlp_d, nsamp=True)
+    ctx.sync_check()
+    b = cow.Batch(ctx, 8, 1024)
+    n = b.set_views(cams, ids)
+    b.set_schedule("grid")
+    assert b.schedule() == "grid"
+    out = (torch.full((n, 3), -1.0, device="cuda"), torch.zeros((n, 8), device="cuda"),
+           torch.zeros(n, dtype=torch.int32, device="cuda"))
+    for graph in (False, True):
+        b.render(mlp_d, *out, graph=graph)
+        ctx.sync_check()
+        assert torch.equal(out[2], ref[2]), graph
+        for k in range(2):  # the reference's 264 records go through the shared-memory kernel
+            assert float((out[k] - ref[k]).abs().max()) <= 2e-6, (graph, k)
+    assert b.last_groups() == 3  # views 0-2 (90 ids), view 3 (30 + 144 > 96), the long view
+    b.tune(mlp_d, torch.empty((n, 3), device="cuda"))
+    assert b.schedule() in ("queue", "grid")
+    out2 = torch.empty((n, 3), device="cuda")
+    ns2 = torch.zeros(n, dtype=torch.int32, device="cuda")
+    b.render(mlp_d, out2, None, ns2, graph=True)
+    ctx.sync_check()
+    assert torch.equal(ns2, ref[2])
+    assert float((out2 - ref[0]).abs().max()) <= 2e-6
+    b.close()
+    ctx.close()
