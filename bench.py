@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-view batched measurement")
     ap.add_argument("--no-sparse-city", action="store_true", help="skip the sparse-city brick measurement")
     ap.add_argument("--batch-storage", default="bf16", help="storage of the 64-view batched measurement")
+    ap.add_argument("--batch-config", default=None,
+                    help="TILE,CTAS: the 64-view batch's tile configuration (0-3) and CTAs per SM, queue schedule, "
+                         "instead of the tuner (profiling runs)")
     ap.add_argument("--minimal", action="store_true",
                     help="the headline frame only: no batched path, per-block MLP form, storage forms, 64-view batch "
                          "or sparse city (profiling runs)")
@@ -521,7 +524,13 @@ def measure_batch64(args, dev, flush, stream, budget_frac=0.0):
     batch = cow.Batch(ctx, len(cams), sum(len(i) for i in ids))
     npix = batch.set_views(cams, ids)
     out = torch.empty((npix, 3), device=dev)
-    tile, ctas, tune_ms = batch.tune(mlp_d, out, ert_eps=args.ert)
+    if args.batch_config:
+        tile, ctas = (int(x) for x in args.batch_config.split(","))
+        batch.set_config(tile, ctas)
+        batch.set_schedule("queue")
+        tune_ms = 0.0
+    else:
+        tile, ctas, tune_ms = batch.tune(mlp_d, out, ert_eps=args.ert)
     clocks = Clocks(torch.cuda.current_device())
     steps = max(5, args.steps // 2)
     times = time_steps(lambda: batch.render(mlp_d, out, ert_eps=args.ert, graph=True), steps, 3, flush, stream)
