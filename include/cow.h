@@ -370,7 +370,11 @@ cow_status cow_refine_view_order(const int64_t *block_bytes, int32_t n_blocks, c
  *                    cow_plan_view_order gives an order that loads few bytes.
  * cow_batch_last_groups : launches (runs) of the last cow_batch_render.
  * cow_batch_set_config : tile_cfg 0 = 16x8, 1 = 8x8, 2 = 16x16, 3 = 32x8
- *                    pixels per CTA; ctas_per_sm resident CTAs per SM (1..32).
+ *                    pixels per CTA; 4 = warp items, 8x4 pixels per warp,
+ *                    each warp taking its own items (no CTA barrier in the
+ *                    loop; records in the parameter buffer only, else
+ *                    cow_batch_render fails with UNSUPPORTED); ctas_per_sm
+ *                    resident CTAs per SM (1..32).
  * cow_batch_tune   : times every (tile_cfg, ctas_per_sm in {2,3,4,6,8}) on the
  *                    set views (reps renders each, into out_rgb) with the
  *                    records in the parameter buffer, then the best of them

@@ -609,7 +609,7 @@ def mse_grad(rgb: torch.Tensor, target: torch.Tensor, stream=None):
 class Batch:
     """Many cameras rendered by one persistent launch (cow_batch_*)."""
 
-    TILE_SHAPES = {0: (16, 8), 1: (8, 8), 2: (16, 16), 3: (32, 8)}
+    TILE_SHAPES = {0: (16, 8), 1: (8, 8), 2: (16, 16), 3: (32, 8), 4: (8, 4)}  # 4: warp items
 
     def __init__(self, ctx: Context, max_views: int, max_ids: int):
         self.ctx = ctx

@@ -18,9 +18,10 @@ COW_FOR_STORAGE(COW_EXTERN_BATCH, kBrickBit)
     extern template cudaError_t launch_batch_param_dt<(D)>(const BatchArgs &, int, int, cudaStream_t, const ParamRecs *);
 COW_FOR_STORAGE(COW_EXTERN_BATCH_PARAM, 0)
 
+// tile_cfg 4: 8x4 pixels per warp (warp items, records by value only).
 void batch_tile_shape(int tile_cfg, int *tw, int *th) {
-    static const int s[4][2] = {{16, 8}, {8, 8}, {16, 16}, {32, 8}};
-    const int k = tile_cfg < 0 || tile_cfg > 3 ? 0 : tile_cfg;
+    static const int s[5][2] = {{16, 8}, {8, 8}, {16, 16}, {32, 8}, {8, 4}};
+    const int k = tile_cfg < 0 || tile_cfg > 4 ? 0 : tile_cfg;
     *tw = s[k][0];
     *th = s[k][1];
 }

@@ -63,6 +63,8 @@ struct cow_batch {
 
 namespace {
 
+constexpr int kWarpItems = 4;  // tile_cfg of the warp-item kernel (8x4 pixels per warp)
+
 void batch_destroy(cow_batch *b) {
     if (!b) return;
     DeviceGuard dg(b->device);
@@ -381,6 +383,8 @@ cow_status render_groups(cow_batch *b, const float *mlp, float ert_eps, uint32_t
         // the run's views in sub-runs with records in the parameter buffer
         // when their lists fit, else one launch staging records in shared memory
         const bool param = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b, lo, hi);
+        if (b->tile_cfg == kWarpItems && !param)
+            return fail(COW_ERR_UNSUPPORTED, "warp items (tile_cfg 4) need records in the parameter buffer");
         if ((rc = param ? build_runs(b, lo, hi) : build_stage(b, lo, hi)) != COW_OK) return rc;
         const cow::BatchArgs a = make_args(b, mlp, ert_eps, flags, rgb, aux, ns);
         COW_CUDA(enqueue(b, a, b->tile_cfg, std::max(1, b->sms * b->ctas_per_sm), st, true));
@@ -560,6 +564,9 @@ cow_status cow_batch_render(cow_batch *b, const float *mlp, float ert_eps, uint3
     if (b->ctx->budget > 0) return render_groups(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
     if (b->sched == COW_BATCH_SCHED_GRID) return render_grid(b, mlp, ert_eps, flags, out_rgb, out_aux, out_nsamp, st);
     const bool want_runs = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b);
+    if (b->tile_cfg == kWarpItems && !want_runs)
+        return fail(COW_ERR_UNSUPPORTED, "warp items (tile_cfg 4) need records in the parameter buffer "
+                                         "(COW_BATCH_RECORDS_PARAM, every view at most 96 blocks)");
     if (b->dirty || b->rec_gen != b->ctx->rec_gen || b->param_mode != want_runs) {
         // new views, tile shape, or block records
         cow_status rc = want_runs ? build_runs(b, 0, (int32_t)b->cams.size()) : build_stage(b, 0, (int32_t)b->cams.size());
@@ -646,7 +653,7 @@ cow_status cow_batch_last_groups(const cow_batch *b, int32_t *out_groups) {
 }
 
 cow_status cow_batch_set_config(cow_batch *b, int32_t tile_cfg, int32_t ctas_per_sm) {
-    if (!b || tile_cfg < 0 || tile_cfg > 3 || ctas_per_sm < 1 || ctas_per_sm > 32)
+    if (!b || tile_cfg < 0 || tile_cfg > kWarpItems || ctas_per_sm < 1 || ctas_per_sm > 32)
         return fail(COW_ERR_INVALID_ARG, "cow_batch_set_config: bad argument");
     if (tile_cfg != b->tile_cfg) b->dirty = true;
     b->tile_cfg = tile_cfg;
@@ -672,7 +679,8 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
     float best = 3.0e38f;
     int best_t = b->tile_cfg, best_c = b->ctas_per_sm;
     cow_status rc = COW_OK;
-    for (int t = 0; t < 4 && rc == COW_OK; t++) {
+    const bool warp_items = b->records == COW_BATCH_RECORDS_PARAM && runs_fit(b);
+    for (int t = 0; t <= (warp_items ? kWarpItems : kWarpItems - 1) && rc == COW_OK; t++) {
         for (int c : kCtas) {
             rc = cow_batch_set_config(b, t, c);
             if (rc != COW_OK) break;
@@ -699,7 +707,7 @@ cow_status cow_batch_tune(cow_batch *b, const float *mlp, float ert_eps, uint32_
     // the record placement at the best tile and CTAs
     const int rec0 = b->records;
     int best_r = rec0;
-    if (rc == COW_OK) {
+    if (rc == COW_OK && best_t != kWarpItems) {
         const int other = rec0 == COW_BATCH_RECORDS_PARAM ? COW_BATCH_RECORDS_SHARED : COW_BATCH_RECORDS_PARAM;
         rc = cow_batch_set_config(b, best_t, best_c);
         if (rc == COW_OK) rc = cow_batch_set_records(b, other);

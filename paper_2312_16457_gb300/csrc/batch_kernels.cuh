@@ -77,20 +77,23 @@ __device__ __forceinline__ bool culled(const BlockRec &b, const float o[3], cons
 // Cull the view's n_blk records (near to far; rec_at(j) the j-th) against
 // the pyramid of tile (tx, ty): s_list[0 .. *s_n) receives key(j) of the kept
 // ones, in order.  Ends with a barrier.
-template <int TW, int TH, class RecAt, class Key>
-__device__ __forceinline__ void cull_tile(const ViewRec &v, int tx, int ty, int n_blk, RecAt rec_at, Key key,
-                                          unsigned char *s_keep, short *s_list, int *s_n) {
-    constexpr int kNT = TW * TH;
+// The side planes of the pyramid of tile (tx, ty) of TW x TH pixels (inward
+// normals n, use[k] false for a degenerate side) and the view direction.
+template <int TW, int TH>
+__device__ __forceinline__ void tile_pyramid(const ViewRec &v, int tx, int ty, float n[4][3], bool use[4],
+                                             float fwd[3]) {
     const int x0 = tx * TW, y0 = ty * TH;
     const int x1 = min(x0 + TW, v.W) - 1, y1 = min(y0 + TH, v.H) - 1;
-    float c[4][3], n[4][3], ctr[3], fwd[3] = {-v.Rm[2], -v.Rm[5], -v.Rm[8]};
+    float c[4][3], ctr[3];
+    fwd[0] = -v.Rm[2];
+    fwd[1] = -v.Rm[5];
+    fwd[2] = -v.Rm[8];
     corner_dir(v, x0, y0, c[0]);
     corner_dir(v, x1, y0, c[1]);
     corner_dir(v, x1, y1, c[2]);
     corner_dir(v, x0, y1, c[3]);
 #pragma unroll
     for (int a3 = 0; a3 < 3; a3++) ctr[a3] = c[0][a3] + c[1][a3] + c[2][a3] + c[3][a3];
-    bool use[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         cross3(c[k], c[(k + 1) & 3], n[k]);
@@ -104,6 +107,15 @@ __device__ __forceinline__ void cull_tile(const ViewRec &v, int tx, int ty, int 
             for (int a3 = 0; a3 < 3; a3++) n[k][a3] = -n[k][a3];
         }
     }
+}
+
+template <int TW, int TH, class RecAt, class Key>
+__device__ __forceinline__ void cull_tile(const ViewRec &v, int tx, int ty, int n_blk, RecAt rec_at, Key key,
+                                          unsigned char *s_keep, short *s_list, int *s_n) {
+    constexpr int kNT = TW * TH;
+    float n[4][3], fwd[3];
+    bool use[4];
+    tile_pyramid<TW, TH>(v, tx, ty, n, use, fwd);
     for (int j = threadIdx.x; j < n_blk; j += kNT) s_keep[j] = culled(rec_at(j), v.o, n, use, fwd) ? 0 : 1;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -289,6 +301,75 @@ __global__ void __launch_bounds__(TW * TH, kBatchThreadsPerSm / (TW * TH))
     }
 }
 
+// Warp items: every warp takes its own 8x4-pixel item from the run's counter,
+// culls the view's list against the item's pyramid with a ballot (the kept
+// blocks as three 32-bit masks, near to far), and marches its 32 rays.  The
+// loop has no CTA barrier, so a warp that finishes its item never waits for
+// another warp of its CTA.  Records by value as k_march_batch_c.
+constexpr int kWarpItemThreads = 128;
+
+template <int DT>
+__global__ void __launch_bounds__(kWarpItemThreads, kBatchThreadsPerSm / kWarpItemThreads)
+    k_march_batch_w(const __grid_constant__ BatchArgs a, const __grid_constant__ ParamRecs pr) {
+    static_assert(kParamRecs <= 96, "three 32-bit masks hold a run's lists");
+    __shared__ float s_mlp[kMlpParams + 1];
+    load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(a.counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= queue_hdr(a, 1)) break;
+        const ViewRec &v = a.views[view_of_item(a, queue_hdr(a, 0), item)];
+        const int t = item - v.tile_begin;
+        const int tx = t % v.tiles_x, ty = t / v.tiles_x;
+        const unsigned char *idx = a.vidx + v.ids_begin;
+        const int n_blk = v.ids_count;
+        unsigned keep[3];
+        {
+            float n[4][3], fwd[3];
+            bool use[4];
+            tile_pyramid<8, 4>(v, tx, ty, n, use, fwd);
+#pragma unroll
+            for (int w = 0; w < 3; w++) {
+                const int j = 32 * w + lane;
+                const bool k = j < n_blk && !culled(pr.r[__ldg(idx + j)], v.o, n, use, fwd);
+                keep[w] = __ballot_sync(0xffffffffu, k);
+            }
+        }
+        const int px = tx * 8 + (lane & 7), py = ty * 4 + (lane >> 3);
+        if (px < v.W && py < v.H) {  // lanes off the image idle until the next item
+            float o[3], d[3], inv_d[3], omax;
+            pixel_ray(v, px, py, o, d);
+            ray_setup(d, o, inv_d, omax);
+            const int64_t row = v.pix_offset + (int64_t)py * v.W + px;
+            RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
+            for (int w = 0; w < 3 && !s.done; w++) {
+                unsigned m = keep[w];
+                while (m && !s.done) {
+                    const int j = 32 * w + __ffs(m) - 1;
+                    m &= m - 1;
+                    march_block<DT>(pr.r[__ldg(idx + j)], o, d, inv_d, omax, a.ert_eps, s, a.err);
+                }
+            }
+            float x[10] = {s.Cd[0], s.Cd[1], s.Cd[2], s.F[0], s.F[1], s.F[2], s.F[3], d[0], d[1], d[2]};
+            float out[3];
+            deferred_mlp(s_mlp, x, (a.flags & 1u) != 0, out);
+            float *rgb = a.out_rgb + 3 * row;
+            rgb[0] = s.Cd[0] + out[0];
+            rgb[1] = s.Cd[1] + out[1];
+            rgb[2] = s.Cd[2] + out[2];
+            if (a.out_aux) {
+                float4 *ap = reinterpret_cast<float4 *>(a.out_aux + 8 * row);
+                ap[0] = make_float4(s.Cd[0], s.Cd[1], s.Cd[2], s.F[0]);
+                ap[1] = make_float4(s.F[1], s.F[2], s.F[3], s.T);
+            }
+            if (a.out_nsamp) a.out_nsamp[row] = s.nsamp;
+        }
+    }
+}
+
 }  // namespace
 
 // Per-dtype launchers: records staged in shared memory (batch.cu, dense;
@@ -314,6 +395,7 @@ cudaError_t launch_batch_param_dt(const BatchArgs &a, int tile_cfg, int grid, cu
     case 1: k_march_batch_c<DT, 8, 8><<<grid, 64, 0, st>>>(a, *pr); break;
     case 2: k_march_batch_c<DT, 16, 16><<<grid, 256, 0, st>>>(a, *pr); break;
     case 3: k_march_batch_c<DT, 32, 8><<<grid, 256, 0, st>>>(a, *pr); break;
+    case 4: k_march_batch_w<DT><<<grid, kWarpItemThreads, 0, st>>>(a, *pr); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

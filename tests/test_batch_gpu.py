@@ -44,7 +44,7 @@ def test_batch_equals_per_view(storage):
     b = cow.Batch(ctx, 16, 4096)
     n = b.set_views(cams, ids)
     assert n == sum(c.width * c.height for c in cams)
-    for cfg in range(4):
+    for cfg in range(5):  # 4: warp items
         for graph in (False, True):
             b.set_config(cfg, 3)
             out = (torch.full((n, 3), -1.0, device="cuda"), torch.zeros((n, 8), device="cuda"),
@@ -57,7 +57,7 @@ def test_batch_equals_per_view(storage):
                 diff = float((out[k] - ref[k]).abs().max())
                 assert diff <= 2e-6, (cfg, graph, k, diff)
     t, c, ms = b.tune(mlp_d, torch.empty((n, 3), device="cuda"), ert_eps=1e-5)
-    assert t in range(4) and c in (2, 3, 4, 6, 8) and ms > 0
+    assert t in range(5) and c in (2, 3, 4, 6, 8) and ms > 0
     out = torch.empty((n, 3), device="cuda")
     b.render(mlp_d, out, ert_eps=1e-5, graph=True)
     ctx.sync_check()
@@ -91,6 +91,16 @@ def test_batch_rejects_bad_arguments():
         b.set_views(cams[:1], [list(range(9))])  # more ids than the batch holds
     with pytest.raises(cow.CowError):
         b.set_config(7, 2)
+    # warp items read records from the parameter buffer only
+    ctx2 = cow.Context(sc, "bf16")
+    b2 = cow.Batch(ctx2, 2, 256)
+    n2 = b2.set_views(cams[:2], [ctx2.select_lod(c, sc.lod_thresh) for c in cams[:2]])
+    b2.set_config(4, 4)
+    b2.set_records("shared")
+    with pytest.raises(cow.CowError, match="parameter buffer"):
+        b2.render(torch.from_numpy(mlp).cuda(), torch.empty((n2, 3), device="cuda"))
+    b2.close()
+    ctx2.close()
 
 
 def test_batch_runs_and_long_lists():
