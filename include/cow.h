@@ -441,8 +441,8 @@ cow_status cow_render_rays(cow_ctx *ctx, const float *o, const float *d, int64_t
                            int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
                            float *out_aux, int32_t *out_nsamp, void *stream);
 
-/* Check aid for the differentiation form (the benchmark spec: FP64 on the GPU only
- * in the finite-difference gradient check): the ray-batch render of
+/* Check aid for the differentiation form (FP64 on the GPU serves only the
+ * finite-difference gradient check): the ray-batch render of
  * cow_render_rays without early termination, taking the same lattice samples
  * (decided by the FP32 sequence of the marcher) but computing every lookup
  * (Sec. 4.1 f^{k,l}), activation, weight (Eq. 1-2), composite (Eq. 12) and
