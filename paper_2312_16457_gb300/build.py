@@ -20,7 +20,7 @@ BUILD_DIR = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libcow.so")
 SOURCES = ["cow_api.cu", "batch_api.cu", "march.cu", "march_bricks.cu", "batch.cu", "batch_bricks.cu", "batch_param.cu",
            "batch_param_bricks.cu", "bwd.cu", "pack.cu", "probe.cu", "scene_io.cu",
-           "check_f64.cu"]
+           "check_f64.cu", "ray_order.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", INCLUDE, "-I", CSRC]

@@ -45,7 +45,7 @@ EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_save_scene", "cow_load_
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
            "cow_batch_last_groups", "cow_batch_set_run_fraction", "cow_batch_set_records", "cow_batch_get_config",
-           "cow_batch_set_schedule", "cow_batch_get_schedule", "cow_tune_schedule", "cow_last_error",
+           "cow_batch_set_schedule", "cow_batch_get_schedule", "cow_set_ray_order", "cow_tune_schedule", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
@@ -134,6 +134,7 @@ def lib():
             "cow_batch_set_records": [P, i32],
             "cow_batch_get_config": [P, P, P, P],
             "cow_batch_set_schedule": [P, i32],
+            "cow_set_ray_order": [P, i32],
             "cow_batch_get_schedule": [P, P],
             "cow_tune_schedule": [P, P, i32, P, P, P, flt, u32, P, i32, P, P, P, P],
             "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
@@ -469,6 +470,13 @@ class Context:
                                        C.byref(ms)))
         self.schedule = {v: k for k, v in SCHEDULES.items()}[s.value]
         return self.schedule, t.value, ms.value
+
+    RAY_ORDERS = {"given": 0, "coherent": 1}
+
+    def set_ray_order(self, mode: str):
+        """Processing order of ray batches: "coherent" (default; rays grouped by
+        entry cell and direction) or "given"."""
+        _check(lib().cow_set_ray_order(self._ctx, self.RAY_ORDERS[mode]))
 
     def set_schedule(self, name: str):
         """"thread_const" (default: one ray per thread, block records in the

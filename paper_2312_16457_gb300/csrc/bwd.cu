@@ -202,8 +202,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(BwdArgs a) {
 template <int DT>
 __global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_remarch_backward(BwdArgs a,
                                                                                 const __grid_constant__ RayRecs rr) {
-    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    if (r >= a.n_rays) return;
+    const int64_t t = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (t >= a.n_rays) return;
+    const int64_t r = a.ray_perm ? (int64_t)__ldg(a.ray_perm + t) : t;
     float o[3], d[3], Cf[3], Ff[4], gC[3], gF[4];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -494,8 +495,9 @@ __device__ __forceinline__ float bm_input(int i, const float ck[7], const float 
 // P1
 template <int DT>
 __global__ void __launch_bounds__(kBwdThreads) k_bm_pass1(BmBwdArgs a, const __grid_constant__ RayRecs rr) {
-    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    if (r >= a.n_rays) return;
+    const int64_t t = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (t >= a.n_rays) return;
+    const int64_t r = a.ray_perm ? (int64_t)__ldg(a.ray_perm + t) : t;
     float o[3], d[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -647,8 +649,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __gri
 template <int DT>
 __global__ void __launch_bounds__(kBwdThreads, COW_BWD_MIN_BLOCKS) k_bm_remarch(BmBwdArgs a,
                                                                           const __grid_constant__ RayRecs rr) {
-    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
-    if (r >= a.n_rays) return;
+    const int64_t t = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    if (t >= a.n_rays) return;
+    const int64_t r = a.ray_perm ? (int64_t)__ldg(a.ray_perm + t) : t;
     float o[3], d[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {

@@ -128,6 +128,9 @@ void destroy(cow_ctx *c) {
     c->staging.release();
     c->block_mlps.release();
     c->bm_scratch.release();
+    c->ray_keys.release();
+    c->ray_hist.release();
+    c->ray_perm.release();
     delete c;
 }
 
@@ -536,6 +539,33 @@ void make_ray_recs(const cow_ctx *c, const int32_t *ids, int32_t n, cow::RayRecs
         rr.r[k] = c->recs[(size_t)ids[k]];
         rr.id[k] = ids[k];
     }
+}
+
+// The coherent processing order of a ray batch (cow_set_ray_order), or null
+// for the order given: batches below kRayOrderMin rays keep theirs (the sort
+// would cost more than it saves).  The box is the call's blocks' bounding
+// box.  The permutation lives in the context until the next call.
+constexpr int64_t kRayOrderMin = 8192;
+
+cow_status ray_order(cow_ctx *c, const float *o, const float *d, int64_t n, const int32_t *ids, int32_t n_ids,
+                     cudaStream_t st, const int32_t **perm) {
+    *perm = nullptr;
+    if (c->ray_order != COW_RAY_ORDER_COHERENT || n < kRayOrderMin || n > 0x7fffffff) return COW_OK;
+    float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
+    for (int32_t k = 0; k < n_ids; k++) {
+        const BlockHost &b = c->blocks[(size_t)ids[k]];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = std::min(lo[a], b.lo[a]);
+            hi[a] = std::max(hi[a], b.hi[a]);
+        }
+    }
+    COW_CUDA(c->ray_keys.reserve((size_t)n * sizeof(uint32_t)));
+    COW_CUDA(c->ray_hist.reserve((size_t)cow::kRayOrderBins * sizeof(uint32_t)));
+    COW_CUDA(c->ray_perm.reserve((size_t)n * sizeof(int32_t)));
+    COW_CUDA(cow::launch_ray_order(o, d, n, lo, hi, (uint32_t *)c->ray_keys.p, (uint32_t *)c->ray_hist.p,
+                                   (int32_t *)c->ray_perm.p, st));
+    *perm = (const int32_t *)c->ray_perm.p;
+    return COW_OK;
 }
 
 // --- dynamic loading / unloading under a device-memory budget (App. D) -----
@@ -1030,6 +1060,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
         a.block_mlp_stride = ctx->block_mlp_nparam;
         a.n_freq = ctx->n_freq;
     }
+    if ((rc = ray_order(ctx, o, d, n_rays, ids, n_ids, st, &a.ray_perm)) != COW_OK) return rc;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_march_rays(a, rr, st));
@@ -1065,6 +1096,7 @@ cow_status cow_render_partials(cow_ctx *ctx, const float *o, const float *d, int
     a.ray_d = d;
     a.n_rays = n_rays;
     a.out_partials = out_partials;
+    if ((rc = ray_order(ctx, o, d, n_rays, ids, n_ids, st, &a.ray_perm)) != COW_OK) return rc;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_march_partials(a, rr, st));
@@ -1228,6 +1260,7 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     a.partials = (float *)ctx->partials.p;
     a.gcf = (float *)((unsigned char *)ctx->partials.p + part_bytes);
     a.err = ctx->d_err;
+    if ((rc = ray_order(ctx, o, d, n_rays, ids, n_ids, st, &a.ray_perm)) != COW_OK) return rc;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_rays(a, rr, st));
@@ -1290,6 +1323,7 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
     a.S = (float *)ctx->bm_scratch.p;
     a.G = (float *)((unsigned char *)ctx->bm_scratch.p + half);
     a.err = ctx->d_err;
+    if ((rc = ray_order(ctx, o, d, n_rays, ids, n_ids, st, &a.ray_perm)) != COW_OK) return rc;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_block_mlps(a, rr, st));
@@ -1805,6 +1839,15 @@ cow_status cow_tune_schedule(cow_ctx *ctx, const cow_camera *cams, int32_t n_vie
     if (out_schedule) *out_schedule = best_s;
     if (out_strip) *out_strip = best_t;
     if (out_ms) *out_ms = best;
+    return COW_OK;
+}
+
+cow_status cow_set_ray_order(cow_ctx *ctx, int32_t mode) {
+    g_last_error.clear();
+    if (!ctx) return fail(COW_ERR_INVALID_ARG, "null context");
+    if (mode != COW_RAY_ORDER_GIVEN && mode != COW_RAY_ORDER_COHERENT)
+        return fail(COW_ERR_INVALID_ARG, "unknown ray order %d", mode);
+    ctx->ray_order = mode;
     return COW_OK;
 }
 

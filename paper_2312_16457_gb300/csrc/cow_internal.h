@@ -178,6 +178,8 @@ struct cow_ctx {
     cowi::DevBuf staging;          // host masters of cow_update_features
     cowi::DevBuf block_mlps;       // cow_set_block_mlps: n_blocks x block_mlp_nparam FP32
     cowi::DevBuf bm_scratch;       // backward of the per-block MLP form: 2 x n_rays x n_ids x 8 FP32
+    int ray_order = COW_RAY_ORDER_COHERENT;  // cow_set_ray_order
+    cowi::DevBuf ray_keys, ray_hist, ray_perm;  // the coherent order of the last ray-batch call
     int32_t n_freq = -1;           // PE frequencies of block_mlps; -1 = none set
     int32_t block_mlp_nparam = 0;
     // dynamic loading: budget for the packed features on the device (0 = all

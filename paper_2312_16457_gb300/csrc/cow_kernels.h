@@ -36,6 +36,7 @@ struct MarchArgs {
     uint32_t wait_polls;             // bound on each mbarrier wait (0: the kernel's default)
     float *out_partials;             // block-parallel form: n_rays x n_ids x 8 per-block partials (written)
     const float *in_partials;        // block-parallel form: the same, read by the compositor
+    const int32_t *ray_perm;         // ray mode, may be null: thread t marches ray ray_perm[t] (outputs at the ray's index)
 };
 
 // Test hook of the kernels that stage block records with a TMA bulk copy:
@@ -51,6 +52,13 @@ struct ParamRecs;
 cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cudaStream_t st,
                                const ParamRecs *pr = nullptr);
 cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
+// A coherent order of a ray batch (ray_order.cu): perm[t] = the ray thread t
+// marches, grouping rays by the cell of their entry into the box [lo, hi]
+// and of their direction.  keys: n scratch words; hist: kRayOrderBins words.
+constexpr int kRayOrderKeyBits = 18;
+constexpr int kRayOrderBins = 1 << kRayOrderKeyBits;
+cudaError_t launch_ray_order(const float *o, const float *d, int64_t n, const float lo[3], const float hi[3],
+                             uint32_t *keys, uint32_t *hist, int32_t *perm, cudaStream_t st);
 // Block-parallel form: per-block partials of a ray batch (8 floats per ray
 // and block, in the order of rr), and K2, their near-to-far "over" with the
 // deferred MLP (Eq. 12-13, Eq. 3).
@@ -74,6 +82,7 @@ struct BwdArgs {                  // the call's block records come by value (Ray
     float *partials;              // scratch: backward_rows(n_rays) x 499
     float *gcf;                   // scratch: n_rays x 8 (dL/dC_d, dL/dF per ray)
     unsigned *err;
+    const int32_t *ray_perm;      // may be null: the re-march's thread t takes ray ray_perm[t]
 };
 
 // Gradients of the ray-batch form with per-block MLPs (Eq. 5), bwd.cu
@@ -93,6 +102,7 @@ struct BmBwdArgs {                // the call's block records come by value (Ray
     float *S;                     // scratch n_rays x n_ids x 8: C^k (3), F^k (4), B_k (-1: no sample)
     float *G;                     // scratch n_rays x n_ids x 8: dL/dC^k (3), dL/dF^k (4), dL/dC . X_k
     unsigned *err;
+    const int32_t *ray_perm;      // may be null: the marching passes' thread t takes ray ray_perm[t]
 };
 cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cudaStream_t st);
 

@@ -385,8 +385,9 @@ __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(Ma
         load_mlp(a.mlp, s_mlp, (a.flags & 1u) != 0);
         __syncthreads();
     }
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= a.n_rays) return;
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= a.n_rays) return;
+    const int64_t r = a.ray_perm ? (int64_t)__ldg(a.ray_perm + t) : t;
     float o[3], d[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
@@ -432,8 +433,9 @@ __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(Ma
 template <int DT>
 __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_partials(MarchArgs a,
                                                                               const __grid_constant__ RayRecs rr) {
-    const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (r >= a.n_rays) return;
+    const int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (t >= a.n_rays) return;
+    const int64_t r = a.ray_perm ? (int64_t)__ldg(a.ray_perm + t) : t;
     float o[3], d[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {

@@ -252,3 +252,47 @@ def test_backward_matches_fp64_gpu_central_differences():
             assert abs(fd - gv) <= bound, (j, fd, gv, scale)
             checked += 1
     assert checked >= 60 and skipped <= 4, (checked, skipped)
+
+
+def test_coherent_ray_order_keeps_results():
+    """The coherent processing order of ray batches (the default for 8192
+    rays or more) writes every ray's forward outputs and per-block partials
+    bit for bit as the given order does, and the same gradients up to the
+    order of their FP32 reductions (global and per-block MLP forms)."""
+    sc = synth.city_scene(21, 2, 2.0, [(12, 32)])
+    n = 20000
+    o, d = synth.random_rays(n, 13, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    mlp = torch.from_numpy(synth.mlp_weights(5)).cuda()
+    g = torch.randn(n, 3, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    ctx = cow.Context(sc, "fp32")
+    ids = list(range(4))
+    res = {}
+    for mode in ("given", "coherent"):
+        ctx.set_ray_order(mode)
+        rgb, ns, gg, gp, gm = _gpu_grads(ctx, sc, o, d, ids, mlp, g)
+        part = ctx.render_partials(o, d, ids)
+        ctx.sync_check()
+        res[mode] = (rgb, ns, gg, gp, gm, part)
+    a, b = res["given"], res["coherent"]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]) and torch.equal(a[5], b[5])
+    for x, y in [*zip(a[2], b[2]), *[(p, q) for pa, pb in zip(a[3], b[3]) for p, q in zip(pa, pb)], (a[4], b[4])]:
+        assert float((x - y).abs().max()) <= 1e-5 * float(x.abs().max()) + 1e-12
+    # per-block MLP form
+    nb, L = len(sc.blocks), 2
+    ctx.set_block_mlps(synth.block_mlp_weights(13, nb, L), L)
+    res = {}
+    for mode in ("given", "coherent"):
+        ctx.set_ray_order(mode)
+        rgb = ctx.render_rays(o, d, ids, None, aux=False, block_mlps=True)[0]
+        gg = [torch.zeros(bk.grid.shape, device="cuda") for bk in sc.blocks]
+        gp = [[torch.zeros(p.shape, device="cuda") for p in bk.planes] for bk in sc.blocks]
+        gw = torch.zeros((nb, synth.block_mlp_nparam(L)), device="cuda")
+        ctx.render_backward_block_mlps(o, d, ids, g, gg, gp, gw)
+        ctx.sync_check()
+        res[mode] = (rgb, gg, gw)
+    a, b = res["given"], res["coherent"]
+    assert torch.equal(a[0], b[0])
+    for x, y in [*zip(a[1], b[1]), (a[2], b[2])]:
+        assert float((x - y).abs().max()) <= 1e-5 * float(x.abs().max()) + 1e-12
+    ctx.close()
