@@ -633,7 +633,7 @@ cow_status cow_set_schedule(cow_ctx *ctx, int32_t schedule);
 
 /* Processing order of the ray-batch calls (cow_render_rays,
  * cow_render_rays_block_t, cow_render_partials, cow_render_backward,
- * cow_render_backward_block_mlps).  COW_RAY_ORDER_COHERENT (default): a
+ * cow_render_backward_block_mlps, cow_opacity_loss).  COW_RAY_ORDER_COHERENT (default): a
  * batch of at least 8192 rays is marched in a coherent order -- rays grouped
  * by the cell of their entry into the call's blocks' bounding box (8 x 8 x 8)
  * and of their direction (8 x 8 x 8), by a counting sort on the device -- so

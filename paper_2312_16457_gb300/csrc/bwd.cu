@@ -375,9 +375,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_sparsity(RegArgs a, const __gri
 template <int DT>
 __global__ void __launch_bounds__(kBwdThreads, COW_REG_MIN_BLOCKS) k_opacity(RegArgs a,
                                                                           const __grid_constant__ RayRecs rr) {
-    const int64_t r = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * kBwdThreads + threadIdx.x;
     float term = 0.f;
-    if (r < a.n) {
+    if (t < a.n) {
+        const int64_t r = a.ray_perm ? (int64_t)__ldg(a.ray_perm + t) : t;
         float o[3], d[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) {

@@ -560,7 +560,7 @@ cow_status ray_order(cow_ctx *c, const float *o, const float *d, int64_t n, cons
         }
     }
     COW_CUDA(c->ray_keys.reserve((size_t)n * sizeof(uint32_t)));
-    COW_CUDA(c->ray_hist.reserve((size_t)cow::kRayOrderBins * sizeof(uint32_t)));
+    COW_CUDA(c->ray_hist.reserve((size_t)cow::kRayOrderHistWords * sizeof(uint32_t)));
     COW_CUDA(c->ray_perm.reserve((size_t)n * sizeof(int32_t)));
     COW_CUDA(cow::launch_ray_order(o, d, n, lo, hi, (uint32_t *)c->ray_keys.p, (uint32_t *)c->ray_hist.p,
                                    (int32_t *)c->ray_perm.p, st));
@@ -1414,6 +1414,7 @@ cow_status cow_opacity_loss(cow_ctx *ctx, const float *o, const float *d, int64_
     a.n = n_rays;
     a.weight = weight;
     a.block_T = block_T;
+    if ((rc = ray_order(ctx, o, d, n_rays, ids, n_ids, st, &a.ray_perm)) != COW_OK) return rc;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_opacity(a, rr, st));

@@ -54,9 +54,11 @@ cudaError_t launch_march_views(const MarchArgs &a, int n_tiles, int schedule, cu
 cudaError_t launch_march_rays(const MarchArgs &a, const RayRecs &rr, cudaStream_t st);
 // A coherent order of a ray batch (ray_order.cu): perm[t] = the ray thread t
 // marches, grouping rays by the cell of their entry into the box [lo, hi]
-// and of their direction.  keys: n scratch words; hist: kRayOrderBins words.
+// and of their direction.  keys: n scratch words; hist: kRayOrderHistWords
+// words (the bins, then the totals of the scan's blocks of 1024 bins).
 constexpr int kRayOrderKeyBits = 18;
 constexpr int kRayOrderBins = 1 << kRayOrderKeyBits;
+constexpr int kRayOrderHistWords = kRayOrderBins + kRayOrderBins / 1024;
 cudaError_t launch_ray_order(const float *o, const float *d, int64_t n, const float lo[3], const float hi[3],
                              uint32_t *keys, uint32_t *hist, int32_t *perm, cudaStream_t st);
 // Block-parallel form: per-block partials of a ray batch (8 floats per ray
@@ -120,6 +122,7 @@ struct RegArgs {                  // the blocks that take part come by value (Ra
     float *const *grad_grid;      // device pointer table as in BwdArgs (null: no gradient)
     float *const *grad_planes;
     unsigned *err;
+    const int32_t *ray_perm;      // opacity, may be null: thread t takes ray ray_perm[t]
 };
 cudaError_t launch_sparsity(const RegArgs &a, const RayRecs &rr, cudaStream_t st);
 cudaError_t launch_opacity(const RegArgs &a, const RayRecs &rr, cudaStream_t st);

@@ -67,49 +67,76 @@ __global__ void k_ray_keys(const float *__restrict__ o, const float *__restrict_
     }
 }
 
-// Exclusive prefix sum of the kRayOrderBins counts, in place, by one CTA.
+// Exclusive prefix sum of the kRayOrderBins counts in two levels: every CTA
+// scans its kScanThreads bins in place and writes its total to sums[]; one
+// CTA then scans the totals, which the scatter adds back.
 constexpr int kScanThreads = 1024;
-__global__ void __launch_bounds__(kScanThreads) k_scan_bins(uint32_t *hist) {
-    constexpr int kPer = kRayOrderBins / kScanThreads;
-    __shared__ uint32_t s[kScanThreads];
-    const int t = threadIdx.x;
-    uint32_t sum = 0;
-    for (int k = 0; k < kPer; k++) sum += hist[t * kPer + k];
-    s[t] = sum;
+constexpr int kScanBlocks = kRayOrderBins / kScanThreads;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
     __syncthreads();
-    for (int off = 1; off < kScanThreads; off <<= 1) {  // inclusive Hillis-Steele scan of the thread sums
-        const uint32_t v = t >= off ? s[t - off] : 0u;
-        __syncthreads();
-        s[t] += v;
-        __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < nw) s_warp[lane] = w;  // inclusive warp totals
     }
-    uint32_t run = s[t] - sum;  // exclusive start of this thread's bins
-    for (int k = 0; k < kPer; k++) {
-        const uint32_t c = hist[t * kPer + k];
-        hist[t * kPer + k] = run;
-        run += c;
-    }
+    __syncthreads();
+    if (total) *total = s_warp[(blockDim.x >> 5) - 1];
+    return x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(uint32_t *hist, uint32_t *sums) {
+    __shared__ uint32_t s_warp[32];
+    const int64_t i = (int64_t)blockIdx.x * kScanThreads + threadIdx.x;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(hist[i], s_warp, &total);
+    hist[i] = ex;
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanBlocks) k_scan_sums(uint32_t *sums) {
+    __shared__ uint32_t s_warp[32];
+    sums[threadIdx.x] = block_exclusive_scan(sums[threadIdx.x], s_warp, nullptr);
 }
 
 __global__ void k_ray_scatter(const uint32_t *__restrict__ keys, int64_t n, uint32_t *__restrict__ offs,
-                              int32_t *__restrict__ perm) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        perm[atomicAdd(offs + keys[i], 1u)] = (int32_t)i;
+                              const uint32_t *__restrict__ sums, int32_t *__restrict__ perm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = keys[i];
+        perm[sums[k / kScanThreads] + atomicAdd(offs + k, 1u)] = (int32_t)i;
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_ray_order(const float *o, const float *d, int64_t n, const float lo[3], const float hi[3],
                              uint32_t *keys, uint32_t *hist, int32_t *perm, cudaStream_t st) {
-    static_assert(kRayOrderBins % kScanThreads == 0, "bins per scan thread");
+    static_assert(kRayOrderBins == kScanBlocks * kScanThreads && kScanBlocks <= 1024 && kScanBlocks % 32 == 0,
+                  "two-level scan shape");
+    static_assert(kRayOrderHistWords == kRayOrderBins + kScanBlocks, "histogram scratch: bins, then block totals");
     if (n <= 0 || n > 0x7fffffff) return cudaErrorInvalidValue;
     cudaError_t e = cudaMemsetAsync(hist, 0, kRayOrderBins * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
+    uint32_t *sums = hist + kRayOrderBins;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
     k_ray_keys<<<grid, 256, 0, st>>>(o, d, n, make_float3(lo[0], lo[1], lo[2]), make_float3(hi[0], hi[1], hi[2]), keys,
                                      hist);
-    k_scan_bins<<<1, kScanThreads, 0, st>>>(hist);
-    k_ray_scatter<<<grid, 256, 0, st>>>(keys, n, hist, perm);
+    k_scan_local<<<kScanBlocks, kScanThreads, 0, st>>>(hist, sums);
+    k_scan_sums<<<1, kScanBlocks, 0, st>>>(sums);
+    k_ray_scatter<<<grid, 256, 0, st>>>(keys, n, hist, sums, perm);
     return cudaGetLastError();
 }
 
