@@ -566,6 +566,26 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
                                           float *const *grad_grid, float *const *grad_planes, float *grad_block_mlps,
                                           void *stream);
 
+/* The same gradients without the backward's first march.  The forward
+ * cow_render_rays_block_state renders like cow_render_rays with
+ * COW_FLAG_BLOCK_MLPS and no early termination (Eq. 5 over the blocks' own
+ * MLPs) and also writes, per (ray, block at its position in ids), what the
+ * first march of the backward would compute: the block's C^k (3) and F^k (4)
+ * and the transmittance in front of it (-1 when the block has no occupied
+ * sample on the ray) -- out_state: device float32 n_rays x n_ids x 8,
+ * 16-byte aligned.  cow_render_backward_block_mlps_state takes that state
+ * (the same rays, ids and per-block MLPs, features unchanged since) and
+ * marches once.  Scratch: 32 bytes per (ray, block of ids), kept by the
+ * context.  Errors: as cow_render_rays / cow_render_backward_block_mlps;
+ * INVALID_ARG for a null, host or misaligned state. */
+cow_status cow_render_rays_block_state(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                       const int32_t *ids, int32_t n_ids, float *out_rgb, float *out_state,
+                                       void *stream);
+cow_status cow_render_backward_block_mlps_state(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                                const int32_t *ids, int32_t n_ids, const float *state,
+                                                const float *dL_drgb, float *const *grad_grid,
+                                                float *const *grad_planes, float *grad_block_mlps, void *stream);
+
 /* Re-pack block `block`'s features from new FP32 masters (same layouts as
  * cow_block_desc; host or device, 16-byte aligned) into the context's
  * storage format; occupancy and z_top stay as loaded (the differentiation

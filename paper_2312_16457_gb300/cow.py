@@ -45,7 +45,8 @@ EXPORTS = ["cow_load_blocks", "cow_load_blocks_ex", "cow_save_scene", "cow_load_
            "cow_update_features", "cow_adam_step", "cow_mse_grad", "cow_batch_create", "cow_batch_free",
            "cow_batch_set_views", "cow_batch_render", "cow_batch_set_config", "cow_batch_tune",
            "cow_batch_last_groups", "cow_batch_set_run_fraction", "cow_batch_set_records", "cow_batch_get_config",
-           "cow_batch_set_schedule", "cow_batch_get_schedule", "cow_set_ray_order", "cow_tune_schedule", "cow_last_error",
+           "cow_batch_set_schedule", "cow_batch_get_schedule", "cow_set_ray_order", "cow_render_rays_block_state",
+           "cow_render_backward_block_mlps_state", "cow_tune_schedule", "cow_last_error",
            "cow_version"]
 SCHEDULES = {"warp": 0, "thread": 1, "thread_const": 2}
 
@@ -135,6 +136,8 @@ def lib():
             "cow_batch_get_config": [P, P, P, P],
             "cow_batch_set_schedule": [P, i32],
             "cow_set_ray_order": [P, i32],
+            "cow_render_rays_block_state": [P, P, P, i64, P, i32, P, P, P],
+            "cow_render_backward_block_mlps_state": [P, P, P, i64, P, i32, P, P, P, P, P, P],
             "cow_batch_get_schedule": [P, P],
             "cow_tune_schedule": [P, P, i32, P, P, P, flt, u32, P, i32, P, P, P, P],
             "cow_batch_tune": [P, P, flt, u32, P, i32, P, P, P, P],
@@ -395,6 +398,27 @@ class Context:
         _check(lib().cow_render_backward_block_mlps(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0],
                                                     _ptr(a), len(a), _ptr(dL_drgb.contiguous()), gg, gp,
                                                     _ptr(grad_block_mlps), _stream_ptr(stream)))
+
+    def render_rays_block_state(self, o, d, ids, stream=None):
+        """Per-block MLP forward without early termination that also returns
+        the per-(ray, block) state the backward's first march would compute:
+        (rgb [n, 3], state [n, len(ids), 8])."""
+        a = np.ascontiguousarray(ids, np.int32)
+        n = o.shape[0]
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=o.device)
+        state = torch.empty((n, len(a), 8), dtype=torch.float32, device=o.device)
+        _check(lib().cow_render_rays_block_state(self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), n, _ptr(a),
+                                                 len(a), _ptr(rgb), _ptr(state), _stream_ptr(stream)))
+        return rgb, state
+
+    def render_backward_block_mlps_state(self, o, d, ids, state, dL_drgb, grad_grids, grad_planes, grad_block_mlps,
+                                         stream=None):
+        """cow_render_backward_block_mlps from the forward's state (one march)."""
+        a = np.ascontiguousarray(ids, np.int32)
+        gg, gp = self._grad_tables((grad_grids, grad_planes))
+        _check(lib().cow_render_backward_block_mlps_state(
+            self._ctx, _ptr(o.contiguous()), _ptr(d.contiguous()), o.shape[0], _ptr(a), len(a), _ptr(state),
+            _ptr(dL_drgb.contiguous()), gg, gp, _ptr(grad_block_mlps), _stream_ptr(stream)))
 
     def _grad_tables(self, grads):
         if grads is None:

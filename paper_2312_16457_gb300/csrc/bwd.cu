@@ -754,7 +754,7 @@ cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cu
     if (a.n_rays <= 0) return cudaSuccess;
     const int nb = backward_rows(a.n_rays);
     const int64_t padded = ((a.n_rays + 31) & ~(int64_t)31) * a.n_ids;  // k_bm_mlp's threads
-    {
+    if (!a.have_state) {
         const cudaError_t e_ = dispatch_dt(a.dtype, [&](auto D) {
             k_bm_pass1<decltype(D)::value><<<nb, kBwdThreads, 0, st>>>(a, rr);
             return cudaSuccess;

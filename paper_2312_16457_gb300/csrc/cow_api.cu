@@ -1007,7 +1007,8 @@ cow_status cow_render(cow_ctx *ctx, const cow_camera *cams, int32_t n_views, con
 
 static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                                    int32_t n_ids, const float *mlp, float ert_eps, uint32_t flags, float *out_rgb,
-                                   float *out_aux, int32_t *out_nsamp, float *out_block_T, void *stream) {
+                                   float *out_aux, int32_t *out_nsamp, float *out_block_T, void *stream,
+                                   float *out_block_state = nullptr) {
     COW_NVTX("cow_render_rays");
     g_last_error.clear();
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
@@ -1055,6 +1056,7 @@ static cow_status render_rays_impl(cow_ctx *ctx, const float *o, const float *d,
     a.ray_d = d;
     a.n_rays = n_rays;
     a.out_block_T = out_block_T;
+    a.out_block_state = out_block_state;
     if (block_mlp) {
         a.block_mlp_base = (const float *)ctx->block_mlps.p;
         a.block_mlp_stride = ctx->block_mlp_nparam;
@@ -1209,6 +1211,17 @@ cow_status cow_render_rays_block_t(cow_ctx *ctx, const float *o, const float *d,
                             stream);
 }
 
+cow_status cow_render_rays_block_state(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                       const int32_t *ids, int32_t n_ids, float *out_rgb, float *out_state,
+                                       void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays == 0) return COW_OK;
+    if (!out_state || !is_device_ptr(out_state) || ((uintptr_t)out_state & 15u))
+        return fail(COW_ERR_INVALID_ARG, "out_state must be 16-byte aligned device memory (n_rays x n_ids x 8 floats)");
+    return render_rays_impl(ctx, o, d, n_rays, ids, n_ids, nullptr, 0.0f, COW_FLAG_BLOCK_MLPS, out_rgb, nullptr,
+                            nullptr, nullptr, stream, out_state);
+}
+
 cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays, const int32_t *ids,
                                int32_t n_ids, const float *mlp, float ert_eps, const float *aux, const float *dL_drgb,
                                float *const *grad_grid, float *const *grad_planes, float *grad_mlp, void *stream) {
@@ -1267,12 +1280,14 @@ cow_status cow_render_backward(cow_ctx *ctx, const float *o, const float *d, int
     return note_use_impl(ctx, ids, n_ids, st);
 }
 
-cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
-                                          const int32_t *ids, int32_t n_ids, const float *dL_drgb,
-                                          float *const *grad_grid, float *const *grad_planes, float *grad_block_mlps,
-                                          void *stream) {
+static cow_status backward_block_mlps_impl(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                           const int32_t *ids, int32_t n_ids, const float *state,
+                                           const float *dL_drgb, float *const *grad_grid, float *const *grad_planes,
+                                           float *grad_block_mlps, void *stream) {
     COW_NVTX("cow_render_backward_block_mlps");
     g_last_error.clear();
+    if (state && (!is_device_ptr(state) || ((uintptr_t)state & 15u)))
+        return fail(COW_ERR_INVALID_ARG, "state must be 16-byte aligned device memory (n_rays x n_ids x 8 floats)");
     if (ctx && n_rays == 0) return COW_OK;  // an empty batch (its arrays may be NULL)
     if (!ctx || !o || !d || n_rays < 0 || !ids || !dL_drgb || !grad_grid || !grad_planes || !grad_block_mlps)
         return fail(COW_ERR_INVALID_ARG, "cow_render_backward_block_mlps: null argument");
@@ -1303,7 +1318,7 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
     COW_CUDA(ctx->gptrs.reserve(ptrs.size() * sizeof(float *)));
     COW_CUDA(cudaMemcpyAsync(ctx->gptrs.p, ptrs.data(), ptrs.size() * sizeof(float *), cudaMemcpyHostToDevice, st));
     const size_t half = (size_t)n_rays * (size_t)n_ids * 8 * sizeof(float);
-    COW_CUDA(ctx->bm_scratch.reserve(2 * half));
+    COW_CUDA(ctx->bm_scratch.reserve(state ? half : 2 * half));
     const int32_t n_in = 10 + 6 * ctx->n_freq;
     cow::BmBwdArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -1320,14 +1335,35 @@ cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const fl
     a.grad_stride = 16 * n_in + 16 + 16 * 16 + 16 + 16 * 3 + 3;
     a.n_freq = ctx->n_freq;
     a.n_ids = n_ids;
-    a.S = (float *)ctx->bm_scratch.p;
-    a.G = (float *)((unsigned char *)ctx->bm_scratch.p + half);
+    // S: the forward's per-block state when given (the first pass is then
+    // skipped), else scratch; G: scratch
+    a.S = state ? const_cast<float *>(state) : (float *)ctx->bm_scratch.p;
+    a.G = state ? (float *)ctx->bm_scratch.p : (float *)((unsigned char *)ctx->bm_scratch.p + half);
+    a.have_state = state ? 1 : 0;
     a.err = ctx->d_err;
     if ((rc = ray_order(ctx, o, d, n_rays, ids, n_ids, st, &a.ray_perm)) != COW_OK) return rc;
     cow::RayRecs rr;
     make_ray_recs(ctx, ids, n_ids, rr);
     COW_CUDA(cow::launch_backward_block_mlps(a, rr, st));
     return note_use_impl(ctx, ids, n_ids, st);
+}
+
+cow_status cow_render_backward_block_mlps(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                          const int32_t *ids, int32_t n_ids, const float *dL_drgb,
+                                          float *const *grad_grid, float *const *grad_planes, float *grad_block_mlps,
+                                          void *stream) {
+    return backward_block_mlps_impl(ctx, o, d, n_rays, ids, n_ids, nullptr, dL_drgb, grad_grid, grad_planes,
+                                    grad_block_mlps, stream);
+}
+
+cow_status cow_render_backward_block_mlps_state(cow_ctx *ctx, const float *o, const float *d, int64_t n_rays,
+                                                const int32_t *ids, int32_t n_ids, const float *state,
+                                                const float *dL_drgb, float *const *grad_grid,
+                                                float *const *grad_planes, float *grad_block_mlps, void *stream) {
+    g_last_error.clear();
+    if (ctx && n_rays > 0 && !state) return fail(COW_ERR_INVALID_ARG, "null state");
+    return backward_block_mlps_impl(ctx, o, d, n_rays, ids, n_ids, state, dL_drgb, grad_grid, grad_planes,
+                                    grad_block_mlps, stream);
 }
 
 namespace {

@@ -37,6 +37,8 @@ struct MarchArgs {
     float *out_partials;             // block-parallel form: n_rays x n_ids x 8 per-block partials (written)
     const float *in_partials;        // block-parallel form: the same, read by the compositor
     const int32_t *ray_perm;         // ray mode, may be null: thread t marches ray ray_perm[t] (outputs at the ray's index)
+    float *out_block_state;          // ray mode, per-block MLPs, may be null: n_rays x n_ids x 8, per (ray, block
+                                     // at its position in ids) C^k (3), F^k (4), the transmittance in front (-1: no sample)
 };
 
 // Test hook of the kernels that stage block records with a TMA bulk copy:
@@ -105,6 +107,7 @@ struct BmBwdArgs {                // the call's block records come by value (Ray
     float *G;                     // scratch n_rays x n_ids x 8: dL/dC^k (3), dL/dF^k (4), dL/dC . X_k
     unsigned *err;
     const int32_t *ray_perm;      // may be null: the marching passes' thread t takes ray ray_perm[t]
+    int32_t have_state;           // S already holds the forward's per-block state: skip the first pass
 };
 cudaError_t launch_backward_block_mlps(const BmBwdArgs &a, const RayRecs &rr, cudaStream_t st);
 

@@ -82,15 +82,27 @@ __device__ __forceinline__ int view_of_tile(const MarchArgs &a, int tile) {
 // the ray's total transmittance: inside block k it stops once
 // T_k < ert_eps / T.  rec_at(k) / mlp_at(k): the k-th block's record and
 // MLP weights in near-to-far order.
-template <int DT, class RecAt, class MlpAt>
+// state(k): where the k-th block's state goes (a.out_block_state, ray mode),
+// or null.
+template <int DT, class RecAt, class MlpAt, class StateAt>
 __device__ __forceinline__ void blend_blocks(const MarchArgs &a, int n_blk, RecAt rec_at, MlpAt mlp_at,
-                                             const float o[3], const float d[3], const float inv_d[3], float omax,
-                                             int64_t row) {
+                                             StateAt state, const float o[3], const float d[3],
+                                             const float inv_d[3], float omax, int64_t row) {
     float C[3] = {0.f, 0.f, 0.f}, Cd[3] = {0.f, 0.f, 0.f}, F[4] = {0.f, 0.f, 0.f, 0.f}, T = 1.f;
     int nsamp = 0;
     for (int k = 0; k < n_blk; k++) {
         RayState sb = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};
         march_block<DT>(rec_at(k), o, d, inv_d, omax, a.ert_eps > 0.f ? a.ert_eps / T : 0.f, sb, a.err);
+        if (float *e = state(k)) {
+            float4 *e4 = reinterpret_cast<float4 *>(e);
+            if (sb.nsamp == 0) {
+                e4[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                e4[1] = make_float4(0.f, 0.f, 0.f, -1.f);
+            } else {
+                e4[0] = make_float4(sb.Cd[0], sb.Cd[1], sb.Cd[2], sb.F[0]);
+                e4[1] = make_float4(sb.F[1], sb.F[2], sb.F[3], T);
+            }
+        }
         if (sb.nsamp == 0) continue;
         float phi[3];
         block_mlp(mlp_at(k), a.n_freq, sb.Cd, sb.F, d, phi);
@@ -123,7 +135,8 @@ __device__ __forceinline__ void march_blocks_blend(const MarchArgs &a, const Vie
                                                    float omax, int64_t row) {
     blend_blocks<DT>(
         a, v.ids_count, [&](int k) -> const BlockRec & { return recs[k]; },
-        [&](int k) { return a.block_mlps[v.ids_begin + k]; }, o, d, inv_d, omax, row);
+        [&](int k) { return a.block_mlps[v.ids_begin + k]; }, [](int) -> float * { return nullptr; }, o, d, inv_d,
+        omax, row);
 }
 
 // One ray per thread of the tile: march the view's near-to-far block list
@@ -402,8 +415,11 @@ __global__ void __launch_bounds__(kThreads, COW_RAYS_MIN_BLOCKS) k_march_rays(Ma
     if (kBlockMlp) {  // Eq. 5 with block id's own MLP at block_mlp_base + id * block_mlp_stride
         blend_blocks<DT>(
             a, n, [&](int k) -> const BlockRec & { return rr.r[order[k]]; },
-            [&](int k) { return a.block_mlp_base + (int64_t)rr.id[order[k]] * a.block_mlp_stride; }, o, d, inv_d,
-            omax, r);
+            [&](int k) { return a.block_mlp_base + (int64_t)rr.id[order[k]] * a.block_mlp_stride; },
+            [&](int k) -> float * {
+                return a.out_block_state ? a.out_block_state + 8 * (r * rr.n + order[k]) : nullptr;
+            },
+            o, d, inv_d, omax, r);
         return;
     }
     RayState s = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}, 1.f, 0, false};

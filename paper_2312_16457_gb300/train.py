@@ -98,7 +98,8 @@ class Fitter:
         if per_block:
             if ert_eps != 0.0:
                 raise ValueError("the per-block MLP form fits without early termination")
-            rgb = self.ctx.render_rays(o, d, self.ids, None, aux=False, block_mlps=True)[0]
+            # the forward keeps every (ray, block) state, so the backward marches once
+            rgb, bm_state = self.ctx.render_rays_block_state(o, d, self.ids)
         elif self.lambda_opacity > 0.0 and ert_eps == 0.0:
             # the forward also keeps every block's transmittance for the opacity term
             rgb, aux, block_T = self.ctx.render_rays_block_t(o, d, self.ids, self.mlp)
@@ -109,7 +110,7 @@ class Fitter:
         gtab = ([grads[4 * i] for i in range(nb)], [grads[4 * i + 1:4 * i + 4] for i in range(nb)])
         if per_block:
             gm = torch.zeros_like(self.block_mlps)
-            self.ctx.render_backward_block_mlps(o, d, self.ids, g, gtab[0], gtab[1], gm)
+            self.ctx.render_backward_block_mlps_state(o, d, self.ids, bm_state, g, gtab[0], gtab[1], gm)
         else:
             gm = torch.zeros_like(self.mlp)
             self.ctx.render_backward(o, d, self.ids, self.mlp, aux, g, gtab[0], gtab[1], gm, ert_eps=ert_eps)

@@ -72,6 +72,8 @@ def test_calls_reject_null_context(L):
     assert L.cow_sync_check(None, None) == 1
     assert L.cow_set_schedule(None, 0) == 1
     assert L.cow_set_ray_order(None, 1) == 1
+    assert L.cow_render_rays_block_state(None, None, None, 1, None, 1, None, None, None) == 1
+    assert L.cow_render_backward_block_mlps_state(None, None, None, 1, None, 1, None, None, None, None, None, None) == 1
     assert L.cow_set_tile_order(None, 0) == 1
     assert b"null context" in L.cow_last_error()
     assert L.cow_render_backward_block_mlps(None, None, None, 1, None, 1, None, None, None, None, None) == 1

@@ -246,3 +246,42 @@ def test_fit_with_block_mlps_reduces_loss():
     assert losses[-1] < 0.85 * losses[0], losses[::8]
     # the fitted per-block MLPs are the context's
     assert not np.allclose(fit.block_mlps.cpu().numpy(), w)
+
+
+def test_backward_from_forward_state():
+    """The forward that keeps every (ray, block) state renders the same
+    pixels as the per-block MLP forward, and the backward from that state
+    gives the gradients of the two-march backward (FP32 reduction order
+    aside)."""
+    sc = synth.city_scene(23, 2, 2.0, [(12, 32)])
+    n, L = 20000, 2
+    o, d = synth.random_rays(n, 5, sc.box_lo, sc.box_hi)
+    o, d = o.cuda(), d.cuda()
+    nb = len(sc.blocks)
+    ids = list(range(nb))
+    ctx = cow.Context(sc, "fp32")
+    ctx.set_block_mlps(synth.block_mlp_weights(14, nb, L), L)
+    g = torch.randn(n, 3, device="cuda", generator=torch.Generator(device="cuda").manual_seed(6))
+    ref = ctx.render_rays(o, d, ids, None, aux=False, block_mlps=True)[0]
+    rgb, state = ctx.render_rays_block_state(o, d, ids)
+    ctx.sync_check()
+    assert torch.equal(rgb, ref)
+    T = state[..., 7]
+    assert bool(((T == -1.0) | ((T >= 0.0) & (T <= 1.0))).all()) and bool((T >= 0.0).any())
+    out = []
+    for use_state in (False, True):
+        gg = [torch.zeros(b.grid.shape, device="cuda") for b in sc.blocks]
+        gp = [[torch.zeros(p.shape, device="cuda") for p in b.planes] for b in sc.blocks]
+        gw = torch.zeros((nb, synth.block_mlp_nparam(L)), device="cuda")
+        if use_state:
+            ctx.render_backward_block_mlps_state(o, d, ids, state, g, gg, gp, gw)
+        else:
+            ctx.render_backward_block_mlps(o, d, ids, g, gg, gp, gw)
+        ctx.sync_check()
+        out.append((gg, gp, gw))
+    a, b = out
+    pairs = [*zip(a[0], b[0]), *[(x, y) for pa, pb in zip(a[1], b[1]) for x, y in zip(pa, pb)], (a[2], b[2])]
+    for x, y in pairs:
+        assert float((x - y).abs().max()) <= 1e-5 * float(x.abs().max()) + 1e-12
+    assert float(a[2].abs().max()) > 0.0
+    ctx.close()
