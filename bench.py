@@ -98,6 +98,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-view batched measurement")
     ap.add_argument("--no-sparse-city", action="store_true", help="skip the sparse-city brick measurement")
     ap.add_argument("--batch-storage", default="bf16", help="storage of the 64-view batched measurement")
+    ap.add_argument("--fit-storage", default="fp32", help="fit_2x2: storage of the render copies of the FP32 parameters")
     ap.add_argument("--batch-config", default=None,
                     help="TILE,CTAS: the 64-view batch's tile configuration (0-3) and CTAs per SM, queue schedule, "
                          "instead of the tuner (profiling runs)")
@@ -630,7 +631,7 @@ def run_fit(args, ws, rank, local):
     bm = synth.block_mlp_weights(104, len(sc.blocks), args.block_mlps) if per_block else None
     fit = train.Fitter(sc, None if per_block else mlp, lambda_sparsity=0.05 if args.reg else 0.0,
                        lambda_opacity=0.001 if args.reg else 0.0, block_mlps=bm,
-                       n_freq=max(args.block_mlps, 0))
+                       n_freq=max(args.block_mlps, 0), storage=args.fit_storage)
     stream = torch.cuda.current_stream()
 
     def psnr_now():
@@ -688,7 +689,7 @@ def run_fit(args, ws, rank, local):
             "unit": "Mrays/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
             "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "fit_2x2", "scene": f"2x2 blocks, {R}^3 grid + {P}^2 planes, FP32 parameters",
-                       "rays": n, "adam_steps": args.warmup + args.steps, "lr_features": fit.lr_feat,
+                       "render_storage": args.fit_storage, "rays": n, "adam_steps": args.warmup + args.steps, "lr_features": fit.lr_feat,
                        "lr_mlp": fit.lr_mlp,
                        "mlp": (f"per-block (Eq. 5), PE with {args.block_mlps} frequencies, "
                                f"{synth.block_mlp_nparam(args.block_mlps)} parameters a block") if per_block

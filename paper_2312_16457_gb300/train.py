@@ -54,15 +54,19 @@ class Fitter:
     batch: forward, MSE gradient, backward, Adam, re-pack -- all in libcow."""
 
     def __init__(self, scene, mlp, lr_feat=1e-2, lr_mlp=1e-3, device="cuda", lambda_sparsity=0.0,
-                 lambda_opacity=0.0, n_sparsity_points=1 << 14, seed=0, block_mlps=None, n_freq=0):
+                 lambda_opacity=0.0, n_sparsity_points=1 << 14, seed=0, block_mlps=None, n_freq=0,
+                 storage="fp32"):
         """lambda_sparsity / lambda_opacity weight the regularisers of Eq. 7
         (mean alpha at n_sparsity_points uniform points of the scene box,
         redrawn every step) and Eq. 8 (entropy of block opacities of the
         step's rays); the paper trains with 0.05 and 0.001.  block_mlps
         ([n_blocks, block_mlp_nparam(n_freq)]) fits one MLP per block,
         blended by Eq. 5, instead of the global `mlp` (which may be None);
-        that form has no early termination."""
-        self.ctx = cow.Context(scene, "fp32")
+        that form has no early termination.  storage: the packed copies the
+        forward and backward read ("fp32", or "bf16" / "fp16" re-packed from
+        the FP32 parameters after every Adam step: FP32 masters, FP32
+        gradients and optimiser, reduced-precision renders)."""
+        self.ctx = cow.Context(scene, storage)
         self.box_lo = torch.tensor(scene.box_lo, dtype=torch.float32, device=device)
         self.box_hi = torch.tensor(scene.box_hi, dtype=torch.float32, device=device)
         self.lambda_sparsity, self.lambda_opacity = float(lambda_sparsity), float(lambda_opacity)

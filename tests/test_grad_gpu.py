@@ -86,15 +86,17 @@ def test_autograd_function_matches_direct_call():
             assert _rel(params[4 * b + 1 + k].grad.cpu().numpy(), gp[b][k].cpu().numpy()) <= 1e-6
 
 
-def test_fit_reduces_loss():
-    """A short fit of one scene's features and MLP to another seed's render."""
+@pytest.mark.parametrize("storage", ["fp32", "bf16"])
+def test_fit_reduces_loss(storage):
+    """A short fit of one scene's features and MLP to another seed's render,
+    rendering from FP32 or from BF16 copies of the FP32 parameters."""
     sc = synth.city_scene(4, 2, 2.0, [(24, 64)])
     tgt_scene = synth.city_scene(40, 2, 2.0, [(24, 64)])
     o, d = synth.random_rays(1 << 16, 4, sc.box_lo, sc.box_hi)
     o, d = o.cuda(), d.cuda()
     tctx = cow.Context(tgt_scene, "fp32")
     target = tctx.render_rays(o, d, [0, 1, 2, 3], synth.mlp_weights(140), aux=False)[0]
-    fit = train.Fitter(sc, synth.mlp_weights(104))
+    fit = train.Fitter(sc, synth.mlp_weights(104), storage=storage)
     losses = [float(fit.step(o, d, target).item()) for _ in range(40)]
     fit.ctx.sync_check()
     assert losses[-1] < 0.6 * losses[0], losses[::8]
