@@ -221,3 +221,31 @@ def test_grid_schedule_equals_per_view():
     assert float((out2 - ref[0]).abs().max()) <= 2e-6
     b.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("sched", ["queue", "grid"])
+def test_batch_view_without_blocks(sched):
+    """A view whose block list is empty (nothing selected) renders the empty
+    ray's colour, in both schedules, as the per-view render does."""
+    sc, cams, mlp = _scene()
+    ctx = cow.Context(sc, "bf16")
+    ids = [ctx.select_lod(cams[0], sc.lod_thresh), np.zeros(0, np.int32), ctx.select_lod(cams[2], sc.lod_thresh)]
+    views = [cams[0], cams[1], cams[2]]
+    mlp_d = torch.from_numpy(mlp).cuda()
+    ref = ctx.render(views, ids, mlp_d, nsamp=True)
+    ctx.sync_check()
+    b = cow.Batch(ctx, 4, 512)
+    n = b.set_views(views, ids)
+    b.set_schedule(sched)
+    out = (torch.full((n, 3), -1.0, device="cuda"), torch.zeros((n, 8), device="cuda"),
+           torch.zeros(n, dtype=torch.int32, device="cuda"))
+    b.render(mlp_d, *out)
+    ctx.sync_check()
+    assert torch.equal(out[2], ref[2])
+    for k in range(2):
+        assert float((out[k] - ref[k]).abs().max()) <= 2e-6, k
+    p0 = cams[0].width * cams[0].height
+    p1 = p0 + cams[1].width * cams[1].height
+    assert int(out[2][p0:p1].sum()) == 0
+    b.close()
+    ctx.close()
