@@ -531,6 +531,29 @@ __device__ __forceinline__ void warp_red(float *dst, float v) {
     if ((threadIdx.x & 31) == 0) red_add1(dst, v);
 }
 
+// Sixteen weight-gradient terms (dst[0 .. 15]) summed over the warp's 32 rays
+// at once: the two half-warps are folded, then at each of the four remaining
+// lane bits every lane keeps one half of its values and adds the partner's
+// copy of that half, so lane l ends with the warp sum of term l & 15 -- 31
+// shuffles for the sixteen sums instead of 80 -- and lanes 0-15 reduce one
+// term each.  v is overwritten.
+__device__ __forceinline__ void warp_red16(float *dst, float v[16]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] += __shfl_xor_sync(0xffffffffu, v[j], 16);
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < s; j++) {
+            const float send = up ? v[j] : v[j + s];
+            const float keep = up ? v[j + s] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    if (lane < 16) red_add1(dst + lane, v[0]);
+}
+
 // P2: one thread per (ray, block) pair.  The pairs are laid out block-major
 // with each block's rays padded to a multiple of 32, so a warp holds one
 // block for 32 rays and sums that block's weight gradients before reducing;
@@ -606,21 +629,24 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __gri
         }
         dz2[i] = h2[i] > 0.f ? s : 0.f;
     }
-    float dz1[16];
+    float dz1[16], gv[16];
 #pragma unroll
-    for (int j = 0; j < 16; j++) warp_red(gb2 + j, dz2[j]);
+    for (int j = 0; j < 16; j++) gv[j] = dz2[j];
+    warp_red16(gb2, gv);
 #pragma unroll
     for (int i = 0; i < 16; i++) {
         float s = 0.f;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             s = fmaf(__ldg(W2 + i * 16 + j), dz2[j], s);
-            warp_red(gW2 + i * 16 + j, h1[i] * dz2[j]);
+            gv[j] = h1[i] * dz2[j];
         }
+        warp_red16(gW2 + i * 16, gv);
         dz1[i] = h1[i] > 0.f ? s : 0.f;
     }
 #pragma unroll
-    for (int j = 0; j < 16; j++) warp_red(gb1 + j, dz1[j]);
+    for (int j = 0; j < 16; j++) gv[j] = dz1[j];
+    warp_red16(gb1, gv);
     float gx[7];
     for (int i = 0; i < n_in; i++) {
         const float xi = bm_input(i, ck, d);
@@ -628,8 +654,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_bm_mlp(BmBwdArgs a, const __gri
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             s = fmaf(__ldg(W1 + i * 16 + j), dz1[j], s);
-            warp_red(gW1 + i * 16 + j, xi * dz1[j]);
+            gv[j] = xi * dz1[j];
         }
+        warp_red16(gW1 + i * 16, gv);
         if (i < 7) gx[i] = s;
     }
     if (!ray) return;
