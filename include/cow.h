@@ -212,10 +212,12 @@ cow_status cow_sort_blocks(const cow_ctx *ctx, const cow_camera *cam, const int3
  *                 are set).  cow_render_rays, cow_render_backward and the
  *                 batched form take neither this flag nor the per-block MLPs.
  *   out_rgb     : float32, (sum of W*H) x 3, views in order, rows top to
- *                 bottom.  Device memory, or host memory (the call then
- *                 renders into context buffers and copies; pinned memory is
- *                 complete when the stream completes, pageable memory when
- *                 the call returns).
+ *                 bottom.  Device memory, or host memory: page-locked memory
+ *                 mapped into the device's address space (cudaHostAlloc on
+ *                 a system with unified addressing) is written by the kernel
+ *                 directly; other host memory is rendered into context
+ *                 buffers and copied.  Host outputs are complete when the
+ *                 stream completes (pageable ones when the call returns).
  *   out_aux     : NULL or float32 (sum W*H) x 8: C_d (3), F (4) and the
  *                 transmittance left after the last block; same rules.
  *   out_nsamp   : NULL or int32 (sum W*H): occupied samples marched per pixel.

@@ -514,6 +514,16 @@ cow_status resolve_out(T *user, size_t bytes, DevBuf &buf, T **dev, bool *host) 
     *dev = user;
     if (!user) return COW_OK;
     if (is_device_ptr(user)) return COW_OK;
+    // page-locked host memory mapped into the device's address space (on a
+    // Grace-Blackwell node, reached over the coherent chip-to-chip link):
+    // the kernel writes the outputs there directly, spread over its run,
+    // instead of a copy of the whole frame after it
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, user) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *dev = (T *)at.devicePointer;
+        return COW_OK;
+    }
+    cudaGetLastError();
     COW_CUDA(buf.reserve(bytes));
     *dev = (T *)buf.p;
     *host = true;
